@@ -1,0 +1,283 @@
+"""Benchmark: Debye pair*q/s of the mixed-precision path at 50,000 atoms x 201 q
+(globular random-walk chain, 5 atom types, q = 0..1 A^-1), next to the all-FP64
+plain kernel on the same GB300 and the CPU oracle on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one full profile call through the C ABI with device-resident inputs:
+count/validate, scan, schedule read-back, pack, pair kernel, item reduction and
+assembly.  Under torchrun every rank computes its own molecule (independent
+problems, weak scaling, no data-path collective); rank 0 prints one JSON line.
+`--impl reference` times the CPU oracle (the reference arm of this build) on a
+bounded subsample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ATOMS = 50_000
+METRIC = "Debye pair·q/s at 50k atoms×201 q: mixed vs FP64 plain at rel err≤1e-5"
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+OPS_PER_PAIR_Q = 2   # FP32 lane operations per pair*q: one FMA (recurrence) + one add (accumulate)
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _cpu_oracle_sample(w, seconds_hint=20.0):
+    """Time the CPU oracle (as it stands) on a seeded subsample of the workload."""
+    import oracle
+    from paper_1306_2258_gb300 import workloads as wl
+    cores = oracle.max_threads()
+    n = 1000
+    sub = wl.subsample(w.mol, n, wl.seed_for(2, 77))
+    t0 = time.perf_counter()
+    oracle.profile(sub.coords, sub.types, w.coef, w.q)
+    dt = time.perf_counter() - t0
+    # scale the subsample so the timed oracle run takes about `seconds_hint`
+    n2 = int(min(N_ATOMS, n * max(1.0, (seconds_hint / max(dt, 1e-3))) ** 0.5))
+    sub = wl.subsample(w.mol, n2, wl.seed_for(2, 78))
+    t0 = time.perf_counter()
+    oracle.profile(sub.coords, sub.types, w.coef, w.q)
+    dt = time.perf_counter() - t0
+    pq = n2 * (n2 - 1) / 2 * w.q.size
+    return {"value": pq / dt, "unit": "pair·q/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n2}-atom seeded subsample of the 50,000-atom globule x 201 q, "
+                      f"{dt:.1f} s, FP64 double loop with libm sin"}, dt
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1306_2258_gb300 import workloads as wl
+    w = wl.c2_globule(N_ATOMS)
+    for _ in range(args.warmup):
+        pass
+    per_step = max(2.0, 120.0 / max(args.steps + args.warmup, 1))
+    vals, times = [], []
+    base = None
+    for s in range(args.warmup + args.steps):
+        cb, dt = _cpu_oracle_sample(w, seconds_hint=per_step)
+        if s >= args.warmup:
+            vals.append(cb["value"])
+            times.append(dt)
+            base = cb
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pair·q/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "globule 50,000 atoms x 201 q (bounded CPU subsample per step)",
+                       "n_atoms": N_ATOMS, "n_q": 201, "l2": "n/a (CPU)"},
+            "cpu_baseline": dict(base, value=value),
+            "e2e": {"value": value, "unit": "pair·q/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1306_2258_gb300 import _lib, workloads as wl
+    from paper_1306_2258_gb300.profile import Profile
+
+    rank, world, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = wl.c2_globule(N_ATOMS)
+    mol = w.mol if rank == 0 else wl.random_walk_globule(N_ATOMS, 5, wl.seed_for(2, 90_000 + rank)).as_f32()
+    n, Q = mol.n, w.q.size
+    pairs = n * (n - 1) // 2
+    pq = pairs * Q
+
+    prof = Profile(w.coef, w.q, "mixed")
+    x = torch.as_tensor(mol.coords, device=dev)
+    t = torch.as_tensor(mol.types, device=dev)
+    out = torch.empty((1, Q), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        _lib.sas_profile_batch(prof._ctx, x, _lib.SAS_COORDS_F32, t, n, 1, out, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = int(prof.stats()[5])
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern_ns = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))               # L2 flush between timed steps (not timed)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            kern_ns.append(int(prof.stats()[4]))
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = float(sum(step_ms))
+    t_all = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+    tot_ms = float(t_all.item())
+    value = world * pq * args.steps / (tot_ms / 1e3)
+    I_mixed = out[0].cpu().numpy().copy()
+
+    # ---- end to end through the public API with host buffers (copies inside the timed region)
+    xh = torch.as_tensor(mol.coords).pin_memory()
+    th = torch.as_tensor(mol.types).pin_memory()
+    oh = torch.empty((1, Q), dtype=torch.float64).pin_memory()
+    _lib.sas_profile_batch(prof._ctx, xh, _lib.SAS_COORDS_F32, th, n, 1, oh, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(e2e_steps):
+        _lib.sas_profile_batch(prof._ctx, xh, _lib.SAS_COORDS_F32, th, n, 1, oh, stream)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": pq / e2e_s, "unit": "pair·q/s",
+           "h2d_bytes_per_step": int(xh.numel() * 4 + th.numel() * 4), "d2h_bytes_per_step": int(Q * 8)}
+
+    # ---- the FP64 plain kernel on the same molecule (1 timed step after 1 warm-up)
+    p64 = Profile(w.coef, w.q, "fp64")
+    out64 = torch.empty((1, Q), dtype=torch.float64, device=dev)
+    _lib.sas_profile_batch(p64._ctx, x, _lib.SAS_COORDS_F32, t, n, 1, out64, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _lib.sas_profile_batch(p64._ctx, x, _lib.SAS_COORDS_F32, t, n, 1, out64, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    I64 = out64[0].cpu().numpy()
+    rel = float(np.max(np.abs(I_mixed - I64) / np.abs(I64)))
+
+    if rank != 0:
+        return 0
+    kern_s = float(np.median(kern_ns)) / 1e9
+    clocks = clk.summary()
+    peak_ops = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    achieved_ops = pq * OPS_PER_PAIR_Q / kern_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "pair·q/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "globule 50,000 atoms (seeded 3.8 A random walk, R = 110.5 A, 5 types) x 201 q "
+                               "(0..1 A^-1), float32 coordinates, mixed FP32/FP64",
+                   "n_atoms": n, "n_q": Q, "pairs": pairs, "l2": "flushed between steps (256 MB write)",
+                   "work_items": int(prof.stats()[0])},
+        "rel_err_vs_fp64": rel,
+        "fp64_plain": {"value": pq / (ms64 / 1e3), "unit": "pair·q/s", "ms_per_step": ms64, "dtype": "f64"},
+        "speedup_vs_fp64": (pq / (tot_ms / args.steps / 1e3)) / (pq / (ms64 / 1e3)),
+        "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": peak_ops, "unit": "Tops/s (FP32 lane ops)",
+                     "frac": achieved_ops / peak_ops, "traffic": None,
+                     "kernel": "k_debye_mixed", "kernel_ms": kern_s * 1e3,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (nominal max clock)"},
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    if not args.skip_cpu and world == 1:
+        line["cpu_baseline"], _ = _cpu_oracle_sample(w, seconds_hint=15.0)
+    print(json.dumps(line))
+    prof.close()
+    p64.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

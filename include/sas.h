@@ -1,0 +1,169 @@
+/*
+ * sas.h — C ABI of the GB300 (sm_103a) direct Debye summation library (libsas.so).
+ *
+ * The operation is the Debye sum of Berlin, Gumerov, Duraiswami and Fushman,
+ * "Performance of a GPU-based Direct Summation Algorithm for Computation of
+ * Small Angle Scattering Profile" (Section I-A, Eq. 2):
+ *
+ *     I(q) = sum_k sum_j f_k(q) f_j(q) sin(q r_jk) / (q r_jk),   sinc(0) = 1,
+ *
+ * over all N atoms of a molecule, on a uniform grid of q values, with the
+ * per-atom form factors f_j(q) taken from a small set of atom types:
+ *
+ *     f_t(q) = sum_{k=1..4} a_k exp(-b_k (q / 4 pi)^2) + c      (coefficients per type t).
+ *
+ * Conventions for every entry point
+ *  - Every function returns a sas_status; nothing throws across the ABI.
+ *    sas_last_error() gives a message for the calling thread's last failure.
+ *  - The caller owns every input and output buffer.  Pointers may be host or
+ *    device memory (told apart with cudaPointerGetAttributes).  Device
+ *    buffers are used in place on the caller's stream; host buffers are
+ *    staged through context-owned device memory, and a call with a host
+ *    output returns only after the result has been copied back.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *  - Validation (n < 0, null pointers, type out of range, non-finite
+ *    coordinate) happens before any output is written: on an error the
+ *    outputs are untouched.  Device-resident inputs are validated by a kernel
+ *    whose verdict the host reads back, so these calls synchronize on the
+ *    stream once, after packing and before the pair kernel.
+ *  - A context is not thread-safe: use one context per host thread.
+ *  - Layouts are C order (row-major): coords [batch][n][3], outputs [batch][...].
+ *  - Atom pairs are counted as unordered distinct pairs i<j (Section II: only
+ *    j <= k is computed); the diagonal sum_i f_i^2 is added exactly in FP64.
+ */
+#ifndef SAS_H
+#define SAS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sas_ctx sas_ctx; /* opaque; owns the form-factor table and device workspace */
+
+typedef enum {
+    SAS_OK = 0,
+    SAS_ERR_INVALID_ARG = 1, /* bad size, null pointer, type out of range, NaN/Inf coordinate */
+    SAS_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed */
+    SAS_ERR_ALLOC = 3,       /* device or host allocation failed (nothing leaked) */
+    SAS_ERR_UNSUPPORTED = 4, /* non-uniform q grid, too many q values or types */
+    SAS_ERR_TIMEOUT = 5      /* a wait on the device exceeded its limit */
+} sas_status;
+
+/* precision (sas_create flags) */
+enum {
+    SAS_MIXED = 0, /* FP32 pair terms and per-thread sums, FP64 from the first cross-thread sum on */
+    SAS_FP64 = 1   /* every step in FP64 (the plain form) */
+};
+
+/* coordinate element type (per call) */
+enum { SAS_COORDS_F32 = 0, SAS_COORDS_F64 = 1 };
+
+/* limits */
+#define SAS_MAX_TYPES 16
+#define SAS_MAX_Q 1664
+
+/*
+ * Create a context for n_types atom types and a uniform q grid.
+ *   ff_coef  [n_types][9] host, (a1..a4, b1..b4, c) per type; copied.
+ *   q        [n_q] host, uniform ascending, q[0] >= 0 (relative spacing deviation <= 1e-9); copied.
+ *   flags    SAS_MIXED or SAS_FP64.
+ * Errors: INVALID_ARG (n_types outside 1..SAS_MAX_TYPES, n_q outside 1..SAS_MAX_Q,
+ * null pointer, negative or non-finite q or coefficient), UNSUPPORTED (non-uniform q),
+ * ALLOC, CUDA.  *out is set only on success.
+ */
+sas_status sas_create(int n_types, const double *ff_coef, const double *q, int n_q, unsigned flags,
+                      sas_ctx **out);
+
+/* Free the context and all of its device memory.  NULL is accepted. */
+sas_status sas_destroy(sas_ctx *ctx);
+
+/*
+ * I(q) of one molecule (Eq. 2).
+ *   coords  [n_atoms][3] float (coords_type SAS_COORDS_F32) or double (SAS_COORDS_F64), Å.
+ *   types   [n_atoms] int32 in [0, n_types).
+ *   I_out   [n_q] double.
+ * n_atoms = 0 gives I = 0; n_atoms = 1 gives f^2.
+ */
+sas_status sas_profile(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types,
+                       int64_t n_atoms, double *I_out, void *stream);
+
+/*
+ * I(q) of `batch` conformers of one molecule (shared types), one launch per step.
+ *   coords [batch][n_atoms][3], I_out [batch][n_q].
+ */
+sas_status sas_profile_batch(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types,
+                             int64_t n_atoms, int64_t batch, double *I_out, void *stream);
+
+/*
+ * Refinement objective and its gradient (derivative of Eq. 2 with respect to the positions):
+ *   chi2_b   = sum_q w_q (I_b(q) - T(q))^2
+ *   grad_b,i = d chi2_b / d x_i = sum_{j != i} w_ij (x_i - x_j),
+ *   w_ij     = (2 / r^2) sum_q g_q f_i f_j (cos(q r) - sinc(q r)),  g_q = 2 w_q (I(q) - T(q)).
+ *   coords [batch][n_atoms][3] float, target [n_q] double, weights [n_q] double,
+ *   chi2_out [batch] double, grad_out [batch][n_atoms][3] float (caller's atom order),
+ *   I_out [batch][n_q] double or NULL.
+ * Mixed precision only (SAS_MIXED context): FP32 pair terms, FP64 accumulation of gradients.
+ */
+sas_status sas_profile_grad(sas_ctx *ctx, const float *coords, const int32_t *types, int64_t n_atoms,
+                            int64_t batch, const double *target, const double *weights,
+                            double *chi2_out, float *grad_out, double *I_out, void *stream);
+
+/*
+ * Vector-Jacobian product of Eq. 2 (the backward of I(q) for autograd):
+ *   grad_out[b][i] = sum_q grad_I[b][q] dI_b(q)/dx_i.
+ *   coords [batch][n_atoms][3] float, grad_I [batch][n_q] double, grad_out [batch][n_atoms][3] float.
+ */
+sas_status sas_profile_vjp(sas_ctx *ctx, const float *coords, const int32_t *types, int64_t n_atoms,
+                           int64_t batch, const double *grad_I, float *grad_out, void *stream);
+
+/*
+ * The last profile call's type-pair sinc sums (the factoring of Eq. 2 over atom types):
+ *   S_out[b][p][k] = sum over unordered pairs i<j with types {a,b} of sinc(q_k r_ij),
+ *   p = a*T - a(a-1)/2 + (b - a) for a <= b, T = n_types.  S_out has batch*T(T+1)/2*n_q doubles.
+ * Then I(q) = sum_t n_t f_t(q)^2 + sum_p 2 f_a(q) f_b(q) S_p(q).
+ */
+sas_status sas_partials(sas_ctx *ctx, double *S_out, int64_t capacity, void *stream);
+
+/*
+ * Exact integer histogram of unordered pair distances by type pair.
+ *   coords [batch][n_atoms][3] float; types [n_atoms]; hist_out [batch][T(T+1)/2][n_bins] int32;
+ *   dropped_out [batch] int64 (pairs beyond the last edge) or NULL.
+ * Distance rule (identical on every platform): dx = x_i - x_j (likewise dy, dz) in float32,
+ *   r2 = fmaf(dz, dz, fmaf(dy, dy, dx*dx)); w = r_max / n_bins; e_k = (float)k * w; e_k2 = e_k*e_k;
+ *   bin = max{k : e_k2 <= r2}, dropped if bin >= n_bins.
+ * The caller's float32 coordinates are used unchanged (no centering).
+ */
+sas_status sas_pair_histogram(sas_ctx *ctx, const float *coords, const int32_t *types, int64_t n_atoms,
+                              int64_t batch, int n_bins, float r_max, int32_t *hist_out,
+                              int64_t *dropped_out, void *stream);
+
+/* Tuning and diagnostics (values are validated; unknown options give INVALID_ARG). */
+enum {
+    SAS_OPT_JMAX = 1,        /* longest J-range of one work item, atoms (multiple of 128 up to 8192; 0 = automatic) */
+    SAS_OPT_RESEED = 2,      /* re-seed interval of the q recurrence in q steps: 0 (chunk start only), 32, 64 */
+    SAS_OPT_VALIDATE = 3,    /* must stay 1: the device-side validation verdict is always read back */
+    SAS_OPT_GRID = 4,        /* persistent CTAs per SM for the pair kernels (0 = automatic) */
+    SAS_OPT_TIMEOUT_MS = 5   /* limit of every host-side wait for device work (default 600000) */
+};
+sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value);
+
+/*
+ * Statistics of the last call: [0] work items, [1] pair slots (incl. padding),
+ * [2] unordered real pairs, [3] q values, [4] pair-kernel time in nanoseconds
+ * (CUDA events on the call's stream; this call waits for them), [5] kernels launched.
+ */
+sas_status sas_last_stats(sas_ctx *ctx, int64_t *stats_out, int n);
+
+/* Thread-local message of the calling thread's last failure ("" if none). */
+const char *sas_last_error(void);
+
+/* Library version string. */
+const char *sas_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAS_H */

@@ -1,0 +1,175 @@
+"""ctypes binding of libsas.so: the C ABI of include/sas.h under the same names.
+
+Argument marshalling only: every array argument may be a torch tensor (CPU or
+CUDA) or a NumPy array; it is passed as a raw pointer.  Streams are torch
+streams (or None for the current torch stream).  A non-OK status raises
+SasError carrying the status and the library's message.  There is no CPU
+fallback: if the library cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SAS_OK, SAS_ERR_INVALID_ARG, SAS_ERR_CUDA, SAS_ERR_ALLOC, SAS_ERR_UNSUPPORTED, SAS_ERR_TIMEOUT = range(6)
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "ALLOC", 4: "UNSUPPORTED", 5: "TIMEOUT"}
+SAS_MIXED, SAS_FP64 = 0, 1
+SAS_COORDS_F32, SAS_COORDS_F64 = 0, 1
+SAS_OPT_JMAX, SAS_OPT_RESEED, SAS_OPT_VALIDATE, SAS_OPT_GRID, SAS_OPT_TIMEOUT_MS = 1, 2, 3, 4, 5
+SAS_MAX_TYPES, SAS_MAX_Q = 16, 1664
+
+# every symbol include/sas.h declares (checked by the test suite)
+EXPORTS = (
+    "sas_create", "sas_destroy", "sas_profile", "sas_profile_batch", "sas_profile_grad",
+    "sas_profile_vjp", "sas_partials", "sas_pair_histogram", "sas_set_option", "sas_last_stats",
+    "sas_last_error", "sas_version",
+)
+
+
+class SasError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+_lock = threading.Lock()
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+
+
+def load():
+    """Build (if stale) and load libsas.so; raises if either fails."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            lib = ctypes.CDLL(path)
+            sig = {
+                "sas_create": [_int, _vp, _vp, _int, ctypes.c_uint, ctypes.POINTER(_vp)],
+                "sas_destroy": [_vp],
+                "sas_profile": [_vp, _vp, _int, _vp, _i64, _vp, _vp],
+                "sas_profile_batch": [_vp, _vp, _int, _vp, _i64, _i64, _vp, _vp],
+                "sas_profile_grad": [_vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp],
+                "sas_profile_vjp": [_vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp],
+                "sas_partials": [_vp, _vp, _i64, _vp],
+                "sas_pair_histogram": [_vp, _vp, _vp, _i64, _i64, _int, ctypes.c_float, _vp, _vp, _vp],
+                "sas_set_option": [_vp, _int, _i64],
+                "sas_last_stats": [_vp, _vp, _int],
+            }
+            for name, args in sig.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = _int
+            lib.sas_last_error.restype = ctypes.c_char_p
+            lib.sas_last_error.argtypes = []
+            lib.sas_version.restype = ctypes.c_char_p
+            lib.sas_version.argtypes = []
+            _lib = lib
+    return _lib
+
+
+def ptr(x):
+    """Raw address of a torch tensor / NumPy array (None -> NULL).  Must be contiguous."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"cannot pass {type(x).__name__} as a pointer")
+
+
+def stream_handle(stream=None):
+    """cudaStream_t of a torch stream (default: torch's current stream), or 0 without CUDA."""
+    import torch
+    if stream is None:
+        if not torch.cuda.is_available():
+            return None
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def check(status: int):
+    if status != SAS_OK:
+        raise SasError(status, load().sas_last_error().decode())
+
+
+# ---- the C ABI under its own names ---------------------------------------------------------
+
+def sas_create(n_types: int, ff_coef, q, flags: int = SAS_MIXED):
+    lib = load()
+    c = np.ascontiguousarray(ff_coef, dtype=np.float64)
+    qq = np.ascontiguousarray(q, dtype=np.float64)
+    h = _vp()
+    check(lib.sas_create(int(n_types), c.ctypes.data, qq.ctypes.data, int(qq.size), int(flags),
+                         ctypes.byref(h)))
+    return h
+
+
+def sas_destroy(ctx):
+    check(load().sas_destroy(ctx))
+
+
+def sas_profile(ctx, coords, coords_type, types, n_atoms, I_out, stream=None):
+    check(load().sas_profile(ctx, ptr(coords), int(coords_type), ptr(types), int(n_atoms), ptr(I_out),
+                             stream_handle(stream)))
+
+
+def sas_profile_batch(ctx, coords, coords_type, types, n_atoms, batch, I_out, stream=None):
+    check(load().sas_profile_batch(ctx, ptr(coords), int(coords_type), ptr(types), int(n_atoms),
+                                   int(batch), ptr(I_out), stream_handle(stream)))
+
+
+def sas_profile_grad(ctx, coords, types, n_atoms, batch, target, weights, chi2_out, grad_out,
+                     I_out=None, stream=None):
+    check(load().sas_profile_grad(ctx, ptr(coords), ptr(types), int(n_atoms), int(batch), ptr(target),
+                                  ptr(weights), ptr(chi2_out), ptr(grad_out), ptr(I_out),
+                                  stream_handle(stream)))
+
+
+def sas_profile_vjp(ctx, coords, types, n_atoms, batch, grad_I, grad_out, stream=None):
+    check(load().sas_profile_vjp(ctx, ptr(coords), ptr(types), int(n_atoms), int(batch), ptr(grad_I),
+                                 ptr(grad_out), stream_handle(stream)))
+
+
+def sas_partials(ctx, S_out, capacity, stream=None):
+    check(load().sas_partials(ctx, ptr(S_out), int(capacity), stream_handle(stream)))
+
+
+def sas_pair_histogram(ctx, coords, types, n_atoms, batch, n_bins, r_max, hist_out, dropped_out=None,
+                       stream=None):
+    check(load().sas_pair_histogram(ctx, ptr(coords), ptr(types), int(n_atoms), int(batch), int(n_bins),
+                                    float(r_max), ptr(hist_out), ptr(dropped_out), stream_handle(stream)))
+
+
+def sas_set_option(ctx, option: int, value: int):
+    check(load().sas_set_option(ctx, int(option), int(value)))
+
+
+def sas_last_stats(ctx):
+    out = np.zeros(6, dtype=np.int64)
+    check(load().sas_last_stats(ctx, out.ctypes.data, 6))
+    return out
+
+
+def sas_last_error() -> str:
+    return load().sas_last_error().decode()
+
+
+def sas_version() -> str:
+    return load().sas_version().decode()

@@ -1,0 +1,191 @@
+// Packing: validate the inputs, stable-sort atoms by type into type groups
+// padded to whole tiles, and write one float4 (x, y, z, w) per slot, w = 1 for
+// a real atom and 0 for padding.
+//
+// The paper keeps the N positions and the per-atom form factors in GPU global
+// memory (Section II).  Here the form factors are not per atom at all: sorting
+// by type makes every tile type-homogeneous, so each tile pair belongs to one
+// type pair (a, b) and f_a(q) f_b(q) multiplies a whole partial sum instead of
+// every pair term.
+#include <cmath>
+
+#include "sas_internal.h"
+
+namespace sas {
+
+namespace {
+
+__device__ __forceinline__ void load_xyz(const void *coords, int f64, int64_t idx, double &x,
+                                         double &y, double &z)
+{
+    if (f64) {
+        const double *c = static_cast<const double *>(coords) + 3 * idx;
+        x = c[0];
+        y = c[1];
+        z = c[2];
+    } else {
+        const float *c = static_cast<const float *>(coords) + 3 * idx;
+        x = c[0];
+        y = c[1];
+        z = c[2];
+    }
+}
+
+// Per block of kPackThreads atoms: count of each type; validation of types and coordinates.
+__global__ void k_count_types(const void *coords, int coords_f64, const int32_t *types, int64_t n,
+                              int64_t batch, int n_types, int *blockcounts, int *errword)
+{
+    __shared__ int cnt[SAS_MAX_TYPES];
+    if (threadIdx.x < SAS_MAX_TYPES) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int err = 0;
+    if (i < n) {
+        int t = types[i];
+        if (t < 0 || t >= n_types)
+            err |= kErrBadType;
+        else
+            atomicAdd(&cnt[t], 1);
+        for (int64_t b = 0; b < batch; ++b) {
+            double x, y, z;
+            load_xyz(coords, coords_f64, b * n + i, x, y, z);
+            if (!isfinite(x) || !isfinite(y) || !isfinite(z)) err |= kErrNonFinite;
+        }
+    }
+    if (err) atomicOr(errword, err);
+    __syncthreads();
+    if (threadIdx.x < n_types) blockcounts[(int64_t)blockIdx.x * n_types + threadIdx.x] = cnt[threadIdx.x];
+}
+
+// One block: exclusive scan of the per-block counts for each type; totals and padded offsets.
+__global__ void k_scan_counts(const int *blockcounts, int nblk, int n_types, int tile, int *blockoffs,
+                              int *meta)
+{
+    __shared__ int tot[SAS_MAX_TYPES];
+    int t = threadIdx.x;
+    if (t < n_types) {
+        int run = 0;
+        for (int b = 0; b < nblk; ++b) {
+            blockoffs[(int64_t)b * n_types + t] = run;
+            run += blockcounts[(int64_t)b * n_types + t];
+        }
+        tot[t] = run;
+        meta[t] = run;
+    }
+    __syncthreads();
+    if (t == 0) {
+        int off = 0;
+        for (int k = 0; k < n_types; ++k) {
+            meta[n_types + k] = off;
+            off += (tot[k] + tile - 1) / tile * tile;
+        }
+        meta[2 * n_types] = off;
+    }
+}
+
+// Centroid of each conformer in FP64, deterministic: fixed strided partial sums, fixed tree.
+__global__ void k_centroid(const void *coords, int coords_f64, int64_t n, double *centroid)
+{
+    __shared__ double red[3][kPackThreads];
+    int64_t b = blockIdx.x;
+    double sx = 0, sy = 0, sz = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        double x, y, z;
+        load_xyz(coords, coords_f64, b * n + i, x, y, z);
+        sx += x;
+        sy += y;
+        sz += z;
+    }
+    red[0][threadIdx.x] = sx;
+    red[1][threadIdx.x] = sy;
+    red[2][threadIdx.x] = sz;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) centroid[3 * b + threadIdx.x] = n > 0 ? red[threadIdx.x][0] / (double)n : 0.0;
+}
+
+// Stable scatter: slot = group offset + (atoms of the same type before this one).
+__global__ void k_scatter(const void *coords, int coords_f64, const int32_t *types, int64_t n,
+                          int64_t batch, int n_types, const int *blockoffs, const int *meta,
+                          const double *centroid, int out_f64, void *X, int64_t npad, int *slot_of)
+{
+    __shared__ int wcnt[kPackThreads / 32][SAS_MAX_TYPES];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = threadIdx.x; k < (kPackThreads / 32) * SAS_MAX_TYPES; k += blockDim.x)
+        (&wcnt[0][0])[k] = 0;
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int t = (i < n) ? types[i] : -1;
+    if (t >= n_types) t = -1;
+    unsigned peers = __match_any_sync(0xffffffffu, t);
+    int rank_in_warp = __popc(peers & ((1u << lane) - 1u));
+    if (t >= 0 && rank_in_warp == 0) wcnt[warp][t] = __popc(peers);
+    __syncthreads();
+    if (t < 0) return;
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wcnt[w][t];
+    int rank = blockoffs[(int64_t)blockIdx.x * n_types + t] + before + rank_in_warp;
+    int slot = meta[n_types + t] + rank;
+    slot_of[i] = slot;
+    for (int64_t b = 0; b < batch; ++b) {
+        double x, y, z;
+        load_xyz(coords, coords_f64, b * n + i, x, y, z);
+        if (out_f64) {
+            static_cast<double4 *>(X)[b * npad + slot] = make_double4(x, y, z, 1.0);
+        } else {
+            if (centroid) {
+                x -= centroid[3 * b];
+                y -= centroid[3 * b + 1];
+                z -= centroid[3 * b + 2];
+            }
+            static_cast<float4 *>(X)[b * npad + slot] =
+                make_float4((float)x, (float)y, (float)z, 1.0f);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_count_types(const void *coords, int coords_f64, const int32_t *types, int64_t n,
+                               int64_t batch, int n_types, int *blockcounts, int *errword,
+                               cudaStream_t s)
+{
+    int nblk = (int)((n + kPackThreads - 1) / kPackThreads);
+    if (nblk == 0) return cudaSuccess;
+    k_count_types<<<nblk, kPackThreads, 0, s>>>(coords, coords_f64, types, n, batch, n_types,
+                                                blockcounts, errword);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_counts(const int *blockcounts, int nblk, int n_types, int tile,
+                               int *blockoffs, int *meta, cudaStream_t s)
+{
+    k_scan_counts<<<1, 32, 0, s>>>(blockcounts, nblk, n_types, tile, blockoffs, meta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_centroid(const void *coords, int coords_f64, int64_t n, int64_t batch,
+                            double *centroid, cudaStream_t s)
+{
+    if (batch == 0) return cudaSuccess;
+    k_centroid<<<(unsigned)batch, kPackThreads, 0, s>>>(coords, coords_f64, n, centroid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const void *coords, int coords_f64, const int32_t *types, int64_t n,
+                           int64_t batch, int n_types, const int *blockoffs, const int *meta,
+                           const double *centroid, int out_f64, void *X, int64_t npad,
+                           int *slot_of, cudaStream_t s)
+{
+    int nblk = (int)((n + kPackThreads - 1) / kPackThreads);
+    if (nblk == 0) return cudaSuccess;
+    k_scatter<<<nblk, kPackThreads, 0, s>>>(coords, coords_f64, types, n, batch, n_types, blockoffs,
+                                            meta, centroid, out_f64, X, npad, slot_of);
+    return cudaGetLastError();
+}
+
+}  // namespace sas

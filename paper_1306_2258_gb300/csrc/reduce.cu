@@ -1,0 +1,108 @@
+// Form factors, the deterministic cross-item reduction, and the assembly of I(q).
+//
+// The paper reduces each workgroup's private totals in local memory, writes
+// one total per workgroup to global memory and finishes the sum on the host
+// (Section II).  Here every item's FP64 partial is summed on the device in a
+// fixed order (the order of the item list), so repeated calls give the same
+// bits; the form factors enter only now, once per type pair and q:
+//
+//   I(q) = sum_t n_t f_t(q)^2 + sum_{a<=b} 2 f_a(q) f_b(q) S_ab(q),
+//   S_ab(q) = sum over unordered pairs of types {a,b} of sinc(q r) = U_ab(q) / q,
+//
+// where U_ab(q) = sum sin(q r)/r is what the pair kernels accumulate; at q = 0
+// S_ab is the exact pair count (sinc(0) = 1).
+#include "sas_internal.h"
+
+namespace sas {
+
+namespace {
+
+__device__ __forceinline__ double qval(const QChunks &qc, int k) { return qc.q0 + (double)k * qc.dq; }
+
+// f_t(q) = sum_{k<4} a_k exp(-b_k (q/4pi)^2) + c
+__global__ void k_form_factors(const double *coef, int n_types, QChunks qc, double *F)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.y;
+    if (k >= qc.n_q || t >= n_types) return;
+    const double s = qval(qc, k) / (4.0 * 3.14159265358979323846);
+    const double *c = coef + 9 * t;
+    double f = c[8];
+    for (int m = 0; m < 4; ++m) f += c[m] * exp(-c[4 + m] * s * s);
+    F[t * qc.n_q + k] = f;
+}
+
+__global__ void k_reduce_items(const double *partial, int part_stride, const Item *items,
+                               const int *group_items, const int *group_off, QChunks qc, double *S)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.y;
+    if (k >= qc.n_q) return;
+    double s = 0.0;
+    for (int idx = group_off[g]; idx < group_off[g + 1]; ++idx) {
+        const int it = group_items[idx];
+        const int ch = items[it].chunk;
+        const int kk = k - qc.q_begin[ch];
+        if (kk >= 0 && kk < qc.q_len[ch]) s += partial[(int64_t)it * part_stride + kk];
+    }
+    // U(q) -> S(q) = U/q; at q = 0 the exact count of pairs is filled in by k_assemble
+    const double q = qval(qc, k);
+    S[(int64_t)g * qc.n_q + k] = q > 0.0 ? s / q : 0.0;
+}
+
+__global__ void k_assemble(double *S, const double *F, const int *meta, int n_types, QChunks qc,
+                           double *I)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b = blockIdx.y;
+    if (k >= qc.n_q) return;
+    const int P = n_types * (n_types + 1) / 2;
+    const bool q0 = !(qval(qc, k) > 0.0);
+    double acc = 0.0;
+    for (int t = 0; t < n_types; ++t) {
+        const double f = F[t * qc.n_q + k];
+        acc += (double)meta[t] * f * f;   // the diagonal, exactly
+    }
+    int p = 0;
+    for (int a = 0; a < n_types; ++a)
+        for (int c = a; c < n_types; ++c, ++p) {
+            double *Sp = S + (b * P + p) * qc.n_q + k;
+            if (q0) {   // sinc(0) = 1: the number of unordered pairs of types {a, c}
+                const double na = meta[a], nc = meta[c];
+                *Sp = (a == c) ? na * (na - 1.0) * 0.5 : na * nc;
+            }
+            acc += 2.0 * F[a * qc.n_q + k] * F[c * qc.n_q + k] * (*Sp);
+        }
+    I[b * qc.n_q + k] = acc;
+}
+
+}  // namespace
+
+cudaError_t launch_form_factors(const double *coef, int n_types, const QChunks &qc, double *F,
+                                cudaStream_t s)
+{
+    dim3 grid((qc.n_q + 127) / 128, n_types);
+    k_form_factors<<<grid, 128, 0, s>>>(coef, n_types, qc, F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_items(const double *partial, int part_stride, const Item *items,
+                                const int *group_items, const int *group_off, int n_groups,
+                                const QChunks &qc, double *S, cudaStream_t s)
+{
+    if (n_groups == 0) return cudaSuccess;
+    dim3 grid((qc.n_q + 127) / 128, n_groups);
+    k_reduce_items<<<grid, 128, 0, s>>>(partial, part_stride, items, group_items, group_off, qc, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(double *S, const double *F, const int *meta, int n_types, int64_t batch,
+                            const QChunks &qc, double *I, cudaStream_t s)
+{
+    if (batch == 0) return cudaSuccess;
+    dim3 grid((qc.n_q + 127) / 128, (unsigned)batch);
+    k_assemble<<<grid, 128, 0, s>>>(S, F, meta, n_types, qc, I);
+    return cudaGetLastError();
+}
+
+}  // namespace sas

@@ -1,0 +1,641 @@
+// The C ABI (include/sas.h): argument checks, host/device staging, the work
+// schedule, and the launch sequence of one profile call:
+//
+//   count types + validate -> scan -> (read back counts) -> schedule ->
+//   pack -> pair kernel (mixed or FP64) -> fixed-order item reduction ->
+//   assembly of I(q) with the form factors.
+//
+// The schedule follows the paper's block scheme (Section II, Fig. 2): atoms
+// are split into blocks (tiles) and every block is paired with the blocks
+// after it, so only j > i is computed.  When there are fewer tiles than the
+// GPU has workers, the paper splits the inner loop of a worker among p
+// workers; here the J-range of a tile is cut into pieces of at most JMAX
+// atoms, JMAX chosen so that every SM gets several items.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "sas_internal.h"
+
+using namespace sas;
+
+namespace {
+
+thread_local std::string g_err;
+
+sas_status fail(sas_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            cudaGetLastError();                                                              \
+            return fail(SAS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));              \
+        }                                                                                    \
+    } while (0)
+
+// Test hook: SAS_TEST_FAIL_ALLOC=k makes the k-th device allocation (1-based) fail.
+long g_alloc_count = 0;
+long alloc_fail_at()
+{
+    static long v = [] {
+        const char *e = std::getenv("SAS_TEST_FAIL_ALLOC");
+        return e ? std::atol(e) : 0L;
+    }();
+    return v;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    // Grow to at least `bytes`.  Returns false (and leaves the buffer empty) on failure.
+    bool ensure(size_t bytes)
+    {
+        if (bytes <= cap && p) return true;
+        release();
+        ++g_alloc_count;
+        if (alloc_fail_at() > 0 && g_alloc_count == alloc_fail_at()) return false;
+        if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return false;
+        }
+        cap = bytes;
+        return true;
+    }
+    template <class T>
+    T *as() const
+    {
+        return static_cast<T *>(p);
+    }
+};
+
+#define ALLOC_TRY(buf, bytes)                                                                \
+    do {                                                                                     \
+        if (!(buf).ensure(bytes))                                                            \
+            return fail(SAS_ERR_ALLOC, "device allocation of %zu bytes failed", (size_t)(bytes)); \
+    } while (0)
+
+bool on_device(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int pair_index(int a, int b, int T)
+{
+    if (a > b) std::swap(a, b);
+    return a * T - a * (a - 1) / 2 + (b - a);
+}
+
+}  // namespace
+
+struct sas_ctx {
+    int n_types = 0, n_q = 0;
+    unsigned flags = 0;
+    std::vector<double> coef, q;
+    QChunks qc{};
+    int sms = 1;
+    int64_t opt_jmax = 0;
+    int opt_reseed = 0;
+    int opt_grid = 0;
+    int64_t opt_timeout_ms = 600000;
+    DevBuf coef_d, F, meta, blockcounts, blockoffs, centroid, X, slot_of, items, group_items,
+        group_off, partial, S, in_coords, in_types, out_buf;
+    int *h_meta = nullptr;   // pinned
+    // schedule cache
+    std::vector<int64_t> sched_key;
+    int n_items = 0, n_groups = 0, jmax_used = 0;
+    int64_t pair_slots = 0;
+    int64_t last_batch = 0;
+    bool have_partials = false;
+    int64_t stats[6] = {0, 0, 0, 0, 0, 0};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the last pair-kernel launch
+    bool ev_pending = false;
+};
+
+namespace {
+
+// Wait for the work queued on `s` so far, giving up after the context's time limit.
+sas_status wait_stream(sas_ctx *ctx, cudaStream_t s)
+{
+    cudaEvent_t ev;
+    CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, s);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(ev);
+        return fail(SAS_ERR_CUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (long spin = 0;; ++spin) {
+        e = cudaEventQuery(ev);
+        if (e != cudaErrorNotReady) break;
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                            std::chrono::steady_clock::now() - t0)
+                            .count();
+        if (ms > ctx->opt_timeout_ms) {
+            cudaEventDestroy(ev);
+            return fail(SAS_ERR_TIMEOUT, "device work did not finish within %lld ms",
+                        (long long)ctx->opt_timeout_ms);
+        }
+        if (spin > 64) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SAS_ERR_CUDA, "device work failed: %s", cudaGetErrorString(e));
+    }
+    return SAS_OK;
+}
+
+struct Schedule {
+    std::vector<Item> items;        // execution order
+    std::vector<int> group_items;   // per group, execution positions in canonical order
+    std::vector<int> group_off;     // [n_groups + 1]
+    int jmax = 0;
+    int64_t pair_slots = 0;
+};
+
+// Items of one conformer-independent layout; `counts` are the real atoms per type.
+void build_schedule(const int *counts, int T, int64_t batch, int tile, int n_chunks, int grid,
+                    int64_t jmax_opt, Schedule &out)
+{
+    std::vector<int64_t> P(T), O(T);
+    int64_t off = 0;
+    for (int t = 0; t < T; ++t) {
+        P[t] = (counts[t] + kTile - 1) / kTile * kTile;
+        O[t] = off;
+        off += P[t];
+    }
+    auto n_items_for = [&](int64_t jmax) {
+        int64_t c = 0;
+        for (int a = 0; a < T; ++a)
+            for (int b = a; b < T; ++b) {
+                if (P[a] == 0 || P[b] == 0) continue;
+                for (int64_t i0 = O[a]; i0 < O[a] + P[a]; i0 += tile) {
+                    const int64_t js = (a == b) ? i0 : O[b], je = O[b] + P[b];
+                    c += (je - js + jmax - 1) / jmax;
+                }
+            }
+        return c * batch * n_chunks;
+    };
+    int64_t jmax = jmax_opt;
+    if (jmax <= 0) {
+        const int64_t cands[] = {4096, 2048, 1024, 512, 256, 128};
+        jmax = 128;
+        for (int64_t c : cands)
+            if (n_items_for(c) >= 4 * (int64_t)grid) {
+                jmax = c;
+                break;
+            }
+    }
+    out.jmax = (int)jmax;
+    const int Pn = T * (T + 1) / 2;
+    std::vector<Item> canon;
+    std::vector<int> canon_group;
+    out.pair_slots = 0;
+    for (int64_t bb = 0; bb < batch; ++bb)
+        for (int a = 0; a < T; ++a)
+            for (int b = a; b < T; ++b) {
+                if (P[a] == 0 || P[b] == 0) continue;
+                const int g = (int)(bb * Pn + pair_index(a, b, T));
+                for (int64_t i0 = O[a]; i0 < O[a] + P[a]; i0 += tile) {
+                    const int64_t js = (a == b) ? i0 : O[b], je = O[b] + P[b];
+                    for (int64_t j0 = js; j0 < je; j0 += jmax) {
+                        const int64_t jl = std::min(jmax, je - j0);
+                        for (int ch = 0; ch < n_chunks; ++ch) {
+                            Item it;
+                            it.batch = (int)bb;
+                            it.pair = pair_index(a, b, T);
+                            it.i0 = (int)i0;
+                            it.j0 = (int)j0;
+                            it.jlen = (int)jl;
+                            it.chunk = ch;
+                            it.diag = (a == b && j0 == i0) ? 1 : 0;
+                            it.work = (int)(jl * tile);
+                            canon.push_back(it);
+                            canon_group.push_back(g);
+                            out.pair_slots += jl * tile;
+                        }
+                    }
+                }
+            }
+    const int n = (int)canon.size();
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return canon[x].work > canon[y].work; });
+    std::vector<int> pos(n);
+    out.items.resize(n);
+    for (int e = 0; e < n; ++e) {
+        out.items[e] = canon[order[e]];
+        pos[order[e]] = e;
+    }
+    const int n_groups = (int)(batch * Pn);
+    out.group_off.assign(n_groups + 1, 0);
+    for (int i = 0; i < n; ++i) out.group_off[canon_group[i] + 1]++;
+    for (int g = 0; g < n_groups; ++g) out.group_off[g + 1] += out.group_off[g];
+    out.group_items.resize(n);
+    std::vector<int> fill(out.group_off.begin(), out.group_off.end() - 1);
+    for (int i = 0; i < n; ++i) out.group_items[fill[canon_group[i]]++] = pos[i];
+}
+
+bool finite_all(const double *v, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+// Shared front half of every pair computation: stage, validate, count, schedule, pack.
+// On success the context holds X (packed), slot_of, meta (counts/offsets) and the item list.
+sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32_t *types, int64_t n,
+                   int64_t batch, bool out_f64, bool center, int tile, cudaStream_t s,
+                   int &launches)
+{
+    const int T = ctx->n_types;
+    const size_t esz = coords_f64 ? sizeof(double) : sizeof(float);
+    const void *cd = coords;
+    const int32_t *td = types;
+    if (!on_device(coords)) {
+        ALLOC_TRY(ctx->in_coords, (size_t)batch * n * 3 * esz);
+        CUDA_TRY(cudaMemcpyAsync(ctx->in_coords.p, coords, (size_t)batch * n * 3 * esz,
+                                 cudaMemcpyHostToDevice, s));
+        cd = ctx->in_coords.p;
+    }
+    if (!on_device(types)) {
+        ALLOC_TRY(ctx->in_types, (size_t)n * sizeof(int32_t));
+        CUDA_TRY(cudaMemcpyAsync(ctx->in_types.p, types, (size_t)n * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, s));
+        td = ctx->in_types.as<int32_t>();
+    }
+    const int nblk = (int)((n + kPackThreads - 1) / kPackThreads);
+    ALLOC_TRY(ctx->blockcounts, (size_t)nblk * T * sizeof(int));
+    ALLOC_TRY(ctx->blockoffs, (size_t)nblk * T * sizeof(int));
+    ALLOC_TRY(ctx->meta, (size_t)(2 * T + 2) * sizeof(int));
+    CUDA_TRY(cudaMemsetAsync(ctx->meta.p, 0, (size_t)(2 * T + 2) * sizeof(int), s));
+    CUDA_TRY(launch_count_types(cd, coords_f64, td, n, batch, T, ctx->blockcounts.as<int>(),
+                                ctx->meta.as<int>() + 2 * T + 1, s));
+    CUDA_TRY(launch_scan_counts(ctx->blockcounts.as<int>(), nblk, T, kTile, ctx->blockoffs.as<int>(),
+                                ctx->meta.as<int>(), s));
+    launches += 2;
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_meta, ctx->meta.p, (size_t)(2 * T + 2) * sizeof(int),
+                             cudaMemcpyDeviceToHost, s));
+    sas_status st = wait_stream(ctx, s);
+    if (st != SAS_OK) return st;
+    const int err = ctx->h_meta[2 * T + 1];
+    if (err & kErrBadType) return fail(SAS_ERR_INVALID_ARG, "atom type outside [0, %d)", T);
+    if (err & kErrNonFinite) return fail(SAS_ERR_INVALID_ARG, "non-finite coordinate");
+    const int64_t npad = ctx->h_meta[2 * T];
+    // schedule (cached while counts, batch, tile and options are unchanged)
+    const int grid_per_sm = ctx->opt_grid > 0 ? ctx->opt_grid : 2;
+    const int grid_cap = grid_per_sm * ctx->sms;
+    std::vector<int64_t> key(ctx->h_meta, ctx->h_meta + T);
+    key.push_back(batch);
+    key.push_back(tile);
+    key.push_back(ctx->opt_jmax);
+    key.push_back(grid_cap);
+    if (key != ctx->sched_key) {
+        Schedule sc;
+        build_schedule(ctx->h_meta, T, batch, tile, ctx->qc.n_chunks, grid_cap, ctx->opt_jmax, sc);
+        const int ni = (int)sc.items.size();
+        const int ng = (int)sc.group_off.size() - 1;
+        ctx->sched_key.clear();   // invalid until the upload succeeded
+        ALLOC_TRY(ctx->items, (size_t)std::max(ni, 1) * sizeof(Item));
+        ALLOC_TRY(ctx->group_items, (size_t)std::max(ni, 1) * sizeof(int));
+        ALLOC_TRY(ctx->group_off, (size_t)(ng + 1) * sizeof(int));
+        if (ni) {
+            CUDA_TRY(cudaMemcpyAsync(ctx->items.p, sc.items.data(), ni * sizeof(Item),
+                                     cudaMemcpyHostToDevice, s));
+            CUDA_TRY(cudaMemcpyAsync(ctx->group_items.p, sc.group_items.data(), ni * sizeof(int),
+                                     cudaMemcpyHostToDevice, s));
+        }
+        CUDA_TRY(cudaMemcpyAsync(ctx->group_off.p, sc.group_off.data(), (ng + 1) * sizeof(int),
+                                 cudaMemcpyHostToDevice, s));
+        ctx->n_items = ni;
+        ctx->n_groups = ng;
+        ctx->jmax_used = sc.jmax;
+        ctx->pair_slots = sc.pair_slots;
+        ctx->sched_key = key;
+    }
+    // pack
+    const size_t xsz = out_f64 ? sizeof(double4) : sizeof(float4);
+    ALLOC_TRY(ctx->X, (size_t)batch * npad * xsz);
+    ALLOC_TRY(ctx->slot_of, (size_t)n * sizeof(int));
+    CUDA_TRY(cudaMemsetAsync(ctx->X.p, 0, (size_t)batch * npad * xsz, s));
+    const double *cen = nullptr;
+    if (center) {
+        ALLOC_TRY(ctx->centroid, (size_t)batch * 3 * sizeof(double));
+        CUDA_TRY(launch_centroid(cd, coords_f64, n, batch, ctx->centroid.as<double>(), s));
+        cen = ctx->centroid.as<double>();
+        launches += 1;
+    }
+    CUDA_TRY(launch_scatter(cd, coords_f64, td, n, batch, T, ctx->blockoffs.as<int>(),
+                            ctx->meta.as<int>(), cen, out_f64 ? 1 : 0, ctx->X.p, npad,
+                            ctx->slot_of.as<int>(), s));
+    launches += 1;
+    ctx->stats[0] = ctx->n_items;
+    ctx->stats[1] = ctx->pair_slots;
+    ctx->stats[2] = batch * (n * (n - 1) / 2);
+    ctx->stats[3] = ctx->n_q;
+    return SAS_OK;
+}
+
+sas_status check_common(sas_ctx *ctx, const void *coords, const int32_t *types, int64_t n,
+                        int64_t batch)
+{
+    if (!ctx) return fail(SAS_ERR_INVALID_ARG, "null context");
+    if (n < 0 || batch < 0) return fail(SAS_ERR_INVALID_ARG, "negative size");
+    if (n > (int64_t)1 << 28) return fail(SAS_ERR_UNSUPPORTED, "more than 2^28 atoms");
+    if (n > 0 && batch > 0 && (!coords || !types)) return fail(SAS_ERR_INVALID_ARG, "null input");
+    if (batch * (n + (int64_t)ctx->n_types * kTile) > ((int64_t)1 << 31))
+        return fail(SAS_ERR_UNSUPPORTED, "batch * atoms too large");
+    return SAS_OK;
+}
+
+sas_status zero_out(void *out, size_t bytes, cudaStream_t s)
+{
+    if (!bytes) return SAS_OK;
+    if (on_device(out)) {
+        CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));
+    } else {
+        std::memset(out, 0, bytes);
+    }
+    return SAS_OK;
+}
+
+sas_status run_profile(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types,
+                       int64_t n, int64_t batch, double *I_out, cudaStream_t s)
+{
+    sas_status st = check_common(ctx, coords, types, n, batch);
+    if (st != SAS_OK) return st;
+    if (coords_type != SAS_COORDS_F32 && coords_type != SAS_COORDS_F64)
+        return fail(SAS_ERR_INVALID_ARG, "coords_type must be SAS_COORDS_F32 or SAS_COORDS_F64");
+    if (batch > 0 && !I_out) return fail(SAS_ERR_INVALID_ARG, "null output");
+    ctx->have_partials = false;
+    if (batch == 0) return SAS_OK;
+    const int T = ctx->n_types, Q = ctx->n_q, Pn = T * (T + 1) / 2;
+    if (n == 0) {
+        ctx->stats[0] = ctx->stats[1] = ctx->stats[2] = 0;
+        return zero_out(I_out, (size_t)batch * Q * sizeof(double), s);
+    }
+    const bool fp64 = (ctx->flags & SAS_FP64) != 0;
+    const int tile = fp64 ? kTile64 : kTile;
+    int launches = 0;
+    st = prepare(ctx, coords, coords_type, types, n, batch, fp64,
+                 !fp64 && coords_type == SAS_COORDS_F64, tile, s, launches);
+    if (st != SAS_OK) return st;
+    const int64_t npad = ctx->h_meta[2 * T];
+    ALLOC_TRY(ctx->partial, (size_t)std::max(ctx->n_items, 1) * kQChunk * sizeof(double));
+    const int grid_per_sm = ctx->opt_grid > 0 ? ctx->opt_grid : 2;
+    const int grid = std::max(1, std::min(ctx->n_items, grid_per_sm * ctx->sms));
+    CUDA_TRY(cudaEventRecord(ctx->ev0, s));
+    if (fp64) {
+        CUDA_TRY(launch_debye_fp64(ctx->X.as<double4>(), npad, ctx->items.as<Item>(), ctx->n_items,
+                                   ctx->qc, ctx->partial.as<double>(), kQChunk, grid, s));
+    } else {
+        CUDA_TRY(launch_debye_mixed(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items,
+                                    ctx->qc, ctx->opt_reseed, ctx->partial.as<double>(), kQChunk,
+                                    grid, ctx->jmax_used, s));
+    }
+    CUDA_TRY(cudaEventRecord(ctx->ev1, s));
+    ctx->ev_pending = true;
+    launches += 1;
+    ALLOC_TRY(ctx->S, (size_t)batch * Pn * Q * sizeof(double));
+    CUDA_TRY(launch_reduce_items(ctx->partial.as<double>(), kQChunk, ctx->items.as<Item>(),
+                                 ctx->group_items.as<int>(), ctx->group_off.as<int>(), ctx->n_groups,
+                                 ctx->qc, ctx->S.as<double>(), s));
+    double *Id = I_out;
+    const bool host_out = !on_device(I_out);
+    if (host_out) {
+        ALLOC_TRY(ctx->out_buf, (size_t)batch * Q * sizeof(double));
+        Id = ctx->out_buf.as<double>();
+    }
+    CUDA_TRY(launch_assemble(ctx->S.as<double>(), ctx->F.as<double>(), ctx->meta.as<int>(), T, batch,
+                             ctx->qc, Id, s));
+    launches += 2;
+    if (host_out) {
+        CUDA_TRY(cudaMemcpyAsync(I_out, Id, (size_t)batch * Q * sizeof(double), cudaMemcpyDeviceToHost,
+                                 s));
+        st = wait_stream(ctx, s);
+        if (st != SAS_OK) return st;
+    }
+    ctx->stats[5] = launches;
+    ctx->last_batch = batch;
+    ctx->have_partials = true;
+    return SAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sas_last_error(void) { return g_err.c_str(); }
+
+const char *sas_version(void) { return "sas 0.1 (sm_103a)"; }
+
+sas_status sas_create(int n_types, const double *ff_coef, const double *q, int n_q, unsigned flags,
+                      sas_ctx **out)
+{
+    if (!out) return fail(SAS_ERR_INVALID_ARG, "null output handle");
+    if (n_types < 1 || n_types > SAS_MAX_TYPES)
+        return fail(SAS_ERR_INVALID_ARG, "n_types must be in [1, %d]", SAS_MAX_TYPES);
+    if (n_q < 1 || n_q > SAS_MAX_Q) return fail(SAS_ERR_INVALID_ARG, "n_q must be in [1, %d]", SAS_MAX_Q);
+    if (!ff_coef || !q) return fail(SAS_ERR_INVALID_ARG, "null coefficients or q grid");
+    if (flags & ~1u) return fail(SAS_ERR_INVALID_ARG, "unknown flags");
+    if (!finite_all(ff_coef, (size_t)9 * n_types)) return fail(SAS_ERR_INVALID_ARG, "non-finite coefficient");
+    if (!finite_all(q, (size_t)n_q)) return fail(SAS_ERR_INVALID_ARG, "non-finite q");
+    if (q[0] < 0) return fail(SAS_ERR_INVALID_ARG, "negative q");
+    const double q0 = q[0];
+    const double dq = n_q > 1 ? (q[n_q - 1] - q[0]) / (double)(n_q - 1) : 0.0;
+    if (n_q > 1 && !(dq > 0)) return fail(SAS_ERR_UNSUPPORTED, "q grid must be strictly ascending");
+    const double qmax = std::max(std::fabs(q[n_q - 1]), dq);
+    for (int k = 0; k < n_q; ++k)
+        if (std::fabs(q[k] - (q0 + k * dq)) > 1e-9 * qmax)
+            return fail(SAS_ERR_UNSUPPORTED, "q grid is not uniform (q[%d] off by %.3g)", k,
+                        q[k] - (q0 + k * dq));
+    sas_ctx *c = new (std::nothrow) sas_ctx;
+    if (!c) return fail(SAS_ERR_ALLOC, "host allocation failed");
+    c->n_types = n_types;
+    c->n_q = n_q;
+    c->flags = flags;
+    c->coef.assign(ff_coef, ff_coef + 9 * n_types);
+    c->q.assign(q, q + n_q);
+    QChunks &qc = c->qc;
+    qc.n_q = n_q;
+    qc.n_chunks = (n_q + kQChunk - 1) / kQChunk;
+    qc.q0 = q0;
+    qc.dq = dq;
+    qc.dq_hi = (float)dq;
+    qc.dq_lo = (float)(dq - (double)qc.dq_hi);
+    for (int ch = 0; ch < qc.n_chunks; ++ch) {
+        qc.q_begin[ch] = ch * kQChunk;
+        qc.q_len[ch] = std::min(kQChunk, n_q - ch * kQChunk);
+        const double qs = q0 + (double)qc.q_begin[ch] * dq;
+        qc.qs_hi[ch] = (float)qs;
+        qc.qs_lo[ch] = (float)(qs - (double)qc.qs_hi[ch]);
+    }
+    int dev = 0;
+    auto bail = [&](sas_status st) {
+        delete c;
+        return st;
+    };
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(SAS_ERR_CUDA, "no usable CUDA device"));
+    }
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(SAS_ERR_CUDA, "event creation failed"));
+    }
+    if (cudaMallocHost((void **)&c->h_meta, (2 * SAS_MAX_TYPES + 2) * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_meta = nullptr;
+        return bail(fail(SAS_ERR_ALLOC, "pinned allocation failed"));
+    }
+    if (!c->coef_d.ensure(9 * n_types * sizeof(double)) ||
+        !c->F.ensure((size_t)n_types * n_q * sizeof(double)))
+        return bail(fail(SAS_ERR_ALLOC, "device allocation failed"));
+    if (cudaMemcpy(c->coef_d.p, ff_coef, 9 * n_types * sizeof(double), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        launch_form_factors(c->coef_d.as<double>(), n_types, qc, c->F.as<double>(), 0) != cudaSuccess ||
+        cudaStreamSynchronize(0) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(SAS_ERR_CUDA, "form-factor table failed"));
+    }
+    *out = c;
+    return SAS_OK;
+}
+
+sas_status sas_destroy(sas_ctx *ctx)
+{
+    if (!ctx) return SAS_OK;
+    if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+    return SAS_OK;
+}
+
+sas_status sas_profile(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types,
+                       int64_t n_atoms, double *I_out, void *stream)
+{
+    return run_profile(ctx, coords, coords_type, types, n_atoms, 1, I_out, (cudaStream_t)stream);
+}
+
+sas_status sas_profile_batch(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types,
+                             int64_t n_atoms, int64_t batch, double *I_out, void *stream)
+{
+    return run_profile(ctx, coords, coords_type, types, n_atoms, batch, I_out, (cudaStream_t)stream);
+}
+
+sas_status sas_partials(sas_ctx *ctx, double *S_out, int64_t capacity, void *stream)
+{
+    if (!ctx || !S_out) return fail(SAS_ERR_INVALID_ARG, "null argument");
+    if (!ctx->have_partials) return fail(SAS_ERR_INVALID_ARG, "no profile computed since the last change");
+    const int Pn = ctx->n_types * (ctx->n_types + 1) / 2;
+    const int64_t need = ctx->last_batch * Pn * ctx->n_q;
+    if (capacity < need) return fail(SAS_ERR_INVALID_ARG, "capacity %lld < %lld", (long long)capacity, (long long)need);
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(S_out, ctx->S.p, (size_t)need * sizeof(double), cudaMemcpyDefault, s));
+    if (!on_device(S_out)) return wait_stream(ctx, s);
+    return SAS_OK;
+}
+
+sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value)
+{
+    if (!ctx) return fail(SAS_ERR_INVALID_ARG, "null context");
+    switch (option) {
+    case SAS_OPT_JMAX:
+        if (value < 0 || value % kTile || value > 8192)
+            return fail(SAS_ERR_INVALID_ARG, "JMAX must be 0 or a multiple of %d up to 8192", kTile);
+        ctx->opt_jmax = value;
+        return SAS_OK;
+    case SAS_OPT_RESEED:
+        if (value != 0 && value != 32 && value != 64)
+            return fail(SAS_ERR_INVALID_ARG, "RESEED must be 0, 32 or 64");
+        ctx->opt_reseed = (int)value;
+        return SAS_OK;
+    case SAS_OPT_VALIDATE:
+        if (value != 1) return fail(SAS_ERR_UNSUPPORTED, "validation cannot be switched off");
+        return SAS_OK;
+    case SAS_OPT_GRID:
+        if (value < 0 || value > 8) return fail(SAS_ERR_INVALID_ARG, "GRID must be in [0, 8]");
+        ctx->opt_grid = (int)value;
+        return SAS_OK;
+    case SAS_OPT_TIMEOUT_MS:
+        if (value <= 0) return fail(SAS_ERR_INVALID_ARG, "timeout must be positive");
+        ctx->opt_timeout_ms = value;
+        return SAS_OK;
+    default:
+        return fail(SAS_ERR_INVALID_ARG, "unknown option %d", option);
+    }
+}
+
+sas_status sas_last_stats(sas_ctx *ctx, int64_t *stats_out, int n)
+{
+    if (!ctx || !stats_out || n < 0) return fail(SAS_ERR_INVALID_ARG, "bad argument");
+    if (ctx->ev_pending) {   // pair-kernel time of the last call, in nanoseconds
+        CUDA_TRY(cudaEventSynchronize(ctx->ev1));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        ctx->stats[4] = (int64_t)((double)ms * 1.0e6);
+        ctx->ev_pending = false;
+    }
+    for (int i = 0; i < n && i < 6; ++i) stats_out[i] = ctx->stats[i];
+    return SAS_OK;
+}
+
+sas_status sas_profile_grad(sas_ctx *ctx, const float *, const int32_t *, int64_t, int64_t,
+                            const double *, const double *, double *, float *, double *, void *)
+{
+    if (!ctx) return fail(SAS_ERR_INVALID_ARG, "null context");
+    return fail(SAS_ERR_UNSUPPORTED, "not built yet");
+}
+
+sas_status sas_profile_vjp(sas_ctx *ctx, const float *, const int32_t *, int64_t, int64_t,
+                           const double *, float *, void *)
+{
+    if (!ctx) return fail(SAS_ERR_INVALID_ARG, "null context");
+    return fail(SAS_ERR_UNSUPPORTED, "not built yet");
+}
+
+sas_status sas_pair_histogram(sas_ctx *ctx, const float *, const int32_t *, int64_t, int64_t, int,
+                              float, int32_t *, int64_t *, void *)
+{
+    if (!ctx) return fail(SAS_ERR_INVALID_ARG, "null context");
+    return fail(SAS_ERR_UNSUPPORTED, "not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sas.h"
+
+namespace sas {
+
+constexpr int kTile = 128;      // atoms per I-tile of the mixed kernel (= its threads per CTA); group padding
+constexpr int kTile64 = 64;     // atoms per I-tile of the FP64 kernel
+constexpr int kQChunk = 208;    // q values one pass of a pair kernel covers (52 blocks of 4)
+constexpr int kMaxChunks = SAS_MAX_Q / kQChunk;
+constexpr int kPackThreads = 256;
+
+// One unit of pair work: an I-tile of one type against a contiguous J-range of
+// one type (both inside one conformer), for one chunk of the q grid.  All
+// pairs of an item share the type pair, so the item's sums belong to one S_ab.
+struct Item {
+    int batch;   // conformer
+    int pair;    // type-pair index p(a,b), a <= b
+    int i0;      // first slot of the I-tile
+    int j0;      // first slot of the J-range
+    int jlen;    // J-range length in slots (a multiple of the I-tile)
+    int chunk;   // q chunk
+    int diag;    // 1 when the J-range starts at the I-tile (same type): pairs with j <= i are masked
+    int work;    // jlen * tile (for scheduling)
+};
+
+// The uniform q grid split into passes of at most kQChunk values.
+struct QChunks {
+    int n_q;
+    int n_chunks;
+    int q_begin[kMaxChunks];
+    int q_len[kMaxChunks];
+    float qs_hi[kMaxChunks];   // first q of the chunk as a float32 pair (hi + lo)
+    float qs_lo[kMaxChunks];
+    float dq_hi, dq_lo;        // grid step as a float32 pair
+    double q0, dq;             // the grid in FP64: q_k = q0 + k*dq
+};
+
+// ---- packing (pack.cu) -------------------------------------------------------
+// meta layout (int32): [0,T) real counts, [T, 2T+1) padded group offsets, [2T+1] error bits
+enum { kErrBadType = 1, kErrNonFinite = 2 };
+
+cudaError_t launch_count_types(const void *coords, int coords_f64, const int32_t *types, int64_t n,
+                               int64_t batch, int n_types, int *blockcounts, int *errword,
+                               cudaStream_t s);
+cudaError_t launch_scan_counts(const int *blockcounts, int nblk, int n_types, int tile,
+                               int *blockoffs, int *meta, cudaStream_t s);
+cudaError_t launch_centroid(const void *coords, int coords_f64, int64_t n, int64_t batch,
+                            double *centroid, cudaStream_t s);
+// X: float4 [batch][npad] (mixed) or double4 (fp64); padding slots must be zero beforehand.
+cudaError_t launch_scatter(const void *coords, int coords_f64, const int32_t *types, int64_t n,
+                           int64_t batch, int n_types, const int *blockoffs, const int *meta,
+                           const double *centroid, int out_f64, void *X, int64_t npad,
+                           int *slot_of, cudaStream_t s);
+
+// ---- form factors and assembly (reduce.cu) -----------------------------------
+// F [T][n_q] f64 from coefficients [T][9]
+cudaError_t launch_form_factors(const double *coef, int n_types, const QChunks &qc, double *F,
+                                cudaStream_t s);
+// S[b][p][k] = sum over the items of group (b,p) of partial[item][k - q_begin(chunk)] (fixed order)
+cudaError_t launch_reduce_items(const double *partial, int part_stride, const Item *items,
+                                const int *group_items, const int *group_off, int n_groups,
+                                const QChunks &qc, double *S, cudaStream_t s);
+// I[b][k] = sum_t n_t F_t^2 + sum_p 2 F_a F_b (q_k > 0 ? S/q_k : count_p)
+cudaError_t launch_assemble(double *S, const double *F, const int *meta, int n_types,
+                            int64_t batch, const QChunks &qc, double *I, cudaStream_t s);
+
+// ---- pair kernels -------------------------------------------------------------
+// partial [n_items][part_stride] f64: sum over the item's pairs of w_i w_j sin(q r)/r
+cudaError_t launch_debye_mixed(const float4 *X, int64_t npad, const Item *items, int n_items,
+                               const QChunks &qc, int reseed, double *partial, int part_stride,
+                               int grid, int jmax, cudaStream_t s);
+cudaError_t launch_debye_fp64(const double4 *X, int64_t npad, const Item *items, int n_items,
+                              const QChunks &qc, double *partial, int part_stride, int grid,
+                              cudaStream_t s);
+
+}  // namespace sas

@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every symbol include/sas.h declares;
+argument checks that need no GPU return the documented status codes."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1306_2258_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sas.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sas_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declarations_match_binding():
+    assert _declared() == sorted(_lib.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    path = _lib.load()._name
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (sas_[a-z_0-9]+)\b", out))
+    missing = set(_declared()) - exported
+    assert not missing, missing
+
+
+def test_version_and_last_error_are_strings():
+    assert "sm_103a" in _lib.sas_version()
+    assert isinstance(_lib.sas_last_error(), str)
+
+
+@pytest.mark.parametrize("n_types,nq,code", [(0, 11, _lib.SAS_ERR_INVALID_ARG),
+                                            (17, 11, _lib.SAS_ERR_INVALID_ARG),
+                                            (3, 0, _lib.SAS_ERR_INVALID_ARG),
+                                            (3, 1665, _lib.SAS_ERR_INVALID_ARG)])
+def test_create_rejects_bad_sizes(n_types, nq, code):
+    import ctypes
+    coef = np.ones((max(n_types, 1), 9))
+    q = np.linspace(0, 1, max(nq, 1))
+    h = ctypes.c_void_p()
+    st = _lib.load().sas_create(n_types, coef.ctypes.data, q.ctypes.data, nq, 0, ctypes.byref(h))
+    assert st == code and not h.value
+
+
+def test_create_rejects_nonuniform_and_bad_grids():
+    coef = np.ones((2, 9))
+    q = np.linspace(0, 1, 51)
+    q[7] += 1e-4
+    with pytest.raises(_lib.SasError) as e:
+        _lib.sas_create(2, coef, q)
+    assert e.value.status == _lib.SAS_ERR_UNSUPPORTED
+    with pytest.raises(_lib.SasError) as e:
+        _lib.sas_create(2, coef, np.linspace(-0.1, 1, 51))
+    assert e.value.status == _lib.SAS_ERR_INVALID_ARG
+    bad = coef.copy()
+    bad[1, 3] = np.nan
+    with pytest.raises(_lib.SasError) as e:
+        _lib.sas_create(2, bad, np.linspace(0, 1, 51))
+    assert e.value.status == _lib.SAS_ERR_INVALID_ARG
+    with pytest.raises(_lib.SasError) as e:
+        _lib.sas_create(2, coef, np.linspace(1, 0, 51))
+    assert e.value.status == _lib.SAS_ERR_UNSUPPORTED
+
+
+def test_null_context_is_rejected():
+    with pytest.raises(_lib.SasError) as e:
+        _lib.sas_profile(None, None, 0, None, 0, None, 0)
+    assert e.value.status == _lib.SAS_ERR_INVALID_ARG
+    with pytest.raises(_lib.SasError):
+        _lib.sas_set_option(None, _lib.SAS_OPT_JMAX, 0)
+    _lib.sas_destroy(None)

@@ -1,0 +1,236 @@
+"""GPU parity of the Debye profile (Section I-A, Eq. 2) against the FP64 CPU oracle.
+
+Tolerances (per q, relative to the oracle's I(q)):
+  mixed precision (FP32 pair terms, FP64 reductions)  1e-5
+  all-FP64 kernel                                     1e-12
+Every call goes through the C ABI (libsas.so) via the ctypes binding.
+"""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1306_2258_gb300 import _lib, workloads as wl
+from paper_1306_2258_gb300.profile import Profile
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-5
+TOL_FP64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    _lib.load()
+
+
+def _rel(a, b):
+    return np.max(np.abs(np.asarray(a) - np.asarray(b)) / np.abs(np.asarray(b)))
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_cached(key):
+    kind = key[0]
+    if kind == "c1":
+        w = wl.c1_plain_fp64()
+        return oracle.profile(w.mol.coords, w.mol.types, w.coef, w.q)
+    if kind == "c2_10k":
+        w = wl.c2_globule(10000)
+        return oracle.profile(w.mol.coords, w.mol.types, w.coef, w.q)
+    raise KeyError(key)
+
+
+def _gpu(w_mol, coef, q, precision="mixed", coords=None, **opts):
+    p = Profile(coef, q, precision)
+    for k, v in opts.items():
+        p.set_option(getattr(_lib, "SAS_OPT_" + k.upper()), v)
+    x = torch.as_tensor(w_mol.coords if coords is None else coords).cuda()
+    I = p(x, torch.as_tensor(w_mol.types).cuda()).cpu().numpy()
+    p.close()
+    return I
+
+
+# ---------------------------------------------------------------- configurations
+
+def test_c1_fp64_kernel_matches_oracle_1e12():
+    w = wl.c1_plain_fp64()
+    ref = _oracle_cached(("c1",))
+    I = _gpu(w.mol, w.coef, w.q, "fp64")
+    assert _rel(I, ref) <= TOL_FP64
+
+
+def test_c1_mixed_matches_oracle():
+    w = wl.c1_plain_fp64()
+    ref = _oracle_cached(("c1",))
+    I = _gpu(w.mol, w.coef, w.q, "mixed", coords=w.mol.coords.astype(np.float32))
+    ref32 = oracle.profile(w.mol.coords.astype(np.float32), w.mol.types, w.coef, w.q)
+    assert _rel(I, ref32) <= TOL_MIXED
+    assert _rel(I, ref) <= 1e-4   # float32 rounding of the input itself stays small
+
+
+@pytest.mark.parametrize("reseed", [0, 32, 64])
+def test_c2_10k_mixed_matches_oracle(reseed):
+    w = wl.c2_globule(10000)
+    ref = _oracle_cached(("c2_10k",))
+    I = _gpu(w.mol, w.coef, w.q, "mixed", reseed=reseed)
+    assert _rel(I, ref) <= TOL_MIXED
+
+
+def test_c2_10k_fp64_matches_oracle():
+    w = wl.c2_globule(10000)
+    ref = _oracle_cached(("c2_10k",))
+    I = _gpu(w.mol, w.coef, w.q, "fp64")
+    assert _rel(I, ref) <= TOL_FP64
+
+
+def test_c2_50k_subsample_mixed_matches_oracle():
+    w = wl.c2_globule(50000)
+    sub = wl.subsample(w.mol, 5000, wl.seed_for(2, 5000))
+    ref = oracle.profile(sub.coords, sub.types, w.coef, w.q)
+    assert _rel(_gpu(sub, w.coef, w.q, "mixed"), ref) <= TOL_MIXED
+
+
+def test_c2_50k_full_mixed_vs_oracle_on_sampled_q_and_vs_fp64_kernel():
+    """The full 50,000-atom profile in the benchmark's configuration: the oracle
+    evaluates a few sampled q values over all 1.25e9 pairs; the FP64 kernel all of them."""
+    w = wl.c2_globule(50000)
+    I = _gpu(w.mol, w.coef, w.q, "mixed")
+    I64 = _gpu(w.mol, w.coef, w.q, "fp64")
+    assert _rel(I, I64) <= TOL_MIXED
+    ks = np.array([0, 37, 100, 163, 200])
+    ref = oracle.profile(w.mol.coords, w.mol.types, w.coef, w.q[ks])
+    assert _rel(I[ks], ref) <= TOL_MIXED
+    assert _rel(I64[ks], ref) <= TOL_FP64
+
+
+@pytest.mark.parametrize("which", ["rod", "sparse"])
+def test_c3_subsamples_mixed_match_oracle(which):
+    w = wl.c3_rod() if which == "rod" else wl.c3_sparse()
+    sub = wl.subsample(w.mol, 4000, wl.seed_for(3, 40 + (which == "sparse")))
+    ref = oracle.profile(sub.coords, sub.types, w.coef, w.q)
+    assert _rel(_gpu(sub, w.coef, w.q, "mixed"), ref) <= TOL_MIXED
+    assert _rel(_gpu(sub, w.coef, w.q, "fp64"), ref) <= TOL_FP64
+
+
+# ---------------------------------------------------------------- edges and closed forms
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 127, 128, 129, 300])
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_small_and_ragged_sizes(n, precision):
+    mol = wl.random_walk_globule(n, 4, 100 + n).as_f32()
+    mol.types[: max(1, n // 3)] = 2          # a big group, and types that may be empty or single
+    coef = wl.form_factor_coefficients(4, 7)
+    q = wl.q_grid(0.0, 1.0, 101)
+    ref = oracle.profile(mol.coords, mol.types, coef, q)
+    tol = TOL_MIXED if precision == "mixed" else TOL_FP64
+    assert _rel(_gpu(mol, coef, q, precision), ref) <= tol
+
+
+def test_empty_molecule_gives_zero():
+    p = Profile(wl.form_factor_coefficients(3, 1), wl.q_grid(0, 1, 11))
+    I = p(torch.zeros((0, 3), device="cuda"), torch.zeros(0, dtype=torch.int32, device="cuda"))
+    assert torch.all(I == 0)
+
+
+@pytest.mark.parametrize("r", [0.0, 1e-7, 3.8, 100.0, 5000.0])
+def test_two_atom_closed_form(r):
+    coef = wl.form_factor_coefficients(2, 11)
+    q = wl.q_grid(0.0, 1.0, 41)
+    mol = wl.Molecule(np.array([[0.5, -1.0, 2.0], [0.5 + r, -1.0, 2.0]], np.float32), np.array([0, 1], np.int32), 2)
+    f = oracle.form_factors(mol.types, coef, q)
+    rr = float(np.float32(0.5 + r) - np.float32(0.5))
+    x = q * rr
+    s = np.where(x == 0, 1.0, np.sin(x) / np.where(x == 0, 1.0, x))
+    expect = f[0] ** 2 + f[1] ** 2 + 2 * f[0] * f[1] * s
+    assert _rel(_gpu(mol, coef, q, "mixed"), expect) <= TOL_MIXED
+    assert _rel(_gpu(mol, coef, q, "fp64"), expect) <= TOL_FP64
+
+
+def test_q_grid_not_from_zero_many_chunks_and_single_q():
+    mol = wl.random_walk_globule(700, 3, 5).as_f32()
+    coef = wl.form_factor_coefficients(3, 6)
+    for q in (wl.q_grid(0.01, 0.5, 101), wl.q_grid(0.0, 2.0, 500), np.array([0.3])):
+        ref = oracle.profile(mol.coords, mol.types, coef, q)
+        assert _rel(_gpu(mol, coef, q, "mixed"), ref) <= TOL_MIXED
+        assert _rel(_gpu(mol, coef, q, "fp64"), ref) <= TOL_FP64
+
+
+# ---------------------------------------------------------------- invariances and API behaviour
+
+def test_rotation_translation_permutation():
+    mol = wl.random_walk_globule(2000, 5, 77)
+    coef = wl.form_factor_coefficients(5, 78)
+    q = wl.q_grid(0, 1, 201)
+    ref = oracle.profile(mol.coords, mol.types, coef, q)
+    R = wl.random_rotation(79)
+    rot = wl.Molecule(mol.coords @ R.T, mol.types, 5)
+    assert _rel(_gpu(rot, coef, q, "mixed", coords=rot.coords), ref) <= TOL_MIXED
+    shifted = mol.coords + np.array([1.0e4, -7.0e3, 3.0e3])   # float64 input: centred before rounding
+    assert _rel(_gpu(mol, coef, q, "mixed", coords=shifted), ref) <= TOL_MIXED
+    assert _rel(_gpu(mol, coef, q, "fp64", coords=shifted), ref) <= 1e-10
+    perm = np.random.default_rng(80).permutation(mol.n)
+    pm = wl.Molecule(mol.coords[perm], mol.types[perm], 5)
+    assert _rel(_gpu(pm, coef, q, "mixed", coords=pm.coords), ref) <= TOL_MIXED
+
+
+def test_batch_equals_single_calls_bitwise_and_repeatable():
+    w = wl.c4_refinement(n=1500, batch=4)
+    p = Profile(w["coef"], w["q"])
+    p.set_option(_lib.SAS_OPT_JMAX, 512)
+    types = torch.as_tensor(w["base"].types).cuda()
+    X = torch.as_tensor(w["conformers"]).cuda()
+    Ib = p(X, types)
+    Ib2 = p(X, types)
+    assert torch.equal(Ib, Ib2)
+    for b in range(4):
+        assert torch.equal(p(X[b], types), Ib[b])
+    p.close()
+
+
+def test_host_and_device_buffers_agree():
+    w = wl.c1_plain_fp64()
+    p = Profile(w.coef, w.q)
+    x32 = w.mol.coords.astype(np.float32)
+    Ih = p(x32, w.mol.types)                       # host in, host out (staged)
+    Id = p(torch.as_tensor(x32).cuda(), torch.as_tensor(w.mol.types).cuda()).cpu()
+    assert torch.equal(Ih, Id)
+    p.close()
+
+
+def test_partials_match_oracle_pair_sums():
+    mol = wl.random_walk_globule(1200, 3, 81).as_f32()
+    coef = wl.form_factor_coefficients(3, 82)
+    q = wl.q_grid(0, 1, 101)
+    p = Profile(coef, q, "fp64")
+    p(torch.as_tensor(mol.coords).cuda(), torch.as_tensor(mol.types).cuda())
+    S = p.partials()[0]
+    ref = oracle.pair_sums(mol.coords, mol.types, 3, q)
+    np.testing.assert_allclose(S, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+    p.close()
+
+
+def test_invalid_inputs_leave_output_untouched():
+    mol = wl.random_walk_globule(300, 3, 83).as_f32()
+    coef = wl.form_factor_coefficients(3, 84)
+    q = wl.q_grid(0, 1, 21)
+    p = Profile(coef, q)
+    x = torch.as_tensor(mol.coords).cuda()
+    t = torch.as_tensor(mol.types).cuda()
+    out = torch.full((1, 21), 7.0, dtype=torch.float64, device="cuda")
+    bad = x.clone()
+    bad[17, 1] = float("nan")
+    with pytest.raises(_lib.SasError) as e:
+        _lib.sas_profile_batch(p._ctx, bad, 0, t, 300, 1, out)
+    assert e.value.status == _lib.SAS_ERR_INVALID_ARG
+    tb = t.clone()
+    tb[5] = 3
+    with pytest.raises(_lib.SasError) as e:
+        _lib.sas_profile_batch(p._ctx, x, 0, tb, 300, 1, out)
+    assert e.value.status == _lib.SAS_ERR_INVALID_ARG
+    assert torch.all(out == 7.0)
+    _lib.sas_profile_batch(p._ctx, x, 0, t, 300, 1, out)    # the context is still usable
+    assert torch.all(torch.isfinite(out))
+    p.close()
