@@ -13,16 +13,18 @@
 //    broadcast reads).
 //  * For each pair it computes r once, then generates w_i w_j sin(q_k r)/r for
 //    every q_k of the chunk with the three-term angle-addition identity
-//        sin(x + 4t) = 2 cos(4t) sin(x) - sin(x - 4t),   t = dq * r,
-//    applied to four interleaved sequences (q_k, q_k+1, q_k+2, q_k+3) held as
-//    two float2 values: one packed FP32 fused multiply-add per two q values,
-//    and one packed FP32 add to accumulate them.  Stepping by 4t instead of t
-//    keeps 2cos(4t) away from 2 for near pairs (small t), where the rounding
-//    of the coefficient would otherwise make the phase drift.
-//  * Seeds (the first eight q of a segment) come from an accurate FP32
-//    sin/cos of the segment's start phase and of t, combined by angle
-//    addition.  The sequence is re-seeded every RB blocks of four q (RB = 0:
-//    only at the chunk start).
+//        sin(x + Mt) = 2 cos(Mt) sin(x) - sin(x - Mt),   t = dq * r,
+//    applied to M interleaved sequences (M = 2 or 4) held as float2 values:
+//    one packed FP32 fused multiply-add per two q values, and one packed FP32
+//    add to accumulate them.  A step of Mt instead of t keeps 2cos(Mt) away
+//    from 2 for near pairs (small t), where the rounding of the coefficient
+//    would otherwise make the phase drift.
+//  * The identity is ill-conditioned wherever Mt is near a multiple of pi
+//    (errors grow like 1/sin(Mt) per step), so the sequences are re-seeded
+//    with exact values every KQ q values: the segment's start phase advances
+//    by an exact rotation through K t, and the first 2M values of a segment
+//    are S cos(jt) + C sin(jt) with cos(jt), sin(jt) from an accurate FP32
+//    sin/cos of t and angle addition.
 //  * The per-thread sums are FP32 over the item's J-range (one tile of the
 //    precision pattern), then lifted to FP64 for a warp reduce-scatter with
 //    shuffles and a fixed-order block sum; one FP64 partial per item and q.
@@ -33,8 +35,6 @@ namespace sas {
 
 namespace {
 
-constexpr int NB = kQChunk / 4;   // blocks of four q values per chunk (52)
-constexpr int NV = kQChunk;       // accumulators per thread (208 floats)
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -66,35 +66,30 @@ __device__ __forceinline__ void multiples(float c1, float s1, Multiples &m)
     m.s[7] = fmaf(m.s[6], c1, m.c[6] * s1);
 }
 
-// Eight consecutive terms S cos(j t) + C sin(j t), j = 0..7, as four float2.
-__device__ __forceinline__ void seed8(float S, float C, const Multiples &m, float2 &p0, float2 &p1,
-                                      float2 &c0, float2 &c1)
-{
-    float v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = fmaf(S, m.c[j], C * m.s[j]);
-    p0 = make_float2(v[0], v[1]);
-    p1 = make_float2(v[2], v[3]);
-    c0 = make_float2(v[4], v[5]);
-    c1 = make_float2(v[6], v[7]);
-}
-
-template <int RB>
+// Terms of one pair for the q values of a chunk, added into acc (float2 slot v holds q = 2v, 2v+1).
+//   M  : recurrence step in q values (2 or 4): u_{k+M} = 2 cos(M t) u_k - u_{k-M}
+//   KQ : re-seed interval in q values (0: only at the chunk start), a multiple of 2M
+template <int NB, int M, int KQ>
 __device__ __forceinline__ void pair_terms(const float4 xi, const float4 xj, float w, float qs_hi,
                                            float qs_lo, bool zero_start, float dq_hi, float dq_lo,
                                            float2 (&acc)[2 * NB])
 {
+    static_assert(M == 2 || M == 4, "step must be 2 or 4");
+    static_assert(KQ == 0 || KQ % (2 * M) == 0, "re-seed interval must be a multiple of 2M");
+    constexpr int G = M / 2;                          // float2 per block of M values
+    constexpr int NBM = 4 * NB / M;                   // blocks of M values per chunk
+    constexpr int SEG = (KQ > 0 && KQ / M < NBM) ? KQ / M : NBM;   // blocks per segment
     const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
     float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
     r2 = fmaxf(r2, 1e-12f);            // coincident atoms: r = 1e-6 A, sin(q r)/r -> q
     const float r = sqrtf(r2);
-    const float scale = w * rsqrtf(r2); // amplitude w_i w_j / r (phase uses the rounded sqrt)
+    const float scale = w * rsqrtf(r2); // amplitude w_i w_j / r (the phase uses the rounded sqrt)
     const float t = fmaf(dq_hi, r, dq_lo * r);
     const SinCos b1 = sincos_f32(t);
     Multiples m;
     multiples(b1.c, b1.s, m);
-    const float C4 = 2.f * m.c[4];      // 2 cos(4t)
-    const float2 C42 = make_float2(C4, C4);
+    const float CM = 2.f * m.c[M];      // 2 cos(M t)
+    const float2 CM2 = make_float2(CM, CM);
     float S, C;
     if (zero_start) {
         S = 0.f;
@@ -104,49 +99,60 @@ __device__ __forceinline__ void pair_terms(const float4 xi, const float4 xj, flo
         S = scale * ph.s;
         C = scale * ph.c;
     }
-    constexpr int SEGB = RB > 0 ? RB : NB;              // blocks per segment
     float cK = 1.f, sK = 0.f;
-    if (SEGB < NB) {
-        const SinCos k = sincos_f32(t * (float)(4 * SEGB));
+    if (SEG < NBM) {   // rotation of the segment start phase by (M*SEG) t
+        const SinCos k = sincos_f32(t * (float)(M * SEG));
         cK = k.c;
         sK = k.s;
     }
-    float2 p0, p1, c0, c1;
+    float2 prev[G], cur[G];
 #pragma unroll
-    for (int blk = 0; blk < NB; ++blk) {
-        if (blk % SEGB == 0) {        // segment start: seed blocks blk and blk+1
-            if (blk > 0) {            // advance the segment phase by 4*SEGB*t
+    for (int blk = 0; blk < NBM; ++blk) {
+        const int v0 = blk * G;
+        if (blk % SEG == 0) {        // segment start: exact values for blocks blk and blk+1
+            if (blk > 0) {
                 const float S2 = fmaf(S, cK, C * sK);
                 C = fmaf(C, cK, -S * sK);
                 S = S2;
             }
-            seed8(S, C, m, p0, p1, c0, c1);
-            acc[2 * blk] = f2add(acc[2 * blk], p0);
-            acc[2 * blk + 1] = f2add(acc[2 * blk + 1], p1);
-        } else if (blk % SEGB == 1) {
-            acc[2 * blk] = f2add(acc[2 * blk], c0);
-            acc[2 * blk + 1] = f2add(acc[2 * blk + 1], c1);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                prev[g] = make_float2(fmaf(S, m.c[2 * g], C * m.s[2 * g]),
+                                      fmaf(S, m.c[2 * g + 1], C * m.s[2 * g + 1]));
+                cur[g] = make_float2(fmaf(S, m.c[M + 2 * g], C * m.s[M + 2 * g]),
+                                     fmaf(S, m.c[M + 2 * g + 1], C * m.s[M + 2 * g + 1]));
+                acc[v0 + g] = f2add(acc[v0 + g], prev[g]);
+            }
+        } else if (blk % SEG == 1) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) acc[v0 + g] = f2add(acc[v0 + g], cur[g]);
         } else {
-            const float2 n0 = f2fma(C42, c0, f2neg(p0));
-            const float2 n1 = f2fma(C42, c1, f2neg(p1));
-            acc[2 * blk] = f2add(acc[2 * blk], n0);
-            acc[2 * blk + 1] = f2add(acc[2 * blk + 1], n1);
-            p0 = c0;
-            p1 = c1;
-            c0 = n0;
-            c1 = n1;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const float2 n = f2fma(CM2, cur[g], f2neg(prev[g]));
+                acc[v0 + g] = f2add(acc[v0 + g], n);
+                prev[g] = cur[g];
+                cur[g] = n;
+            }
         }
     }
 }
 
+template <int NB>
 __device__ __forceinline__ float acc_elem(const float2 (&acc)[2 * NB], int k)
 {
     return (k & 1) ? acc[k >> 1].y : acc[k >> 1].x;
 }
 
-// One halving level of the FP64 warp reduce-scatter: lanes with `up` keep the upper half.
-template <int H>
-__device__ __forceinline__ void halve(double (&d)[NV / 2], bool up, int off)
+// Number of halving levels of the reduce-scatter for V values (at most 5, while V stays even).
+__host__ __device__ constexpr int halvings(int V, int lvl = 0)
+{
+    return (lvl < 5 && V % 2 == 0) ? halvings(V / 2, lvl + 1) : lvl;
+}
+
+// One halving level: lanes with `up` keep the upper half of the H values, add the partner's.
+template <int H, int N>
+__device__ __forceinline__ void halve(double (&d)[N], bool up, int off)
 {
 #pragma unroll
     for (int k = 0; k < H / 2; ++k) {
@@ -156,39 +162,52 @@ __device__ __forceinline__ void halve(double (&d)[NV / 2], bool up, int off)
     }
 }
 
-// Sum the 32 lanes' accumulators; the warp's totals land in red[0..NV).
+// Sum the 32 lanes' V = 4*NB accumulators (FP64 from the first cross-thread add on);
+// the warp's totals land in red[0..V).
+template <int NB>
 __device__ __forceinline__ void flush_warp(const float2 (&acc)[2 * NB], double *red, int lane)
 {
-    constexpr int H1 = NV / 2;   // 104
+    constexpr int V = 4 * NB;
+    constexpr int L = halvings(V);      // reduce-scatter levels (offsets 16, 8, ...)
+    constexpr int H1 = V / 2;
+    constexpr int R = V >> L;           // values per lane after the reduce-scatter
     double d[H1];
     const bool up16 = lane & 16;
 #pragma unroll
-    for (int k = 0; k < H1; ++k) {   // lift to FP64 at the first cross-thread sum
-        const float lo = acc_elem(acc, k), hi = acc_elem(acc, k + H1);
+    for (int k = 0; k < H1; ++k) {      // the lift to FP64
+        const float lo = acc_elem<NB>(acc, k), hi = acc_elem<NB>(acc, k + H1);
         const float mine = up16 ? hi : lo, other = up16 ? lo : hi;
         d[k] = (double)mine + (double)__shfl_xor_sync(kFull, other, 16);
     }
-    halve<H1>(d, lane & 8, 8);        // 104 -> 52
-    halve<H1 / 2>(d, lane & 4, 4);    // 52 -> 26
-    halve<H1 / 4>(d, lane & 2, 2);    // 26 -> 13
-    constexpr int R = H1 / 8;         // 13
+    if (L > 1) halve<(V >> 1), H1>(d, lane & 8, 8);
+    if (L > 2) halve<(V >> 2), H1>(d, lane & 4, 4);
+    if (L > 3) halve<(V >> 3), H1>(d, lane & 2, 2);
+    if (L > 4) halve<(V >> 4), H1>(d, lane & 1, 1);
+    // the lane bits not used for scattering: plain butterfly over the R remaining values
 #pragma unroll
-    for (int k = 0; k < R; ++k) d[k] += __shfl_xor_sync(kFull, d[k], 1);
-    const int off = ((lane & 16) ? H1 : 0) + ((lane & 8) ? H1 / 2 : 0) + ((lane & 4) ? H1 / 4 : 0) +
-                    ((lane & 2) ? R : 0);
-    if ((lane & 1) == 0) {
+    for (int b = L; b < 5; ++b) {
+        const int off = 16 >> b;
 #pragma unroll
-        for (int k = 0; k < R; ++k) red[off + k] = d[k];
+        for (int k = 0; k < R; ++k) d[k] += __shfl_xor_sync(kFull, d[k], off);
+    }
+    int base = 0;
+#pragma unroll
+    for (int b = 0; b < L; ++b)
+        if (lane & (16 >> b)) base += V >> (b + 1);
+    const int keep_mask = (1 << (5 - L)) - 1;   // lanes that differ only in butterfly bits hold copies
+    if ((lane & keep_mask) == 0) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) red[base + k] = d[k];
     }
 }
 
-template <int RB>
+template <int NB, int M, int KQ>
 __global__ void __launch_bounds__(kTile, 2)
     k_debye_mixed(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items,
                   int n_items, QChunks qc, double *__restrict__ partial, int part_stride)
 {
     extern __shared__ float4 sj[];
-    __shared__ double red[kTile / 32][NV];
+    __shared__ double red[kTile / 32][4 * NB];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const Item item = items[it];
@@ -207,9 +226,9 @@ __global__ void __launch_bounds__(kTile, 2)
         for (int j = 0; j < item.jlen; ++j) {
             const float4 xj = sj[j];
             const float w = (j <= jmask) ? 0.f : xi.w * xj.w;
-            pair_terms<RB>(xi, xj, w, qs_hi, qs_lo, zero_start, qc.dq_hi, qc.dq_lo, acc);
+            pair_terms<NB, M, KQ>(xi, xj, w, qs_hi, qs_lo, zero_start, qc.dq_hi, qc.dq_lo, acc);
         }
-        flush_warp(acc, red[warp], lane);
+        flush_warp<NB>(acc, red[warp], lane);
         __syncthreads();
         const int qlen = qc.q_len[ch];
         for (int k = tid; k < qlen; k += kTile) {
@@ -221,32 +240,64 @@ __global__ void __launch_bounds__(kTile, 2)
     }
 }
 
-template <int RB>
-cudaError_t launch_rb(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
-                      double *partial, int part_stride, int grid, int jmax, cudaStream_t s)
+template <int NB, int M, int KQ>
+cudaError_t launch_v(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
+                     double *partial, int part_stride, int grid, int jmax, cudaStream_t s)
 {
     const size_t smem = (size_t)jmax * sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(k_debye_mixed<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_debye_mixed<NB, M, KQ>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_debye_mixed<RB><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, partial, part_stride);
+    k_debye_mixed<NB, M, KQ><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, partial, part_stride);
     return cudaGetLastError();
+}
+
+template <int NB, int M>
+cudaError_t launch_k(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
+                     int reseed, double *partial, int part_stride, int grid, int jmax, cudaStream_t s)
+{
+    switch (reseed) {
+    case 32:
+        return launch_v<NB, M, 32>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, s);
+    case 64:
+        return launch_v<NB, M, 64>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, s);
+    default:
+        return launch_v<NB, M, 0>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, s);
+    }
+}
+
+template <int NB>
+cudaError_t launch_nb(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
+                      int step, int reseed, double *partial, int part_stride, int grid, int jmax,
+                      cudaStream_t s)
+{
+    if (step == 2)
+        return launch_k<NB, 2>(X, npad, items, n_items, qc, reseed, partial, part_stride, grid, jmax, s);
+    return launch_k<NB, 4>(X, npad, items, n_items, qc, reseed, partial, part_stride, grid, jmax, s);
 }
 
 }  // namespace
 
+int mixed_blocks_for(int qlen_max)
+{
+    const int nb = (qlen_max + 3) / 4;
+    return nb <= 13 ? 13 : (nb <= 26 ? 26 : 52);
+}
+
 cudaError_t launch_debye_mixed(const float4 *X, int64_t npad, const Item *items, int n_items,
-                               const QChunks &qc, int reseed, double *partial, int part_stride,
+                               const QChunks &qc, int step, int reseed, double *partial, int part_stride,
                                int grid, int jmax, cudaStream_t s)
 {
     if (n_items == 0) return cudaSuccess;
-    switch (reseed) {
-    case 32:
-        return launch_rb<8>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, s);
-    case 64:
-        return launch_rb<16>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, s);
+    int qmax = 0;
+    for (int c = 0; c < qc.n_chunks; ++c) qmax = qc.q_len[c] > qmax ? qc.q_len[c] : qmax;
+    switch (mixed_blocks_for(qmax)) {
+    case 13:
+        return launch_nb<13>(X, npad, items, n_items, qc, step, reseed, partial, part_stride, grid, jmax, s);
+    case 26:
+        return launch_nb<26>(X, npad, items, n_items, qc, step, reseed, partial, part_stride, grid, jmax, s);
     default:
-        return launch_rb<0>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, s);
+        return launch_nb<52>(X, npad, items, n_items, qc, step, reseed, partial, part_stride, grid, jmax, s);
     }
 }
 

@@ -127,11 +127,13 @@ struct sas_ctx {
     QChunks qc{};
     int sms = 1;
     int64_t opt_jmax = 0;
-    int opt_reseed = 0;
+    int opt_reseed = 32;
+    int opt_step = 4;
     int opt_grid = 0;
     int64_t opt_timeout_ms = 600000;
     DevBuf coef_d, F, meta, blockcounts, blockoffs, centroid, X, slot_of, items, group_items,
-        group_off, partial, S, in_coords, in_types, out_buf;
+        group_off, partial, S, in_coords, in_types, out_buf, Ibuf, gbuf, chi2buf, H, G, gout, tgt, wts,
+        hist, dropped;
     int *h_meta = nullptr;   // pinned
     // schedule cache
     std::vector<int64_t> sched_key;
@@ -188,7 +190,7 @@ struct Schedule {
 
 // Items of one conformer-independent layout; `counts` are the real atoms per type.
 void build_schedule(const int *counts, int T, int64_t batch, int tile, int n_chunks, int grid,
-                    int64_t jmax_opt, Schedule &out)
+                    int64_t jmax_opt, int64_t jmax_cap, Schedule &out)
 {
     std::vector<int64_t> P(T), O(T);
     int64_t off = 0;
@@ -214,7 +216,7 @@ void build_schedule(const int *counts, int T, int64_t batch, int tile, int n_chu
         const int64_t cands[] = {4096, 2048, 1024, 512, 256, 128};
         jmax = 128;
         for (int64_t c : cands)
-            if (n_items_for(c) >= 4 * (int64_t)grid) {
+            if (c <= jmax_cap && n_items_for(c) >= 4 * (int64_t)grid) {
                 jmax = c;
                 break;
             }
@@ -280,8 +282,8 @@ bool finite_all(const double *v, size_t n)
 // Shared front half of every pair computation: stage, validate, count, schedule, pack.
 // On success the context holds X (packed), slot_of, meta (counts/offsets) and the item list.
 sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32_t *types, int64_t n,
-                   int64_t batch, bool out_f64, bool center, int tile, cudaStream_t s,
-                   int &launches)
+                   int64_t batch, bool out_f64, bool center, int tile, int n_chunks, int64_t jmax_cap,
+                   cudaStream_t s, int &launches)
 {
     const int T = ctx->n_types;
     const size_t esz = coords_f64 ? sizeof(double) : sizeof(float);
@@ -325,9 +327,12 @@ sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32
     key.push_back(tile);
     key.push_back(ctx->opt_jmax);
     key.push_back(grid_cap);
+    key.push_back(n_chunks);
+    key.push_back(jmax_cap);
     if (key != ctx->sched_key) {
         Schedule sc;
-        build_schedule(ctx->h_meta, T, batch, tile, ctx->qc.n_chunks, grid_cap, ctx->opt_jmax, sc);
+        const int64_t jm = ctx->opt_jmax > 0 ? std::min(ctx->opt_jmax, jmax_cap) : 0;
+        build_schedule(ctx->h_meta, T, batch, tile, n_chunks, grid_cap, jm, jmax_cap, sc);
         const int ni = (int)sc.items.size();
         const int ng = (int)sc.group_off.size() - 1;
         ctx->sched_key.clear();   // invalid until the upload succeeded
@@ -394,26 +399,16 @@ sas_status zero_out(void *out, size_t bytes, cudaStream_t s)
     return SAS_OK;
 }
 
-sas_status run_profile(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types,
-                       int64_t n, int64_t batch, double *I_out, cudaStream_t s)
+// I(q) of `batch` conformers into the device buffer I_dev (all steps on stream s).
+sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types, int64_t n,
+                   int64_t batch, double *I_dev, int64_t jmax_cap, cudaStream_t s, int &launches)
 {
-    sas_status st = check_common(ctx, coords, types, n, batch);
-    if (st != SAS_OK) return st;
-    if (coords_type != SAS_COORDS_F32 && coords_type != SAS_COORDS_F64)
-        return fail(SAS_ERR_INVALID_ARG, "coords_type must be SAS_COORDS_F32 or SAS_COORDS_F64");
-    if (batch > 0 && !I_out) return fail(SAS_ERR_INVALID_ARG, "null output");
-    ctx->have_partials = false;
-    if (batch == 0) return SAS_OK;
     const int T = ctx->n_types, Q = ctx->n_q, Pn = T * (T + 1) / 2;
-    if (n == 0) {
-        ctx->stats[0] = ctx->stats[1] = ctx->stats[2] = 0;
-        return zero_out(I_out, (size_t)batch * Q * sizeof(double), s);
-    }
     const bool fp64 = (ctx->flags & SAS_FP64) != 0;
     const int tile = fp64 ? kTile64 : kTile;
-    int launches = 0;
-    st = prepare(ctx, coords, coords_type, types, n, batch, fp64,
-                 !fp64 && coords_type == SAS_COORDS_F64, tile, s, launches);
+    sas_status st = prepare(ctx, coords, coords_type, types, n, batch, fp64,
+                            !fp64 && coords_type == SAS_COORDS_F64, tile, ctx->qc.n_chunks, jmax_cap, s,
+                            launches);
     if (st != SAS_OK) return st;
     const int64_t npad = ctx->h_meta[2 * T];
     ALLOC_TRY(ctx->partial, (size_t)std::max(ctx->n_items, 1) * kQChunk * sizeof(double));
@@ -425,25 +420,72 @@ sas_status run_profile(sas_ctx *ctx, const void *coords, int coords_type, const 
                                    ctx->qc, ctx->partial.as<double>(), kQChunk, grid, s));
     } else {
         CUDA_TRY(launch_debye_mixed(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items,
-                                    ctx->qc, ctx->opt_reseed, ctx->partial.as<double>(), kQChunk,
+                                    ctx->qc, ctx->opt_step, ctx->opt_reseed, ctx->partial.as<double>(), kQChunk,
                                     grid, ctx->jmax_used, s));
     }
     CUDA_TRY(cudaEventRecord(ctx->ev1, s));
     ctx->ev_pending = true;
-    launches += 1;
     ALLOC_TRY(ctx->S, (size_t)batch * Pn * Q * sizeof(double));
     CUDA_TRY(launch_reduce_items(ctx->partial.as<double>(), kQChunk, ctx->items.as<Item>(),
                                  ctx->group_items.as<int>(), ctx->group_off.as<int>(), ctx->n_groups,
                                  ctx->qc, ctx->S.as<double>(), s));
-    double *Id = I_out;
+    CUDA_TRY(launch_assemble(ctx->S.as<double>(), ctx->F.as<double>(), ctx->meta.as<int>(), T, batch,
+                             ctx->qc, I_dev, s));
+    launches += 3;
+    ctx->last_batch = batch;
+    ctx->have_partials = true;
+    return SAS_OK;
+}
+
+// Copy `bytes` from device buffer `src` to the caller's `dst` (host or device) on stream s.
+sas_status deliver(sas_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s, bool &host)
+{
+    if (!dst || !bytes) return SAS_OK;
+    if (dst == src) return SAS_OK;
+    const bool h = !on_device(dst);
+    host = host || h;
+    CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, h ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    (void)ctx;
+    return SAS_OK;
+}
+
+// A device copy of a small caller array (host or device) of `bytes`.
+sas_status stage_in(DevBuf &buf, const void *src, size_t bytes, cudaStream_t s, const void *&dev)
+{
+    if (on_device(src)) {
+        dev = src;
+        return SAS_OK;
+    }
+    ALLOC_TRY(buf, bytes);
+    CUDA_TRY(cudaMemcpyAsync(buf.p, src, bytes, cudaMemcpyHostToDevice, s));
+    dev = buf.p;
+    return SAS_OK;
+}
+
+sas_status run_profile(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types,
+                       int64_t n, int64_t batch, double *I_out, cudaStream_t s)
+{
+    sas_status st = check_common(ctx, coords, types, n, batch);
+    if (st != SAS_OK) return st;
+    if (coords_type != SAS_COORDS_F32 && coords_type != SAS_COORDS_F64)
+        return fail(SAS_ERR_INVALID_ARG, "coords_type must be SAS_COORDS_F32 or SAS_COORDS_F64");
+    if (batch > 0 && !I_out) return fail(SAS_ERR_INVALID_ARG, "null output");
+    ctx->have_partials = false;
+    if (batch == 0) return SAS_OK;
+    const int Q = ctx->n_q;
+    if (n == 0) {
+        ctx->stats[0] = ctx->stats[1] = ctx->stats[2] = 0;
+        return zero_out(I_out, (size_t)batch * Q * sizeof(double), s);
+    }
+    int launches = 0;
     const bool host_out = !on_device(I_out);
+    double *Id = I_out;
     if (host_out) {
         ALLOC_TRY(ctx->out_buf, (size_t)batch * Q * sizeof(double));
         Id = ctx->out_buf.as<double>();
     }
-    CUDA_TRY(launch_assemble(ctx->S.as<double>(), ctx->F.as<double>(), ctx->meta.as<int>(), T, batch,
-                             ctx->qc, Id, s));
-    launches += 2;
+    st = forward(ctx, coords, coords_type, types, n, batch, Id, 8192, s, launches);
+    if (st != SAS_OK) return st;
     if (host_out) {
         CUDA_TRY(cudaMemcpyAsync(I_out, Id, (size_t)batch * Q * sizeof(double), cudaMemcpyDeviceToHost,
                                  s));
@@ -451,8 +493,34 @@ sas_status run_profile(sas_ctx *ctx, const void *coords, int coords_type, const 
         if (st != SAS_OK) return st;
     }
     ctx->stats[5] = launches;
-    ctx->last_batch = batch;
-    ctx->have_partials = true;
+    return SAS_OK;
+}
+
+// Shared back half of sas_profile_grad / sas_profile_vjp: g [batch][Q] (device) -> gradient.
+sas_status adjoint(sas_ctx *ctx, int64_t n, int64_t batch, const double *g_dev, float *grad_out,
+                   cudaStream_t s, int &launches, bool &host)
+{
+    const int T = ctx->n_types, Q = ctx->n_q, Pn = T * (T + 1) / 2;
+    const int64_t npad = ctx->h_meta[2 * T];
+    ALLOC_TRY(ctx->H, (size_t)batch * Pn * Q * sizeof(float2));
+    CUDA_TRY(launch_adjoint_coef(g_dev, ctx->F.as<double>(), T, batch, ctx->qc, ctx->H.as<float2>(), Q, s));
+    ALLOC_TRY(ctx->G, (size_t)batch * npad * 3 * sizeof(double));
+    CUDA_TRY(cudaMemsetAsync(ctx->G.p, 0, (size_t)batch * npad * 3 * sizeof(double), s));
+    const int grid = std::max(1, std::min(ctx->n_items, 2 * ctx->sms));
+    CUDA_TRY(launch_debye_adjoint(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, ctx->qc,
+                                  ctx->H.as<float2>(), Pn, Q, ctx->G.as<double>(), grid, ctx->jmax_used, s));
+    float *gd = grad_out;
+    const bool h = !on_device(grad_out);
+    if (h) {
+        ALLOC_TRY(ctx->gout, (size_t)batch * n * 3 * sizeof(float));
+        gd = ctx->gout.as<float>();
+    }
+    CUDA_TRY(launch_unpermute(ctx->G.as<double>(), ctx->slot_of.as<int>(), n, npad, batch, gd, s));
+    launches += 3;
+    if (h) {
+        host = true;
+        CUDA_TRY(cudaMemcpyAsync(grad_out, gd, (size_t)batch * n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s));
+    }
     return SAS_OK;
 }
 
@@ -587,6 +655,10 @@ sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value)
             return fail(SAS_ERR_INVALID_ARG, "RESEED must be 0, 32 or 64");
         ctx->opt_reseed = (int)value;
         return SAS_OK;
+    case SAS_OPT_STEP:
+        if (value != 2 && value != 4) return fail(SAS_ERR_INVALID_ARG, "STEP must be 2 or 4");
+        ctx->opt_step = (int)value;
+        return SAS_OK;
     case SAS_OPT_VALIDATE:
         if (value != 1) return fail(SAS_ERR_UNSUPPORTED, "validation cannot be switched off");
         return SAS_OK;
@@ -617,25 +689,115 @@ sas_status sas_last_stats(sas_ctx *ctx, int64_t *stats_out, int n)
     return SAS_OK;
 }
 
-sas_status sas_profile_grad(sas_ctx *ctx, const float *, const int32_t *, int64_t, int64_t,
-                            const double *, const double *, double *, float *, double *, void *)
+sas_status sas_profile_grad(sas_ctx *ctx, const float *coords, const int32_t *types, int64_t n,
+                            int64_t batch, const double *target, const double *weights,
+                            double *chi2_out, float *grad_out, double *I_out, void *stream)
 {
-    if (!ctx) return fail(SAS_ERR_INVALID_ARG, "null context");
-    return fail(SAS_ERR_UNSUPPORTED, "not built yet");
+    sas_status st = check_common(ctx, coords, types, n, batch);
+    if (st != SAS_OK) return st;
+    if (ctx->flags & SAS_FP64) return fail(SAS_ERR_UNSUPPORTED, "the adjoint needs a SAS_MIXED context");
+    if (batch > 0 && (!target || !weights || !chi2_out || (n > 0 && !grad_out)))
+        return fail(SAS_ERR_INVALID_ARG, "null argument");
+    if (batch == 0) return SAS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int Q = ctx->n_q;
+    int launches = 0;
+    bool host = false;
+    const void *tg = nullptr, *wt = nullptr;
+    st = stage_in(ctx->tgt, target, Q * sizeof(double), s, tg);
+    if (st != SAS_OK) return st;
+    st = stage_in(ctx->wts, weights, Q * sizeof(double), s, wt);
+    if (st != SAS_OK) return st;
+    ALLOC_TRY(ctx->Ibuf, (size_t)batch * Q * sizeof(double));
+    if (n == 0) {
+        CUDA_TRY(cudaMemsetAsync(ctx->Ibuf.p, 0, (size_t)batch * Q * sizeof(double), s));
+    } else {
+        st = forward(ctx, coords, SAS_COORDS_F32, types, n, batch, ctx->Ibuf.as<double>(), 2048, s, launches);
+        if (st != SAS_OK) return st;
+    }
+    ALLOC_TRY(ctx->gbuf, (size_t)batch * Q * sizeof(double));
+    ALLOC_TRY(ctx->chi2buf, (size_t)batch * sizeof(double));
+    CUDA_TRY(launch_chi2(ctx->Ibuf.as<double>(), (const double *)tg, (const double *)wt, Q, batch,
+                         ctx->gbuf.as<double>(), ctx->chi2buf.as<double>(), s));
+    launches += 1;
+    if (n > 0) {
+        st = adjoint(ctx, n, batch, ctx->gbuf.as<double>(), grad_out, s, launches, host);
+        if (st != SAS_OK) return st;
+    }
+    st = deliver(ctx, chi2_out, ctx->chi2buf.p, (size_t)batch * sizeof(double), s, host);
+    if (st != SAS_OK) return st;
+    st = deliver(ctx, I_out, ctx->Ibuf.p, (size_t)batch * Q * sizeof(double), s, host);
+    if (st != SAS_OK) return st;
+    ctx->stats[5] = launches;
+    return host ? wait_stream(ctx, s) : SAS_OK;
 }
 
-sas_status sas_profile_vjp(sas_ctx *ctx, const float *, const int32_t *, int64_t, int64_t,
-                           const double *, float *, void *)
+sas_status sas_profile_vjp(sas_ctx *ctx, const float *coords, const int32_t *types, int64_t n,
+                           int64_t batch, const double *grad_I, float *grad_out, void *stream)
 {
-    if (!ctx) return fail(SAS_ERR_INVALID_ARG, "null context");
-    return fail(SAS_ERR_UNSUPPORTED, "not built yet");
+    sas_status st = check_common(ctx, coords, types, n, batch);
+    if (st != SAS_OK) return st;
+    if (ctx->flags & SAS_FP64) return fail(SAS_ERR_UNSUPPORTED, "the adjoint needs a SAS_MIXED context");
+    if (batch > 0 && n > 0 && (!grad_I || !grad_out)) return fail(SAS_ERR_INVALID_ARG, "null argument");
+    if (batch == 0 || n == 0) return SAS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int T = ctx->n_types, Q = ctx->n_q;
+    int launches = 0;
+    bool host = false;
+    const void *gI = nullptr;
+    st = stage_in(ctx->gbuf, grad_I, (size_t)batch * Q * sizeof(double), s, gI);
+    if (st != SAS_OK) return st;
+    // the adjoint needs the packed coordinates and items: pack without the pair kernel
+    st = prepare(ctx, coords, SAS_COORDS_F32, types, n, batch, false, false, kTile, ctx->qc.n_chunks, 2048,
+                 s, launches);
+    if (st != SAS_OK) return st;
+    (void)T;
+    st = adjoint(ctx, n, batch, (const double *)gI, grad_out, s, launches, host);
+    if (st != SAS_OK) return st;
+    ctx->stats[5] = launches;
+    return host ? wait_stream(ctx, s) : SAS_OK;
 }
 
-sas_status sas_pair_histogram(sas_ctx *ctx, const float *, const int32_t *, int64_t, int64_t, int,
-                              float, int32_t *, int64_t *, void *)
+sas_status sas_pair_histogram(sas_ctx *ctx, const float *coords, const int32_t *types, int64_t n,
+                              int64_t batch, int n_bins, float r_max, int32_t *hist_out,
+                              int64_t *dropped_out, void *stream)
 {
-    if (!ctx) return fail(SAS_ERR_INVALID_ARG, "null context");
-    return fail(SAS_ERR_UNSUPPORTED, "not built yet");
+    sas_status st = check_common(ctx, coords, types, n, batch);
+    if (st != SAS_OK) return st;
+    if (n_bins < 1 || n_bins > 4096) return fail(SAS_ERR_INVALID_ARG, "n_bins must be in [1, 4096]");
+    if (!(r_max > 0.f) || !std::isfinite(r_max)) return fail(SAS_ERR_INVALID_ARG, "r_max must be positive");
+    if (batch > 0 && !hist_out) return fail(SAS_ERR_INVALID_ARG, "null output");
+    if (batch == 0) return SAS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int T = ctx->n_types, Pn = T * (T + 1) / 2;
+    const size_t hbytes = (size_t)batch * Pn * n_bins * sizeof(int32_t);
+    if (n == 0) {
+        st = zero_out(hist_out, hbytes, s);
+        if (st == SAS_OK && dropped_out) st = zero_out(dropped_out, (size_t)batch * sizeof(int64_t), s);
+        return st;
+    }
+    int launches = 0;
+    const int64_t jcap = 4096;
+    st = prepare(ctx, coords, SAS_COORDS_F32, types, n, batch, false, false, kTile, 1, jcap, s, launches);
+    if (st != SAS_OK) return st;
+    const int64_t npad = ctx->h_meta[2 * T];
+    ALLOC_TRY(ctx->hist, hbytes);
+    ALLOC_TRY(ctx->dropped, (size_t)batch * sizeof(int64_t));
+    CUDA_TRY(cudaMemsetAsync(ctx->hist.p, 0, hbytes, s));
+    CUDA_TRY(cudaMemsetAsync(ctx->dropped.p, 0, (size_t)batch * sizeof(int64_t), s));
+    const int grid = std::max(1, std::min(ctx->n_items, 4 * ctx->sms));
+    CUDA_TRY(launch_pair_histogram(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, n_bins,
+                                   r_max, Pn, ctx->hist.as<int>(), ctx->dropped.as<unsigned long long>(),
+                                   grid, ctx->jmax_used, s));
+    launches += 1;
+    bool host = false;
+    st = deliver(ctx, hist_out, ctx->hist.p, hbytes, s, host);
+    if (st != SAS_OK) return st;
+    st = deliver(ctx, dropped_out, ctx->dropped.p, (size_t)batch * sizeof(int64_t), s, host);
+    if (st != SAS_OK) return st;
+    ctx->stats[5] = launches;
+    ctx->have_partials = false;
+    return host ? wait_stream(ctx, s) : SAS_OK;
 }
 
 }  // extern "C"

@@ -72,10 +72,32 @@ cudaError_t launch_assemble(double *S, const double *F, const int *meta, int n_t
 // ---- pair kernels -------------------------------------------------------------
 // partial [n_items][part_stride] f64: sum over the item's pairs of w_i w_j sin(q r)/r
 cudaError_t launch_debye_mixed(const float4 *X, int64_t npad, const Item *items, int n_items,
-                               const QChunks &qc, int reseed, double *partial, int part_stride,
+                               const QChunks &qc, int step, int reseed, double *partial, int part_stride,
                                int grid, int jmax, cudaStream_t s);
 cudaError_t launch_debye_fp64(const double4 *X, int64_t npad, const Item *items, int n_items,
                               const QChunks &qc, double *partial, int part_stride, int grid,
                               cudaStream_t s);
+// q capacity (in blocks of four q) of the mixed-precision kernels for a chunk of qlen_max values
+int mixed_blocks_for(int qlen_max);
+
+// ---- adjoint (adjoint.cu) -------------------------------------------------------
+// g[b][k] = 2 w_k (I_bk - T_k), chi2[b] = sum_k w_k (I_bk - T_k)^2 (chi2 may be null)
+cudaError_t launch_chi2(const double *I, const double *T, const double *w, int n_q, int64_t batch,
+                        double *g, double *chi2, cudaStream_t s);
+// H[b][p][k] = (g f_a f_b, g f_a f_b / q) as float2, row stride hstride
+cudaError_t launch_adjoint_coef(const double *g, const double *F, int n_types, int64_t batch,
+                                const QChunks &qc, float2 *H, int hstride, cudaStream_t s);
+// G[b][slot][3] += d(sum_q g_q I(q)) / dx (G must be zeroed); jmax <= 2048
+cudaError_t launch_debye_adjoint(const float4 *X, int64_t npad, const Item *items, int n_items,
+                                 const QChunks &qc, const float2 *H, int n_pairs, int hstride, double *G,
+                                 int grid, int jmax, cudaStream_t s);
+cudaError_t launch_unpermute(const double *G, const int *slot_of, int64_t n, int64_t npad, int64_t batch,
+                             float *grad_out, cudaStream_t s);
+
+// ---- histogram (histogram.cu) -----------------------------------------------------
+size_t histogram_smem(int jmax, int n_bins);
+cudaError_t launch_pair_histogram(const float4 *X, int64_t npad, const Item *items, int n_items,
+                                  int n_bins, float r_max, int n_pairs, int *hist,
+                                  unsigned long long *dropped, int grid, int jmax, cudaStream_t s);
 
 }  // namespace sas
