@@ -35,8 +35,31 @@ struct PairSetup {
     float rinv;
 };
 
+__device__ __forceinline__ float coef_sr(float mu, unsigned hash)
+{
+    const float c = 2.f - mu;
+    const float e = (2.f - c) - mu;
+    const float ulp = __int_as_float(__float_as_int(fabsf(c)) & 0x7f800000) * 1.1920928955078125e-7f;
+    const float u = (float)(hash >> 8) * 5.9604644775390625e-8f;
+    return (u * ulp < fabsf(e)) ? c + copysignf(ulp, e) : c;
+}
+
+__device__ __forceinline__ unsigned pair_hash(unsigned i, unsigned j)
+{
+    unsigned h = i * 0x9E3779B1u ^ (j * 0x85EBCA77u + 0x165667B1u);
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    h *= 0x297A2D39u;
+    h ^= h >> 15;
+    return h;
+}
+
+// Distance, seeds and the stochastically rounded coefficient 2cos(4t) of one pair
+// (the same construction as the forward kernel's).
 __device__ __forceinline__ void setup_pair(const float4 xi, const float4 xj, float qs_hi, float qs_lo,
-                                           bool zero_start, float dq_hi, float dq_lo, PairSetup &p)
+                                           bool zero_start, float dq_hi, float dq_lo, unsigned hash,
+                                           PairSetup &p)
 {
     const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
     float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -64,7 +87,8 @@ __device__ __forceinline__ void setup_pair(const float4 xi, const float4 xj, flo
     cj[6] = fmaf(-2.f * sj[3], sj[3], 1.f);
     cj[7] = fmaf(cj[6], c1, -sj[6] * s1);
     sj[7] = fmaf(sj[6], c1, cj[6] * s1);
-    p.C4 = make_float2(2.f * cj[4], 2.f * cj[4]);
+    const float c4 = coef_sr(4.f * sj[2] * sj[2], hash);
+    p.C4 = make_float2(c4, c4);
     float S = 0.f, C = 1.f;
     if (!zero_start) {
         const SinCos ph = sincos_f32(fmaf(qs_hi, r, qs_lo * r));
@@ -114,8 +138,10 @@ __global__ void __launch_bounds__(kTile, 2)
         for (int j = 0; j < item.jlen; j += 2) {
             const float4 xa = sj[j], xb = sj[j + 1];
             PairSetup pa, pb;
-            setup_pair(xi, xa, qs_hi, qs_lo, zero_start, qc.dq_hi, qc.dq_lo, pa);
-            setup_pair(xi, xb, qs_hi, qs_lo, zero_start, qc.dq_hi, qc.dq_lo, pb);
+            setup_pair(xi, xa, qs_hi, qs_lo, zero_start, qc.dq_hi, qc.dq_lo,
+                       pair_hash(item.i0 + tid, item.j0 + j), pa);
+            setup_pair(xi, xb, qs_hi, qs_lo, zero_start, qc.dq_hi, qc.dq_lo,
+                       pair_hash(item.i0 + tid, item.j0 + j + 1), pb);
             float2 aa[4], ab[4];
             {
                 const float4 h01 = sh[0], h23 = sh[1], h45 = sh[2], h67 = sh[3];

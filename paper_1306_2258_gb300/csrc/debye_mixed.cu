@@ -19,6 +19,10 @@
 //    add to accumulate them.  A step of Mt instead of t keeps 2cos(Mt) away
 //    from 2 for near pairs (small t), where the rounding of the coefficient
 //    would otherwise make the phase drift.
+//  * The coefficient 2cos(Mt) is rounded stochastically (unbiased, seeded by a
+//    hash of the pair's slots): molecules hold thousands of pairs at the same
+//    distance (bonds), whose identical rounding errors would otherwise drift
+//    in phase together.
 //  * The identity is ill-conditioned wherever Mt is near a multiple of pi
 //    (errors grow like 1/sin(Mt) per step), so the sequences are re-seeded
 //    with exact values every KQ q values: the segment's start phase advances
@@ -66,13 +70,37 @@ __device__ __forceinline__ void multiples(float c1, float s1, Multiples &m)
     m.s[7] = fmaf(m.s[6], c1, m.c[6] * s1);
 }
 
+// 2 cos(M t) = 2 - mu rounded to float32 stochastically: up or down with the probabilities that
+// make its expected value exact, decided by the pair's hash.  Pairs with equal distances (bonds)
+// would otherwise share one rounding error of the coefficient, and their phase drifts would add
+// up coherently instead of averaging out.
+__device__ __forceinline__ float coef_sr(float mu, unsigned hash)
+{
+    const float c = 2.f - mu;                        // nearest float32
+    const float e = (2.f - c) - mu;                  // remaining error: exact value ~ c + e
+    const float ulp = __int_as_float(__float_as_int(fabsf(c)) & 0x7f800000) * 1.1920928955078125e-7f;
+    const float u = (float)(hash >> 8) * 5.9604644775390625e-8f;   // uniform in [0, 1)
+    return (u * ulp < fabsf(e)) ? c + copysignf(ulp, e) : c;
+}
+
+__device__ __forceinline__ unsigned pair_hash(unsigned i, unsigned j)
+{
+    unsigned h = i * 0x9E3779B1u ^ (j * 0x85EBCA77u + 0x165667B1u);
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    h *= 0x297A2D39u;
+    h ^= h >> 15;
+    return h;
+}
+
 // Terms of one pair for the q values of a chunk, added into acc (float2 slot v holds q = 2v, 2v+1).
 //   M  : recurrence step in q values (2 or 4): u_{k+M} = 2 cos(M t) u_k - u_{k-M}
 //   KQ : re-seed interval in q values (0: only at the chunk start), a multiple of 2M
 template <int NB, int M, int KQ>
 __device__ __forceinline__ void pair_terms(const float4 xi, const float4 xj, float w, float qs_hi,
                                            float qs_lo, bool zero_start, float dq_hi, float dq_lo,
-                                           float2 (&acc)[2 * NB])
+                                           unsigned hash, float2 (&acc)[2 * NB])
 {
     static_assert(M == 2 || M == 4, "step must be 2 or 4");
     static_assert(KQ == 0 || KQ % (2 * M) == 0, "re-seed interval must be a multiple of 2M");
@@ -88,7 +116,9 @@ __device__ __forceinline__ void pair_terms(const float4 xi, const float4 xj, flo
     const SinCos b1 = sincos_f32(t);
     Multiples m;
     multiples(b1.c, b1.s, m);
-    const float CM = 2.f * m.c[M];      // 2 cos(M t)
+    // 2 cos(M t) = 2 - 4 sin^2(M t / 2), the small term kept with full relative accuracy
+    const float sh = m.s[M / 2];
+    const float CM = coef_sr(4.f * sh * sh, hash);
     const float2 CM2 = make_float2(CM, CM);
     float S, C;
     if (zero_start) {
@@ -226,7 +256,8 @@ __global__ void __launch_bounds__(kTile, 2)
         for (int j = 0; j < item.jlen; ++j) {
             const float4 xj = sj[j];
             const float w = (j <= jmask) ? 0.f : xi.w * xj.w;
-            pair_terms<NB, M, KQ>(xi, xj, w, qs_hi, qs_lo, zero_start, qc.dq_hi, qc.dq_lo, acc);
+            pair_terms<NB, M, KQ>(xi, xj, w, qs_hi, qs_lo, zero_start, qc.dq_hi, qc.dq_lo,
+                                  pair_hash(item.i0 + tid, item.j0 + j), acc);
         }
         flush_warp<NB>(acc, red[warp], lane);
         __syncthreads();

@@ -127,8 +127,8 @@ struct sas_ctx {
     QChunks qc{};
     int sms = 1;
     int64_t opt_jmax = 0;
-    int opt_reseed = 32;
-    int opt_step = 4;
+    int opt_reseed = 0;
+    int opt_step = 2;
     int opt_grid = 0;
     int64_t opt_timeout_ms = 600000;
     DevBuf coef_d, F, meta, blockcounts, blockoffs, centroid, X, slot_of, items, group_items,
