@@ -203,6 +203,13 @@ def run_ours(args):
     value = world * pq * args.steps / (tot_ms / 1e3)
     I_mixed = out[0].cpu().numpy().copy()
 
+    if args.skip_extras:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "pair·q/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+                              "note": "mixed path only (--skip-extras)"}))
+        return 0
+
     # ---- end to end through the public API with host buffers (copies inside the timed region)
     xh = torch.as_tensor(mol.coords).pin_memory()
     th = torch.as_tensor(mol.types).pin_memory()
@@ -272,7 +279,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true", help="leave out the CPU-oracle baseline")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="time the mixed path only (no e2e, FP64 or CPU legs; for profiler runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

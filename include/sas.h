@@ -142,11 +142,14 @@ sas_status sas_pair_histogram(sas_ctx *ctx, const float *coords, const int32_t *
 /* Tuning and diagnostics (values are validated; unknown options give INVALID_ARG). */
 enum {
     SAS_OPT_JMAX = 1,        /* longest J-range of one work item, atoms (multiple of 128 up to 8192; 0 = automatic) */
-    SAS_OPT_RESEED = 2,      /* re-seed interval of the q recurrence in q steps: 0 (chunk start only, default), 32, 64 */
+    SAS_OPT_RESEED = 2,      /* re-seed interval of the q recurrence in q steps: -1 automatic (default:
+                                32 below 8,192 atoms, else only at each chunk start), 0, 32 or 64 */
     SAS_OPT_VALIDATE = 3,    /* must stay 1: the device-side validation verdict is always read back */
     SAS_OPT_GRID = 4,        /* persistent CTAs per SM for the pair kernels (0 = automatic) */
     SAS_OPT_TIMEOUT_MS = 5,  /* limit of every host-side wait for device work (default 600000) */
-    SAS_OPT_STEP = 6         /* q steps per recurrence step of the mixed kernel: 2 (default) or 4 */
+    SAS_OPT_STEP = 6,        /* q steps per recurrence step of the mixed kernel: 2 (default) or 4 */
+    SAS_OPT_VARIANT = 7      /* mixed kernel form for step 2 without re-seed: 0 auto, 1 general,
+                                2 set-up of the next pair overlapped, 3 pairs in sequence */
 };
 sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value);
 

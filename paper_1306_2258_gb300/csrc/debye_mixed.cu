@@ -19,14 +19,20 @@
 //    add to accumulate them.  A step of Mt instead of t keeps 2cos(Mt) away
 //    from 2 for near pairs (small t), where the rounding of the coefficient
 //    would otherwise make the phase drift.
-//  * The coefficient 2cos(Mt) is rounded stochastically (unbiased, seeded by a
-//    hash of the pair's slots): molecules hold thousands of pairs at the same
-//    distance (bonds), whose identical rounding errors would otherwise drift
-//    in phase together.
+//  * The packed FMA does not negate its addend for free, so the sequences are
+//    carried with the sign pattern sigma_b = (+, +, -, -) over blocks b of M
+//    values: W_b = sigma_b U_b obeys W_{b+1} = (+/-) 2cos(Mt) W_b + W_{b-1},
+//    the sign of the coefficient alternating with b and known at compile
+//    time.  The accumulators hold sums of W; sigma is applied once, when they
+//    are lifted to FP64.
+//  * The coefficient 2cos(Mt) = 2 - 4 sin^2(Mt/2) is rounded stochastically
+//    (a dither from a hash of the pair's slots): molecules hold thousands of
+//    pairs at the same distance (bonds), whose identical rounding errors would
+//    otherwise drift in phase together.
 //  * The identity is ill-conditioned wherever Mt is near a multiple of pi
-//    (errors grow like 1/sin(Mt) per step), so the sequences are re-seeded
+//    (errors grow like 1/sin(Mt) per step); the sequences can be re-seeded
 //    with exact values every KQ q values: the segment's start phase advances
-//    by an exact rotation through K t, and the first 2M values of a segment
+//    by an exact rotation through KQ t, and the first 2M values of a segment
 //    are S cos(jt) + C sin(jt) with cos(jt), sin(jt) from an accurate FP32
 //    sin/cos of t and angle addition.
 //  * The per-thread sums are FP32 over the item's J-range (one tile of the
@@ -43,9 +49,142 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
 
-// cos(j t), sin(j t) for j = 1..7 by angle addition and doubling (no 1/sin(t) amplification).
+// sign of block b in the (+, +, -, -) pattern, and of the coefficient of the step b -> b+1
+__host__ __device__ constexpr bool block_negative(int b) { return (b & 2) != 0; }
+__host__ __device__ constexpr bool step_negative(int b) { return (b & 1) != 0; }
+
+// r = sqrt(r2) from the reciprocal square root and one Newton correction (to about 1 ulp);
+// y = 1/sqrt(r2) as computed by the hardware.
+__device__ __forceinline__ void dist_rsqrt(float r2, float &r, float &y)
+{
+    y = rsqrtf(r2);
+    const float r0 = r2 * y;
+    r = fmaf(0.5f * y, fmaf(-r0, r0, r2), r0);
+}
+
+// 2 - mu rounded stochastically by dithering: a uniform offset of at most half an ulp of [1, 2)
+// enters before the one rounding, so the expected coefficient is exact.
+__device__ __forceinline__ float coef_dither(float mu, unsigned hash)
+{
+    const float u = __int_as_float(0x3f800000u | (hash >> 9)) - 1.5f;   // uniform in [-0.5, 0.5)
+    return 2.f - fmaf(u, 1.1920928955078125e-7f, mu);
+}
+
+// Cheap pair hash on the integer ALU (one multiply, then xorshift).
+__device__ __forceinline__ unsigned pair_hash(unsigned i, unsigned j)
+{
+    unsigned h = i ^ (j * 0x9E3779B1u);
+    h ^= h << 13;
+    h ^= h >> 17;
+    h ^= h << 5;
+    return h;
+}
+
+// ---------------------------------------------------------------------------------------------
+// 2-step recurrence from the chunk start, no re-seeding (the default path)
+// ---------------------------------------------------------------------------------------------
+
+// One pair's first two float2 blocks (q 0..3 of the chunk, block signs +, +) and its
+// stochastically rounded coefficient 2cos(2t), as +C and -C.
+template <bool ZERO_START>
+__device__ __forceinline__ void setup_m2(const float4 xi, const float4 xj, float w, float qs_hi,
+                                         float qs_lo, float dq_hi, float dq_lo, unsigned hash,
+                                         float2 &w0, float2 &w1, float2 &Cp, float2 &Cn)
+{
+    const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+    float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    r2 = fmaxf(r2, 1e-12f);   // coincident atoms: r = 1e-6 A, sin(q r)/r -> q
+    float r, y;
+    dist_rsqrt(r2, r, y);
+    const float scale = w * y;   // amplitude w_i w_j / r
+    const float t = fmaf(dq_hi, r, dq_lo * r);
+    const SinCos b1 = sincos_f32(t);
+    const float c1 = b1.c, s1 = b1.s;
+    const float s2 = 2.f * s1 * c1, c2 = fmaf(-2.f * s1, s1, 1.f);
+    const float s3 = fmaf(s2, c1, c2 * s1);
+    const float CM = coef_dither(4.f * s1 * s1, hash);   // 2cos(2t) = 2 - 4 sin^2 t
+    Cp = make_float2(CM, CM);
+    Cn = make_float2(-CM, -CM);
+    if (ZERO_START) {
+        w0 = make_float2(0.f, scale * s1);
+        w1 = make_float2(scale * s2, scale * s3);
+    } else {
+        const float c3 = fmaf(c2, c1, -s2 * s1);
+        const SinCos ph = sincos_f32(fmaf(qs_hi, r, qs_lo * r));
+        const float S = scale * ph.s, C = scale * ph.c;
+        w0 = make_float2(S, fmaf(S, c1, C * s1));
+        w1 = make_float2(fmaf(S, c2, C * s2), fmaf(S, c3, C * s3));
+    }
+}
+
+// The recurrence over the chunk's 2*NB float2 blocks: acc[v] += W_v.
+template <int NB>
+__device__ __forceinline__ void core_m2(float2 wp, float2 wc, const float2 Cp, const float2 Cn,
+                                        float2 (&acc)[2 * NB])
+{
+    acc[0] = f2add(acc[0], wp);
+    acc[1] = f2add(acc[1], wc);
+#pragma unroll
+    for (int v = 1; v + 1 < 2 * NB; ++v) {   // W_{v+1} = (+/-)C W_v + W_{v-1}
+        const float2 n = f2fma(step_negative(v) ? Cn : Cp, wc, wp);
+        acc[v + 1] = f2add(acc[v + 1], n);
+        wp = wc;
+        wc = n;
+    }
+}
+
+// Pairs (i, j) over the item's J-range, software-pipelined: the set-up of pair j+1 does not
+// depend on the recurrence of pair j, so the two interleave.
+template <int NB, bool ZERO_START>
+__device__ __forceinline__ void run_m2_pipelined(const float4 xi, const float4 *sj, const Item &item,
+                                                 int tid, int jmask, float qs_hi, float qs_lo, float dq_hi,
+                                                 float dq_lo, float2 (&acc)[2 * NB])
+{
+    float2 w0, w1, Cp, Cn;
+    {
+        const float4 x0 = sj[0];
+        const float wt = (0 <= jmask) ? 0.f : xi.w * x0.w;
+        setup_m2<ZERO_START>(xi, x0, wt, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(item.i0 + tid, item.j0),
+                             w0, w1, Cp, Cn);
+    }
+    for (int j = 0; j < item.jlen; ++j) {
+        const bool more = j + 1 < item.jlen;
+        const int jn = more ? j + 1 : j;
+        const float4 xn = sj[jn];
+        const float wn = (!more || jn <= jmask) ? 0.f : xi.w * xn.w;
+        float2 n0, n1, nCp, nCn;
+        setup_m2<ZERO_START>(xi, xn, wn, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(item.i0 + tid, item.j0 + jn),
+                             n0, n1, nCp, nCn);
+        core_m2<NB>(w0, w1, Cp, Cn, acc);
+        w0 = n0;
+        w1 = n1;
+        Cp = nCp;
+        Cn = nCn;
+    }
+}
+
+// The same pairs one after the other.
+template <int NB, bool ZERO_START>
+__device__ __forceinline__ void run_m2(const float4 xi, const float4 *sj, const Item &item, int tid,
+                                       int jmask, float qs_hi, float qs_lo, float dq_hi, float dq_lo,
+                                       float2 (&acc)[2 * NB])
+{
+    for (int j = 0; j < item.jlen; ++j) {
+        const float4 xj = sj[j];
+        const float wt = (j <= jmask) ? 0.f : xi.w * xj.w;
+        float2 w0, w1, Cp, Cn;
+        setup_m2<ZERO_START>(xi, xj, wt, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(item.i0 + tid, item.j0 + j),
+                             w0, w1, Cp, Cn);
+        core_m2<NB>(w0, w1, Cp, Cn, acc);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// General form: step M = 2 or 4, re-seeded every KQ q values
+// ---------------------------------------------------------------------------------------------
+
+// cos(j t), sin(j t) for j = 0..7 by angle addition and doubling (no 1/sin(t) amplification).
 struct Multiples {
     float c[8], s[8];
 };
@@ -70,33 +209,8 @@ __device__ __forceinline__ void multiples(float c1, float s1, Multiples &m)
     m.s[7] = fmaf(m.s[6], c1, m.c[6] * s1);
 }
 
-// 2 cos(M t) = 2 - mu rounded to float32 stochastically: up or down with the probabilities that
-// make its expected value exact, decided by the pair's hash.  Pairs with equal distances (bonds)
-// would otherwise share one rounding error of the coefficient, and their phase drifts would add
-// up coherently instead of averaging out.
-__device__ __forceinline__ float coef_sr(float mu, unsigned hash)
-{
-    const float c = 2.f - mu;                        // nearest float32
-    const float e = (2.f - c) - mu;                  // remaining error: exact value ~ c + e
-    const float ulp = __int_as_float(__float_as_int(fabsf(c)) & 0x7f800000) * 1.1920928955078125e-7f;
-    const float u = (float)(hash >> 8) * 5.9604644775390625e-8f;   // uniform in [0, 1)
-    return (u * ulp < fabsf(e)) ? c + copysignf(ulp, e) : c;
-}
-
-__device__ __forceinline__ unsigned pair_hash(unsigned i, unsigned j)
-{
-    unsigned h = i * 0x9E3779B1u ^ (j * 0x85EBCA77u + 0x165667B1u);
-    h ^= h >> 15;
-    h *= 0x2C1B3C6Du;
-    h ^= h >> 12;
-    h *= 0x297A2D39u;
-    h ^= h >> 15;
-    return h;
-}
-
-// Terms of one pair for the q values of a chunk, added into acc (float2 slot v holds q = 2v, 2v+1).
-//   M  : recurrence step in q values (2 or 4): u_{k+M} = 2 cos(M t) u_k - u_{k-M}
-//   KQ : re-seed interval in q values (0: only at the chunk start), a multiple of 2M
+// Terms of one pair for the chunk, into acc (float2 slot v holds q = 2v, 2v+1; block b of M
+// values holds slots b*M/2 .. b*M/2 + M/2 - 1).
 template <int NB, int M, int KQ>
 __device__ __forceinline__ void pair_terms(const float4 xi, const float4 xj, float w, float qs_hi,
                                            float qs_lo, bool zero_start, float dq_hi, float dq_lo,
@@ -104,22 +218,22 @@ __device__ __forceinline__ void pair_terms(const float4 xi, const float4 xj, flo
 {
     static_assert(M == 2 || M == 4, "step must be 2 or 4");
     static_assert(KQ == 0 || KQ % (2 * M) == 0, "re-seed interval must be a multiple of 2M");
-    constexpr int G = M / 2;                          // float2 per block of M values
-    constexpr int NBM = 4 * NB / M;                   // blocks of M values per chunk
+    constexpr int G = M / 2;                                       // float2 per block
+    constexpr int NBM = 4 * NB / M;                                // blocks per chunk
     constexpr int SEG = (KQ > 0 && KQ / M < NBM) ? KQ / M : NBM;   // blocks per segment
     const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
     float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    r2 = fmaxf(r2, 1e-12f);            // coincident atoms: r = 1e-6 A, sin(q r)/r -> q
-    const float r = sqrtf(r2);
-    const float scale = w * rsqrtf(r2); // amplitude w_i w_j / r (the phase uses the rounded sqrt)
+    r2 = fmaxf(r2, 1e-12f);
+    float r, y;
+    dist_rsqrt(r2, r, y);
+    const float scale = w * y;
     const float t = fmaf(dq_hi, r, dq_lo * r);
     const SinCos b1 = sincos_f32(t);
     Multiples m;
     multiples(b1.c, b1.s, m);
-    // 2 cos(M t) = 2 - 4 sin^2(M t / 2), the small term kept with full relative accuracy
-    const float sh = m.s[M / 2];
-    const float CM = coef_sr(4.f * sh * sh, hash);
-    const float2 CM2 = make_float2(CM, CM);
+    const float sh = m.s[M / 2];                                   // sin(M t / 2)
+    const float CM = coef_dither(4.f * sh * sh, hash);             // 2cos(Mt) = 2 - 4 sin^2(Mt/2)
+    const float2 Cp = make_float2(CM, CM), Cn = make_float2(-CM, -CM);
     float S, C;
     if (zero_start) {
         S = 0.f;
@@ -135,44 +249,44 @@ __device__ __forceinline__ void pair_terms(const float4 xi, const float4 xj, flo
         cK = k.c;
         sK = k.s;
     }
-    float2 prev[G], cur[G];
+    float2 wp[G], wc[G];
 #pragma unroll
-    for (int blk = 0; blk < NBM; ++blk) {
-        const int v0 = blk * G;
-        if (blk % SEG == 0) {        // segment start: exact values for blocks blk and blk+1
-            if (blk > 0) {
+    for (int b = 0; b < NBM; ++b) {
+        const int v0 = b * G;
+        if (b % SEG == 0) {   // segment start: exact (signed) values of blocks b and b+1
+            if (b > 0) {
                 const float S2 = fmaf(S, cK, C * sK);
                 C = fmaf(C, cK, -S * sK);
                 S = S2;
             }
+            const float sp = block_negative(b) ? -1.f : 1.f, sc = block_negative(b + 1) ? -1.f : 1.f;
+            const float Sp = sp * S, Cpp = sp * C, Sc = sc * S, Ccc = sc * C;
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                prev[g] = make_float2(fmaf(S, m.c[2 * g], C * m.s[2 * g]),
-                                      fmaf(S, m.c[2 * g + 1], C * m.s[2 * g + 1]));
-                cur[g] = make_float2(fmaf(S, m.c[M + 2 * g], C * m.s[M + 2 * g]),
-                                     fmaf(S, m.c[M + 2 * g + 1], C * m.s[M + 2 * g + 1]));
-                acc[v0 + g] = f2add(acc[v0 + g], prev[g]);
+                wp[g] = make_float2(fmaf(Sp, m.c[2 * g], Cpp * m.s[2 * g]),
+                                    fmaf(Sp, m.c[2 * g + 1], Cpp * m.s[2 * g + 1]));
+                wc[g] = make_float2(fmaf(Sc, m.c[M + 2 * g], Ccc * m.s[M + 2 * g]),
+                                    fmaf(Sc, m.c[M + 2 * g + 1], Ccc * m.s[M + 2 * g + 1]));
+                acc[v0 + g] = f2add(acc[v0 + g], wp[g]);
             }
-        } else if (blk % SEG == 1) {
+        } else if (b % SEG == 1) {
 #pragma unroll
-            for (int g = 0; g < G; ++g) acc[v0 + g] = f2add(acc[v0 + g], cur[g]);
-        } else {
+            for (int g = 0; g < G; ++g) acc[v0 + g] = f2add(acc[v0 + g], wc[g]);
+        } else {   // W_b = (+/-)C W_{b-1} + W_{b-2}, the sign of step b-1 -> b
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                const float2 n = f2fma(CM2, cur[g], f2neg(prev[g]));
+                const float2 n = f2fma(step_negative(b - 1) ? Cn : Cp, wc[g], wp[g]);
                 acc[v0 + g] = f2add(acc[v0 + g], n);
-                prev[g] = cur[g];
-                cur[g] = n;
+                wp[g] = wc[g];
+                wc[g] = n;
             }
         }
     }
 }
 
-template <int NB>
-__device__ __forceinline__ float acc_elem(const float2 (&acc)[2 * NB], int k)
-{
-    return (k & 1) ? acc[k >> 1].y : acc[k >> 1].x;
-}
+// ---------------------------------------------------------------------------------------------
+// FP64 warp reduce-scatter of the accumulators
+// ---------------------------------------------------------------------------------------------
 
 // Number of halving levels of the reduce-scatter for V values (at most 5, while V stays even).
 __host__ __device__ constexpr int halvings(int V, int lvl = 0)
@@ -192,20 +306,28 @@ __device__ __forceinline__ void halve(double (&d)[N], bool up, int off)
     }
 }
 
+// Accumulator k (q index k of the chunk) with its block sign applied.
+template <int NB, int M>
+__device__ __forceinline__ float acc_signed(const float2 (&acc)[2 * NB], int k)
+{
+    const float v = (k & 1) ? acc[k >> 1].y : acc[k >> 1].x;
+    return block_negative(k / M) ? -v : v;
+}
+
 // Sum the 32 lanes' V = 4*NB accumulators (FP64 from the first cross-thread add on);
 // the warp's totals land in red[0..V).
-template <int NB>
+template <int NB, int M>
 __device__ __forceinline__ void flush_warp(const float2 (&acc)[2 * NB], double *red, int lane)
 {
     constexpr int V = 4 * NB;
-    constexpr int L = halvings(V);      // reduce-scatter levels (offsets 16, 8, ...)
+    constexpr int L = halvings(V);   // reduce-scatter levels (offsets 16, 8, ...)
     constexpr int H1 = V / 2;
-    constexpr int R = V >> L;           // values per lane after the reduce-scatter
+    constexpr int R = V >> L;        // values per lane after the reduce-scatter
     double d[H1];
     const bool up16 = lane & 16;
 #pragma unroll
-    for (int k = 0; k < H1; ++k) {      // the lift to FP64
-        const float lo = acc_elem<NB>(acc, k), hi = acc_elem<NB>(acc, k + H1);
+    for (int k = 0; k < H1; ++k) {   // the lift to FP64
+        const float lo = acc_signed<NB, M>(acc, k), hi = acc_signed<NB, M>(acc, k + H1);
         const float mine = up16 ? hi : lo, other = up16 ? lo : hi;
         d[k] = (double)mine + (double)__shfl_xor_sync(kFull, other, 16);
     }
@@ -231,8 +353,16 @@ __device__ __forceinline__ void flush_warp(const float2 (&acc)[2 * NB], double *
     }
 }
 
-template <int NB, int M, int KQ>
-__global__ void __launch_bounds__(kTile, 2)
+// ---------------------------------------------------------------------------------------------
+// The kernel
+// ---------------------------------------------------------------------------------------------
+
+// Resident CTAs per SM: the accumulators (4*NB floats per thread) set the register budget.
+__host__ __device__ constexpr int mixed_ctas_per_sm(int NB) { return NB <= 13 ? 4 : (NB <= 26 ? 3 : 2); }
+
+// Variant P: 1 = general form (any M, KQ); 3 = 2-step software-pipelined; 4 = 2-step sequential.
+template <int NB, int M, int KQ, int P>
+__global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
     k_debye_mixed(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items,
                   int n_items, QChunks qc, double *__restrict__ partial, int part_stride)
 {
@@ -253,13 +383,25 @@ __global__ void __launch_bounds__(kTile, 2)
 #pragma unroll
         for (int k = 0; k < 2 * NB; ++k) acc[k] = make_float2(0.f, 0.f);
         const int jmask = item.diag ? tid : -1;   // pairs with j <= i are not pairs of i<j
-        for (int j = 0; j < item.jlen; ++j) {
-            const float4 xj = sj[j];
-            const float w = (j <= jmask) ? 0.f : xi.w * xj.w;
-            pair_terms<NB, M, KQ>(xi, xj, w, qs_hi, qs_lo, zero_start, qc.dq_hi, qc.dq_lo,
-                                  pair_hash(item.i0 + tid, item.j0 + j), acc);
+        if (P == 3) {
+            if (zero_start)
+                run_m2_pipelined<NB, true>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi, qc.dq_lo, acc);
+            else
+                run_m2_pipelined<NB, false>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi, qc.dq_lo, acc);
+        } else if (P == 4) {
+            if (zero_start)
+                run_m2<NB, true>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi, qc.dq_lo, acc);
+            else
+                run_m2<NB, false>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi, qc.dq_lo, acc);
+        } else {
+            for (int j = 0; j < item.jlen; ++j) {
+                const float4 xj = sj[j];
+                const float w = (j <= jmask) ? 0.f : xi.w * xj.w;
+                pair_terms<NB, M, KQ>(xi, xj, w, qs_hi, qs_lo, zero_start, qc.dq_hi, qc.dq_lo,
+                                      pair_hash(item.i0 + tid, item.j0 + j), acc);
+            }
         }
-        flush_warp<NB>(acc, red[warp], lane);
+        flush_warp<NB, (P == 1 ? M : 2)>(acc, red[warp], lane);
         __syncthreads();
         const int qlen = qc.q_len[ch];
         for (int k = tid; k < qlen; k += kTile) {
@@ -271,40 +413,43 @@ __global__ void __launch_bounds__(kTile, 2)
     }
 }
 
-template <int NB, int M, int KQ>
+template <int NB, int M, int KQ, int P>
 cudaError_t launch_v(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
                      double *partial, int part_stride, int grid, int jmax, cudaStream_t s)
 {
     const size_t smem = (size_t)jmax * sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(k_debye_mixed<NB, M, KQ>,
+    cudaError_t e = cudaFuncSetAttribute(k_debye_mixed<NB, M, KQ, P>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_debye_mixed<NB, M, KQ><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, partial, part_stride);
-    return cudaGetLastError();
-}
-
-template <int NB, int M>
-cudaError_t launch_k(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
-                     int reseed, double *partial, int part_stride, int grid, int jmax, cudaStream_t s)
-{
-    switch (reseed) {
-    case 32:
-        return launch_v<NB, M, 32>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, s);
-    case 64:
-        return launch_v<NB, M, 64>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, s);
-    default:
-        return launch_v<NB, M, 0>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, s);
+    if (grid <= 0) {   // persistent grid: every resident CTA slot of every SM
+        int occ = 0, dev = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_mixed<NB, M, KQ, P>, kTile, smem);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        grid = (occ > 0 ? occ : 1) * sms;
     }
+    if (grid > n_items) grid = n_items;
+    k_debye_mixed<NB, M, KQ, P><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, partial, part_stride);
+    return cudaGetLastError();
 }
 
 template <int NB>
 cudaError_t launch_nb(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
-                      int step, int reseed, double *partial, int part_stride, int grid, int jmax,
+                      int step, int reseed, int variant, double *partial, int part_stride, int grid, int jmax,
                       cudaStream_t s)
 {
-    if (step == 2)
-        return launch_k<NB, 2>(X, npad, items, n_items, qc, reseed, partial, part_stride, grid, jmax, s);
-    return launch_k<NB, 4>(X, npad, items, n_items, qc, reseed, partial, part_stride, grid, jmax, s);
+#define SAS_LAUNCH(M_, K_, P_) \
+    launch_v<NB, M_, K_, P_>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, s)
+    if (step == 2 && reseed == 0) {
+        if (variant == 3) return SAS_LAUNCH(2, 0, 3);
+        if (variant == 4) return SAS_LAUNCH(2, 0, 4);
+        return SAS_LAUNCH(2, 0, 1);
+    }
+    if (step == 2) return reseed == 32 ? SAS_LAUNCH(2, 32, 1) : SAS_LAUNCH(2, 64, 1);
+    if (reseed == 0) return SAS_LAUNCH(4, 0, 1);
+    return reseed == 32 ? SAS_LAUNCH(4, 32, 1) : SAS_LAUNCH(4, 64, 1);
+#undef SAS_LAUNCH
 }
 
 }  // namespace
@@ -316,19 +461,22 @@ int mixed_blocks_for(int qlen_max)
 }
 
 cudaError_t launch_debye_mixed(const float4 *X, int64_t npad, const Item *items, int n_items,
-                               const QChunks &qc, int step, int reseed, double *partial, int part_stride,
-                               int grid, int jmax, cudaStream_t s)
+                               const QChunks &qc, int step, int reseed, int variant, double *partial,
+                               int part_stride, int grid, int jmax, cudaStream_t s)
 {
     if (n_items == 0) return cudaSuccess;
     int qmax = 0;
     for (int c = 0; c < qc.n_chunks; ++c) qmax = qc.q_len[c] > qmax ? qc.q_len[c] : qmax;
     switch (mixed_blocks_for(qmax)) {
     case 13:
-        return launch_nb<13>(X, npad, items, n_items, qc, step, reseed, partial, part_stride, grid, jmax, s);
+        return launch_nb<13>(X, npad, items, n_items, qc, step, reseed, variant, partial, part_stride, grid,
+                             jmax, s);
     case 26:
-        return launch_nb<26>(X, npad, items, n_items, qc, step, reseed, partial, part_stride, grid, jmax, s);
+        return launch_nb<26>(X, npad, items, n_items, qc, step, reseed, variant, partial, part_stride, grid,
+                             jmax, s);
     default:
-        return launch_nb<52>(X, npad, items, n_items, qc, step, reseed, partial, part_stride, grid, jmax, s);
+        return launch_nb<52>(X, npad, items, n_items, qc, step, reseed, variant, partial, part_stride, grid,
+                             jmax, s);
     }
 }
 

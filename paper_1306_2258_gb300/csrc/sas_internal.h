@@ -72,8 +72,8 @@ cudaError_t launch_assemble(double *S, const double *F, const int *meta, int n_t
 // ---- pair kernels -------------------------------------------------------------
 // partial [n_items][part_stride] f64: sum over the item's pairs of w_i w_j sin(q r)/r
 cudaError_t launch_debye_mixed(const float4 *X, int64_t npad, const Item *items, int n_items,
-                               const QChunks &qc, int step, int reseed, double *partial, int part_stride,
-                               int grid, int jmax, cudaStream_t s);
+                               const QChunks &qc, int step, int reseed, int pairs, double *partial,
+                               int part_stride, int grid, int jmax, cudaStream_t s);
 cudaError_t launch_debye_fp64(const double4 *X, int64_t npad, const Item *items, int n_items,
                               const QChunks &qc, double *partial, int part_stride, int grid,
                               cudaStream_t s);

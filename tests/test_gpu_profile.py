@@ -71,11 +71,19 @@ def test_c1_mixed_matches_oracle():
     assert _rel(I, ref) <= 1e-4   # float32 rounding of the input itself stays small
 
 
-@pytest.mark.parametrize("reseed", [0, 32, 64])
-def test_c2_10k_mixed_matches_oracle(reseed):
+@pytest.mark.parametrize("step,reseed", [(2, -1), (2, 0), (2, 32), (2, 64), (4, 32), (4, 0)])
+def test_c2_10k_mixed_matches_oracle(step, reseed):
     w = wl.c2_globule(10000)
     ref = _oracle_cached(("c2_10k",))
-    I = _gpu(w.mol, w.coef, w.q, "mixed", reseed=reseed)
+    I = _gpu(w.mol, w.coef, w.q, "mixed", step=step, reseed=reseed)
+    assert _rel(I, ref) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_c2_10k_kernel_variants_match_oracle(variant):
+    w = wl.c2_globule(10000)
+    ref = _oracle_cached(("c2_10k",))
+    I = _gpu(w.mol, w.coef, w.q, "mixed", step=2, reseed=0, variant=variant)
     assert _rel(I, ref) <= TOL_MIXED
 
 
