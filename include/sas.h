@@ -160,6 +160,29 @@ sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value);
  */
 sas_status sas_last_stats(sas_ctx *ctx, int64_t *stats_out, int n);
 
+/*
+ * Allocation-free variant of sas_profile for callers that must not allocate GPU memory at the
+ * point of use (a memory budget reserved up front, an allocator that must not be re-entered, or
+ * a loop where cudaMalloc/cudaFree, which synchronize the device, are not allowed).  The paper
+ * has no counterpart; the arithmetic is that of sas_profile on a SAS_MIXED context.
+ *   coords [n_atoms][3] float, types [n_atoms] int32, I_out [n_q] double: device memory only.
+ *   ff_coef [n_types][9] host memory, as in sas_create.  q_k = q0 + k*dq, k < n_q.
+ * No context, no cudaMalloc/cudaFree, no host heap: all scratch lives in one fixed __device__
+ * array of SAS_STATIC_SCRATCH_BYTES that every GPU loading the library holds until exit.
+ * Limits: n_atoms <= SAS_STATIC_MAX_ATOMS, n_q <= 208, n_types <= SAS_MAX_TYPES; larger sizes
+ * give SAS_ERR_UNSUPPORTED; device inputs on the host give SAS_ERR_INVALID_ARG.  The call
+ * returns when I_out is written (it synchronizes on `stream`).  Errors are reported by the
+ * status code only (sas_last_error is not updated).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls on a device share the array, so
+ * calls that overlap on the GPU (other streams or host threads) race: serialize them.
+ */
+#define SAS_STATIC_MAX_ATOMS 16384
+#define SAS_STATIC_SCRATCH_BYTES (7 << 20)
+sas_status sas_profile_static(const float *coords, const int32_t *types, int64_t n_atoms, int n_types,
+                              const double *ff_coef, double q0, double dq, int n_q, double *I_out,
+                              void *stream);
+
 /* Thread-local message of the calling thread's last failure ("" if none). */
 const char *sas_last_error(void);
 

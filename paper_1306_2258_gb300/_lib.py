@@ -26,7 +26,7 @@ SAS_MAX_TYPES, SAS_MAX_Q = 16, 1664
 EXPORTS = (
     "sas_create", "sas_destroy", "sas_profile", "sas_profile_batch", "sas_profile_grad",
     "sas_profile_vjp", "sas_partials", "sas_pair_histogram", "sas_set_option", "sas_last_stats",
-    "sas_last_error", "sas_version",
+    "sas_last_error", "sas_version", "sas_profile_static",
 )
 
 
@@ -62,6 +62,8 @@ def load():
                 "sas_pair_histogram": [_vp, _vp, _vp, _i64, _i64, _int, ctypes.c_float, _vp, _vp, _vp],
                 "sas_set_option": [_vp, _int, _i64],
                 "sas_last_stats": [_vp, _vp, _int],
+                "sas_profile_static": [_vp, _vp, _i64, _int, _vp, ctypes.c_double, ctypes.c_double, _int,
+                                       _vp, _vp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -165,6 +167,15 @@ def sas_last_stats(ctx):
     out = np.zeros(6, dtype=np.int64)
     check(load().sas_last_stats(ctx, out.ctypes.data, 6))
     return out
+
+
+def sas_profile_static(coords, types, n_atoms, n_types, ff_coef, q0, dq, n_q, I_out, stream=None):
+    """Allocation-free profile (device coords/types/I_out, host coefficients); status codes only."""
+    c = np.ascontiguousarray(ff_coef, dtype=np.float64)
+    st = load().sas_profile_static(ptr(coords), ptr(types), int(n_atoms), int(n_types), c.ctypes.data,
+                                   float(q0), float(dq), int(n_q), ptr(I_out), stream_handle(stream))
+    if st != SAS_OK:
+        raise SasError(st, "sas_profile_static failed")
 
 
 def sas_last_error() -> str:
