@@ -183,6 +183,46 @@ sas_status sas_profile_static(const float *coords, const int32_t *types, int64_t
                               const double *ff_coef, double q0, double dq, int n_q, double *I_out,
                               void *stream);
 
+/* ---- learned surrogate -------------------------------------------------------------------
+ * Not part of the paper's method: a multilayer perceptron that maps per-type-pair distance
+ * histograms (sas_pair_histogram) to a standardized log I(q), used to rank conformers before the
+ * exact Debye kernel re-scores the best ones.
+ *   y = W3 GELU(W2 GELU(W1 x + b1) + b2) + b3,  GELU(z) = z (1 + erf(z / sqrt 2)) / 2,
+ *   loss = mean over batch and outputs of (y - t)^2, Adam (beta = 0.9, 0.999, eps = 1e-8).
+ * FP32 master weights; every GEMM operand is rounded to bfloat16 and accumulated in FP32 on the
+ * tensor cores.  Parameters travel in the packed order W1 [h][n_in], b1 [h], W2 [h][h], b2 [h],
+ * W3 [n_out][h], b3 [n_out] (float32, sas_mlp_param_count values).  Inputs x [batch][n_in] and
+ * targets t [batch][n_out] are float32, host or device; outputs likewise.
+ */
+typedef struct sas_mlp sas_mlp;
+
+/* n_in and n_hidden: positive multiples of 16; max_batch <= 65536.  Parameters start at zero. */
+sas_status sas_mlp_create(int n_in, int n_hidden, int n_out, int max_batch, sas_mlp **out);
+sas_status sas_mlp_destroy(sas_mlp *mlp);
+int64_t sas_mlp_param_count(const sas_mlp *mlp);
+
+/* Load / read the full training state (host buffers of sas_mlp_param_count floats each; adam_m and
+ * adam_v may be NULL: zero on load, skipped on read).  For checkpoints and deterministic resume. */
+sas_status sas_mlp_set_state(sas_mlp *mlp, const float *params, const float *adam_m, const float *adam_v,
+                             int64_t step);
+sas_status sas_mlp_get_state(sas_mlp *mlp, float *params, float *adam_m, float *adam_v, int64_t *step);
+
+/* y [batch][n_out] = network(x). */
+sas_status sas_mlp_forward(sas_mlp *mlp, const float *x, int batch, float *y, void *stream);
+
+/* One Adam step on the MSE loss of (x, t); the batch loss (before the step) goes to loss_out if given. */
+sas_status sas_mlp_train_step(sas_mlp *mlp, const float *x, const float *t, int batch, float lr, float *loss_out,
+                              void *stream);
+
+/* Loss and gradients (packed order, host) of (x, t) without updating anything. */
+sas_status sas_mlp_grads(sas_mlp *mlp, const float *x, const float *t, int batch, float *grads, float *loss_out,
+                         void *stream);
+
+/* C[M][N] = A[M][K] B[N][K]^T (+ bias[N]): bfloat16 A and B (device, K contiguous, 16-byte aligned,
+ * K % 16 == 0, lda and ldb multiples of 8), float32 C (device), FP32 accumulation. */
+sas_status sas_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
+                         float *C, int ldc, void *stream);
+
 /* Thread-local message of the calling thread's last failure ("" if none). */
 const char *sas_last_error(void);
 

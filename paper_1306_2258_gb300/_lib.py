@@ -26,7 +26,9 @@ SAS_MAX_TYPES, SAS_MAX_Q = 16, 1664
 EXPORTS = (
     "sas_create", "sas_destroy", "sas_profile", "sas_profile_batch", "sas_profile_grad",
     "sas_profile_vjp", "sas_partials", "sas_pair_histogram", "sas_set_option", "sas_last_stats",
-    "sas_last_error", "sas_version", "sas_profile_static",
+    "sas_last_error", "sas_version", "sas_profile_static", "sas_mlp_create", "sas_mlp_destroy",
+    "sas_mlp_param_count", "sas_mlp_set_state", "sas_mlp_get_state", "sas_mlp_forward", "sas_mlp_train_step",
+    "sas_mlp_grads", "sas_gemm_bf16",
 )
 
 
@@ -64,6 +66,14 @@ def load():
                 "sas_last_stats": [_vp, _vp, _int],
                 "sas_profile_static": [_vp, _vp, _i64, _int, _vp, ctypes.c_double, ctypes.c_double, _int,
                                        _vp, _vp],
+                "sas_mlp_create": [_int, _int, _int, _int, ctypes.POINTER(_vp)],
+                "sas_mlp_destroy": [_vp],
+                "sas_mlp_set_state": [_vp, _vp, _vp, _vp, _i64],
+                "sas_mlp_get_state": [_vp, _vp, _vp, _vp, _vp],
+                "sas_mlp_forward": [_vp, _vp, _int, _vp, _vp],
+                "sas_mlp_train_step": [_vp, _vp, _vp, _int, ctypes.c_float, _vp, _vp],
+                "sas_mlp_grads": [_vp, _vp, _vp, _int, _vp, _vp, _vp],
+                "sas_gemm_bf16": [_int, _int, _int, _vp, _int, _vp, _int, _vp, _vp, _int, _vp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -73,6 +83,8 @@ def load():
             lib.sas_last_error.argtypes = []
             lib.sas_version.restype = ctypes.c_char_p
             lib.sas_version.argtypes = []
+            lib.sas_mlp_param_count.restype = _i64
+            lib.sas_mlp_param_count.argtypes = [_vp]
             _lib = lib
     return _lib
 
@@ -176,6 +188,48 @@ def sas_profile_static(coords, types, n_atoms, n_types, ff_coef, q0, dq, n_q, I_
                                    float(q0), float(dq), int(n_q), ptr(I_out), stream_handle(stream))
     if st != SAS_OK:
         raise SasError(st, "sas_profile_static failed")
+
+
+def sas_mlp_create(n_in, n_hidden, n_out, max_batch):
+    h = _vp()
+    check(load().sas_mlp_create(int(n_in), int(n_hidden), int(n_out), int(max_batch), ctypes.byref(h)))
+    return h
+
+
+def sas_mlp_destroy(mlp):
+    check(load().sas_mlp_destroy(mlp))
+
+
+def sas_mlp_param_count(mlp) -> int:
+    return int(load().sas_mlp_param_count(mlp))
+
+
+def sas_mlp_set_state(mlp, params, adam_m=None, adam_v=None, step=0):
+    check(load().sas_mlp_set_state(mlp, ptr(params), ptr(adam_m), ptr(adam_v), int(step)))
+
+
+def sas_mlp_get_state(mlp, params, adam_m=None, adam_v=None):
+    st = ctypes.c_int64(0)
+    check(load().sas_mlp_get_state(mlp, ptr(params), ptr(adam_m), ptr(adam_v), ctypes.byref(st)))
+    return int(st.value)
+
+
+def sas_mlp_forward(mlp, x, batch, y, stream=None):
+    check(load().sas_mlp_forward(mlp, ptr(x), int(batch), ptr(y), stream_handle(stream)))
+
+
+def sas_mlp_train_step(mlp, x, t, batch, lr, loss_out=None, stream=None):
+    check(load().sas_mlp_train_step(mlp, ptr(x), ptr(t), int(batch), float(lr), ptr(loss_out),
+                                    stream_handle(stream)))
+
+
+def sas_mlp_grads(mlp, x, t, batch, grads, loss_out=None, stream=None):
+    check(load().sas_mlp_grads(mlp, ptr(x), ptr(t), int(batch), ptr(grads), ptr(loss_out), stream_handle(stream)))
+
+
+def sas_gemm_bf16(M, N, K, A, lda, B, ldb, bias, C, ldc, stream=None):
+    check(load().sas_gemm_bf16(int(M), int(N), int(K), ptr(A), int(lda), ptr(B), int(ldb), ptr(bias), ptr(C),
+                               int(ldc), stream_handle(stream)))
 
 
 def sas_last_error() -> str:

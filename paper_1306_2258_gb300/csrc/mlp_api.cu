@@ -1,0 +1,335 @@
+// C ABI of the surrogate MLP (include/sas.h): the network object, its training step and
+// inference, state transfer for checkpoints, and a plain bfloat16 GEMM for tests.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sas_internal.h"
+
+using namespace sas;
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+sas_status mlp_fail(sas_status st, const char *what, cudaError_t e = cudaSuccess)
+{
+    char buf[256];
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    } else {
+        snprintf(buf, sizeof buf, "%s", what);
+    }
+    return set_error(st, buf);
+}
+
+#define MLP_TRY(call)                                                          \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) return mlp_fail(SAS_ERR_CUDA, #call, e_);       \
+    } while (0)
+
+bool on_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline int round16(int x) { return (x + 15) / 16 * 16; }
+
+}  // namespace
+
+struct sas_mlp {
+    int n_in = 0, h = 0, n_out = 0, n_outp = 0, max_b = 0;
+    // packed parameter block in device layout: W1 [h][n_in], b1 [h], W2 [h][h], b2 [h],
+    // W3 [n_outp][h] (rows >= n_out stay zero), b3 [n_outp]
+    int64_t oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0, np = 0;
+    float *P = nullptr, *G = nullptr, *Mo = nullptr, *Vo = nullptr;
+    bf16 *Pb = nullptr;             // bfloat16 mirror of P
+    bf16 *W2t = nullptr, *W3t = nullptr;
+    float *Xf = nullptr, *Tf = nullptr, *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dY = nullptr, *dA2 = nullptr,
+          *dZ2 = nullptr, *dA1 = nullptr, *dZ1 = nullptr, *loss = nullptr;
+    bf16 *Xb = nullptr, *Xt = nullptr, *A1b = nullptr, *A1t = nullptr, *A2b = nullptr, *A2t = nullptr, *dYb = nullptr,
+         *dYt = nullptr, *dZ2b = nullptr, *dZ2t = nullptr, *dZ1b = nullptr, *dZ1t = nullptr;
+    std::vector<void *> owned;
+    int64_t step = 0;
+};
+
+namespace {
+
+template <class T>
+bool mlp_alloc(sas_mlp *m, T *&p, int64_t n)
+{
+    void *q = nullptr;
+    if (cudaMalloc(&q, sizeof(T) * (size_t)(n > 0 ? n : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    m->owned.push_back(q);
+    p = static_cast<T *>(q);
+    return true;
+}
+
+void mlp_free(sas_mlp *m)
+{
+    for (void *p : m->owned) cudaFree(p);
+    m->owned.clear();
+}
+
+// x (host or device, [B][n_in] f32) and optionally t ([B][n_out]) to device; forward to Y.
+sas_status mlp_forward(sas_mlp *m, const float *x, const float *t, int B, cudaStream_t s)
+{
+    if (B < 1 || B > m->max_b) return mlp_fail(SAS_ERR_INVALID_ARG, "batch outside [1, max_batch]");
+    const int Bp = round16(B);
+    const float *xd = x;
+    if (!on_device_ptr(x)) {
+        MLP_TRY(cudaMemcpyAsync(m->Xf, x, sizeof(float) * (size_t)B * m->n_in, cudaMemcpyHostToDevice, s));
+        xd = m->Xf;
+    }
+    if (t) {
+        MLP_TRY(cudaMemcpyAsync(m->Tf, t, sizeof(float) * (size_t)B * m->n_out,
+                                on_device_ptr(t) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    }
+    MLP_TRY(launch_to_bf16((int64_t)B * m->n_in, xd, m->Xb, s));
+    const bf16 *W1b = m->Pb + m->oW1, *W2b = m->Pb + m->oW2, *W3b = m->Pb + m->oW3;
+    MLP_TRY(launch_gemm_tn(B, m->h, m->n_in, m->Xb, m->n_in, W1b, m->n_in, m->P + m->ob1, m->Z1, m->h, m->A1b, m->h, 1,
+                           s));
+    MLP_TRY(launch_gemm_tn(B, m->h, m->h, m->A1b, m->h, W2b, m->h, m->P + m->ob2, m->Z2, m->h, m->A2b, m->h, 1, s));
+    MLP_TRY(launch_gemm_tn(B, m->n_outp, m->h, m->A2b, m->h, W3b, m->h, m->P + m->ob3, m->Y, m->n_outp, nullptr, 0, 0,
+                           s));
+    (void)Bp;
+    return SAS_OK;
+}
+
+// Gradients of the MSE loss for the batch already in Xb/Tf (after mlp_forward) into G.
+sas_status mlp_backward(sas_mlp *m, int B, cudaStream_t s)
+{
+    const int Bp = round16(B), h = m->h, Qp = m->n_outp;
+    MLP_TRY(launch_mse(B, Bp, m->n_out, Qp, m->Y, m->Tf, m->dY, m->dYb, m->loss, s));
+    // layer 3
+    MLP_TRY(launch_transpose_bf16(Bp, Bp, Qp, m->dYb, Qp, m->dYt, Bp, s));
+    MLP_TRY(launch_transpose_bf16(B, Bp, h, m->A2b, h, m->A2t, Bp, s));
+    MLP_TRY(launch_gemm_tn(Qp, h, Bp, m->dYt, Bp, m->A2t, Bp, nullptr, m->G + m->oW3, h, nullptr, 0, 0, s));
+    MLP_TRY(launch_colsum(Bp, Qp, m->dY, Qp, m->G + m->ob3, s));
+    MLP_TRY(launch_gemm_tn(B, h, Qp, m->dYb, Qp, m->W3t, Qp, nullptr, m->dA2, h, nullptr, 0, 0, s));
+    // layer 2
+    MLP_TRY(launch_gelu_bwd((int64_t)B * h, m->dA2, m->Z2, m->dZ2, m->dZ2b, s));
+    MLP_TRY(launch_transpose_bf16(B, Bp, h, m->dZ2b, h, m->dZ2t, Bp, s));
+    MLP_TRY(launch_transpose_bf16(B, Bp, h, m->A1b, h, m->A1t, Bp, s));
+    MLP_TRY(launch_gemm_tn(h, h, Bp, m->dZ2t, Bp, m->A1t, Bp, nullptr, m->G + m->oW2, h, nullptr, 0, 0, s));
+    MLP_TRY(launch_colsum(B, h, m->dZ2, h, m->G + m->ob2, s));
+    MLP_TRY(launch_gemm_tn(B, h, h, m->dZ2b, h, m->W2t, h, nullptr, m->dA1, h, nullptr, 0, 0, s));
+    // layer 1
+    MLP_TRY(launch_gelu_bwd((int64_t)B * h, m->dA1, m->Z1, m->dZ1, m->dZ1b, s));
+    MLP_TRY(launch_transpose_bf16(B, Bp, h, m->dZ1b, h, m->dZ1t, Bp, s));
+    MLP_TRY(launch_transpose_bf16(B, Bp, m->n_in, m->Xb, m->n_in, m->Xt, Bp, s));
+    MLP_TRY(launch_gemm_tn(h, m->n_in, Bp, m->dZ1t, Bp, m->Xt, Bp, nullptr, m->G + m->oW1, m->n_in, nullptr, 0, 0, s));
+    MLP_TRY(launch_colsum(B, h, m->dZ1, h, m->G + m->ob1, s));
+    return SAS_OK;
+}
+
+// bfloat16 mirror of the masters and the transposed weights the backward pass uses
+sas_status mlp_refresh(sas_mlp *m, cudaStream_t s)
+{
+    MLP_TRY(launch_to_bf16(m->np, m->P, m->Pb, s));
+    MLP_TRY(launch_transpose_bf16(m->h, m->h, m->h, m->Pb + m->oW2, m->h, m->W2t, m->h, s));
+    MLP_TRY(launch_transpose_bf16(m->n_outp, m->n_outp, m->h, m->Pb + m->oW3, m->h, m->W3t, m->n_outp, s));
+    return SAS_OK;
+}
+
+// Device layout <-> packed layout (W3 and b3 with n_out rows) for one float block.
+void pack_layout(const sas_mlp *m, const float *dev_layout, float *packed)
+{
+    const int64_t nW3 = (int64_t)m->n_out * m->h;
+    std::memcpy(packed, dev_layout, sizeof(float) * (size_t)m->oW3);
+    std::memcpy(packed + m->oW3, dev_layout + m->oW3, sizeof(float) * (size_t)nW3);
+    std::memcpy(packed + m->oW3 + nW3, dev_layout + m->ob3, sizeof(float) * (size_t)m->n_out);
+}
+
+void unpack_layout(const sas_mlp *m, const float *packed, float *dev_layout)
+{
+    const int64_t nW3 = (int64_t)m->n_out * m->h;
+    std::memset(dev_layout, 0, sizeof(float) * (size_t)m->np);
+    std::memcpy(dev_layout, packed, sizeof(float) * (size_t)m->oW3);
+    std::memcpy(dev_layout + m->oW3, packed + m->oW3, sizeof(float) * (size_t)nW3);
+    std::memcpy(dev_layout + m->ob3, packed + m->oW3 + nW3, sizeof(float) * (size_t)m->n_out);
+}
+
+int64_t packed_count(const sas_mlp *m) { return m->oW3 + (int64_t)m->n_out * m->h + m->n_out; }
+
+sas_status copy_block(const sas_mlp *m, const float *dev, float *host_packed)
+{
+    std::vector<float> tmp((size_t)m->np);
+    MLP_TRY(cudaMemcpy(tmp.data(), dev, sizeof(float) * (size_t)m->np, cudaMemcpyDeviceToHost));
+    pack_layout(m, tmp.data(), host_packed);
+    return SAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sas_status sas_mlp_create(int n_in, int n_hidden, int n_out, int max_batch, sas_mlp **out)
+{
+    if (!out) return mlp_fail(SAS_ERR_INVALID_ARG, "null output handle");
+    if (n_in < 16 || n_in % 16 || n_hidden < 16 || n_hidden % 16 || n_out < 1 || max_batch < 1 || max_batch > 65536)
+        return mlp_fail(SAS_ERR_INVALID_ARG, "n_in and n_hidden must be positive multiples of 16, n_out >= 1, "
+                                             "max_batch in [1, 65536]");
+    sas_mlp *m = new (std::nothrow) sas_mlp;
+    if (!m) return mlp_fail(SAS_ERR_ALLOC, "host allocation failed");
+    m->n_in = n_in;
+    m->h = n_hidden;
+    m->n_out = n_out;
+    m->n_outp = round16(n_out);
+    m->max_b = max_batch;
+    const int64_t h = n_hidden, Qp = m->n_outp, Bp = round16(max_batch);
+    m->oW1 = 0;
+    m->ob1 = h * n_in;
+    m->oW2 = m->ob1 + h;
+    m->ob2 = m->oW2 + h * h;
+    m->oW3 = m->ob2 + h;
+    m->ob3 = m->oW3 + Qp * h;
+    m->np = m->ob3 + Qp;
+    bool ok = mlp_alloc(m, m->P, m->np) && mlp_alloc(m, m->G, m->np) && mlp_alloc(m, m->Mo, m->np) &&
+              mlp_alloc(m, m->Vo, m->np) && mlp_alloc(m, m->Pb, m->np) && mlp_alloc(m, m->W2t, h * h) &&
+              mlp_alloc(m, m->W3t, h * Qp) && mlp_alloc(m, m->Xf, Bp * n_in) && mlp_alloc(m, m->Tf, Bp * n_out) &&
+              mlp_alloc(m, m->Z1, Bp * h) && mlp_alloc(m, m->Z2, Bp * h) && mlp_alloc(m, m->Y, Bp * Qp) &&
+              mlp_alloc(m, m->dY, Bp * Qp) && mlp_alloc(m, m->dA2, Bp * h) && mlp_alloc(m, m->dZ2, Bp * h) &&
+              mlp_alloc(m, m->dA1, Bp * h) && mlp_alloc(m, m->dZ1, Bp * h) && mlp_alloc(m, m->loss, 1) &&
+              mlp_alloc(m, m->Xb, Bp * n_in) && mlp_alloc(m, m->Xt, Bp * n_in) && mlp_alloc(m, m->A1b, Bp * h) &&
+              mlp_alloc(m, m->A1t, Bp * h) && mlp_alloc(m, m->A2b, Bp * h) && mlp_alloc(m, m->A2t, Bp * h) &&
+              mlp_alloc(m, m->dYb, Bp * Qp) && mlp_alloc(m, m->dYt, Bp * Qp) && mlp_alloc(m, m->dZ2b, Bp * h) &&
+              mlp_alloc(m, m->dZ2t, Bp * h) && mlp_alloc(m, m->dZ1b, Bp * h) && mlp_alloc(m, m->dZ1t, Bp * h);
+    if (!ok) {
+        mlp_free(m);
+        delete m;
+        return mlp_fail(SAS_ERR_ALLOC, "device allocation failed");
+    }
+    if (cudaMemset(m->P, 0, sizeof(float) * m->np) != cudaSuccess ||
+        cudaMemset(m->Mo, 0, sizeof(float) * m->np) != cudaSuccess ||
+        cudaMemset(m->Vo, 0, sizeof(float) * m->np) != cudaSuccess ||
+        cudaMemset(m->G, 0, sizeof(float) * m->np) != cudaSuccess || mlp_refresh(m, 0) != SAS_OK ||
+        cudaStreamSynchronize(0) != cudaSuccess) {
+        cudaGetLastError();
+        mlp_free(m);
+        delete m;
+        return mlp_fail(SAS_ERR_CUDA, "initialisation failed");
+    }
+    *out = m;
+    return SAS_OK;
+}
+
+sas_status sas_mlp_destroy(sas_mlp *m)
+{
+    if (!m) return SAS_OK;
+    mlp_free(m);
+    delete m;
+    return SAS_OK;
+}
+
+int64_t sas_mlp_param_count(const sas_mlp *m) { return m ? packed_count(m) : 0; }
+
+sas_status sas_mlp_set_state(sas_mlp *m, const float *params, const float *adam_m, const float *adam_v,
+                             int64_t step)
+{
+    if (!m || !params || step < 0) return mlp_fail(SAS_ERR_INVALID_ARG, "bad argument");
+    std::vector<float> tmp((size_t)m->np);
+    const float *src[3] = {params, adam_m, adam_v};
+    float *dst[3] = {m->P, m->Mo, m->Vo};
+    for (int k = 0; k < 3; ++k) {
+        if (src[k])
+            unpack_layout(m, src[k], tmp.data());
+        else
+            std::fill(tmp.begin(), tmp.end(), 0.f);
+        MLP_TRY(cudaMemcpy(dst[k], tmp.data(), sizeof(float) * (size_t)m->np, cudaMemcpyHostToDevice));
+    }
+    m->step = step;
+    sas_status st = mlp_refresh(m, 0);
+    if (st != SAS_OK) return st;
+    MLP_TRY(cudaStreamSynchronize(0));
+    return SAS_OK;
+}
+
+sas_status sas_mlp_get_state(sas_mlp *m, float *params, float *adam_m, float *adam_v, int64_t *step)
+{
+    if (!m) return mlp_fail(SAS_ERR_INVALID_ARG, "null network");
+    MLP_TRY(cudaDeviceSynchronize());
+    sas_status st;
+    if (params && (st = copy_block(m, m->P, params)) != SAS_OK) return st;
+    if (adam_m && (st = copy_block(m, m->Mo, adam_m)) != SAS_OK) return st;
+    if (adam_v && (st = copy_block(m, m->Vo, adam_v)) != SAS_OK) return st;
+    if (step) *step = m->step;
+    return SAS_OK;
+}
+
+sas_status sas_mlp_forward(sas_mlp *m, const float *x, int batch, float *y, void *stream)
+{
+    if (!m || !x || !y) return mlp_fail(SAS_ERR_INVALID_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    sas_status st = mlp_forward(m, x, nullptr, batch, s);
+    if (st != SAS_OK) return st;
+    const bool host = !on_device_ptr(y);
+    MLP_TRY(cudaMemcpy2DAsync(y, sizeof(float) * m->n_out, m->Y, sizeof(float) * m->n_outp, sizeof(float) * m->n_out,
+                              batch, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    if (host) MLP_TRY(cudaStreamSynchronize(s));
+    return SAS_OK;
+}
+
+sas_status sas_mlp_grads(sas_mlp *m, const float *x, const float *t, int batch, float *grads, float *loss_out,
+                         void *stream)
+{
+    if (!m || !x || !t) return mlp_fail(SAS_ERR_INVALID_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    sas_status st = mlp_forward(m, x, t, batch, s);
+    if (st == SAS_OK) st = mlp_backward(m, batch, s);
+    if (st != SAS_OK) return st;
+    MLP_TRY(cudaStreamSynchronize(s));
+    if (grads && (st = copy_block(m, m->G, grads)) != SAS_OK) return st;
+    if (loss_out) MLP_TRY(cudaMemcpy(loss_out, m->loss, sizeof(float), cudaMemcpyDefault));
+    return SAS_OK;
+}
+
+sas_status sas_mlp_train_step(sas_mlp *m, const float *x, const float *t, int batch, float lr, float *loss_out,
+                              void *stream)
+{
+    if (!m || !x || !t) return mlp_fail(SAS_ERR_INVALID_ARG, "null argument");
+    if (!(lr > 0.f) || !std::isfinite(lr)) return mlp_fail(SAS_ERR_INVALID_ARG, "learning rate must be positive");
+    cudaStream_t s = (cudaStream_t)stream;
+    sas_status st = mlp_forward(m, x, t, batch, s);
+    if (st == SAS_OK) st = mlp_backward(m, batch, s);
+    if (st != SAS_OK) return st;
+    m->step += 1;
+    MLP_TRY(launch_adam(m->np, m->P, m->G, m->Mo, m->Vo, lr, 0.9f, 0.999f, 1e-8f, m->step, m->Pb, s));
+    st = mlp_refresh(m, s);
+    if (st != SAS_OK) return st;
+    if (loss_out) {
+        const bool host = !on_device_ptr(loss_out);
+        MLP_TRY(cudaMemcpyAsync(loss_out, m->loss, sizeof(float), host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                s));
+        if (host) MLP_TRY(cudaStreamSynchronize(s));
+    }
+    return SAS_OK;
+}
+
+sas_status sas_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias, float *C,
+                         int ldc, void *stream)
+{
+    if (M < 0 || N < 0 || K < 0 || K % 16 || lda % 8 || ldb % 8 || lda < K || ldb < K || ldc < N)
+        return mlp_fail(SAS_ERR_INVALID_ARG, "sizes: K % 16 == 0, lda and ldb multiples of 8 and >= K, ldc >= N");
+    if ((M && N && K) && (!A || !B || !C)) return mlp_fail(SAS_ERR_INVALID_ARG, "null argument");
+    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15)
+        return mlp_fail(SAS_ERR_INVALID_ARG, "A and B must be 16-byte aligned");
+    MLP_TRY(launch_gemm_tn(M, N, K, A, lda, B, ldb, bias, C, ldc, nullptr, 0, 0, (cudaStream_t)stream));
+    return SAS_OK;
+}
+
+}  // extern "C"

@@ -41,6 +41,18 @@ sas_status fail(sas_status st, const char *fmt, ...)
     return st;
 }
 
+}  // namespace
+
+namespace sas {
+sas_status set_error(sas_status st, const char *msg)
+{
+    g_err = msg;
+    return st;
+}
+}  // namespace sas
+
+namespace {
+
 #define CUDA_TRY(call)                                                                       \
     do {                                                                                     \
         cudaError_t e_ = (call);                                                             \

@@ -100,4 +100,22 @@ cudaError_t launch_pair_histogram(const float4 *X, int64_t npad, const Item *ite
                                   int n_bins, float r_max, int n_pairs, int *hist,
                                   unsigned long long *dropped, int grid, int jmax, cudaStream_t s);
 
+// ---- MLP (mlp.cu) -------------------------------------------------------------------
+// C[M][N] = A[M][K] B[N][K]^T (+ bias); bfloat16 A, B (K % 16 == 0, ld % 8 == 0, 16-byte
+// aligned), FP32 C (may be null); D (bfloat16, may be null) gets the value or GELU(value).
+cudaError_t launch_gemm_tn(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
+                           float *C, int ldc, void *D, int ldd, int gelu, cudaStream_t s);
+cudaError_t launch_to_bf16(int64_t n, const float *x, void *y, cudaStream_t s);
+cudaError_t launch_transpose_bf16(int R, int Rpad, int C, const void *in, int ldin, void *out, int ldout,
+                                  cudaStream_t s);
+cudaError_t launch_mse(int B, int Bpad, int Q, int Qpad, const float *Y, const float *T, float *dY, void *dYb,
+                       float *loss, cudaStream_t s);
+cudaError_t launch_gelu_bwd(int64_t n, const float *dA, const float *Z, float *dZ, void *dZb, cudaStream_t s);
+cudaError_t launch_colsum(int R, int C, const float *in, int ld, float *out, cudaStream_t s);
+cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,
+                        int64_t step, void *pb, cudaStream_t s);
+
+// the calling thread's error message (sas_last_error)
+sas_status set_error(sas_status st, const char *msg);
+
 }  // namespace sas
