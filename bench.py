@@ -32,6 +32,9 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
 OPS_PER_PAIR_Q = 2   # FP32 lane operations per pair*q: one FMA (recurrence) + one add (accumulate)
+# DRAM bytes (read + write) of one k_debye_mixed<52,2,0,3> launch on this workload, from the ncu
+# capture summarised in profiles/k_debye_mixed_globule50k_q201.md (same kernel source).
+MIXED_KERNEL_DRAM_BYTES = 977_664
 
 
 def _dist():
@@ -146,6 +149,29 @@ def run_reference(args):
     return 0
 
 
+def rank_molecule(w, rank: int, n: int = N_ATOMS):
+    """Rank r's independent problem: rank 0 the canonical globule of the workload, every other rank
+    its own seeded globule of the same size and shape (weak scaling, no data-path collective)."""
+    from paper_1306_2258_gb300 import workloads as wl
+    if rank == 0 and w is not None:
+        return w.mol
+    return wl.random_walk_globule(n, 5, wl.seed_for(2, 90_000 + rank)).as_f32()
+
+
+def aggregate(tot_ms: float, units_per_step: float, steps: int, world: int, device=None):
+    """(max over ranks of the timed-region duration in ms, whole-job throughput = all ranks' units
+    over that duration).  Collective only when world > 1."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([tot_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units_per_step * steps], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    max_ms = float(t.item())
+    return max_ms, float(u.item()) / (max_ms / 1e3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -159,7 +185,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = wl.c2_globule(N_ATOMS)
-    mol = w.mol if rank == 0 else wl.random_walk_globule(N_ATOMS, 5, wl.seed_for(2, 90_000 + rank)).as_f32()
+    mol = rank_molecule(w, rank)
     n, Q = mol.n, w.q.size
     pairs = n * (n - 1) // 2
     pq = pairs * Q
@@ -195,12 +221,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = float(sum(step_ms))
-    t_all = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-    tot_ms = float(t_all.item())
-    value = world * pq * args.steps / (tot_ms / 1e3)
+    tot_ms, value = aggregate(float(sum(step_ms)), pq, args.steps, world, dev)
     I_mixed = out[0].cpu().numpy().copy()
 
     if args.skip_extras:
@@ -256,7 +277,7 @@ def run_ours(args):
         "fp64_plain": {"value": pq / (ms64 / 1e3), "unit": "pair·q/s", "ms_per_step": ms64, "dtype": "f64"},
         "speedup_vs_fp64": (pq / (tot_ms / args.steps / 1e3)) / (pq / (ms64 / 1e3)),
         "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": peak_ops, "unit": "Tops/s (FP32 lane ops)",
-                     "frac": achieved_ops / peak_ops, "traffic": None,
+                     "frac": achieved_ops / peak_ops, "traffic": MIXED_KERNEL_DRAM_BYTES,
                      "kernel": "k_debye_mixed", "kernel_ms": kern_s * 1e3,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (nominal max clock)"},
         "e2e": e2e,

@@ -179,6 +179,8 @@ struct sas_ctx {
     int64_t stats[6] = {0, 0, 0, 0, 0, 0};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the last pair-kernel launch
     bool ev_pending = false;
+    void *h_stage = nullptr;   // pinned staging of host outputs
+    size_t h_stage_cap = 0;
 };
 
 namespace {
@@ -472,15 +474,63 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
     return SAS_OK;
 }
 
-// Copy `bytes` from device buffer `src` to the caller's `dst` (host or device) on stream s.
-sas_status deliver(sas_ctx *ctx, void *dst, const void *src, size_t bytes, cudaStream_t s, bool &host)
+// Outputs of one call: device destinations are copied at once on the stream; host destinations
+// are staged through pinned memory, so that the wait for them obeys the context's time limit
+// (a copy into pageable memory would block inside cudaMemcpyAsync instead).
+struct HostCopies {
+    void *dst[4];
+    const void *src[4];
+    size_t bytes[4];
+    int n = 0;
+};
+
+sas_status out_copy(HostCopies &hc, void *dst, const void *src, size_t bytes, cudaStream_t s)
 {
-    if (!dst || !bytes) return SAS_OK;
-    if (dst == src) return SAS_OK;
-    const bool h = !on_device(dst);
-    host = host || h;
-    CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, h ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
-    (void)ctx;
+    if (!dst || !bytes || dst == src) return SAS_OK;
+    if (on_device(dst)) {
+        CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
+        return SAS_OK;
+    }
+    hc.dst[hc.n] = dst;
+    hc.src[hc.n] = src;
+    hc.bytes[hc.n] = bytes;
+    ++hc.n;
+    return SAS_OK;
+}
+
+sas_status finish_copies(sas_ctx *ctx, HostCopies &hc, cudaStream_t s)
+{
+    if (hc.n == 0) return SAS_OK;
+    size_t total = 0;
+    for (int k = 0; k < hc.n; ++k) total += (hc.bytes[k] + 255) / 256 * 256;
+    if (ctx->h_stage_cap < total) {
+        if (ctx->h_stage) {
+            cudaDeviceSynchronize();
+            cudaFreeHost(ctx->h_stage);
+            ctx->h_stage = nullptr;
+            ctx->h_stage_cap = 0;
+        }
+        if (cudaMallocHost(&ctx->h_stage, total) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->h_stage = nullptr;
+            return fail(SAS_ERR_ALLOC, "pinned allocation of %zu bytes failed", total);
+        }
+        ctx->h_stage_cap = total;
+    }
+    size_t off = 0;
+    for (int k = 0; k < hc.n; ++k) {
+        CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(ctx->h_stage) + off, hc.src[k], hc.bytes[k],
+                                 cudaMemcpyDeviceToHost, s));
+        off += (hc.bytes[k] + 255) / 256 * 256;
+    }
+    sas_status st = wait_stream(ctx, s);
+    if (st != SAS_OK) return st;
+    off = 0;
+    for (int k = 0; k < hc.n; ++k) {
+        std::memcpy(hc.dst[k], static_cast<const char *>(ctx->h_stage) + off, hc.bytes[k]);
+        off += (hc.bytes[k] + 255) / 256 * 256;
+    }
+    hc.n = 0;
     return SAS_OK;
 }
 
@@ -522,9 +572,9 @@ sas_status run_profile(sas_ctx *ctx, const void *coords, int coords_type, const 
     st = forward(ctx, coords, coords_type, types, n, batch, Id, 8192, s, launches);
     if (st != SAS_OK) return st;
     if (host_out) {
-        CUDA_TRY(cudaMemcpyAsync(I_out, Id, (size_t)batch * Q * sizeof(double), cudaMemcpyDeviceToHost,
-                                 s));
-        st = wait_stream(ctx, s);
+        HostCopies hc;
+        st = out_copy(hc, I_out, Id, (size_t)batch * Q * sizeof(double), s);
+        if (st == SAS_OK) st = finish_copies(ctx, hc, s);
         if (st != SAS_OK) return st;
     }
     ctx->stats[5] = launches;
@@ -533,7 +583,7 @@ sas_status run_profile(sas_ctx *ctx, const void *coords, int coords_type, const 
 
 // Shared back half of sas_profile_grad / sas_profile_vjp: g [batch][Q] (device) -> gradient.
 sas_status adjoint(sas_ctx *ctx, int64_t n, int64_t batch, const double *g_dev, float *grad_out,
-                   cudaStream_t s, int &launches, bool &host)
+                   cudaStream_t s, int &launches, HostCopies &hc)
 {
     const int T = ctx->n_types, Q = ctx->n_q, Pn = T * (T + 1) / 2;
     const int64_t npad = ctx->h_meta[2 * T];
@@ -552,10 +602,7 @@ sas_status adjoint(sas_ctx *ctx, int64_t n, int64_t batch, const double *g_dev, 
     }
     CUDA_TRY(launch_unpermute(ctx->G.as<double>(), ctx->slot_of.as<int>(), n, npad, batch, gd, s));
     launches += 3;
-    if (h) {
-        host = true;
-        CUDA_TRY(cudaMemcpyAsync(grad_out, gd, (size_t)batch * n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s));
-    }
+    if (h) return out_copy(hc, grad_out, gd, (size_t)batch * n * 3 * sizeof(float), s);
     return SAS_OK;
 }
 
@@ -645,6 +692,10 @@ sas_status sas_destroy(sas_ctx *ctx)
 {
     if (!ctx) return SAS_OK;
     if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
+    if (ctx->h_stage) {
+        cudaDeviceSynchronize();   // copies of a call that timed out may still target it
+        cudaFreeHost(ctx->h_stage);
+    }
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;
@@ -671,9 +722,10 @@ sas_status sas_partials(sas_ctx *ctx, double *S_out, int64_t capacity, void *str
     const int64_t need = ctx->last_batch * Pn * ctx->n_q;
     if (capacity < need) return fail(SAS_ERR_INVALID_ARG, "capacity %lld < %lld", (long long)capacity, (long long)need);
     cudaStream_t s = (cudaStream_t)stream;
-    CUDA_TRY(cudaMemcpyAsync(S_out, ctx->S.p, (size_t)need * sizeof(double), cudaMemcpyDefault, s));
-    if (!on_device(S_out)) return wait_stream(ctx, s);
-    return SAS_OK;
+    HostCopies hc;
+    sas_status st = out_copy(hc, S_out, ctx->S.p, (size_t)need * sizeof(double), s);
+    if (st != SAS_OK) return st;
+    return finish_copies(ctx, hc, s);
 }
 
 sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value)
@@ -741,7 +793,7 @@ sas_status sas_profile_grad(sas_ctx *ctx, const float *coords, const int32_t *ty
     cudaStream_t s = (cudaStream_t)stream;
     const int Q = ctx->n_q;
     int launches = 0;
-    bool host = false;
+    HostCopies hc;
     const void *tg = nullptr, *wt = nullptr;
     st = stage_in(ctx->tgt, target, Q * sizeof(double), s, tg);
     if (st != SAS_OK) return st;
@@ -760,15 +812,15 @@ sas_status sas_profile_grad(sas_ctx *ctx, const float *coords, const int32_t *ty
                          ctx->gbuf.as<double>(), ctx->chi2buf.as<double>(), s));
     launches += 1;
     if (n > 0) {
-        st = adjoint(ctx, n, batch, ctx->gbuf.as<double>(), grad_out, s, launches, host);
+        st = adjoint(ctx, n, batch, ctx->gbuf.as<double>(), grad_out, s, launches, hc);
         if (st != SAS_OK) return st;
     }
-    st = deliver(ctx, chi2_out, ctx->chi2buf.p, (size_t)batch * sizeof(double), s, host);
+    st = out_copy(hc, chi2_out, ctx->chi2buf.p, (size_t)batch * sizeof(double), s);
     if (st != SAS_OK) return st;
-    st = deliver(ctx, I_out, ctx->Ibuf.p, (size_t)batch * Q * sizeof(double), s, host);
+    st = out_copy(hc, I_out, ctx->Ibuf.p, (size_t)batch * Q * sizeof(double), s);
     if (st != SAS_OK) return st;
     ctx->stats[5] = launches;
-    return host ? wait_stream(ctx, s) : SAS_OK;
+    return finish_copies(ctx, hc, s);
 }
 
 sas_status sas_profile_vjp(sas_ctx *ctx, const float *coords, const int32_t *types, int64_t n,
@@ -782,7 +834,7 @@ sas_status sas_profile_vjp(sas_ctx *ctx, const float *coords, const int32_t *typ
     cudaStream_t s = (cudaStream_t)stream;
     const int T = ctx->n_types, Q = ctx->n_q;
     int launches = 0;
-    bool host = false;
+    HostCopies hc;
     const void *gI = nullptr;
     st = stage_in(ctx->gbuf, grad_I, (size_t)batch * Q * sizeof(double), s, gI);
     if (st != SAS_OK) return st;
@@ -791,10 +843,10 @@ sas_status sas_profile_vjp(sas_ctx *ctx, const float *coords, const int32_t *typ
                  s, launches);
     if (st != SAS_OK) return st;
     (void)T;
-    st = adjoint(ctx, n, batch, (const double *)gI, grad_out, s, launches, host);
+    st = adjoint(ctx, n, batch, (const double *)gI, grad_out, s, launches, hc);
     if (st != SAS_OK) return st;
     ctx->stats[5] = launches;
-    return host ? wait_stream(ctx, s) : SAS_OK;
+    return finish_copies(ctx, hc, s);
 }
 
 sas_status sas_pair_histogram(sas_ctx *ctx, const float *coords, const int32_t *types, int64_t n,
@@ -829,14 +881,14 @@ sas_status sas_pair_histogram(sas_ctx *ctx, const float *coords, const int32_t *
                                    r_max, Pn, ctx->hist.as<int>(), ctx->dropped.as<unsigned long long>(),
                                    grid, ctx->jmax_used, s));
     launches += 1;
-    bool host = false;
-    st = deliver(ctx, hist_out, ctx->hist.p, hbytes, s, host);
+    HostCopies hc;
+    st = out_copy(hc, hist_out, ctx->hist.p, hbytes, s);
     if (st != SAS_OK) return st;
-    st = deliver(ctx, dropped_out, ctx->dropped.p, (size_t)batch * sizeof(int64_t), s, host);
+    st = out_copy(hc, dropped_out, ctx->dropped.p, (size_t)batch * sizeof(int64_t), s);
     if (st != SAS_OK) return st;
     ctx->stats[5] = launches;
     ctx->have_partials = false;
-    return host ? wait_stream(ctx, s) : SAS_OK;
+    return finish_copies(ctx, hc, s);
 }
 
 }  // extern "C"
