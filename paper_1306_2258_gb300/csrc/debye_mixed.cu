@@ -118,15 +118,17 @@ __device__ __forceinline__ void setup_m2(const float4 xi, const float4 xj, float
     }
 }
 
-// The recurrence over the chunk's 2*NB float2 blocks: acc[v] += W_v.
-template <int NB>
+// The recurrence over the first NV float2 blocks of the chunk (NV <= 2*NB, the chunk's q values
+// rounded up to pairs): acc[v] += W_v.
+template <int NB, int NV>
 __device__ __forceinline__ void core_m2(float2 wp, float2 wc, const float2 Cp, const float2 Cn,
                                         float2 (&acc)[2 * NB])
 {
+    static_assert(NV >= 2 && NV <= 2 * NB, "slot count out of range");
     acc[0] = f2add(acc[0], wp);
     acc[1] = f2add(acc[1], wc);
 #pragma unroll
-    for (int v = 1; v + 1 < 2 * NB; ++v) {   // W_{v+1} = (+/-)C W_v + W_{v-1}
+    for (int v = 1; v + 1 < NV; ++v) {   // W_{v+1} = (+/-)C W_v + W_{v-1}
         const float2 n = f2fma(step_negative(v) ? Cn : Cp, wc, wp);
         acc[v + 1] = f2add(acc[v + 1], n);
         wp = wc;
@@ -134,34 +136,45 @@ __device__ __forceinline__ void core_m2(float2 wp, float2 wc, const float2 Cp, c
     }
 }
 
+// Seeds and coefficient of one pair.
+struct M2Pair {
+    float2 w0, w1, Cp, Cn;
+};
+
+// Set-up of pair (i, j) of the item; `valid` false gives a zero-weight stand-in (no pair).
+template <bool ZERO_START>
+__device__ __forceinline__ void setup_at(const float4 xi, const float4 *sj, const Item &item, int tid,
+                                         int jmask, int j, bool valid, float qs_hi, float qs_lo, float dq_hi,
+                                         float dq_lo, M2Pair &o)
+{
+    const float4 xj = sj[j];
+    const float w = (!valid || j <= jmask) ? 0.f : xi.w * xj.w;
+    setup_m2<ZERO_START>(xi, xj, w, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(item.i0 + tid, item.j0 + j), o.w0,
+                         o.w1, o.Cp, o.Cn);
+}
+
 // Pairs (i, j) over the item's J-range, software-pipelined: the set-up of pair j+1 does not
-// depend on the recurrence of pair j, so the two interleave.
-template <int NB, bool ZERO_START>
+// depend on the recurrence of pair j, so the two interleave.  Two pair states alternate
+// (unrolled by two), so no state is copied between pairs.
+template <int NB, int NV, bool ZERO_START>
 __device__ __forceinline__ void run_m2_pipelined(const float4 xi, const float4 *sj, const Item &item,
                                                  int tid, int jmask, float qs_hi, float qs_lo, float dq_hi,
                                                  float dq_lo, float2 (&acc)[2 * NB])
 {
-    float2 w0, w1, Cp, Cn;
-    {
-        const float4 x0 = sj[0];
-        const float wt = (0 <= jmask) ? 0.f : xi.w * x0.w;
-        setup_m2<ZERO_START>(xi, x0, wt, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(item.i0 + tid, item.j0),
-                             w0, w1, Cp, Cn);
+    const int jlen = item.jlen;
+    if (jlen <= 0) return;
+    M2Pair a, b;
+    setup_at<ZERO_START>(xi, sj, item, tid, jmask, 0, true, qs_hi, qs_lo, dq_hi, dq_lo, a);
+    int j = 0;
+    for (; j + 1 < jlen; j += 2) {
+        setup_at<ZERO_START>(xi, sj, item, tid, jmask, j + 1, true, qs_hi, qs_lo, dq_hi, dq_lo, b);
+        core_m2<NB, NV>(a.w0, a.w1, a.Cp, a.Cn, acc);
+        const bool more = j + 2 < jlen;
+        setup_at<ZERO_START>(xi, sj, item, tid, jmask, more ? j + 2 : j + 1, more, qs_hi, qs_lo, dq_hi, dq_lo,
+                             a);
+        core_m2<NB, NV>(b.w0, b.w1, b.Cp, b.Cn, acc);
     }
-    for (int j = 0; j < item.jlen; ++j) {
-        const bool more = j + 1 < item.jlen;
-        const int jn = more ? j + 1 : j;
-        const float4 xn = sj[jn];
-        const float wn = (!more || jn <= jmask) ? 0.f : xi.w * xn.w;
-        float2 n0, n1, nCp, nCn;
-        setup_m2<ZERO_START>(xi, xn, wn, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(item.i0 + tid, item.j0 + jn),
-                             n0, n1, nCp, nCn);
-        core_m2<NB>(w0, w1, Cp, Cn, acc);
-        w0 = n0;
-        w1 = n1;
-        Cp = nCp;
-        Cn = nCn;
-    }
+    if (j < jlen) core_m2<NB, NV>(a.w0, a.w1, a.Cp, a.Cn, acc);   // odd J-range: its last pair
 }
 
 // The same pairs one after the other.
@@ -171,12 +184,32 @@ __device__ __forceinline__ void run_m2(const float4 xi, const float4 *sj, const 
                                        float2 (&acc)[2 * NB])
 {
     for (int j = 0; j < item.jlen; ++j) {
-        const float4 xj = sj[j];
-        const float wt = (j <= jmask) ? 0.f : xi.w * xj.w;
-        float2 w0, w1, Cp, Cn;
-        setup_m2<ZERO_START>(xi, xj, wt, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(item.i0 + tid, item.j0 + j),
-                             w0, w1, Cp, Cn);
-        core_m2<NB>(w0, w1, Cp, Cn, acc);
+        M2Pair a;
+        setup_at<ZERO_START>(xi, sj, item, tid, jmask, j, true, qs_hi, qs_lo, dq_hi, dq_lo, a);
+        core_m2<NB, 2 * NB>(a.w0, a.w1, a.Cp, a.Cn, acc);
+    }
+}
+
+// The pipelined loop with the slot count fixed at compile time: the chunk's nv float2 slots,
+// for nv within 3 of the capacity (beyond that the spare slots are computed and discarded).
+template <int NB, bool ZERO_START>
+__device__ __forceinline__ void run_m2_fitted(int nv, const float4 xi, const float4 *sj, const Item &item,
+                                              int tid, int jmask, float qs_hi, float qs_lo, float dq_hi,
+                                              float dq_lo, float2 (&acc)[2 * NB])
+{
+    switch (2 * NB - nv) {
+    case 1:
+        run_m2_pipelined<NB, 2 * NB - 1, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc);
+        break;
+    case 2:
+        run_m2_pipelined<NB, 2 * NB - 2, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc);
+        break;
+    case 3:
+        run_m2_pipelined<NB, 2 * NB - 3, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc);
+        break;
+    default:
+        run_m2_pipelined<NB, 2 * NB, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc);
+        break;
     }
 }
 
@@ -364,30 +397,38 @@ __host__ __device__ constexpr int mixed_ctas_per_sm(int NB) { return NB <= 13 ? 
 template <int NB, int M, int KQ, int P>
 __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
     k_debye_mixed(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items,
-                  int n_items, QChunks qc, double *__restrict__ partial, int part_stride)
+                  int n_items, QChunks qc, double *__restrict__ partial, int part_stride,
+                  int *__restrict__ ticket)
 {
     extern __shared__ float4 sj[];
     __shared__ double red[kTile / 32][4 * NB];
+    __shared__ int next_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    // Items are handed out dynamically: CTA b starts with item b, then draws tickets; the list is
+    // sorted by decreasing work, so the CTAs finish close together.
+    int it = blockIdx.x;
+    while (it < n_items) {
         const Item item = items[it];
         const float4 *Xb = X + (int64_t)item.batch * npad;
-        __syncthreads();   // the previous item is done with sj and red
+        __syncthreads();   // the previous item is done with sj, red and next_item
+        if (tid == 0) next_item = (int)gridDim.x + atomicAdd(ticket, 1);
         for (int j = tid; j < item.jlen; j += kTile) sj[j] = Xb[item.j0 + j];
         const float4 xi = Xb[item.i0 + tid];
         __syncthreads();
         const int ch = item.chunk;
         const float qs_hi = qc.qs_hi[ch], qs_lo = qc.qs_lo[ch];
         const bool zero_start = (qs_hi == 0.f) && (qs_lo == 0.f);
+        const int qlen = qc.q_len[ch];
         float2 acc[2 * NB];
 #pragma unroll
         for (int k = 0; k < 2 * NB; ++k) acc[k] = make_float2(0.f, 0.f);
         const int jmask = item.diag ? tid : -1;   // pairs with j <= i are not pairs of i<j
         if (P == 3) {
+            const int nv = (qlen + 1) >> 1;
             if (zero_start)
-                run_m2_pipelined<NB, true>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi, qc.dq_lo, acc);
+                run_m2_fitted<NB, true>(nv, xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi, qc.dq_lo, acc);
             else
-                run_m2_pipelined<NB, false>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi, qc.dq_lo, acc);
+                run_m2_fitted<NB, false>(nv, xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi, qc.dq_lo, acc);
         } else if (P == 4) {
             if (zero_start)
                 run_m2<NB, true>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi, qc.dq_lo, acc);
@@ -403,19 +444,19 @@ __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
         }
         flush_warp<NB, (P == 1 ? M : 2)>(acc, red[warp], lane);
         __syncthreads();
-        const int qlen = qc.q_len[ch];
         for (int k = tid; k < qlen; k += kTile) {
             double s = red[0][k];
 #pragma unroll
             for (int w = 1; w < kTile / 32; ++w) s += red[w][k];
             partial[(int64_t)it * part_stride + k] = s;
         }
+        it = next_item;
     }
 }
 
 template <int NB, int M, int KQ, int P>
 cudaError_t launch_v(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
-                     double *partial, int part_stride, int grid, int jmax, cudaStream_t s)
+                     double *partial, int part_stride, int grid, int jmax, int *ticket, cudaStream_t s)
 {
     const size_t smem = (size_t)jmax * sizeof(float4);
     cudaError_t e = cudaFuncSetAttribute(k_debye_mixed<NB, M, KQ, P>,
@@ -430,17 +471,18 @@ cudaError_t launch_v(const float4 *X, int64_t npad, const Item *items, int n_ite
         grid = (occ > 0 ? occ : 1) * sms;
     }
     if (grid > n_items) grid = n_items;
-    k_debye_mixed<NB, M, KQ, P><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, partial, part_stride);
+    k_debye_mixed<NB, M, KQ, P><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, partial, part_stride,
+                                                           ticket);
     return cudaGetLastError();
 }
 
 template <int NB>
 cudaError_t launch_nb(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
                       int step, int reseed, int variant, double *partial, int part_stride, int grid, int jmax,
-                      cudaStream_t s)
+                      int *ticket, cudaStream_t s)
 {
 #define SAS_LAUNCH(M_, K_, P_) \
-    launch_v<NB, M_, K_, P_>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, s)
+    launch_v<NB, M_, K_, P_>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s)
     if (step == 2 && reseed == 0) {
         if (variant == 3) return SAS_LAUNCH(2, 0, 3);
         if (variant == 4) return SAS_LAUNCH(2, 0, 4);
@@ -462,7 +504,7 @@ int mixed_blocks_for(int qlen_max)
 
 cudaError_t launch_debye_mixed(const float4 *X, int64_t npad, const Item *items, int n_items,
                                const QChunks &qc, int step, int reseed, int variant, double *partial,
-                               int part_stride, int grid, int jmax, cudaStream_t s)
+                               int part_stride, int grid, int jmax, int *ticket, cudaStream_t s)
 {
     if (n_items == 0) return cudaSuccess;
     int qmax = 0;
@@ -470,13 +512,13 @@ cudaError_t launch_debye_mixed(const float4 *X, int64_t npad, const Item *items,
     switch (mixed_blocks_for(qmax)) {
     case 13:
         return launch_nb<13>(X, npad, items, n_items, qc, step, reseed, variant, partial, part_stride, grid,
-                             jmax, s);
+                             jmax, ticket, s);
     case 26:
         return launch_nb<26>(X, npad, items, n_items, qc, step, reseed, variant, partial, part_stride, grid,
-                             jmax, s);
+                             jmax, ticket, s);
     default:
         return launch_nb<52>(X, npad, items, n_items, qc, step, reseed, variant, partial, part_stride, grid,
-                             jmax, s);
+                             jmax, ticket, s);
     }
 }
 

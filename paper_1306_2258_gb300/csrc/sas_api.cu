@@ -167,7 +167,7 @@ struct sas_ctx {
     int opt_grid = 0;
     int64_t opt_timeout_ms = 600000;
     DevBuf coef_d, F, meta, blockcounts, blockoffs, centroid, X, slot_of, items, group_items,
-        group_off, partial, S, in_coords, in_types, out_buf, Ibuf, gbuf, chi2buf, H, G, gout, tgt, wts,
+        group_off, partial, ticket, S, in_coords, in_types, out_buf, Ibuf, gbuf, chi2buf, H, G, gout, tgt, wts,
         hist, dropped;
     int *h_meta = nullptr;   // pinned
     // schedule cache
@@ -229,11 +229,15 @@ struct Schedule {
 void build_schedule(const int *counts, int T, int64_t batch, int tile, int n_chunks, int grid,
                     int64_t jmax_opt, int64_t jmax_cap, Schedule &out)
 {
-    std::vector<int64_t> P(T), O(T);
+    // Type group t occupies slots [O[t], O[t] + P[t]) of the packed array, its atoms the first
+    // counts[t]; an I-tile spans `tile` slots, a J-range ends at E[t], the count rounded up to 4
+    // (the slots past the count hold zero-weight padding).
+    std::vector<int64_t> P(T), O(T), E(T);
     int64_t off = 0;
     for (int t = 0; t < T; ++t) {
         P[t] = (counts[t] + kTile - 1) / kTile * kTile;
         O[t] = off;
+        E[t] = off + std::min<int64_t>(P[t], (counts[t] + 3) / 4 * 4);
         off += P[t];
     }
     auto n_items_for = [&](int64_t jmax) {
@@ -241,9 +245,9 @@ void build_schedule(const int *counts, int T, int64_t batch, int tile, int n_chu
         for (int a = 0; a < T; ++a)
             for (int b = a; b < T; ++b) {
                 if (P[a] == 0 || P[b] == 0) continue;
-                for (int64_t i0 = O[a]; i0 < O[a] + P[a]; i0 += tile) {
-                    const int64_t js = (a == b) ? i0 : O[b], je = O[b] + P[b];
-                    c += (je - js + jmax - 1) / jmax;
+                for (int64_t i0 = O[a]; i0 < O[a] + counts[a]; i0 += tile) {
+                    const int64_t js = (a == b) ? i0 : O[b], je = E[b];
+                    if (je > js) c += (je - js + jmax - 1) / jmax;
                 }
             }
         return c * batch * n_chunks;
@@ -268,8 +272,8 @@ void build_schedule(const int *counts, int T, int64_t batch, int tile, int n_chu
             for (int b = a; b < T; ++b) {
                 if (P[a] == 0 || P[b] == 0) continue;
                 const int g = (int)(bb * Pn + pair_index(a, b, T));
-                for (int64_t i0 = O[a]; i0 < O[a] + P[a]; i0 += tile) {
-                    const int64_t js = (a == b) ? i0 : O[b], je = O[b] + P[b];
+                for (int64_t i0 = O[a]; i0 < O[a] + counts[a]; i0 += tile) {
+                    const int64_t js = (a == b) ? i0 : O[b], je = E[b];
                     for (int64_t j0 = js; j0 < je; j0 += jmax) {
                         const int64_t jl = std::min(jmax, je - j0);
                         for (int ch = 0; ch < n_chunks; ++ch) {
@@ -451,6 +455,10 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
     ALLOC_TRY(ctx->partial, (size_t)std::max(ctx->n_items, 1) * kQChunk * sizeof(double));
     const int grid_per_sm = ctx->opt_grid > 0 ? ctx->opt_grid : 2;
     const int grid = std::max(1, std::min(ctx->n_items, grid_per_sm * ctx->sms));
+    if (!fp64) {
+        ALLOC_TRY(ctx->ticket, sizeof(int));
+        CUDA_TRY(cudaMemsetAsync(ctx->ticket.p, 0, sizeof(int), s));
+    }
     CUDA_TRY(cudaEventRecord(ctx->ev0, s));
     if (fp64) {
         CUDA_TRY(launch_debye_fp64(ctx->X.as<double4>(), npad, ctx->items.as<Item>(), ctx->n_items,
@@ -458,7 +466,8 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
     } else {
         CUDA_TRY(launch_debye_mixed(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items,
                                     ctx->qc, ctx->opt_step, reseed_for(ctx->opt_reseed, n), mixed_variant(ctx->opt_variant, std::min(ctx->n_q, kQChunk)), ctx->partial.as<double>(),
-                                    kQChunk, ctx->opt_grid > 0 ? ctx->opt_grid * ctx->sms : 0, ctx->jmax_used, s));
+                                    kQChunk, ctx->opt_grid > 0 ? ctx->opt_grid * ctx->sms : 0, ctx->jmax_used,
+                                    ctx->ticket.as<int>(), s));
     }
     CUDA_TRY(cudaEventRecord(ctx->ev1, s));
     ctx->ev_pending = true;

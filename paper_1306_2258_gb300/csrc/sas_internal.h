@@ -70,10 +70,11 @@ cudaError_t launch_assemble(double *S, const double *F, const int *meta, int n_t
                             int64_t batch, const QChunks &qc, double *I, cudaStream_t s);
 
 // ---- pair kernels -------------------------------------------------------------
-// partial [n_items][part_stride] f64: sum over the item's pairs of w_i w_j sin(q r)/r
+// partial [n_items][part_stride] f64: sum over the item's pairs of w_i w_j sin(q r)/r.
+// ticket: one device int, zero when the kernel starts (the CTAs draw items from it).
 cudaError_t launch_debye_mixed(const float4 *X, int64_t npad, const Item *items, int n_items,
-                               const QChunks &qc, int step, int reseed, int pairs, double *partial,
-                               int part_stride, int grid, int jmax, cudaStream_t s);
+                               const QChunks &qc, int step, int reseed, int variant, double *partial,
+                               int part_stride, int grid, int jmax, int *ticket, cudaStream_t s);
 cudaError_t launch_debye_fp64(const double4 *X, int64_t npad, const Item *items, int n_items,
                               const QChunks &qc, double *partial, int part_stride, int grid,
                               cudaStream_t s);

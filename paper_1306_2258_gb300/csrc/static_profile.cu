@@ -51,7 +51,8 @@ constexpr size_t kOffPartial = kOffGroupOff + align256(sizeof(int) * (kStaticPai
 constexpr size_t kOffS = kOffPartial + align256(sizeof(double) * kStaticItems * kQChunk);
 constexpr size_t kOffF = kOffS + align256(sizeof(double) * kStaticPairs * kQChunk);
 constexpr size_t kOffCoef = kOffF + align256(sizeof(double) * kStaticTypes * kQChunk);
-constexpr size_t kStaticBytes = kOffCoef + align256(sizeof(double) * 9 * kStaticTypes);
+constexpr size_t kOffTicket = kOffCoef + align256(sizeof(double) * 9 * kStaticTypes);
+constexpr size_t kStaticBytes = kOffTicket + align256(sizeof(int));
 
 // The scratch array.  Device code could name it directly; host code must not pass its name to a
 // kernel (there it is a host-side stand-in), only the address cudaGetSymbolAddress returns.
@@ -147,6 +148,7 @@ extern "C" sas_status sas_profile_static(const float *coords, const int32_t *typ
     double *S = reinterpret_cast<double *>(base + kOffS);
     double *F = reinterpret_cast<double *>(base + kOffF);
     double *coef = reinterpret_cast<double *>(base + kOffCoef);
+    int *ticket = reinterpret_cast<int *>(base + kOffTicket);
 
     // the q grid as one chunk
     QChunks qc{};
@@ -221,8 +223,9 @@ extern "C" sas_status sas_profile_static(const float *coords, const int32_t *typ
     STATIC_TRY(cudaMemsetAsync(X, 0, sizeof(float4) * npad, s));
     STATIC_TRY(launch_scatter(coords, 0, types, n, 1, T, blockoffs, meta, nullptr, 0, X, npad, slot_of, s));
     const int reseed = n < 8192 ? 32 : 0;
+    STATIC_TRY(cudaMemsetAsync(ticket, 0, sizeof(int), s));
     STATIC_TRY(launch_debye_mixed(X, npad, items, ni, qc, 2, reseed, reseed == 0 ? 3 : 1, partial, kQChunk, 0,
-                                  kStaticJmax, s));
+                                  kStaticJmax, ticket, s));
     STATIC_TRY(launch_reduce_items(partial, kQChunk, items, group_items, group_off, Pn, qc, S, s));
     STATIC_TRY(launch_assemble(S, F, meta, T, 1, qc, I_out, s));
     // the host-side arrays above are gone when this returns: wait until the copies from them are done
