@@ -32,9 +32,11 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
 OPS_PER_PAIR_Q = 2   # FP32 lane operations per pair*q: one FMA (recurrence) + one add (accumulate)
-# DRAM bytes (read + write) of one k_debye_mixed<52,2,0,3> launch on this workload, from the ncu
-# capture summarised in profiles/k_debye_mixed_globule50k_q201.md (same kernel source).
-MIXED_KERNEL_DRAM_BYTES = 977_664
+PAIR_KERNEL = "k_debye_mixed_pairs2<52,101>"
+# DRAM bytes (read + write) of one pair-kernel launch on this workload, from the ncu capture
+# summarised in profiles/k_debye_mixed_pairs2_globule50k_q201.md (same kernel source); None
+# while the kernel has changed since that capture.
+MIXED_KERNEL_DRAM_BYTES = 988_160
 
 
 def _dist():
@@ -172,6 +174,108 @@ def aggregate(tot_ms: float, units_per_step: float, steps: int, world: int, devi
     return max_ms, float(u.item()) / (max_ms / 1e3)
 
 
+def _timed(fn, stream, reps=3):
+    """Median CUDA-event time (ms) of fn() on `stream` after one untimed call."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return float(statistics.median(ms))
+
+
+def run_rows(dev, stream):
+    """Every other step of the path on its own workload (device-resident inputs, CUDA events)."""
+    import torch
+
+    from paper_1306_2258_gb300 import _lib, workloads as wl
+    from paper_1306_2258_gb300.profile import Profile
+    from paper_1306_2258_gb300.surrogate import (N_BINS, R_MAX, SurrogateMLP, histogram_features,
+                                                 pair_totals)
+
+    rows = {}
+
+    def pairs(n):
+        return n * (n - 1) // 2
+
+    # elongated rod and sparse chain (configuration 3), mixed profile
+    for name, w in (("profile_rod_c3", wl.c3_rod()), ("profile_sparse_chain_c3", wl.c3_sparse())):
+        p = Profile(w.coef, w.q, "mixed")
+        x = torch.as_tensor(w.mol.coords, device=dev)
+        t = torch.as_tensor(w.mol.types, device=dev)
+        ms = _timed(lambda: p(x, t, stream), stream)
+        pq = pairs(w.mol.n) * w.q.size
+        rows[name] = {"workload": f"{w.mol.n} atoms x {w.q.size} q", "ms": ms, "value": pq / (ms / 1e3),
+                      "unit": "pair·q/s"}
+        p.close()
+
+    # refinement (configuration 4): chi^2 and its gradient for 64 conformers of 5,000 atoms
+    c4 = wl.c4_refinement()
+    p = Profile(c4["coef"], c4["q"], "mixed")
+    tt = torch.as_tensor(c4["base"].types, device=dev)
+    target = p(torch.as_tensor(c4["target"].coords.astype(np.float32), device=dev), tt)
+    wq = 1.0 / target ** 2
+    X4 = torch.as_tensor(c4["conformers"], device=dev)
+    B4, n4 = X4.shape[0], X4.shape[1]
+    ms = _timed(lambda: p.chi2_grad(X4, tt, target, wq, stream), stream)
+    pq = B4 * pairs(n4) * c4["q"].size
+    rows["chi2_gradient_c4"] = {"workload": f"{B4} conformers x {n4} atoms x {c4['q'].size} q, forward + adjoint",
+                                "ms": ms, "value": pq / (ms / 1e3), "unit": "pair·q/s (forward and adjoint each)",
+                                "gradients_per_s": B4 / (ms / 1e3)}
+    p.close()
+
+    # ensemble (configuration 5): exact profiles, pair histograms, surrogate epoch and screen
+    c5 = wl.c5_ensemble()
+    X5 = torch.as_tensor(c5["conformers"], device=dev)
+    B5, n5 = X5.shape[0], X5.shape[1]
+    types5 = c5["base"].types
+    t5 = torch.as_tensor(types5, device=dev)
+    p = Profile(c5["coef"], c5["q"], "mixed")
+    ms = _timed(lambda: p(X5, t5, stream), stream)
+    pq = B5 * pairs(n5) * c5["q"].size
+    rows["profiles_c5"] = {"workload": f"{B5} conformers x {n5} atoms x {c5['q'].size} q", "ms": ms,
+                           "value": pq / (ms / 1e3), "unit": "pair·q/s"}
+    ms = _timed(lambda: p.pair_histogram(X5, t5, N_BINS, R_MAX, stream), stream)
+    rows["histogram_c5"] = {"workload": f"{B5} conformers x {n5} atoms, {N_BINS} bins", "ms": ms,
+                            "value": B5 * pairs(n5) / (ms / 1e3), "unit": "pairs/s"}
+    hist = p.pair_histogram(X5, t5, N_BINS, R_MAX, stream)[0].cpu().numpy()
+    feats = torch.as_tensor(histogram_features(hist, pair_totals(types5, c5["coef"].shape[0])).astype(np.float32),
+                            device=dev)
+    n_in, n_out, hidden, batch = feats.shape[1], c5["q"].size, 512, 256
+    n_train = B5 - B5 // 8
+    net = SurrogateMLP(n_in, hidden, n_out, max_batch=B5, seed=0)
+    tgt = torch.zeros((batch, n_out), dtype=torch.float32, device=dev)
+
+    def epoch():
+        for s0 in range(0, n_train - batch + 1, batch):
+            net.train_step(feats[s0:s0 + batch], tgt, 1e-3)
+
+    ms = _timed(epoch, stream)
+    steps = n_train // batch
+    flop = steps * 3 * 2 * batch * (n_in * hidden + hidden * hidden + hidden * n_out)
+    rows["surrogate_epoch_c5"] = {"workload": f"{steps} Adam steps of batch {batch}, {n_in}-{hidden}-{hidden}-{n_out} MLP",
+                                  "ms": ms, "value": flop / (ms / 1e3) / 1e12, "unit": "TFLOP/s (GEMM flop)"}
+    k = int(round(0.05 * B5))
+
+    def screen():
+        pred = net.predict(feats)
+        top = torch.argsort(torch.sum(pred.double() ** 2, dim=1))[:k]
+        p(X5[top].contiguous(), t5, stream)
+
+    ms = _timed(screen, stream)
+    rows["screen_c5"] = {"workload": f"surrogate over {B5} conformers, top {k} re-scored exactly", "ms": ms,
+                         "value": B5 / (ms / 1e3), "unit": "conformers screened/s"}
+    net.close()
+    p.close()
+    return rows
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -278,12 +382,14 @@ def run_ours(args):
         "speedup_vs_fp64": (pq / (tot_ms / args.steps / 1e3)) / (pq / (ms64 / 1e3)),
         "roofline": {"bound": "alu", "achieved": achieved_ops, "peak": peak_ops, "unit": "Tops/s (FP32 lane ops)",
                      "frac": achieved_ops / peak_ops, "traffic": MIXED_KERNEL_DRAM_BYTES,
-                     "kernel": "k_debye_mixed", "kernel_ms": kern_s * 1e3,
+                     "kernel": PAIR_KERNEL, "kernel_ms": kern_s * 1e3,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (nominal max clock)"},
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
+    if not args.skip_rows:
+        line["rows"] = run_rows(dev, stream)
     if not args.skip_cpu and world == 1:
         line["cpu_baseline"], _ = _cpu_oracle_sample(w, seconds_hint=15.0)
     print(json.dumps(line))
@@ -301,6 +407,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-cpu", action="store_true", help="leave out the CPU-oracle baseline")
+    ap.add_argument("--skip-rows", action="store_true",
+                    help="leave out the timings of the other path steps (rod, sparse chain, gradient, ensemble)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the mixed path only (no e2e, FP64 or CPU legs; for profiler runs)")
     args = ap.parse_args()

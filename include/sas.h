@@ -149,7 +149,8 @@ enum {
     SAS_OPT_TIMEOUT_MS = 5,  /* limit of every host-side wait for device work (default 600000) */
     SAS_OPT_STEP = 6,        /* q steps per recurrence step of the mixed kernel: 2 (default) or 4 */
     SAS_OPT_VARIANT = 7      /* mixed kernel form for step 2 without re-seed: 0 auto, 1 general,
-                                2 set-up of the next pair overlapped, 3 pairs in sequence */
+                                2 set-up of the next pair overlapped, 3 pairs in sequence,
+                                4 two pairs per step on packed FP32 (same result bit for bit as 2 and 3) */
 };
 sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value);
 

@@ -38,6 +38,7 @@
 //  * The per-thread sums are FP32 over the item's J-range (one tile of the
 //    precision pattern), then lifted to FP64 for a warp reduce-scatter with
 //    shuffles and a fixed-order block sum; one FP64 partial per item and q.
+#include "mixed_common.cuh"
 #include "sas_internal.h"
 #include "sincos_f32.cuh"
 
@@ -45,41 +46,7 @@ namespace sas {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
-// sign of block b in the (+, +, -, -) pattern, and of the coefficient of the step b -> b+1
-__host__ __device__ constexpr bool block_negative(int b) { return (b & 2) != 0; }
-__host__ __device__ constexpr bool step_negative(int b) { return (b & 1) != 0; }
-
-// r = sqrt(r2) from the reciprocal square root and one Newton correction (to about 1 ulp);
-// y = 1/sqrt(r2) as computed by the hardware.
-__device__ __forceinline__ void dist_rsqrt(float r2, float &r, float &y)
-{
-    y = rsqrtf(r2);
-    const float r0 = r2 * y;
-    r = fmaf(0.5f * y, fmaf(-r0, r0, r2), r0);
-}
-
-// 2 - mu rounded stochastically by dithering: a uniform offset of at most half an ulp of [1, 2)
-// enters before the one rounding, so the expected coefficient is exact.
-__device__ __forceinline__ float coef_dither(float mu, unsigned hash)
-{
-    const float u = __int_as_float(0x3f800000u | (hash >> 9)) - 1.5f;   // uniform in [-0.5, 0.5)
-    return 2.f - fmaf(u, 1.1920928955078125e-7f, mu);
-}
-
-// Cheap pair hash on the integer ALU (one multiply, then xorshift).
-__device__ __forceinline__ unsigned pair_hash(unsigned i, unsigned j)
-{
-    unsigned h = i ^ (j * 0x9E3779B1u);
-    h ^= h << 13;
-    h ^= h >> 17;
-    h ^= h << 5;
-    return h;
-}
+using namespace mixed;
 
 // ---------------------------------------------------------------------------------------------
 // 2-step recurrence from the chunk start, no re-seeding (the default path)
@@ -318,82 +285,11 @@ __device__ __forceinline__ void pair_terms(const float4 xi, const float4 xj, flo
 }
 
 // ---------------------------------------------------------------------------------------------
-// FP64 warp reduce-scatter of the accumulators
-// ---------------------------------------------------------------------------------------------
-
-// Number of halving levels of the reduce-scatter for V values (at most 5, while V stays even).
-__host__ __device__ constexpr int halvings(int V, int lvl = 0)
-{
-    return (lvl < 5 && V % 2 == 0) ? halvings(V / 2, lvl + 1) : lvl;
-}
-
-// One halving level: lanes with `up` keep the upper half of the H values, add the partner's.
-template <int H, int N>
-__device__ __forceinline__ void halve(double (&d)[N], bool up, int off)
-{
-#pragma unroll
-    for (int k = 0; k < H / 2; ++k) {
-        const double lo = d[k], hi = d[k + H / 2];
-        const double mine = up ? hi : lo, other = up ? lo : hi;
-        d[k] = mine + __shfl_xor_sync(kFull, other, off);
-    }
-}
-
-// Accumulator k (q index k of the chunk) with its block sign applied.
-template <int NB, int M>
-__device__ __forceinline__ float acc_signed(const float2 (&acc)[2 * NB], int k)
-{
-    const float v = (k & 1) ? acc[k >> 1].y : acc[k >> 1].x;
-    return block_negative(k / M) ? -v : v;
-}
-
-// Sum the 32 lanes' V = 4*NB accumulators (FP64 from the first cross-thread add on);
-// the warp's totals land in red[0..V).
-template <int NB, int M>
-__device__ __forceinline__ void flush_warp(const float2 (&acc)[2 * NB], double *red, int lane)
-{
-    constexpr int V = 4 * NB;
-    constexpr int L = halvings(V);   // reduce-scatter levels (offsets 16, 8, ...)
-    constexpr int H1 = V / 2;
-    constexpr int R = V >> L;        // values per lane after the reduce-scatter
-    double d[H1];
-    const bool up16 = lane & 16;
-#pragma unroll
-    for (int k = 0; k < H1; ++k) {   // the lift to FP64
-        const float lo = acc_signed<NB, M>(acc, k), hi = acc_signed<NB, M>(acc, k + H1);
-        const float mine = up16 ? hi : lo, other = up16 ? lo : hi;
-        d[k] = (double)mine + (double)__shfl_xor_sync(kFull, other, 16);
-    }
-    if (L > 1) halve<(V >> 1), H1>(d, lane & 8, 8);
-    if (L > 2) halve<(V >> 2), H1>(d, lane & 4, 4);
-    if (L > 3) halve<(V >> 3), H1>(d, lane & 2, 2);
-    if (L > 4) halve<(V >> 4), H1>(d, lane & 1, 1);
-    // the lane bits not used for scattering: plain butterfly over the R remaining values
-#pragma unroll
-    for (int b = L; b < 5; ++b) {
-        const int off = 16 >> b;
-#pragma unroll
-        for (int k = 0; k < R; ++k) d[k] += __shfl_xor_sync(kFull, d[k], off);
-    }
-    int base = 0;
-#pragma unroll
-    for (int b = 0; b < L; ++b)
-        if (lane & (16 >> b)) base += V >> (b + 1);
-    const int keep_mask = (1 << (5 - L)) - 1;   // lanes that differ only in butterfly bits hold copies
-    if ((lane & keep_mask) == 0) {
-#pragma unroll
-        for (int k = 0; k < R; ++k) red[base + k] = d[k];
-    }
-}
-
-// ---------------------------------------------------------------------------------------------
 // The kernel
 // ---------------------------------------------------------------------------------------------
 
-// Resident CTAs per SM: the accumulators (4*NB floats per thread) set the register budget.
-__host__ __device__ constexpr int mixed_ctas_per_sm(int NB) { return NB <= 13 ? 4 : (NB <= 26 ? 3 : 2); }
-
-// Variant P: 1 = general form (any M, KQ); 3 = 2-step software-pipelined; 4 = 2-step sequential.
+// Variant P: 1 = general form (any M, KQ); 3 = 2-step software-pipelined; 4 = 2-step sequential
+// (variant 5, two pairs per step, is debye_mixed_pairs2.cu).
 template <int NB, int M, int KQ, int P>
 __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
     k_debye_mixed(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items,
@@ -484,6 +380,8 @@ cudaError_t launch_nb(const float4 *X, int64_t npad, const Item *items, int n_it
 #define SAS_LAUNCH(M_, K_, P_) \
     launch_v<NB, M_, K_, P_>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s)
     if (step == 2 && reseed == 0) {
+        if (variant == 5)
+            return launch_debye_mixed_pairs2(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
         if (variant == 3) return SAS_LAUNCH(2, 0, 3);
         if (variant == 4) return SAS_LAUNCH(2, 0, 4);
         return SAS_LAUNCH(2, 0, 1);

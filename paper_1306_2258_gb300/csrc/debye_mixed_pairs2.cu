@@ -1,0 +1,243 @@
+// Mixed-precision pair kernel, two pairs per step (Section I-A, Eq. 2; the recurrence, seeds,
+// stochastic coefficient and FP64 reduction are those of debye_mixed.cu, step 2, seeded once
+// per q chunk).
+//
+// Why two pairs: the recurrence itself runs on packed f32x2 instructions, and a scalar FP32
+// instruction issued between packed ones holds the FP32 pipe about as long as a packed one.
+// The per-pair set-up (distance, sin/cos of dq*r, seeds, coefficient: ~60 FP32 operations)
+// therefore cost nearly twice its operation count when done one pair at a time.  Here each
+// thread sets up pairs (i, j) and (i, j+1) together, lane 0 and lane 1 of every packed
+// instruction, and then runs the two recurrences in lockstep (two independent dependency
+// chains).  The J atoms are staged in shared memory already transposed into lane pairs:
+// (x_j, x_j+1, y_j, y_j+1) and (z_j, z_j+1, w_j, w_j+1).
+//
+// Every operation matches the one-pair kernel lane by lane, and each accumulator receives pair
+// j before pair j+1, so the partial sums are the same bit for bit.
+#include "mixed_common.cuh"
+#include "sas_internal.h"
+#include "sincos_f32.cuh"
+
+namespace sas {
+
+namespace {
+
+using namespace mixed;
+
+__device__ __forceinline__ float2 bc(float v) { return make_float2(v, v); }
+
+// Two pairs (A = lane 0, B = lane 1) after set-up: their first two float2 blocks and their
+// coefficients 2cos(2t) as (+C, +C) and (-C, -C).
+struct PairState2 {
+    float2 w0A, w1A, w0B, w1B;
+    float2 CpA, CnA, CpB, CnB;
+};
+
+template <bool ZERO_START>
+__device__ __forceinline__ void setup2(const float4 pxy, const float4 pzw, const float2 nX, const float2 nY,
+                                       const float2 nZ, const float2 wi, bool keepA, bool keepB, float2 qs_hi,
+                                       float2 qs_lo, float2 dq_hi, float2 dq_lo, unsigned hA, unsigned hB,
+                                       PairState2 &o)
+{
+    // x_j - x_i (the negated difference: its square is the same)
+    const float2 dx = f2add(make_float2(pxy.x, pxy.y), nX);
+    const float2 dy = f2add(make_float2(pxy.z, pxy.w), nY);
+    const float2 dz = f2add(make_float2(pzw.x, pzw.y), nZ);
+    float2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+    r2.x = fmaxf(r2.x, 1e-12f);   // coincident atoms: r = 1e-6 A
+    r2.y = fmaxf(r2.y, 1e-12f);
+    const float2 y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 r0 = f2mul(r2, y);
+    // r = r0 + (y/2)(r2 - r0^2), as (-y/2)(r0^2 - r2) + r0
+    const float2 r = f2fma(f2mul(y, bc(-0.5f)), f2fma(r0, r0, f2mul(r2, bc(-1.f))), r0);
+    float2 w = f2mul(wi, make_float2(pzw.z, pzw.w));
+    if (!keepA) w.x = 0.f;
+    if (!keepB) w.y = 0.f;
+    const float2 scale = f2mul(w, y);
+    const float2 t = f2fma(dq_hi, r, f2mul(dq_lo, r));
+    const SinCos2 b1 = sincos2_f32(t);
+    const float2 s1 = b1.s, c1 = b1.c;
+    const float2 s2 = f2mul(f2add(s1, s1), c1);
+    const float2 c2 = f2fma(f2mul(s1, bc(-2.f)), s1, bc(1.f));
+    const float2 s3 = f2fma(s2, c1, f2mul(c2, s1));
+    // 2cos(2t) = 2 - 4 sin^2 t, rounded stochastically (dither from the pair hash)
+    const float2 mu = f2mul(f2mul(s1, bc(4.f)), s1);
+    const float2 u = f2add(make_float2(__int_as_float(0x3f800000u | (hA >> 9)),
+                                       __int_as_float(0x3f800000u | (hB >> 9))),
+                           bc(-1.5f));
+    const float2 md = f2fma(u, bc(1.1920928955078125e-7f), mu);
+    const float2 C = f2fma(md, bc(-1.f), bc(2.f));
+    const float2 Cn = f2add(md, bc(-2.f));
+    o.CpA = bc(C.x);
+    o.CpB = bc(C.y);
+    o.CnA = bc(Cn.x);
+    o.CnB = bc(Cn.y);
+    if (ZERO_START) {
+        const float2 a1 = f2mul(scale, s1), a2 = f2mul(scale, s2), a3 = f2mul(scale, s3);
+        o.w0A = make_float2(0.f, a1.x);
+        o.w0B = make_float2(0.f, a1.y);
+        o.w1A = make_float2(a2.x, a3.x);
+        o.w1B = make_float2(a2.y, a3.y);
+    } else {
+        const float2 c3 = f2fma(c2, c1, f2mul(s2, f2mul(s1, bc(-1.f))));
+        const SinCos2 ph = sincos2_f32(f2fma(qs_hi, r, f2mul(qs_lo, r)));
+        const float2 S = f2mul(scale, ph.s), Cc = f2mul(scale, ph.c);
+        const float2 v1 = f2fma(S, c1, f2mul(Cc, s1));
+        const float2 v2 = f2fma(S, c2, f2mul(Cc, s2));
+        const float2 v3 = f2fma(S, c3, f2mul(Cc, s3));
+        o.w0A = make_float2(S.x, v1.x);
+        o.w0B = make_float2(S.y, v1.y);
+        o.w1A = make_float2(v2.x, v3.x);
+        o.w1B = make_float2(v2.y, v3.y);
+    }
+}
+
+// Both recurrences over the first NV float2 blocks, in lockstep; slot v receives A then B.
+template <int NB, int NV>
+__device__ __forceinline__ void core2(const PairState2 &p, float2 (&acc)[2 * NB])
+{
+    static_assert(NV >= 2 && NV <= 2 * NB, "slot count out of range");
+    float2 pA = p.w0A, cA = p.w1A, pB = p.w0B, cB = p.w1B;
+    acc[0] = f2add(f2add(acc[0], pA), pB);
+    acc[1] = f2add(f2add(acc[1], cA), cB);
+#pragma unroll
+    for (int v = 1; v + 1 < NV; ++v) {   // W_{v+1} = (+/-)C W_v + W_{v-1}
+        const float2 nA = f2fma(step_negative(v) ? p.CnA : p.CpA, cA, pA);
+        const float2 nB = f2fma(step_negative(v) ? p.CnB : p.CpB, cB, pB);
+        acc[v + 1] = f2add(f2add(acc[v + 1], nA), nB);
+        pA = cA;
+        cA = nA;
+        pB = cB;
+        cB = nB;
+    }
+}
+
+template <int NB, int NV, bool ZERO_START>
+__device__ __forceinline__ void run_pairs2(const float4 *sxy, const float4 *szw, int jpairs, const float4 xi,
+                                           const Item &item, int tid, int jmask, float2 qs_hi, float2 qs_lo,
+                                           float2 dq_hi, float2 dq_lo, float2 (&acc)[2 * NB])
+{
+    const float2 nX = bc(-xi.x), nY = bc(-xi.y), nZ = bc(-xi.z), wi = bc(xi.w);
+    const unsigned ih = item.i0 + tid;
+    for (int k = 0; k < jpairs; ++k) {
+        const int j = 2 * k;
+        PairState2 p;
+        setup2<ZERO_START>(sxy[k], szw[k], nX, nY, nZ, wi, j > jmask, j + 1 > jmask, qs_hi, qs_lo, dq_hi, dq_lo,
+                           pair_hash(ih, item.j0 + j), pair_hash(ih, item.j0 + j + 1), p);
+        core2<NB, NV>(p, acc);
+    }
+}
+
+template <int NB, int NV>
+__global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
+    k_debye_mixed_pairs2(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items,
+                         int n_items, QChunks qc, double *__restrict__ partial, int part_stride, int jmax,
+                         int *__restrict__ ticket)
+{
+    extern __shared__ float4 smem[];
+    float4 *sxy = smem;              // [jmax / 2]: (x_j, x_j+1, y_j, y_j+1)
+    float4 *szw = smem + jmax / 2;   // [jmax / 2]: (z_j, z_j+1, w_j, w_j+1)
+    __shared__ double red[kTile / 32][4 * NB];
+    __shared__ int next_item;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int it = blockIdx.x;   // first item: the CTA's index; then tickets (items sorted by work)
+    while (it < n_items) {
+        const Item item = items[it];
+        const float4 *Xb = X + (int64_t)item.batch * npad;
+        __syncthreads();   // the previous item is done with the staging, red and next_item
+        if (tid == 0) next_item = (int)gridDim.x + atomicAdd(ticket, 1);
+        const int jpairs = (item.jlen + 1) >> 1;
+        for (int k = tid; k < jpairs; k += kTile) {
+            const float4 a = Xb[item.j0 + 2 * k];
+            const float4 b = (2 * k + 1 < item.jlen) ? Xb[item.j0 + 2 * k + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            sxy[k] = make_float4(a.x, b.x, a.y, b.y);
+            szw[k] = make_float4(a.z, b.z, a.w, b.w);
+        }
+        const float4 xi = Xb[item.i0 + tid];
+        __syncthreads();
+        const int ch = item.chunk;
+        const float2 qs_hi = bc(qc.qs_hi[ch]), qs_lo = bc(qc.qs_lo[ch]);
+        const bool zero_start = (qs_hi.x == 0.f) && (qs_lo.x == 0.f);
+        float2 acc[2 * NB];
+#pragma unroll
+        for (int k = 0; k < 2 * NB; ++k) acc[k] = make_float2(0.f, 0.f);
+        const int jmask = item.diag ? tid : -1;   // pairs with j <= i are not pairs of i<j
+        if (zero_start)
+            run_pairs2<NB, NV, true>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi),
+                                     bc(qc.dq_lo), acc);
+        else
+            run_pairs2<NB, NV, false>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi),
+                                      bc(qc.dq_lo), acc);
+        flush_warp<NB, 2>(acc, red[warp], lane);
+        __syncthreads();
+        const int qlen = qc.q_len[ch];
+        for (int k = tid; k < qlen; k += kTile) {
+            double s = red[0][k];
+#pragma unroll
+            for (int w = 1; w < kTile / 32; ++w) s += red[w][k];
+            partial[(int64_t)it * part_stride + k] = s;
+        }
+        it = next_item;
+    }
+}
+
+template <int NB, int NV>
+cudaError_t launch_nv(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
+                      double *partial, int part_stride, int grid, int jmax, int *ticket, cudaStream_t s)
+{
+    const size_t smem = (size_t)jmax * sizeof(float4);
+    cudaError_t e = cudaFuncSetAttribute(k_debye_mixed_pairs2<NB, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    if (grid <= 0) {   // persistent grid: every resident CTA slot of every SM
+        int occ = 0, dev = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_mixed_pairs2<NB, NV>, kTile, smem);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        grid = (occ > 0 ? occ : 1) * sms;
+    }
+    if (grid > n_items) grid = n_items;
+    k_debye_mixed_pairs2<NB, NV><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, partial, part_stride, jmax,
+                                                           ticket);
+    return cudaGetLastError();
+}
+
+// NV: the slots of the longest chunk when within 3 of the capacity 2*NB, else the capacity.
+template <int NB>
+cudaError_t launch_nb2(int nv, const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
+                       double *partial, int part_stride, int grid, int jmax, int *ticket, cudaStream_t s)
+{
+    switch (2 * NB - nv) {
+    case 1:
+        return launch_nv<NB, 2 * NB - 1>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+    case 2:
+        return launch_nv<NB, 2 * NB - 2>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+    case 3:
+        return launch_nv<NB, 2 * NB - 3>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+    default:
+        return launch_nv<NB, 2 * NB>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_debye_mixed_pairs2(const float4 *X, int64_t npad, const Item *items, int n_items,
+                                      const QChunks &qc, double *partial, int part_stride, int grid, int jmax,
+                                      int *ticket, cudaStream_t s)
+{
+    if (n_items == 0) return cudaSuccess;
+    if (jmax % 2 != 0) return cudaErrorInvalidValue;
+    int qmax = 0;
+    for (int c = 0; c < qc.n_chunks; ++c) qmax = qc.q_len[c] > qmax ? qc.q_len[c] : qmax;
+    const int nv = (qmax + 1) / 2;
+    switch (mixed_blocks_for(qmax)) {
+    case 13:
+        return launch_nb2<13>(nv, X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+    case 26:
+        return launch_nb2<26>(nv, X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+    default:
+        return launch_nb2<52>(nv, X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+    }
+}
+
+}  // namespace sas

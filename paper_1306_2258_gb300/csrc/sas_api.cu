@@ -135,15 +135,16 @@ int reseed_for(int opt, int64_t n_atoms)
     return n_atoms < 8192 ? 32 : 0;
 }
 
-// SAS_OPT_VARIANT (0 auto, 1 general, 2 pipelined, 3 sequential) -> kernel variant code.
-// Auto: the pipelined form for the 208-q capacity, the sequential one for smaller capacities
-// (measured on the 50,000-atom globule, 201 q, and the 30,000-atom rod, 101 q).
+// SAS_OPT_VARIANT (0 auto, 1 general, 2 pipelined, 3 sequential, 4 two pairs per step) -> kernel
+// variant code.  Auto: two pairs per step, the fastest form for every q capacity (measured on the
+// 50,000- and 10,000-atom globules, 201 q, and the 30,000-atom rod, 101 q).
 int mixed_variant(int opt, int n_q_max)
 {
     if (opt == 1) return 1;
     if (opt == 2) return 3;
     if (opt == 3) return 4;
-    return mixed_blocks_for(n_q_max) == 52 ? 3 : 4;
+    (void)n_q_max;
+    return 5;
 }
 
 int pair_index(int a, int b, int T)
@@ -756,7 +757,7 @@ sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value)
         ctx->opt_step = (int)value;
         return SAS_OK;
     case SAS_OPT_VARIANT:
-        if (value < 0 || value > 3) return fail(SAS_ERR_INVALID_ARG, "VARIANT must be in [0, 3]");
+        if (value < 0 || value > 4) return fail(SAS_ERR_INVALID_ARG, "VARIANT must be in [0, 4]");
         ctx->opt_variant = (int)value;
         return SAS_OK;
     case SAS_OPT_VALIDATE:

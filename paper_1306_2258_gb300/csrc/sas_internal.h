@@ -75,6 +75,10 @@ cudaError_t launch_assemble(double *S, const double *F, const int *meta, int n_t
 cudaError_t launch_debye_mixed(const float4 *X, int64_t npad, const Item *items, int n_items,
                                const QChunks &qc, int step, int reseed, int variant, double *partial,
                                int part_stride, int grid, int jmax, int *ticket, cudaStream_t s);
+// The two-pairs-per-step form of the 2-step kernel without re-seeding (same arguments and result).
+cudaError_t launch_debye_mixed_pairs2(const float4 *X, int64_t npad, const Item *items, int n_items,
+                                      const QChunks &qc, double *partial, int part_stride, int grid, int jmax,
+                                      int *ticket, cudaStream_t s);
 cudaError_t launch_debye_fp64(const double4 *X, int64_t npad, const Item *items, int n_items,
                               const QChunks &qc, double *partial, int part_stride, int grid,
                               cudaStream_t s);

@@ -1,4 +1,5 @@
-// Single-precision sine and cosine on the FP32 FMA pipe.
+// Single-precision sine and cosine on the FP32 FMA pipe (one argument, or two with packed
+// f32x2 arithmetic).
 //
 // Used for the per-pair seeds of the q recurrence, where the phase can be
 // small (near pairs at low q: the value must keep full relative accuracy, so
@@ -32,13 +33,29 @@ struct SinCos {
     float s, c;
 };
 
+// Constants of the reduction and of the polynomials.
+namespace sc {
+constexpr float kTwoOverPi = 0.636619746685028076171875f;   // float32(2/pi)
+constexpr float kP1 = 1.57079637050628662109375f;            // float32(pi/2)
+constexpr float kP2 = -4.37113882867379300296306610107421875e-08f;
+constexpr float kP3 = -1.71512451000588188257046e-15f;
+constexpr float kRound = 12582912.0f;                        // 1.5 * 2^23: adds to round to integer
+// sin y = y + y^3 * (S3 + y^2 (S5 + y^2 (S7 + y^2 S9))),  Sk = (-1)^((k-1)/2) / k!
+constexpr float kS9 = 2.75573188446287531405687332153320312e-06f;
+constexpr float kS7 = -1.98412701138295233249664306640625e-04f;
+constexpr float kS5 = 8.33333376795053482055664062500000000e-03f;
+constexpr float kS3 = -1.66666671633720397949218750000000000e-01f;
+// cos y = 1 + y^2 (C2 + y^2 (C4 + y^2 (C6 + y^2 (C8 + y^2 C10)))),  Ck = (-1)^(k/2) / k!
+constexpr float kC10 = -2.75573199814971303567290306091308594e-07f;
+constexpr float kC8 = 2.48015876422869041562080383300781250e-05f;
+constexpr float kC6 = -1.38888892251998186111450195312500000e-03f;
+constexpr float kC4 = 4.16666679084300994873046875000000000e-02f;
+constexpr float kC2 = -0.5f;
+}  // namespace sc
+
 __device__ __forceinline__ SinCos sincos_f32(float x)
 {
-    const float kTwoOverPi = 0.636619746685028076171875f;   // float32(2/pi)
-    const float kP1 = 1.57079637050628662109375f;            // float32(pi/2)
-    const float kP2 = -4.37113882867379300296306610107421875e-08f;
-    const float kP3 = -1.71512451000588188257046e-15f;
-    const float kRound = 12582912.0f;                        // 1.5 * 2^23: adds to round to integer
+    using namespace sc;
     float t = fmaf(x, kTwoOverPi, kRound);
     int quad = __float_as_int(t);                            // low bits of t hold n (two's complement)
     float n = t - kRound;
@@ -47,15 +64,13 @@ __device__ __forceinline__ SinCos sincos_f32(float x)
     const float y = yhi + ylo;
     const float d = ylo - (y - yhi);
     float y2 = y * y;
-    // sin y = y + y^3 * (-1/3! + y^2 (1/5! + y^2 (-1/7! + y^2/9!)))
-    float ps = fmaf(y2, 2.75573188446287531405687332153320312e-06f, -1.98412701138295233249664306640625e-04f);
-    ps = fmaf(ps, y2, 8.33333376795053482055664062500000000e-03f);
-    ps = fmaf(ps, y2, -1.66666671633720397949218750000000000e-01f);
-    // cos y = 1 + y^2 (-1/2 + y^2 (1/4! + y^2 (-1/6! + y^2 (1/8! - y^2/10!))))
-    float pc = fmaf(y2, -2.75573199814971303567290306091308594e-07f, 2.48015876422869041562080383300781250e-05f);
-    pc = fmaf(pc, y2, -1.38888892251998186111450195312500000e-03f);
-    pc = fmaf(pc, y2, 4.16666679084300994873046875000000000e-02f);
-    pc = fmaf(pc, y2, -0.5f);
+    float ps = fmaf(y2, kS9, kS7);
+    ps = fmaf(ps, y2, kS5);
+    ps = fmaf(ps, y2, kS3);
+    float pc = fmaf(y2, kC10, kC8);
+    pc = fmaf(pc, y2, kC6);
+    pc = fmaf(pc, y2, kC4);
+    pc = fmaf(pc, y2, kC2);
     const float cm1 = pc * y2;                              // cos y - 1
     const float sy = y + fmaf(ps * y2, y, fmaf(d, cm1, d));  // y + (y^3 P + d cos y)
     const float cy = 1.0f + fmaf(pc, y2, -d * y);            // 1 + (y^2 Q - d sin y)
@@ -64,6 +79,51 @@ __device__ __forceinline__ SinCos sincos_f32(float x)
     r.c = (quad & 1) ? sy : cy;
     if (quad & 2) r.s = -r.s;
     if ((quad + 1) & 2) r.c = -r.c;
+    return r;
+}
+
+// Two arguments at once with packed FP32 arithmetic (one f32x2 instruction per step for both),
+// the same operations and roundings as sincos_f32 lane by lane.  Negations are folded into
+// constants or into multiplications by -1, which are exact.
+struct SinCos2 {
+    float2 s, c;
+};
+
+__device__ __forceinline__ float2 sc_bcast(float v) { return make_float2(v, v); }
+
+// The quadrant of lane value `quad` applied to (sy, cy): swap, then sign flips on the sign bit.
+__device__ __forceinline__ void sc_quadrant(int quad, float sy, float cy, float &s, float &c)
+{
+    const float a = (quad & 1) ? cy : sy, b = (quad & 1) ? sy : cy;
+    s = __int_as_float(__float_as_int(a) ^ ((quad & 2) << 30));
+    c = __int_as_float(__float_as_int(b) ^ (((quad + 1) & 2) << 30));
+}
+
+__device__ __forceinline__ SinCos2 sincos2_f32(float2 x)
+{
+    using namespace sc;
+    const float2 t = __ffma2_rn(x, sc_bcast(kTwoOverPi), sc_bcast(kRound));
+    const float2 n = __fadd2_rn(t, sc_bcast(-kRound));
+    const float2 yhi = __ffma2_rn(n, sc_bcast(-kP1), x);
+    const float2 ylo = __ffma2_rn(n, sc_bcast(-kP2), __fmul2_rn(n, sc_bcast(-kP3)));
+    const float2 y = __fadd2_rn(yhi, ylo);
+    const float2 e = __ffma2_rn(yhi, sc_bcast(-1.f), y);     // y - yhi
+    const float2 d = __ffma2_rn(e, sc_bcast(-1.f), ylo);     // ylo - (y - yhi)
+    const float2 nd = __ffma2_rn(ylo, sc_bcast(-1.f), e);    // -d
+    const float2 y2 = __fmul2_rn(y, y);
+    float2 ps = __ffma2_rn(y2, sc_bcast(kS9), sc_bcast(kS7));
+    ps = __ffma2_rn(ps, y2, sc_bcast(kS5));
+    ps = __ffma2_rn(ps, y2, sc_bcast(kS3));
+    float2 pc = __ffma2_rn(y2, sc_bcast(kC10), sc_bcast(kC8));
+    pc = __ffma2_rn(pc, y2, sc_bcast(kC6));
+    pc = __ffma2_rn(pc, y2, sc_bcast(kC4));
+    pc = __ffma2_rn(pc, y2, sc_bcast(kC2));
+    const float2 cm1 = __fmul2_rn(pc, y2);
+    const float2 sy = __fadd2_rn(y, __ffma2_rn(__fmul2_rn(ps, y2), y, __ffma2_rn(d, cm1, d)));
+    const float2 cy = __fadd2_rn(sc_bcast(1.0f), __ffma2_rn(pc, y2, __fmul2_rn(nd, y)));
+    SinCos2 r;
+    sc_quadrant(__float_as_int(t.x), sy.x, cy.x, r.s.x, r.c.x);
+    sc_quadrant(__float_as_int(t.y), sy.y, cy.y, r.s.y, r.c.y);
     return r;
 }
 

@@ -224,7 +224,7 @@ extern "C" sas_status sas_profile_static(const float *coords, const int32_t *typ
     STATIC_TRY(launch_scatter(coords, 0, types, n, 1, T, blockoffs, meta, nullptr, 0, X, npad, slot_of, s));
     const int reseed = n < 8192 ? 32 : 0;
     STATIC_TRY(cudaMemsetAsync(ticket, 0, sizeof(int), s));
-    STATIC_TRY(launch_debye_mixed(X, npad, items, ni, qc, 2, reseed, reseed == 0 ? 3 : 1, partial, kQChunk, 0,
+    STATIC_TRY(launch_debye_mixed(X, npad, items, ni, qc, 2, reseed, reseed == 0 ? 5 : 1, partial, kQChunk, 0,
                                   kStaticJmax, ticket, s));
     STATIC_TRY(launch_reduce_items(partial, kQChunk, items, group_items, group_off, Pn, qc, S, s));
     STATIC_TRY(launch_assemble(S, F, meta, T, 1, qc, I_out, s));

@@ -79,12 +79,47 @@ def test_c2_10k_mixed_matches_oracle(step, reseed):
     assert _rel(I, ref) <= TOL_MIXED
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_c2_10k_kernel_variants_match_oracle(variant):
     w = wl.c2_globule(10000)
     ref = _oracle_cached(("c2_10k",))
     I = _gpu(w.mol, w.coef, w.q, "mixed", step=2, reseed=0, variant=variant)
     assert _rel(I, ref) <= TOL_MIXED
+
+
+def _variant_case(name):
+    if name == "globule10k_q201":
+        w = wl.c2_globule(10000)
+        return w.mol, w.coef, w.q
+    if name == "rod6k_q101":
+        w = wl.c3_rod()
+        return wl.subsample(w.mol, 6000, 77), w.coef, w.q
+    if name == "globule3k_q300_offset":   # two q chunks, neither starting at q = 0
+        m = wl.random_walk_globule(3000, 4, 78)
+        return m.as_f32(), wl.form_factor_coefficients(4, 79), wl.q_grid(0.05, 1.2, 300)
+    if name == "n37_q51":
+        m = wl.random_walk_globule(37, 3, 80)
+        return m.as_f32(), wl.form_factor_coefficients(3, 81), wl.q_grid(0.0, 0.5, 51)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["globule10k_q201", "rod6k_q101", "globule3k_q300_offset", "n37_q51"])
+def test_two_pair_kernel_is_bitwise_equal_to_one_pair_kernels(name):
+    """Variant 4 (two pairs per step, packed set-up) performs the same operations lane by lane and
+    adds pair j before pair j+1 into every accumulator: I(q) and S_ab(q) equal bit for bit."""
+    mol, coef, q = _variant_case(name)
+    x = torch.as_tensor(mol.coords).cuda()
+    t = torch.as_tensor(mol.types).cuda()
+    out = {}
+    for v in (2, 3, 4):
+        p = Profile(coef, q, "mixed")
+        p.set_option(_lib.SAS_OPT_RESEED, 0)
+        p.set_option(_lib.SAS_OPT_VARIANT, v)
+        out[v] = (p(x, t).cpu().numpy(), p.partials())
+        p.close()
+    for v in (3, 4):
+        assert np.array_equal(out[v][0], out[2][0]), v
+        assert np.array_equal(out[v][1], out[2][1]), v
 
 
 def test_c2_10k_fp64_matches_oracle():
