@@ -125,14 +125,19 @@ bool on_device(const void *p)
 }
 
 // Re-seed interval of the mixed kernel.  The drift of the FP32 recurrence for near pairs is
-// random across pairs, so its effect on I(q) shrinks as the molecule grows; measured with the
-// 2-step recurrence and no re-seeding it is 2.7e-6 at 10,000 and 50,000 atoms but 1.9e-5 at 600
-// atoms.  Automatic: every 32 q values below 8,192 atoms (where the pair work is small anyway),
-// otherwise only at the chunk start.
-int reseed_for(int opt, int64_t n_atoms)
+// random across pairs, so its effect on I(q) shrinks as the molecule grows, and it grows with the
+// number of recurrence steps, i.e. with the q values of a chunk.  Measured with the 2-step
+// recurrence and no re-seeding (max over q and six seeded globules each): 201 q (0..1/A):
+// 2.5e-5 at 600 atoms, 1.0e-5 at 3,000, 6.4e-6 at 8,000, 2.7e-6 at 50,000; 101 q (0..0.5/A):
+// 8.1e-6 at 600, 4.1e-6 at 1,000, 2.8e-6 at 2,000, 1.2e-6 at 5,000 atoms.  Automatic: no
+// re-seeding from 8,192 atoms, or from 2,000 atoms when a chunk holds at most 104 q values;
+// otherwise every 32 q values (at most 3.5e-6 in the same study).
+int reseed_for(int opt, int64_t n_atoms, int n_q_chunk)
 {
     if (opt >= 0) return opt;
-    return n_atoms < 8192 ? 32 : 0;
+    if (n_atoms >= 8192) return 0;
+    if (n_q_chunk <= 104 && n_atoms >= 2000) return 0;
+    return 32;
 }
 
 // SAS_OPT_VARIANT (0 auto, 1 general, 2 pipelined, 3 sequential, 4 two pairs per step) -> kernel
@@ -466,7 +471,8 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
                                    ctx->qc, ctx->partial.as<double>(), kQChunk, grid, s));
     } else {
         CUDA_TRY(launch_debye_mixed(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items,
-                                    ctx->qc, ctx->opt_step, reseed_for(ctx->opt_reseed, n), mixed_variant(ctx->opt_variant, std::min(ctx->n_q, kQChunk)), ctx->partial.as<double>(),
+                                    ctx->qc, ctx->opt_step, reseed_for(ctx->opt_reseed, n, std::min(ctx->n_q, kQChunk)),
+                                    mixed_variant(ctx->opt_variant, std::min(ctx->n_q, kQChunk)), ctx->partial.as<double>(),
                                     kQChunk, ctx->opt_grid > 0 ? ctx->opt_grid * ctx->sms : 0, ctx->jmax_used,
                                     ctx->ticket.as<int>(), s));
     }

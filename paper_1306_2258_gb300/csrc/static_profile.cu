@@ -222,7 +222,9 @@ extern "C" sas_status sas_profile_static(const float *coords, const int32_t *typ
     // pack (padding slots cleared first), pair kernel, item reduction, assembly
     STATIC_TRY(cudaMemsetAsync(X, 0, sizeof(float4) * npad, s));
     STATIC_TRY(launch_scatter(coords, 0, types, n, 1, T, blockoffs, meta, nullptr, 0, X, npad, slot_of, s));
-    const int reseed = n < 8192 ? 32 : 0;
+    // the automatic re-seed rule of sas_profile (no re-seeding from 8,192 atoms, or from 2,000 atoms
+    // when the chunk holds at most 104 q values)
+    const int reseed = (n >= 8192 || (std::min(n_q, kQChunk) <= 104 && n >= 2000)) ? 0 : 32;
     STATIC_TRY(cudaMemsetAsync(ticket, 0, sizeof(int), s));
     STATIC_TRY(launch_debye_mixed(X, npad, items, ni, qc, 2, reseed, reseed == 0 ? 5 : 1, partial, kQChunk, 0,
                                   kStaticJmax, ticket, s));

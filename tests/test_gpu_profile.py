@@ -87,6 +87,32 @@ def test_c2_10k_kernel_variants_match_oracle(variant):
     assert _rel(I, ref) <= TOL_MIXED
 
 
+@pytest.mark.parametrize("case", ["c5_conformers", "c4_conformers", "n1999_q101", "n3000_q201"])
+def test_automatic_reseed_rule_cases_match_oracle(case):
+    """The automatic re-seed rule on both sides of its boundaries: the 2,000-atom ensemble and the
+    5,000-atom refinement conformers (101 q: no re-seeding), 1,999 atoms with 101 q and 3,000 atoms
+    with 201 q (re-seeded)."""
+    if case == "c5_conformers":
+        w = wl.c5_ensemble(n_conf=3)
+        coef, q, types = w["coef"], w["q"], w["base"].types
+        X = w["conformers"]
+    elif case == "c4_conformers":
+        w = wl.c4_refinement(batch=2)
+        coef, q, types = w["coef"], w["q"], w["base"].types
+        X = w["conformers"]
+    else:
+        n, nq = (1999, 101) if case == "n1999_q101" else (3000, 201)
+        m = wl.random_walk_globule(n, 5, 90 + n).as_f32()
+        coef, q, types = wl.form_factor_coefficients(5, 91), wl.q_grid(0.0, 0.5 * (nq - 1) / 100, nq), m.types
+        X = m.coords[None]
+    p = Profile(coef, q, "mixed")
+    I = p(torch.as_tensor(X).cuda(), torch.as_tensor(types).cuda()).cpu().numpy()
+    p.close()
+    for b in range(X.shape[0]):
+        ref = oracle.profile(X[b], types, coef, q)
+        assert _rel(I[b], ref) <= TOL_MIXED, b
+
+
 def _variant_case(name):
     if name == "globule10k_q201":
         w = wl.c2_globule(10000)
