@@ -7,16 +7,20 @@
 //   W_ij = (2 / r^2) (A - B / r),  A = sum_q h_q cos(q r),  B = sum_q (h_q / q) sin(q r),
 //   h_q = g_q f_a(q) f_b(q)   (q = 0 contributes nothing: cos 0 - sinc 0 = 0).
 //
-// Same work items as the forward kernel.  Each thread owns atom i of the
-// I-tile and handles two J atoms per step.  For each pair, cos(q r) and
-// sin(q r) run together as a float2 through the 4-step three-term recurrence
-// (one packed FMA per q), and (A, B) accumulate with a second packed FMA
-// against (h_q, h_q/q), which sits in shared memory and is read as float4
-// broadcasts (one load serves two q values and both pairs).  W_ij is applied
-// at once: the thread's own G_i accumulates in registers, and -W_ij (x_i - x_j)
-// for atom j is summed over the warp with shuffles and over the block in
-// shared memory.  Item totals go to a [batch][slot][3] FP64 array with FP64
+// Same work items as the forward kernel, handed out by the same ticket counter.  Each thread owns
+// atom i of the I-tile and takes the J atoms two at a time: the set-up of pairs (i, j) and
+// (i, j+1) runs in the two lanes of packed f32x2 instructions (the forward kernel's set-up, with
+// the J atoms staged transposed into lane pairs), and then, for each pair, (cos q r, sin q r)
+// runs as a float2 through the 2-step three-term recurrence in two interleaved chains (even and
+// odd q), one packed FMA per q, while (A, B) accumulate with a second packed FMA against
+// (h_q, h_q/q) read from shared memory as float4 broadcasts (one load serves two q values and
+// both pairs).  The chains carry the sign pattern (+, +, -, -) over their blocks, so the packed
+// FMA never negates its addend; the table h holds the same signs, which cancel in the products.
+// W_ij is applied at once: the thread's own G_i accumulates in registers, and -W_ij (x_i - x_j)
+// for atoms j and j+1 (six values) is reduce-scattered over the warp with shuffles and added to
+// shared memory by six lanes.  Item totals go to a [batch][slot][3] FP64 array with FP64
 // atomics.
+#include "mixed_common.cuh"
 #include "sas_internal.h"
 #include "sincos_f32.cuh"
 
@@ -24,190 +28,237 @@ namespace sas {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+using namespace mixed;
 
-__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 bc(float v) { return make_float2(v, v); }
 
-struct PairSetup {
-    float2 prev[4], cur[4];   // (cos, sin) at q_k for the 4 interleaved sequences
-    float2 C4;                // (2 cos 4t, 2 cos 4t)
-    float rinv;
+// Two pairs (A = lane 0, B = lane 1) after set-up.
+struct AdjPair2 {
+    float2 eA0, eA1, oA0, oA1, eB0, eB1, oB0, oB1;   // (cos, sin) at q blocks 0, 1 of the even/odd chains
+    float2 CpA, CnA, CpB, CnB;                       // (C, C) and (-C, -C), C = 2cos(2t)
+    float2 y;                                        // 1/r per lane
+    float2 w;                                        // pair weights w_i w_j (0: no pair)
+    float2 dx, dy, dz;                               // x_j - x_i per lane
 };
 
-__device__ __forceinline__ float coef_sr(float mu, unsigned hash)
+template <bool ZERO_START>
+__device__ __forceinline__ void setup_adj2(const float4 pxy, const float4 pzw, const float2 nX, const float2 nY,
+                                           const float2 nZ, const float2 wi, bool keepA, bool keepB,
+                                           float2 qs_hi, float2 qs_lo, float2 dq_hi, float2 dq_lo, unsigned hA,
+                                           unsigned hB, AdjPair2 &o)
 {
-    const float c = 2.f - mu;
-    const float e = (2.f - c) - mu;
-    const float ulp = __int_as_float(__float_as_int(fabsf(c)) & 0x7f800000) * 1.1920928955078125e-7f;
-    const float u = (float)(hash >> 8) * 5.9604644775390625e-8f;
-    return (u * ulp < fabsf(e)) ? c + copysignf(ulp, e) : c;
+    o.dx = f2add(make_float2(pxy.x, pxy.y), nX);
+    o.dy = f2add(make_float2(pxy.z, pxy.w), nY);
+    o.dz = f2add(make_float2(pzw.x, pzw.y), nZ);
+    float2 r2 = f2fma(o.dz, o.dz, f2fma(o.dy, o.dy, f2mul(o.dx, o.dx)));
+    r2.x = fmaxf(r2.x, 1e-12f);
+    r2.y = fmaxf(r2.y, 1e-12f);
+    o.y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 r0 = f2mul(r2, o.y);
+    const float2 r = f2fma(f2mul(o.y, bc(-0.5f)), f2fma(r0, r0, f2mul(r2, bc(-1.f))), r0);
+    o.w = f2mul(wi, make_float2(pzw.z, pzw.w));
+    if (!keepA) o.w.x = 0.f;
+    if (!keepB) o.w.y = 0.f;
+    const float2 t = f2fma(dq_hi, r, f2mul(dq_lo, r));
+    const SinCos2 b1 = sincos2_f32(t);
+    const float2 s1 = b1.s, c1 = b1.c;
+    const float2 s2 = f2mul(f2add(s1, s1), c1);
+    const float2 c2 = f2fma(f2mul(s1, bc(-2.f)), s1, bc(1.f));
+    const float2 s3 = f2fma(s2, c1, f2mul(c2, s1));
+    const float2 c3 = f2fma(c2, c1, f2mul(s2, f2mul(s1, bc(-1.f))));
+    const float2 mu = f2mul(f2mul(s1, bc(4.f)), s1);
+    const float2 u = f2add(make_float2(__int_as_float(0x3f800000u | (hA >> 9)),
+                                       __int_as_float(0x3f800000u | (hB >> 9))),
+                           bc(-1.5f));
+    const float2 md = f2fma(u, bc(1.1920928955078125e-7f), mu);
+    const float2 C = f2fma(md, bc(-1.f), bc(2.f));
+    const float2 Cn = f2add(md, bc(-2.f));
+    o.CpA = bc(C.x);
+    o.CpB = bc(C.y);
+    o.CnA = bc(Cn.x);
+    o.CnB = bc(Cn.y);
+    if (ZERO_START) {   // phases 0, t, 2t, 3t
+        o.eA0 = make_float2(1.f, 0.f);
+        o.eB0 = make_float2(1.f, 0.f);
+        o.oA0 = make_float2(c1.x, s1.x);
+        o.oB0 = make_float2(c1.y, s1.y);
+        o.eA1 = make_float2(c2.x, s2.x);
+        o.eB1 = make_float2(c2.y, s2.y);
+        o.oA1 = make_float2(c3.x, s3.x);
+        o.oB1 = make_float2(c3.y, s3.y);
+    } else {            // phi0 + (0, t, 2t, 3t): rotations of (cos phi0, sin phi0)
+        const SinCos2 ph = sincos2_f32(f2fma(qs_hi, r, f2mul(qs_lo, r)));
+        const float2 C0 = ph.c, S0 = ph.s, nS0 = f2mul(S0, bc(-1.f));
+        const float2 c_1 = f2fma(C0, c1, f2mul(nS0, s1)), s_1 = f2fma(S0, c1, f2mul(C0, s1));
+        const float2 c_2 = f2fma(C0, c2, f2mul(nS0, s2)), s_2 = f2fma(S0, c2, f2mul(C0, s2));
+        const float2 c_3 = f2fma(C0, c3, f2mul(nS0, s3)), s_3 = f2fma(S0, c3, f2mul(C0, s3));
+        o.eA0 = make_float2(C0.x, S0.x);
+        o.eB0 = make_float2(C0.y, S0.y);
+        o.oA0 = make_float2(c_1.x, s_1.x);
+        o.oB0 = make_float2(c_1.y, s_1.y);
+        o.eA1 = make_float2(c_2.x, s_2.x);
+        o.eB1 = make_float2(c_2.y, s_2.y);
+        o.oA1 = make_float2(c_3.x, s_3.x);
+        o.oB1 = make_float2(c_3.y, s_3.y);
+    }
 }
 
-__device__ __forceinline__ unsigned pair_hash(unsigned i, unsigned j)
+// (A, B) of both pairs: sums over the chunk's NV float2 slots of (h, h/q) * (cos, sin); slot v holds
+// q values 2v (even chain) and 2v+1 (odd chain), sh[v] = sigma_v (h_2v, h_2v/q, h_2v+1, h_2v+1/q).
+template <int NV>
+__device__ __forceinline__ void core_adj2(const AdjPair2 &p, const float4 *sh, float2 &abA, float2 &abB)
 {
-    unsigned h = i * 0x9E3779B1u ^ (j * 0x85EBCA77u + 0x165667B1u);
-    h ^= h >> 15;
-    h *= 0x2C1B3C6Du;
-    h ^= h >> 12;
-    h *= 0x297A2D39u;
-    h ^= h >> 15;
-    return h;
-}
-
-// Distance, seeds and the stochastically rounded coefficient 2cos(4t) of one pair
-// (the same construction as the forward kernel's).
-__device__ __forceinline__ void setup_pair(const float4 xi, const float4 xj, float qs_hi, float qs_lo,
-                                           bool zero_start, float dq_hi, float dq_lo, unsigned hash,
-                                           PairSetup &p)
-{
-    const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-    float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    r2 = fmaxf(r2, 1e-12f);
-    const float r = sqrtf(r2);
-    p.rinv = rsqrtf(r2);
-    const float t = fmaf(dq_hi, r, dq_lo * r);
-    const SinCos b1 = sincos_f32(t);
-    const float c1 = b1.c, s1 = b1.s;
-    // cos(j t), sin(j t), j = 0..7, by angle addition and doubling
-    float cj[8], sj[8];
-    cj[0] = 1.f;
-    sj[0] = 0.f;
-    cj[1] = c1;
-    sj[1] = s1;
-    sj[2] = 2.f * s1 * c1;
-    cj[2] = fmaf(-2.f * s1, s1, 1.f);
-    cj[3] = fmaf(cj[2], c1, -sj[2] * s1);
-    sj[3] = fmaf(sj[2], c1, cj[2] * s1);
-    sj[4] = 2.f * sj[2] * cj[2];
-    cj[4] = fmaf(-2.f * sj[2], sj[2], 1.f);
-    cj[5] = fmaf(cj[4], c1, -sj[4] * s1);
-    sj[5] = fmaf(sj[4], c1, cj[4] * s1);
-    sj[6] = 2.f * sj[3] * cj[3];
-    cj[6] = fmaf(-2.f * sj[3], sj[3], 1.f);
-    cj[7] = fmaf(cj[6], c1, -sj[6] * s1);
-    sj[7] = fmaf(sj[6], c1, cj[6] * s1);
-    const float c4 = coef_sr(4.f * sj[2] * sj[2], hash);
-    p.C4 = make_float2(c4, c4);
-    float S = 0.f, C = 1.f;
-    if (!zero_start) {
-        const SinCos ph = sincos_f32(fmaf(qs_hi, r, qs_lo * r));
-        S = ph.s;
-        C = ph.c;
+    float2 peA = p.eA0, ceA = p.eA1, poA = p.oA0, coA = p.oA1;
+    float2 peB = p.eB0, ceB = p.eB1, poB = p.oB0, coB = p.oB1;
+    float2 aeA, aoA, aeB, aoB;
+    {
+        const float4 h0 = sh[0], h1 = sh[1];
+        const float2 he0 = make_float2(h0.x, h0.y), ho0 = make_float2(h0.z, h0.w);
+        const float2 he1 = make_float2(h1.x, h1.y), ho1 = make_float2(h1.z, h1.w);
+        aeA = f2fma(he1, ceA, f2mul(he0, peA));
+        aoA = f2fma(ho1, coA, f2mul(ho0, poA));
+        aeB = f2fma(he1, ceB, f2mul(he0, peB));
+        aoB = f2fma(ho1, coB, f2mul(ho0, poB));
     }
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {   // cos/sin of (phi0 + j t) = rotation of (C, S) by j t
-        p.prev[m] = make_float2(fmaf(C, cj[m], -S * sj[m]), fmaf(S, cj[m], C * sj[m]));
-        p.cur[m] = make_float2(fmaf(C, cj[m + 4], -S * sj[m + 4]), fmaf(S, cj[m + 4], C * sj[m + 4]));
+    for (int v = 1; v + 1 < NV; ++v) {   // block v+1 = (+/-)C block v + block v-1
+        const float4 h = sh[v + 1];
+        const float2 he = make_float2(h.x, h.y), ho = make_float2(h.z, h.w);
+        const float2 CA = step_negative(v) ? p.CnA : p.CpA, CB = step_negative(v) ? p.CnB : p.CpB;
+        const float2 neA = f2fma(CA, ceA, peA), noA = f2fma(CA, coA, poA);
+        const float2 neB = f2fma(CB, ceB, peB), noB = f2fma(CB, coB, poB);
+        aeA = f2fma(he, neA, aeA);
+        aoA = f2fma(ho, noA, aoA);
+        aeB = f2fma(he, neB, aeB);
+        aoB = f2fma(ho, noB, aoB);
+        peA = ceA;
+        ceA = neA;
+        poA = coA;
+        coA = noA;
+        peB = ceB;
+        ceB = neB;
+        poB = coB;
+        coB = noB;
+    }
+    abA = f2add(aeA, aoA);
+    abB = f2add(aeB, aoB);
+}
+
+// Sum of 8 per-lane values over the warp, scattered: afterwards lane l holds the total of value
+// (l >> 2) when (l & 3) == 0.
+__device__ __forceinline__ float reduce_scatter8(const float (&v)[8], int lane)
+{
+    float a[4];
+    {
+        const bool up = lane & 16;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float mine = up ? v[k + 4] : v[k], other = up ? v[k] : v[k + 4];
+            a[k] = mine + __shfl_xor_sync(kFull, other, 16);
+        }
+    }
+    float b[2];
+    {
+        const bool up = lane & 8;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float mine = up ? a[k + 2] : a[k], other = up ? a[k] : a[k + 2];
+            b[k] = mine + __shfl_xor_sync(kFull, other, 8);
+        }
+    }
+    const bool up = lane & 4;
+    float c = (up ? b[1] : b[0]) + __shfl_xor_sync(kFull, up ? b[0] : b[1], 4);
+    c += __shfl_xor_sync(kFull, c, 2);
+    c += __shfl_xor_sync(kFull, c, 1);
+    return c;
+}
+
+template <int NV, bool ZERO_START>
+__device__ __forceinline__ void run_adj2(const float4 *sxy, const float4 *szw, const float4 *sh, float *gj,
+                                         int jpairs, const float4 xi, const Item &item, int tid, int lane, int jmask,
+                                         float2 qs_hi, float2 qs_lo, float2 dq_hi, float2 dq_lo, float2 &gx,
+                                         float2 &gy, float2 &gz)
+{
+    const float2 nX = bc(-xi.x), nY = bc(-xi.y), nZ = bc(-xi.z), wi = bc(xi.w);
+    const unsigned ih = item.i0 + tid;
+    const int kslot = lane >> 2;   // the value this lane adds after the reduce-scatter
+    for (int k = 0; k < jpairs; ++k) {
+        const int j = 2 * k;
+        AdjPair2 p;
+        setup_adj2<ZERO_START>(sxy[k], szw[k], nX, nY, nZ, wi, j > jmask, j + 1 > jmask, qs_hi, qs_lo, dq_hi, dq_lo,
+                               pair_hash(ih, item.j0 + j), pair_hash(ih, item.j0 + j + 1), p);
+        float2 abA, abB;
+        core_adj2<NV>(p, sh, abA, abB);
+        // -W_ij = w (2/r^2) (B/r - A), per lane; G_i += -W_ij (x_j - x_i)
+        const float2 A = make_float2(abA.x, abB.x), B = make_float2(abA.y, abB.y);
+        const float2 y2 = f2mul(p.y, p.y);
+        const float2 nW = f2mul(f2mul(p.w, f2add(y2, y2)), f2fma(B, p.y, f2mul(A, bc(-1.f))));
+        gx = f2fma(nW, p.dx, gx);
+        gy = f2fma(nW, p.dy, gy);
+        gz = f2fma(nW, p.dz, gz);
+        // atoms j, j+1 receive +W_ij (x_j - x_i)... = -(-W_ij)(x_j - x_i)
+        const float2 fx = f2mul(nW, p.dx), fy = f2mul(nW, p.dy), fz = f2mul(nW, p.dz);
+        const float v[8] = {-fx.x, -fy.x, -fz.x, -fx.y, -fy.y, -fz.y, 0.f, 0.f};
+        const float tot = reduce_scatter8(v, lane);
+        if ((lane & 3) == 0 && kslot < 6) atomicAdd(&gj[3 * j + kslot], tot);
     }
 }
 
-template <int NB>
-__global__ void __launch_bounds__(kTile, 2)
-    k_debye_adjoint(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items,
-                    int n_items, QChunks qc, const float2 *__restrict__ H, int n_pairs, int hstride,
-                    double *__restrict__ G, int jmax)
+template <int NV>
+__global__ void __launch_bounds__(kTile, 4)
+    k_debye_adjoint(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items, int n_items,
+                    QChunks qc, const float2 *__restrict__ H, int n_pairs, int hstride, double *__restrict__ G,
+                    int jcap, int *__restrict__ ticket)
 {
     extern __shared__ float4 smem[];
-    float4 *sj = smem;                                   // [jmax]
-    float4 *sh = smem + jmax;                            // [2*NB]: (h, h/q) for q 2k and 2k+1
-    float *gj = reinterpret_cast<float *>(sh + 2 * NB);  // [jmax][3]
+    float4 *sxy = smem;                                   // [jcap / 2]: (x_j, x_j+1, y_j, y_j+1)
+    float4 *szw = smem + jcap / 2;                        // [jcap / 2]: (z_j, z_j+1, w_j, w_j+1)
+    float4 *sh = smem + jcap;                             // [NV]: signed (h, h/q) for q 2v and 2v+1
+    float *gj = reinterpret_cast<float *>(sh + NV);       // [jcap][3]
+    __shared__ int next_item;
     const int tid = threadIdx.x, lane = tid & 31;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    int it = blockIdx.x;
+    while (it < n_items) {
         const Item item = items[it];
         const float4 *Xb = X + (int64_t)item.batch * npad;
         const int ch = item.chunk;
-        __syncthreads();
-        for (int j = tid; j < item.jlen; j += kTile) {
-            sj[j] = Xb[item.j0 + j];
-            gj[3 * j] = gj[3 * j + 1] = gj[3 * j + 2] = 0.f;
+        __syncthreads();   // the previous item is done with the staging, gj and next_item
+        if (tid == 0) next_item = (int)gridDim.x + atomicAdd(ticket, 1);
+        const int jpairs = (item.jlen + 1) >> 1;
+        for (int k = tid; k < jpairs; k += kTile) {
+            const float4 a = Xb[item.j0 + 2 * k];
+            const float4 b = (2 * k + 1 < item.jlen) ? Xb[item.j0 + 2 * k + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            sxy[k] = make_float4(a.x, b.x, a.y, b.y);
+            szw[k] = make_float4(a.z, b.z, a.w, b.w);
         }
+        for (int k = tid; k < 6 * jpairs; k += kTile) gj[k] = 0.f;
         const float2 *Hc = H + ((int64_t)item.batch * n_pairs + item.pair) * hstride + qc.q_begin[ch];
         const int qlen = qc.q_len[ch];
-        for (int k = tid; k < 2 * NB; k += kTile) {   // zero beyond the chunk's q values
-            const float2 a = (2 * k < qlen) ? Hc[2 * k] : make_float2(0.f, 0.f);
-            const float2 b = (2 * k + 1 < qlen) ? Hc[2 * k + 1] : make_float2(0.f, 0.f);
-            sh[k] = make_float4(a.x, a.y, b.x, b.y);
+        for (int v = tid; v < NV; v += kTile) {   // zero beyond the chunk's q values
+            const float2 a = (2 * v < qlen) ? Hc[2 * v] : make_float2(0.f, 0.f);
+            const float2 b = (2 * v + 1 < qlen) ? Hc[2 * v + 1] : make_float2(0.f, 0.f);
+            const float sg = block_negative(v) ? -1.f : 1.f;
+            sh[v] = make_float4(sg * a.x, sg * a.y, sg * b.x, sg * b.y);
         }
         const float4 xi = Xb[item.i0 + tid];
         __syncthreads();
-        const float qs_hi = qc.qs_hi[ch], qs_lo = qc.qs_lo[ch];
-        const bool zero_start = (qs_hi == 0.f) && (qs_lo == 0.f);
-        const int jmask = item.diag ? tid : -1;
-        float gx = 0.f, gy = 0.f, gz = 0.f;
-        for (int j = 0; j < item.jlen; j += 2) {
-            const float4 xa = sj[j], xb = sj[j + 1];
-            PairSetup pa, pb;
-            setup_pair(xi, xa, qs_hi, qs_lo, zero_start, qc.dq_hi, qc.dq_lo,
-                       pair_hash(item.i0 + tid, item.j0 + j), pa);
-            setup_pair(xi, xb, qs_hi, qs_lo, zero_start, qc.dq_hi, qc.dq_lo,
-                       pair_hash(item.i0 + tid, item.j0 + j + 1), pb);
-            float2 aa[4], ab[4];
-            {
-                const float4 h01 = sh[0], h23 = sh[1], h45 = sh[2], h67 = sh[3];
-                const float2 h[8] = {make_float2(h01.x, h01.y), make_float2(h01.z, h01.w),
-                                     make_float2(h23.x, h23.y), make_float2(h23.z, h23.w),
-                                     make_float2(h45.x, h45.y), make_float2(h45.z, h45.w),
-                                     make_float2(h67.x, h67.y), make_float2(h67.z, h67.w)};
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    aa[m] = f2fma(h[m], pa.prev[m], make_float2(0.f, 0.f));
-                    aa[m] = f2fma(h[m + 4], pa.cur[m], aa[m]);
-                    ab[m] = f2fma(h[m], pb.prev[m], make_float2(0.f, 0.f));
-                    ab[m] = f2fma(h[m + 4], pb.cur[m], ab[m]);
-                }
-            }
-#pragma unroll
-            for (int blk = 2; blk < NB; ++blk) {
-                const float4 hA = sh[2 * blk], hB = sh[2 * blk + 1];
-                const float2 h[4] = {make_float2(hA.x, hA.y), make_float2(hA.z, hA.w),
-                                     make_float2(hB.x, hB.y), make_float2(hB.z, hB.w)};
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    const float2 na = f2fma(pa.C4, pa.cur[m], f2neg(pa.prev[m]));
-                    const float2 nb = f2fma(pb.C4, pb.cur[m], f2neg(pb.prev[m]));
-                    aa[m] = f2fma(h[m], na, aa[m]);
-                    ab[m] = f2fma(h[m], nb, ab[m]);
-                    pa.prev[m] = pa.cur[m];
-                    pa.cur[m] = na;
-                    pb.prev[m] = pb.cur[m];
-                    pb.cur[m] = nb;
-                }
-            }
-            const float Aa = (aa[0].x + aa[1].x) + (aa[2].x + aa[3].x);
-            const float Ba = (aa[0].y + aa[1].y) + (aa[2].y + aa[3].y);
-            const float Ab = (ab[0].x + ab[1].x) + (ab[2].x + ab[3].x);
-            const float Bb = (ab[0].y + ab[1].y) + (ab[2].y + ab[3].y);
-            const float wa = (j <= jmask) ? 0.f : xi.w * xa.w;
-            const float wb = (j + 1 <= jmask) ? 0.f : xi.w * xb.w;
-            const float Wa = wa * 2.f * pa.rinv * pa.rinv * fmaf(-Ba, pa.rinv, Aa);
-            const float Wb = wb * 2.f * pb.rinv * pb.rinv * fmaf(-Bb, pb.rinv, Ab);
-            const float dax = xi.x - xa.x, day = xi.y - xa.y, daz = xi.z - xa.z;
-            const float dbx = xi.x - xb.x, dby = xi.y - xb.y, dbz = xi.z - xb.z;
-            gx = fmaf(Wa, dax, fmaf(Wb, dbx, gx));
-            gy = fmaf(Wa, day, fmaf(Wb, dby, gy));
-            gz = fmaf(Wa, daz, fmaf(Wb, dbz, gz));
-            // atom j receives -W (x_i - x_j): sum over the warp, then over the block
-            float v[6] = {-Wa * dax, -Wa * day, -Wa * daz, -Wb * dbx, -Wb * dby, -Wb * dbz};
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-                for (int c = 0; c < 6; ++c) v[c] += __shfl_xor_sync(kFull, v[c], off);
-            if (lane == 0) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    atomicAdd(&gj[3 * j + c], v[c]);
-                    atomicAdd(&gj[3 * (j + 1) + c], v[3 + c]);
-                }
-            }
-        }
+        const float2 qs_hi = bc(qc.qs_hi[ch]), qs_lo = bc(qc.qs_lo[ch]);
+        const bool zero_start = (qs_hi.x == 0.f) && (qs_lo.x == 0.f);
+        const int jmask = item.diag ? tid : -1;   // pairs with j <= i are not pairs of i<j
+        float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
+        if (zero_start)
+            run_adj2<NV, true>(sxy, szw, sh, gj, jpairs, xi, item, tid, lane, jmask, qs_hi, qs_lo, bc(qc.dq_hi),
+                               bc(qc.dq_lo), gx, gy, gz);
+        else
+            run_adj2<NV, false>(sxy, szw, sh, gj, jpairs, xi, item, tid, lane, jmask, qs_hi, qs_lo, bc(qc.dq_hi),
+                                bc(qc.dq_lo), gx, gy, gz);
         double *Gb = G + (int64_t)item.batch * npad * 3;
-        atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid)], (double)gx);
-        atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid) + 1], (double)gy);
-        atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid) + 2], (double)gz);
+        atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid)], (double)(gx.x + gx.y));
+        atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid) + 1], (double)(gy.x + gy.y));
+        atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid) + 2], (double)(gz.x + gz.y));
         __syncthreads();
-        for (int k = tid; k < 3 * item.jlen; k += kTile)
-            atomicAdd(&Gb[3 * (int64_t)item.j0 + k], (double)gj[k]);
+        for (int k = tid; k < 3 * item.jlen; k += kTile) atomicAdd(&Gb[3 * (int64_t)item.j0 + k], (double)gj[k]);
+        it = next_item;
     }
 }
 
@@ -260,17 +311,39 @@ __global__ void k_unpermute(const double *G, const int *slot_of, int64_t n, int6
     for (int c = 0; c < 3; ++c) grad_out[3 * idx + c] = (float)G[(b * npad + s) * 3 + c];
 }
 
-template <int NB>
-cudaError_t launch_nb(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
-                      const float2 *H, int n_pairs, int hstride, double *G, int grid, int jmax,
-                      cudaStream_t s)
+template <int NV>
+cudaError_t launch_nv(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
+                      const float2 *H, int n_pairs, int hstride, double *G, int jcap, int *ticket, cudaStream_t s)
 {
-    const size_t smem = (size_t)jmax * sizeof(float4) + 2 * NB * sizeof(float4) + (size_t)jmax * 3 * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_debye_adjoint<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const size_t smem = (size_t)jcap * sizeof(float4) + NV * sizeof(float4) + (size_t)jcap * 3 * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_debye_adjoint<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_debye_adjoint<NB><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jmax);
+    int occ = 0, dev = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_adjoint<NV>, kTile, smem)) != cudaSuccess)
+        return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    int grid = (occ > 0 ? occ : 1) * sms;
+    if (grid > n_items) grid = n_items;
+    k_debye_adjoint<NV><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket);
     return cudaGetLastError();
+}
+
+// NV: the slots of the longest chunk when within 3 of the capacity 2*NB, else the capacity.
+template <int NB>
+cudaError_t launch_nb(int nv, const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
+                      const float2 *H, int n_pairs, int hstride, double *G, int jcap, int *ticket, cudaStream_t s)
+{
+    switch (2 * NB - nv) {
+    case 1:
+        return launch_nv<2 * NB - 1>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, s);
+    case 2:
+        return launch_nv<2 * NB - 2>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, s);
+    case 3:
+        return launch_nv<2 * NB - 3>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, s);
+    default:
+        return launch_nv<2 * NB>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, s);
+    }
 }
 
 }  // namespace
@@ -294,18 +367,20 @@ cudaError_t launch_adjoint_coef(const double *g, const double *F, int n_types, i
 
 cudaError_t launch_debye_adjoint(const float4 *X, int64_t npad, const Item *items, int n_items,
                                  const QChunks &qc, const float2 *H, int n_pairs, int hstride, double *G,
-                                 int grid, int jmax, cudaStream_t s)
+                                 int jlen_max, int *ticket, cudaStream_t s)
 {
     if (n_items == 0) return cudaSuccess;
+    const int jcap = (jlen_max + 1) / 2 * 2;
     int qmax = 0;
     for (int c = 0; c < qc.n_chunks; ++c) qmax = qc.q_len[c] > qmax ? qc.q_len[c] : qmax;
+    const int nv = (qmax + 1) / 2;
     switch (mixed_blocks_for(qmax)) {
     case 13:
-        return launch_nb<13>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, grid, jmax, s);
+        return launch_nb<13>(nv, X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, s);
     case 26:
-        return launch_nb<26>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, grid, jmax, s);
+        return launch_nb<26>(nv, X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, s);
     default:
-        return launch_nb<52>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, grid, jmax, s);
+        return launch_nb<52>(nv, X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, s);
     }
 }
 

@@ -178,7 +178,7 @@ struct sas_ctx {
     int *h_meta = nullptr;   // pinned
     // schedule cache
     std::vector<int64_t> sched_key;
-    int n_items = 0, n_groups = 0, jmax_used = 0;
+    int n_items = 0, n_groups = 0, jmax_used = 0, jlen_max = 0;
     int64_t pair_slots = 0;
     int64_t last_batch = 0;
     bool have_partials = false;
@@ -228,6 +228,7 @@ struct Schedule {
     std::vector<int> group_items;   // per group, execution positions in canonical order
     std::vector<int> group_off;     // [n_groups + 1]
     int jmax = 0;
+    int jlen_max = 0;   // longest J-range of the items
     int64_t pair_slots = 0;
 };
 
@@ -292,6 +293,7 @@ void build_schedule(const int *counts, int T, int64_t batch, int tile, int n_chu
                             it.chunk = ch;
                             it.diag = (a == b && j0 == i0) ? 1 : 0;
                             it.work = (int)(jl * tile);
+                            out.jlen_max = std::max(out.jlen_max, it.jlen);
                             canon.push_back(it);
                             canon_group.push_back(g);
                             out.pair_slots += jl * tile;
@@ -397,6 +399,7 @@ sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32
         ctx->n_items = ni;
         ctx->n_groups = ng;
         ctx->jmax_used = sc.jmax;
+        ctx->jlen_max = sc.jlen_max;
         ctx->pair_slots = sc.pair_slots;
         ctx->sched_key = key;
     }
@@ -607,9 +610,11 @@ sas_status adjoint(sas_ctx *ctx, int64_t n, int64_t batch, const double *g_dev, 
     CUDA_TRY(launch_adjoint_coef(g_dev, ctx->F.as<double>(), T, batch, ctx->qc, ctx->H.as<float2>(), Q, s));
     ALLOC_TRY(ctx->G, (size_t)batch * npad * 3 * sizeof(double));
     CUDA_TRY(cudaMemsetAsync(ctx->G.p, 0, (size_t)batch * npad * 3 * sizeof(double), s));
-    const int grid = std::max(1, std::min(ctx->n_items, 2 * ctx->sms));
+    ALLOC_TRY(ctx->ticket, sizeof(int));
+    CUDA_TRY(cudaMemsetAsync(ctx->ticket.p, 0, sizeof(int), s));
     CUDA_TRY(launch_debye_adjoint(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, ctx->qc,
-                                  ctx->H.as<float2>(), Pn, Q, ctx->G.as<double>(), grid, ctx->jmax_used, s));
+                                  ctx->H.as<float2>(), Pn, Q, ctx->G.as<double>(), ctx->jlen_max,
+                                  ctx->ticket.as<int>(), s));
     float *gd = grad_out;
     const bool h = !on_device(grad_out);
     if (h) {

@@ -92,10 +92,11 @@ cudaError_t launch_chi2(const double *I, const double *T, const double *w, int n
 // H[b][p][k] = (g f_a f_b, g f_a f_b / q) as float2, row stride hstride
 cudaError_t launch_adjoint_coef(const double *g, const double *F, int n_types, int64_t batch,
                                 const QChunks &qc, float2 *H, int hstride, cudaStream_t s);
-// G[b][slot][3] += d(sum_q g_q I(q)) / dx (G must be zeroed); jmax <= 2048
+// G[b][slot][3] += d(sum_q g_q I(q)) / dx (G must be zeroed); jlen_max: the longest J-range of
+// the items (sets the shared memory); ticket: one device int, zero when the kernel starts.
 cudaError_t launch_debye_adjoint(const float4 *X, int64_t npad, const Item *items, int n_items,
                                  const QChunks &qc, const float2 *H, int n_pairs, int hstride, double *G,
-                                 int grid, int jmax, cudaStream_t s);
+                                 int jlen_max, int *ticket, cudaStream_t s);
 cudaError_t launch_unpermute(const double *G, const int *slot_of, int64_t n, int64_t npad, int64_t batch,
                              float *grad_out, cudaStream_t s);
 
