@@ -17,46 +17,71 @@ namespace {
 
 constexpr int kWarps = kTile / 32;
 
+// Bin of r2 under the rule above: max{k : e_k^2 <= r2} with e_k^2 = fl(fl(k w)^2), capped at
+// n_bins.  The first guess comes from the hardware reciprocal square root; the edge comparisons
+// (the rule's own float32 roundings) decide.
+__device__ __forceinline__ int bin_of(float r2, float w, float inv_w, int n_bins)
+{
+    const float nb = (float)n_bins;
+    float k = fminf(floorf(r2 * rsqrtf(fmaxf(r2, 1e-30f)) * inv_w), nb);
+    k = fmaxf(k, 0.f);
+    for (int guard = 0; guard < 8 && k > 0.f; ++guard) {   // never more than a step or two
+        const float ek = __fmul_rn(k, w);
+        if (__fmul_rn(ek, ek) <= r2) break;
+        k -= 1.f;
+    }
+    for (int guard = 0; guard < 8 && k < nb; ++guard) {
+        const float ek = __fmul_rn(k + 1.f, w);
+        if (__fmul_rn(ek, ek) > r2) break;
+        k += 1.f;
+    }
+    return (int)k;
+}
+
+// One work item per CTA at a time.  Warp v takes the real rows i = v, v+4, ... of the I-tile (the
+// padding slots at the end of a type group are skipped) and its lanes take 32 consecutive J atoms
+// at a time, so every lane holds a real pair except at the end of a row.  Counts go to one shared
+// histogram per warp, then to the global histogram with integer atomics.
 __global__ void __launch_bounds__(kTile)
-    k_pair_histogram(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items,
-                     int n_items, int n_bins, float r_max, int n_pairs, int *__restrict__ hist,
-                     unsigned long long *__restrict__ dropped, int jmax)
+    k_pair_histogram(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items, int n_items,
+                     int n_bins, float r_max, int n_pairs, int *__restrict__ hist,
+                     unsigned long long *__restrict__ dropped, int jcap, int *__restrict__ ticket)
 {
     extern __shared__ float4 smem[];
-    float4 *sj = smem;                                            // [jmax]
-    float *e2 = reinterpret_cast<float *>(sj + jmax);             // [n_bins + 1]
-    int *wh = reinterpret_cast<int *>(e2 + n_bins + 1);           // [kWarps][n_bins]
+    float4 *sj = smem;                                            // [jcap]
+    float4 *si = sj + jcap;                                       // [kTile]
+    int *wh = reinterpret_cast<int *>(si + kTile);                // [kWarps][n_bins]
+    __shared__ int next_item;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float w = __fdiv_rn(r_max, (float)n_bins);
     const float inv_w = __fdiv_rn(1.0f, w);
-    for (int k = tid; k <= n_bins; k += kTile) {
-        const float ek = __fmul_rn((float)k, w);
-        e2[k] = __fmul_rn(ek, ek);
-    }
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    int it = blockIdx.x;
+    while (it < n_items) {
         const Item item = items[it];
         const float4 *Xb = X + (int64_t)item.batch * npad;
-        __syncthreads();
+        __syncthreads();   // the previous item is done with the staging, histograms and next_item
+        if (tid == 0) next_item = (int)gridDim.x + atomicAdd(ticket, 1);
         for (int j = tid; j < item.jlen; j += kTile) sj[j] = Xb[item.j0 + j];
         for (int k = tid; k < kWarps * n_bins; k += kTile) wh[k] = 0;
-        const float4 xi = Xb[item.i0 + tid];
-        __syncthreads();
-        const int jmask = item.diag ? tid : -1;
+        const float4 xt = Xb[item.i0 + tid];
+        si[tid] = xt;
+        // real atoms are a prefix of the tile (padding sits at the end of each type group)
+        const int ilen = __syncthreads_count(xt.w != 0.f);
+        int *h = wh + warp * n_bins;
         unsigned drop = 0;
-        if (xi.w != 0.f) {
-            for (int j = jmask + 1; j < item.jlen; ++j) {
+        for (int i = warp; i < ilen; i += kWarps) {
+            const float4 xi = si[i];
+            const int jstart = item.diag ? i + 1 : 0;   // pairs with j <= i are not pairs of i<j
+            for (int j = jstart + lane; j < item.jlen; j += 32) {
                 const float4 xj = sj[j];
                 if (xj.w == 0.f) continue;
-                const float dx = __fsub_rn(xi.x, xj.x), dy = __fsub_rn(xi.y, xj.y),
-                            dz = __fsub_rn(xi.z, xj.z);
+                const float dx = __fsub_rn(xi.x, xj.x), dy = __fsub_rn(xi.y, xj.y), dz = __fsub_rn(xi.z, xj.z);
                 const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                int k = (int)fminf(__fmul_rn(__fsqrt_rn(r2), inv_w), (float)n_bins);
-                while (k > 0 && e2[k] > r2) --k;
-                while (k < n_bins && e2[k + 1] <= r2) ++k;
+                const int k = bin_of(r2, w, inv_w, n_bins);
                 if (k >= n_bins)
                     ++drop;
                 else
-                    atomicAdd(&wh[warp * n_bins + k], 1);
+                    atomicAdd(&h[k], 1);
             }
         }
         for (int o = 16; o > 0; o >>= 1) drop += __shfl_xor_sync(0xffffffffu, drop, o);
@@ -64,33 +89,40 @@ __global__ void __launch_bounds__(kTile)
         __syncthreads();
         int *hb = hist + ((int64_t)item.batch * n_pairs + item.pair) * n_bins;
         for (int k = tid; k < n_bins; k += kTile) {
-            int s = 0;
+            int sum = 0;
 #pragma unroll
-            for (int v = 0; v < kWarps; ++v) s += wh[v * n_bins + k];
-            if (s) atomicAdd(&hb[k], s);
+            for (int v = 0; v < kWarps; ++v) sum += wh[v * n_bins + k];
+            if (sum) atomicAdd(&hb[k], sum);
         }
+        it = next_item;
     }
 }
 
 }  // namespace
 
-size_t histogram_smem(int jmax, int n_bins)
+size_t histogram_smem(int jcap, int n_bins)
 {
-    return (size_t)jmax * sizeof(float4) + (size_t)(n_bins + 1) * sizeof(float) +
-           (size_t)kWarps * n_bins * sizeof(int);
+    return (size_t)(jcap + kTile) * sizeof(float4) + (size_t)kWarps * n_bins * sizeof(int);
 }
 
 cudaError_t launch_pair_histogram(const float4 *X, int64_t npad, const Item *items, int n_items,
                                   int n_bins, float r_max, int n_pairs, int *hist,
-                                  unsigned long long *dropped, int grid, int jmax, cudaStream_t s)
+                                  unsigned long long *dropped, int jlen_max, int *ticket, cudaStream_t s)
 {
     if (n_items == 0) return cudaSuccess;
-    const size_t smem = histogram_smem(jmax, n_bins);
+    const size_t smem = histogram_smem(jlen_max, n_bins);
     cudaError_t e = cudaFuncSetAttribute(k_pair_histogram, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_pair_histogram<<<grid, kTile, smem, s>>>(X, npad, items, n_items, n_bins, r_max, n_pairs, hist,
-                                               dropped, jmax);
+    int occ = 0, dev = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair_histogram, kTile, smem)) != cudaSuccess)
+        return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    int grid = (occ > 0 ? occ : 1) * sms;
+    if (grid > n_items) grid = n_items;
+    k_pair_histogram<<<grid, kTile, smem, s>>>(X, npad, items, n_items, n_bins, r_max, n_pairs, hist, dropped,
+                                               jlen_max, ticket);
     return cudaGetLastError();
 }
 

@@ -897,10 +897,11 @@ sas_status sas_pair_histogram(sas_ctx *ctx, const float *coords, const int32_t *
     ALLOC_TRY(ctx->dropped, (size_t)batch * sizeof(int64_t));
     CUDA_TRY(cudaMemsetAsync(ctx->hist.p, 0, hbytes, s));
     CUDA_TRY(cudaMemsetAsync(ctx->dropped.p, 0, (size_t)batch * sizeof(int64_t), s));
-    const int grid = std::max(1, std::min(ctx->n_items, 4 * ctx->sms));
+    ALLOC_TRY(ctx->ticket, sizeof(int));
+    CUDA_TRY(cudaMemsetAsync(ctx->ticket.p, 0, sizeof(int), s));
     CUDA_TRY(launch_pair_histogram(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, n_bins,
                                    r_max, Pn, ctx->hist.as<int>(), ctx->dropped.as<unsigned long long>(),
-                                   grid, ctx->jmax_used, s));
+                                   ctx->jlen_max, ctx->ticket.as<int>(), s));
     launches += 1;
     HostCopies hc;
     st = out_copy(hc, hist_out, ctx->hist.p, hbytes, s);

@@ -101,10 +101,11 @@ cudaError_t launch_unpermute(const double *G, const int *slot_of, int64_t n, int
                              float *grad_out, cudaStream_t s);
 
 // ---- histogram (histogram.cu) -----------------------------------------------------
-size_t histogram_smem(int jmax, int n_bins);
+size_t histogram_smem(int jcap, int n_bins);
+// jlen_max: the longest J-range of the items; ticket: one device int, zero when the kernel starts.
 cudaError_t launch_pair_histogram(const float4 *X, int64_t npad, const Item *items, int n_items,
                                   int n_bins, float r_max, int n_pairs, int *hist,
-                                  unsigned long long *dropped, int grid, int jmax, cudaStream_t s);
+                                  unsigned long long *dropped, int jlen_max, int *ticket, cudaStream_t s);
 
 // ---- MLP (mlp.cu) -------------------------------------------------------------------
 // C[M][N] = A[M][K] B[N][K]^T (+ bias); bfloat16 A, B (K % 16 == 0, ld % 8 == 0, 16-byte
