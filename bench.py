@@ -174,6 +174,14 @@ def aggregate(tot_ms: float, units_per_step: float, steps: int, world: int, devi
     return max_ms, float(u.item()) / (max_ms / 1e3)
 
 
+def _measured_peak(key):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def _timed(fn, stream, reps=3):
     """Median CUDA-event time (ms) of fn() on `stream` after one untimed call."""
     import torch
@@ -273,6 +281,19 @@ def run_rows(dev, stream):
                          "value": B5 / (ms / 1e3), "unit": "conformers screened/s"}
     net.close()
     p.close()
+
+    # the surrogate's GEMM (tcgen05, TMA-fed) on a large square problem, against the measured peak
+    G = 8192
+    gA = torch.randn((G, G), device=dev).to(torch.bfloat16)
+    gB = torch.randn((G, G), device=dev).to(torch.bfloat16)
+    gC = torch.empty((G, G), dtype=torch.float32, device=dev)
+    ms = _timed(lambda: _lib.sas_gemm_bf16(G, G, G, gA, G, gB, G, None, gC, G, stream), stream)
+    tflops = 2.0 * G ** 3 / (ms / 1e3) / 1e12
+    peak = _measured_peak("bf16_tflops")
+    rows["gemm_bf16_tcgen05"] = {"workload": f"{G}^3 bf16 -> fp32 (C = A B^T)", "ms": ms, "value": tflops,
+                                 "unit": "TFLOP/s", "peak": peak, "frac": (tflops / peak) if peak else None,
+                                 "peak_basis": "cuBLAS bf16 burst, MEASURED_PEAKS.json"}
+    del gA, gB, gC
     return rows
 
 

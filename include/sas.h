@@ -221,7 +221,9 @@ sas_status sas_mlp_grads(sas_mlp *mlp, const float *x, const float *t, int batch
                          void *stream);
 
 /* C[M][N] = A[M][K] B[N][K]^T (+ bias[N]): bfloat16 A and B (device, K contiguous, 16-byte aligned,
- * K % 16 == 0, lda and ldb multiples of 8), float32 C (device), FP32 accumulation. */
+ * K % 16 == 0, lda and ldb multiples of 8), float32 C (device), FP32 accumulation on the tcgen05
+ * tensor cores (TMA-fed shared-memory stages, accumulator in tensor memory).  Asynchronous on the
+ * stream; a failed internal wait is reported by the next synchronizing sas_mlp_* call. */
 sas_status sas_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
                          float *C, int ldc, void *stream);
 

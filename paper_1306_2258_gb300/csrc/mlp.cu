@@ -4,7 +4,8 @@
 // I(q) directly, Section I-A, Eq. 2); it ranks conformers before the exact kernel re-scores them.
 //
 // Kernels:
-//   k_gemm_tn      C[M][N] = A[M][K] B[N][K]^T (+ bias), A and B bfloat16 with K contiguous,
+//   k_gemm_tn      C[M][N] = A[M][K] B[N][K]^T (+ bias), A and B bfloat16 with K contiguous (the
+//                  fallback of the tcgen05 GEMM in gemm_tc.cu for operands TMA cannot describe),
 //                  FP32 accumulation with mma.sync m16n8k16 (64x64 CTA tile, four 32x32 warp
 //                  tiles); epilogue writes FP32 and/or bfloat16 of the value or of GELU(value).
 //   k_transpose    bfloat16 [R][C] -> [C][R] (the backward GEMMs' operands)

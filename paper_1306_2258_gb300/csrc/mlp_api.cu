@@ -34,6 +34,14 @@ sas_status mlp_fail(sas_status st, const char *what, cudaError_t e = cudaSuccess
         if (e_ != cudaSuccess) return mlp_fail(SAS_ERR_CUDA, #call, e_);       \
     } while (0)
 
+// After a synchronization: the tensor-core GEMM's error word (a wait that ran out of iterations).
+sas_status gemm_check()
+{
+    int err = 0;
+    MLP_TRY(gemm_tc_error(&err));
+    return err ? mlp_fail(SAS_ERR_TIMEOUT, "a tensor-core GEMM wait ran out of iterations") : SAS_OK;
+}
+
 bool on_device_ptr(const void *p)
 {
     cudaPointerAttributes a;
@@ -101,10 +109,10 @@ sas_status mlp_forward(sas_mlp *m, const float *x, const float *t, int B, cudaSt
     }
     MLP_TRY(launch_to_bf16((int64_t)B * m->n_in, xd, m->Xb, s));
     const bf16 *W1b = m->Pb + m->oW1, *W2b = m->Pb + m->oW2, *W3b = m->Pb + m->oW3;
-    MLP_TRY(launch_gemm_tn(B, m->h, m->n_in, m->Xb, m->n_in, W1b, m->n_in, m->P + m->ob1, m->Z1, m->h, m->A1b, m->h, 1,
+    MLP_TRY(launch_gemm(B, m->h, m->n_in, m->Xb, m->n_in, W1b, m->n_in, m->P + m->ob1, m->Z1, m->h, m->A1b, m->h, 1,
                            s));
-    MLP_TRY(launch_gemm_tn(B, m->h, m->h, m->A1b, m->h, W2b, m->h, m->P + m->ob2, m->Z2, m->h, m->A2b, m->h, 1, s));
-    MLP_TRY(launch_gemm_tn(B, m->n_outp, m->h, m->A2b, m->h, W3b, m->h, m->P + m->ob3, m->Y, m->n_outp, nullptr, 0, 0,
+    MLP_TRY(launch_gemm(B, m->h, m->h, m->A1b, m->h, W2b, m->h, m->P + m->ob2, m->Z2, m->h, m->A2b, m->h, 1, s));
+    MLP_TRY(launch_gemm(B, m->n_outp, m->h, m->A2b, m->h, W3b, m->h, m->P + m->ob3, m->Y, m->n_outp, nullptr, 0, 0,
                            s));
     (void)Bp;
     return SAS_OK;
@@ -118,21 +126,21 @@ sas_status mlp_backward(sas_mlp *m, int B, cudaStream_t s)
     // layer 3
     MLP_TRY(launch_transpose_bf16(Bp, Bp, Qp, m->dYb, Qp, m->dYt, Bp, s));
     MLP_TRY(launch_transpose_bf16(B, Bp, h, m->A2b, h, m->A2t, Bp, s));
-    MLP_TRY(launch_gemm_tn(Qp, h, Bp, m->dYt, Bp, m->A2t, Bp, nullptr, m->G + m->oW3, h, nullptr, 0, 0, s));
+    MLP_TRY(launch_gemm(Qp, h, Bp, m->dYt, Bp, m->A2t, Bp, nullptr, m->G + m->oW3, h, nullptr, 0, 0, s));
     MLP_TRY(launch_colsum(Bp, Qp, m->dY, Qp, m->G + m->ob3, s));
-    MLP_TRY(launch_gemm_tn(B, h, Qp, m->dYb, Qp, m->W3t, Qp, nullptr, m->dA2, h, nullptr, 0, 0, s));
+    MLP_TRY(launch_gemm(B, h, Qp, m->dYb, Qp, m->W3t, Qp, nullptr, m->dA2, h, nullptr, 0, 0, s));
     // layer 2
     MLP_TRY(launch_gelu_bwd((int64_t)B * h, m->dA2, m->Z2, m->dZ2, m->dZ2b, s));
     MLP_TRY(launch_transpose_bf16(B, Bp, h, m->dZ2b, h, m->dZ2t, Bp, s));
     MLP_TRY(launch_transpose_bf16(B, Bp, h, m->A1b, h, m->A1t, Bp, s));
-    MLP_TRY(launch_gemm_tn(h, h, Bp, m->dZ2t, Bp, m->A1t, Bp, nullptr, m->G + m->oW2, h, nullptr, 0, 0, s));
+    MLP_TRY(launch_gemm(h, h, Bp, m->dZ2t, Bp, m->A1t, Bp, nullptr, m->G + m->oW2, h, nullptr, 0, 0, s));
     MLP_TRY(launch_colsum(B, h, m->dZ2, h, m->G + m->ob2, s));
-    MLP_TRY(launch_gemm_tn(B, h, h, m->dZ2b, h, m->W2t, h, nullptr, m->dA1, h, nullptr, 0, 0, s));
+    MLP_TRY(launch_gemm(B, h, h, m->dZ2b, h, m->W2t, h, nullptr, m->dA1, h, nullptr, 0, 0, s));
     // layer 1
     MLP_TRY(launch_gelu_bwd((int64_t)B * h, m->dA1, m->Z1, m->dZ1, m->dZ1b, s));
     MLP_TRY(launch_transpose_bf16(B, Bp, h, m->dZ1b, h, m->dZ1t, Bp, s));
     MLP_TRY(launch_transpose_bf16(B, Bp, m->n_in, m->Xb, m->n_in, m->Xt, Bp, s));
-    MLP_TRY(launch_gemm_tn(h, m->n_in, Bp, m->dZ1t, Bp, m->Xt, Bp, nullptr, m->G + m->oW1, m->n_in, nullptr, 0, 0, s));
+    MLP_TRY(launch_gemm(h, m->n_in, Bp, m->dZ1t, Bp, m->Xt, Bp, nullptr, m->G + m->oW1, m->n_in, nullptr, 0, 0, s));
     MLP_TRY(launch_colsum(B, h, m->dZ1, h, m->G + m->ob1, s));
     return SAS_OK;
 }
@@ -280,7 +288,10 @@ sas_status sas_mlp_forward(sas_mlp *m, const float *x, int batch, float *y, void
     const bool host = !on_device_ptr(y);
     MLP_TRY(cudaMemcpy2DAsync(y, sizeof(float) * m->n_out, m->Y, sizeof(float) * m->n_outp, sizeof(float) * m->n_out,
                               batch, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
-    if (host) MLP_TRY(cudaStreamSynchronize(s));
+    if (host) {
+        MLP_TRY(cudaStreamSynchronize(s));
+        return gemm_check();
+    }
     return SAS_OK;
 }
 
@@ -293,6 +304,7 @@ sas_status sas_mlp_grads(sas_mlp *m, const float *x, const float *t, int batch, 
     if (st == SAS_OK) st = mlp_backward(m, batch, s);
     if (st != SAS_OK) return st;
     MLP_TRY(cudaStreamSynchronize(s));
+    if ((st = gemm_check()) != SAS_OK) return st;
     if (grads && (st = copy_block(m, m->G, grads)) != SAS_OK) return st;
     if (loss_out) MLP_TRY(cudaMemcpy(loss_out, m->loss, sizeof(float), cudaMemcpyDefault));
     return SAS_OK;
@@ -315,7 +327,10 @@ sas_status sas_mlp_train_step(sas_mlp *m, const float *x, const float *t, int ba
         const bool host = !on_device_ptr(loss_out);
         MLP_TRY(cudaMemcpyAsync(loss_out, m->loss, sizeof(float), host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                                 s));
-        if (host) MLP_TRY(cudaStreamSynchronize(s));
+        if (host) {
+            MLP_TRY(cudaStreamSynchronize(s));
+            return gemm_check();
+        }
     }
     return SAS_OK;
 }
@@ -328,7 +343,7 @@ sas_status sas_gemm_bf16(int M, int N, int K, const void *A, int lda, const void
     if ((M && N && K) && (!A || !B || !C)) return mlp_fail(SAS_ERR_INVALID_ARG, "null argument");
     if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15)
         return mlp_fail(SAS_ERR_INVALID_ARG, "A and B must be 16-byte aligned");
-    MLP_TRY(launch_gemm_tn(M, N, K, A, lda, B, ldb, bias, C, ldc, nullptr, 0, 0, (cudaStream_t)stream));
+    MLP_TRY(launch_gemm(M, N, K, A, lda, B, ldb, bias, C, ldc, nullptr, 0, 0, (cudaStream_t)stream));
     return SAS_OK;
 }
 

@@ -112,6 +112,16 @@ cudaError_t launch_pair_histogram(const float4 *X, int64_t npad, const Item *ite
 // aligned), FP32 C (may be null); D (bfloat16, may be null) gets the value or GELU(value).
 cudaError_t launch_gemm_tn(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
                            float *C, int ldc, void *D, int ldd, int gelu, cudaStream_t s);
+// The same product on the tcgen05 tensor cores (TMA-fed, TMEM accumulator); usable when
+// gemm_tc_supported(K, A, lda, B, ldb).  gemm_tc_error reads the device error word (nonzero after
+// a wait inside the kernel ran out of iterations).
+bool gemm_tc_supported(int K, const void *A, int lda, const void *B, int ldb);
+cudaError_t launch_gemm_tc(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
+                           float *C, int ldc, void *D, int ldd, int gelu, cudaStream_t s);
+cudaError_t gemm_tc_error(int *err);
+// launch_gemm_tc where supported, else launch_gemm_tn.
+cudaError_t launch_gemm(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
+                        float *C, int ldc, void *D, int ldd, int gelu, cudaStream_t s);
 cudaError_t launch_to_bf16(int64_t n, const float *x, void *y, cudaStream_t s);
 cudaError_t launch_transpose_bf16(int R, int Rpad, int C, const void *in, int ldin, void *out, int ldout,
                                   cudaStream_t s);

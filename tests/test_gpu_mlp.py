@@ -22,7 +22,8 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("M,N,K", [(200, 130, 96), (64, 64, 3840), (1, 7, 16), (257, 512, 512)])
+@pytest.mark.parametrize("M,N,K", [(200, 130, 96), (64, 64, 3840), (1, 7, 16), (257, 512, 512), (256, 512, 3840),
+                                   (300, 1000, 208), (128, 64, 64)])
 def test_gemm_bf16_matches_fp64(M, N, K):
     rng = np.random.default_rng(M + N + K)
     A = torch.from_numpy(rng.standard_normal((M, K)).astype(np.float32)).to(torch.bfloat16).cuda()
