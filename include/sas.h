@@ -227,6 +227,24 @@ sas_status sas_mlp_grads(sas_mlp *mlp, const float *x, const float *t, int batch
 sas_status sas_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
                          float *C, int ldc, void *stream);
 
+/*
+ * Screening of a conformer ensemble (the high-throughput setting of Section I; not part of the
+ * paper's method): chi2_c = sum_q w_q (exp(z_cq stdv_q + mean_q) - target_q)^2 for n_conf
+ * standardized log-profiles z (float32, row stride ld), written to chi2_all [n_conf]; then the
+ * indices of the k smallest chi2 in increasing order (equal values by index, NaN last) to top_idx
+ * [k] and their chi2 to top_chi2 [k] (may be NULL).  Every buffer is device memory; chi2_all is
+ * required.  Limits: 1 <= n_conf <= 8192 (one CTA sorts them in shared memory), 1 <= k <= n_conf,
+ * ld >= n_q.  Asynchronous on the stream.
+ */
+sas_status sas_screen_select(int n_conf, int n_q, const float *z, int ld, const double *mean, const double *stdv,
+                             const double *target, const double *weights, int k, int32_t *top_idx, double *top_chi2,
+                             double *chi2_all, void *stream);
+
+/* dst[r] = src[idx[r]] for r < n_idx, rows of row_bytes bytes (device src, idx, dst; idx values
+ * must address rows of src).  Packs selected conformers for the exact kernels. */
+sas_status sas_gather_rows(const void *src, int64_t row_bytes, const int32_t *idx, int64_t n_idx, void *dst,
+                           void *stream);
+
 /* Thread-local message of the calling thread's last failure ("" if none). */
 const char *sas_last_error(void);
 

@@ -28,7 +28,7 @@ EXPORTS = (
     "sas_profile_vjp", "sas_partials", "sas_pair_histogram", "sas_set_option", "sas_last_stats",
     "sas_last_error", "sas_version", "sas_profile_static", "sas_mlp_create", "sas_mlp_destroy",
     "sas_mlp_param_count", "sas_mlp_set_state", "sas_mlp_get_state", "sas_mlp_forward", "sas_mlp_train_step",
-    "sas_mlp_grads", "sas_gemm_bf16",
+    "sas_mlp_grads", "sas_gemm_bf16", "sas_screen_select", "sas_gather_rows",
 )
 
 
@@ -74,6 +74,8 @@ def load():
                 "sas_mlp_train_step": [_vp, _vp, _vp, _int, ctypes.c_float, _vp, _vp],
                 "sas_mlp_grads": [_vp, _vp, _vp, _int, _vp, _vp, _vp],
                 "sas_gemm_bf16": [_int, _int, _int, _vp, _int, _vp, _int, _vp, _vp, _int, _vp],
+                "sas_screen_select": [_int, _int, _vp, _int, _vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _vp],
+                "sas_gather_rows": [_vp, _i64, _vp, _i64, _vp, _vp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -230,6 +232,17 @@ def sas_mlp_grads(mlp, x, t, batch, grads, loss_out=None, stream=None):
 def sas_gemm_bf16(M, N, K, A, lda, B, ldb, bias, C, ldc, stream=None):
     check(load().sas_gemm_bf16(int(M), int(N), int(K), ptr(A), int(lda), ptr(B), int(ldb), ptr(bias), ptr(C),
                                int(ldc), stream_handle(stream)))
+
+
+def sas_screen_select(n_conf, n_q, z, ld, mean, stdv, target, weights, k, top_idx, top_chi2, chi2_all,
+                      stream=None):
+    check(load().sas_screen_select(int(n_conf), int(n_q), ptr(z), int(ld), ptr(mean), ptr(stdv), ptr(target),
+                                   ptr(weights), int(k), ptr(top_idx), ptr(top_chi2), ptr(chi2_all),
+                                   stream_handle(stream)))
+
+
+def sas_gather_rows(src, row_bytes, idx, n_idx, dst, stream=None):
+    check(load().sas_gather_rows(ptr(src), int(row_bytes), ptr(idx), int(n_idx), ptr(dst), stream_handle(stream)))
 
 
 def sas_last_error() -> str:

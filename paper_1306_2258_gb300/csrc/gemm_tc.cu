@@ -7,7 +7,7 @@
 // One CTA computes a 128 x BN tile (BN = 64 or 128) with four warps:
 //  * thread 0 streams K in slices of 64 (one 128-byte row of bfloat16 per tile row) with 2-D TMA
 //    loads (cp.async.bulk.tensor, 128-byte swizzle, zero fill outside the matrices) into a ring
-//    of 4 shared-memory stages, each guarded by a "full" mbarrier (transaction bytes);
+//    of shared-memory stages, each guarded by a "full" mbarrier (transaction bytes);
 //  * thread 32 issues tcgen05.mma (kind::f16, M = 128, N = BN, K = 16) from shared-memory matrix
 //    descriptors into an FP32 accumulator in tensor memory, and frees a stage by committing the
 //    stage's MMAs to its "empty" mbarrier; a last commit signals "done";
@@ -29,7 +29,6 @@ using bf16 = __nv_bfloat16;
 
 constexpr int kTcM = 128;                 // tile rows: the M of one tcgen05.mma
 constexpr int kTcK = 64;                  // K per stage: 64 bfloat16 = one 128-byte swizzle row
-constexpr int kStages = 4;
 constexpr uint32_t kSpinLimit = 1u << 26;
 constexpr uint32_t kABytes = kTcM * kTcK * 2;
 
@@ -129,8 +128,10 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 
-template <int BN>
-__global__ void __launch_bounds__(128, 1)
+// S shared-memory stages: 3 for 128-column tiles and 4 for 64-column ones (about 97 KB either way,
+// so two CTAs share an SM and one's epilogue overlaps the other's main loop).
+template <int BN, int S>
+__global__ void __launch_bounds__(128, 2)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
               const float *__restrict__ bias, float *__restrict__ C, int ldc, bf16 *__restrict__ D, int ldd, int gelu)
 {
@@ -138,9 +139,9 @@ __global__ void __launch_bounds__(128, 1)
     extern __shared__ uint8_t smem_raw[];
     // stage tiles on 1024-byte boundaries (the 128-byte swizzle pattern repeats every 8 rows)
     uint8_t *smem = smem_raw + (((smem_u32(smem_raw) + 1023u) & ~1023u) - smem_u32(smem_raw));
-    uint8_t *sA = smem;                       // [kStages][128 rows][128 B]
-    uint8_t *sB = smem + kStages * kABytes;   // [kStages][BN rows][128 B]
-    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+    uint8_t *sA = smem;                       // [S][128 rows][128 B]
+    uint8_t *sB = smem + S * kABytes;   // [S][BN rows][128 B]
+    __shared__ __align__(8) uint64_t full[S], empty[S], done;
     __shared__ uint32_t tmem_base;
     __shared__ int fail;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(128, 1)
     const int ksteps = (K + kTcK - 1) / kTcK;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -170,8 +171,8 @@ __global__ void __launch_bounds__(128, 1)
     if (threadIdx.x == 0) {   // TMA producer
         int issued = 0;
         for (int ks = 0; ks < ksteps; ++ks) {
-            const int s = ks % kStages;
-            if (ks >= kStages && !mbar_wait(&empty[s], (uint32_t)((ks / kStages) - 1) & 1u)) {
+            const int s = ks % S;
+            if (ks >= S && !mbar_wait(&empty[s], (uint32_t)((ks / S) - 1) & 1u)) {
                 fail = 1;
                 break;
             }
@@ -182,13 +183,13 @@ __global__ void __launch_bounds__(128, 1)
         }
         // the copies still in flight (normally all were consumed already): wait for the last phase
         // of every stage that received one
-        for (int ks = issued > kStages ? issued - kStages : 0; ks < issued; ++ks)
-            if (!mbar_wait(&full[ks % kStages], (uint32_t)(ks / kStages) & 1u)) fail = 1;
+        for (int ks = issued > S ? issued - S : 0; ks < issued; ++ks)
+            if (!mbar_wait(&full[ks % S], (uint32_t)(ks / S) & 1u)) fail = 1;
     } else if (threadIdx.x == 32) {   // MMA issuer
         const uint32_t idesc = idesc_bf16(kTcM, BN);
         for (int ks = 0; ks < ksteps; ++ks) {
-            const int s = ks % kStages;
-            if (!mbar_wait(&full[s], (uint32_t)(ks / kStages) & 1u)) {
+            const int s = ks % S;
+            if (!mbar_wait(&full[s], (uint32_t)(ks / S) & 1u)) {
                 fail = 1;
                 break;
             }
@@ -276,11 +277,12 @@ cudaError_t launch_bn(int M, int N, int K, const void *A, int lda, const void *B
 {
     CUtensorMap ta, tb;
     if (!make_map(ta, A, M, K, lda, kTcM) || !make_map(tb, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)kStages * (kABytes + BN * kTcK * 2) + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr int S = BN == 128 ? 3 : 4;
+    const size_t smem = (size_t)S * (kABytes + BN * kTcK * 2) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + kTcM - 1) / kTcM));
-    k_gemm_tc<BN><<<grid, 128, smem, s>>>(ta, tb, M, N, K, bias, C, ldc, static_cast<bf16 *>(D), ldd, gelu);
+    k_gemm_tc<BN, S><<<grid, 128, smem, s>>>(ta, tb, M, N, K, bias, C, ldc, static_cast<bf16 *>(D), ldd, gelu);
     return cudaGetLastError();
 }
 

@@ -119,6 +119,13 @@ bool gemm_tc_supported(int K, const void *A, int lda, const void *B, int ldb);
 cudaError_t launch_gemm_tc(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
                            float *C, int ldc, void *D, int ldd, int gelu, cudaStream_t s);
 cudaError_t gemm_tc_error(int *err);
+// Screening: surrogate chi^2 per conformer, top-k selection (n <= select_max()), row gather.
+int select_max();
+cudaError_t launch_surrogate_chi2(int n_conf, int n_q, const float *z, int ld, const double *mean, const double *stdv,
+                                  const double *target, const double *w, double *chi2, cudaStream_t s);
+cudaError_t launch_select_topk(int n, const double *chi2, int k, int32_t *top_idx, double *top_chi2, cudaStream_t s);
+cudaError_t launch_gather_rows(const void *src, int64_t row_bytes, const int32_t *idx, int64_t n_idx, void *dst,
+                               cudaStream_t s);
 // launch_gemm_tc where supported, else launch_gemm_tn.
 cudaError_t launch_gemm(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
                         float *C, int ldc, void *D, int ldd, int gelu, cudaStream_t s);

@@ -202,6 +202,28 @@ def train(net: SurrogateMLP, X: np.ndarray, Y: np.ndarray, epochs: int, batch: i
     return losses
 
 
+def screen_select(net: "SurrogateMLP", feats: torch.Tensor, ys: "Standardizer", target, weights, k: int):
+    """Rank conformers by the surrogate's chi^2 against `target` (weights w_q) and return (indices of the
+    k best in increasing chi^2, chi^2 of all), both device tensors; the chi^2, ranking and selection run
+    in the library (sas_screen_select)."""
+    dev = feats.device
+    pred = net.predict(feats)
+    n_conf, n_q = int(pred.shape[0]), int(pred.shape[1])
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    chi2 = torch.empty(n_conf, dtype=torch.float64, device=dev)
+    top = torch.empty(k, dtype=torch.int32, device=dev)
+    _lib.sas_screen_select(n_conf, n_q, pred, pred.stride(0), d(ys.mean), d(ys.std), d(target), d(weights), k, top,
+                           None, chi2)
+    return top, chi2
+
+
+def gather_conformers(X: torch.Tensor, idx: torch.Tensor) -> torch.Tensor:
+    """X[idx] for conformers X [C][n][3] float32 on the device (sas_gather_rows)."""
+    out = torch.empty((int(idx.numel()),) + tuple(X.shape[1:]), dtype=X.dtype, device=X.device)
+    _lib.sas_gather_rows(X, X[0].numel() * X.element_size(), idx, int(idx.numel()), out)
+    return out
+
+
 def run_screen(n_conf: int = 4096, n_atoms: int = 2000, n_train: int | None = None, epochs: int = 60,
                batch: int = 256, lr: float = 1e-3, hidden: int = 512, top_frac: float = 0.05, seed: int = 0):
     """Configuration 5 end to end; returns a report dict."""
@@ -245,11 +267,12 @@ def run_screen(n_conf: int = 4096, n_atoms: int = 2000, n_train: int | None = No
     wq = 1.0 / target ** 2
     torch.cuda.synchronize()
     t3 = time.perf_counter()
-    I_all = np.exp(ys.inverse(net.predict(torch.as_tensor(Xn, device="cuda")).double().cpu().numpy()))
-    chi_sur = np.sum(wq * (I_all - target) ** 2, axis=1)
     k = max(1, int(round(top_frac * n_conf)))
-    top = np.argsort(chi_sur)[:k]
-    I_top = prof(X[torch.as_tensor(top, device="cuda")].contiguous(), tt).cpu().numpy()
+    top_t, chi_sur_t = screen_select(net, torch.as_tensor(Xn, device="cuda"), ys, target, wq, k)
+    Xtop = gather_conformers(X, top_t)
+    I_top = prof(Xtop, tt).cpu().numpy()
+    top = top_t.cpu().numpy()
+    chi_sur = chi_sur_t.cpu().numpy()
     chi_top = np.sum(wq * (I_top - target) ** 2, axis=1)
     best_screen = int(top[np.argmin(chi_top)])
     torch.cuda.synchronize()

@@ -1,0 +1,81 @@
+"""GPU screening kernels (sas_screen_select, sas_gather_rows) against plain NumPy: the surrogate chi^2
+in FP64, the unique (chi^2, index) order with NaN last, and the row gather."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1306_2258_gb300 import _lib
+from paper_1306_2258_gb300.surrogate import gather_conformers
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    _lib.load()
+
+
+def _select(z, mean, std, target, w, k):
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    zt = torch.as_tensor(z).cuda()
+    chi2 = torch.empty(z.shape[0], dtype=torch.float64, device="cuda")
+    top = torch.empty(k, dtype=torch.int32, device="cuda")
+    topc = torch.empty(k, dtype=torch.float64, device="cuda")
+    _lib.sas_screen_select(z.shape[0], z.shape[1], zt, z.shape[1], d(mean), d(std), d(target), d(w), k, top, topc,
+                           chi2)
+    return top.cpu().numpy(), topc.cpu().numpy(), chi2.cpu().numpy()
+
+
+@pytest.mark.parametrize("n_conf,n_q,k", [(4096, 101, 205), (1, 7, 1), (1000, 51, 1000), (8192, 33, 17)])
+def test_screen_select_matches_numpy(n_conf, n_q, k):
+    rng = np.random.default_rng(n_conf + n_q)
+    z = rng.standard_normal((n_conf, n_q)).astype(np.float32)
+    mean, std = rng.uniform(2, 8, n_q), rng.uniform(0.1, 2.0, n_q)
+    target = np.exp(mean + rng.standard_normal(n_q) * std)
+    w = 1.0 / target ** 2
+    top, topc, chi2 = _select(z, mean, std, target, w, k)
+    ref = np.sum(w * (np.exp(z.astype(np.float64) * std + mean) - target) ** 2, axis=1)
+    assert np.allclose(chi2, ref, rtol=1e-12, atol=0)
+    order = np.lexsort((np.arange(n_conf), chi2))   # by chi2, then index (the kernel's unique order)
+    assert np.array_equal(top, order[:k])
+    assert np.array_equal(topc, chi2[order[:k]])
+
+
+def test_screen_select_ties_by_index_and_nan_last():
+    rng = np.random.default_rng(5)
+    base = rng.standard_normal((1, 20)).astype(np.float32)
+    z = np.repeat(base, 300, axis=0)              # 300 identical rows: equal chi2
+    z[7, 3] = np.nan                              # NaN rows rank after every number
+    z[100, 0] = np.nan
+    z[250] += 0.5                                 # a different row
+    mean, std = np.zeros(20), np.ones(20)
+    target, w = np.ones(20), np.ones(20)
+    top, topc, chi2 = _select(z, mean, std, target, w, 300)
+    assert np.isnan(chi2[7]) and np.isnan(chi2[100])
+    assert list(top[-2:]) == [7, 100]
+    finite = [i for i in range(300) if i not in (7, 100)]
+    order = sorted(finite, key=lambda i: (chi2[i], i))
+    assert list(top[:-2]) == order
+
+
+def test_select_and_gather_limits():
+    z = torch.zeros((2, 3), device="cuda")
+    d = torch.ones(3, dtype=torch.float64, device="cuda")
+    top = torch.empty(2, dtype=torch.int32, device="cuda")
+    chi2 = torch.empty(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.SasError):   # k > n_conf
+        _lib.sas_screen_select(2, 3, z, 3, d, d, d, d, 3, top, None, chi2)
+    with pytest.raises(_lib.SasError):   # host buffer
+        _lib.sas_screen_select(2, 3, z, 3, d.cpu(), d, d, d, 1, top, None, chi2)
+    with pytest.raises(_lib.SasError):   # too many conformers for one CTA
+        _lib.sas_screen_select(8193, 3, z, 3, d, d, d, d, 1, top, None, chi2)
+
+
+@pytest.mark.parametrize("shape", [(50, 2000, 3), (7, 3, 3), (1, 1, 1)])
+def test_gather_rows(shape):
+    rng = np.random.default_rng(sum(shape))
+    X = torch.as_tensor(rng.standard_normal(shape).astype(np.float32)).cuda()
+    idx_np = rng.integers(0, shape[0], size=2 * shape[0]).astype(np.int32)
+    out = gather_conformers(X, torch.as_tensor(idx_np).cuda())
+    assert torch.equal(out, X[torch.as_tensor(idx_np, dtype=torch.long).cuda()])
