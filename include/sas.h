@@ -149,9 +149,17 @@ enum {
     SAS_OPT_GRID = 4,        /* persistent CTAs per SM for the pair kernels (0 = automatic) */
     SAS_OPT_TIMEOUT_MS = 5,  /* limit of every host-side wait for device work (default 600000) */
     SAS_OPT_STEP = 6,        /* q steps per recurrence step of the mixed kernel: 2 (default) or 4 */
-    SAS_OPT_VARIANT = 7      /* mixed kernel form for step 2 without re-seed: 0 auto, 1 general,
+    SAS_OPT_VARIANT = 7,     /* mixed kernel form for step 2 without re-seed: 0 auto, 1 general,
                                 2 set-up of the next pair overlapped, 3 pairs in sequence,
                                 4 two pairs per step on packed FP32 (same result bit for bit as 2 and 3) */
+    SAS_OPT_SHARD = 8        /* world * 65536 + rank (default 1 * 65536 + 0): later calls compute shard
+                                `rank` of a work list split into `world` contiguous parts of equal pair
+                                work.  sas_profile / sas_profile_batch then return that shard's share
+                                of I(q) (the diagonal and the exact q = 0 pair counts go to rank 0),
+                                so the shards of all ranks sum to the whole profile; sas_partials,
+                                sas_profile_vjp and sas_pair_histogram likewise return additive
+                                shares; sas_profile_grad needs the whole profile and returns
+                                UNSUPPORTED while world > 1. */
 };
 sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value);
 

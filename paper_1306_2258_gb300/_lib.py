@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "ALLOC", 4: "UNSUPPORTE
 SAS_MIXED, SAS_FP64 = 0, 1
 SAS_COORDS_F32, SAS_COORDS_F64 = 0, 1
 SAS_OPT_JMAX, SAS_OPT_RESEED, SAS_OPT_VALIDATE, SAS_OPT_GRID, SAS_OPT_TIMEOUT_MS, SAS_OPT_STEP, SAS_OPT_VARIANT = 1, 2, 3, 4, 5, 6, 7
+SAS_OPT_SHARD = 8
 SAS_MAX_TYPES, SAS_MAX_Q = 16, 1664
 
 # every symbol include/sas.h declares (checked by the test suite)

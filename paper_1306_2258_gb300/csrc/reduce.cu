@@ -50,7 +50,9 @@ __global__ void k_reduce_items(const double *partial, int part_stride, const Ite
     S[(int64_t)g * qc.n_q + k] = q > 0.0 ? s / q : 0.0;
 }
 
-__global__ void k_assemble(double *S, const double *F, const int *meta, int n_types, QChunks qc,
+// whole = 0 (a shard other than the first of a split work list): no diagonal, and S(0) = 0, since
+// the first shard carries the exact pair counts at q = 0.
+__global__ void k_assemble(double *S, const double *F, const int *meta, int n_types, QChunks qc, int whole,
                            double *I)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -59,7 +61,7 @@ __global__ void k_assemble(double *S, const double *F, const int *meta, int n_ty
     const int P = n_types * (n_types + 1) / 2;
     const bool q0 = !(qval(qc, k) > 0.0);
     double acc = 0.0;
-    for (int t = 0; t < n_types; ++t) {
+    for (int t = 0; whole && t < n_types; ++t) {
         const double f = F[t * qc.n_q + k];
         acc += (double)meta[t] * f * f;   // the diagonal, exactly
     }
@@ -69,7 +71,7 @@ __global__ void k_assemble(double *S, const double *F, const int *meta, int n_ty
             double *Sp = S + (b * P + p) * qc.n_q + k;
             if (q0) {   // sinc(0) = 1: the number of unordered pairs of types {a, c}
                 const double na = meta[a], nc = meta[c];
-                *Sp = (a == c) ? na * (na - 1.0) * 0.5 : na * nc;
+                *Sp = !whole ? 0.0 : (a == c) ? na * (na - 1.0) * 0.5 : na * nc;
             }
             acc += 2.0 * F[a * qc.n_q + k] * F[c * qc.n_q + k] * (*Sp);
         }
@@ -97,11 +99,11 @@ cudaError_t launch_reduce_items(const double *partial, int part_stride, const It
 }
 
 cudaError_t launch_assemble(double *S, const double *F, const int *meta, int n_types, int64_t batch,
-                            const QChunks &qc, double *I, cudaStream_t s)
+                            const QChunks &qc, int whole, double *I, cudaStream_t s)
 {
     if (batch == 0) return cudaSuccess;
     dim3 grid((qc.n_q + 127) / 128, (unsigned)batch);
-    k_assemble<<<grid, 128, 0, s>>>(S, F, meta, n_types, qc, I);
+    k_assemble<<<grid, 128, 0, s>>>(S, F, meta, n_types, qc, whole, I);
     return cudaGetLastError();
 }
 

@@ -171,6 +171,7 @@ struct sas_ctx {
     int opt_step = 2;
     int opt_variant = 0;
     int opt_grid = 0;
+    int opt_shard_rank = 0, opt_shard_world = 1;   // this call computes shard rank of world
     int64_t opt_timeout_ms = 600000;
     DevBuf coef_d, F, meta, blockcounts, blockoffs, centroid, X, slot_of, items, group_items,
         group_off, partial, ticket, S, in_coords, in_types, out_buf, Ibuf, gbuf, chi2buf, H, G, gout, tgt, wts,
@@ -234,7 +235,7 @@ struct Schedule {
 
 // Items of one conformer-independent layout; `counts` are the real atoms per type.
 void build_schedule(const int *counts, int T, int64_t batch, int tile, int n_chunks, int grid,
-                    int64_t jmax_opt, int64_t jmax_cap, Schedule &out)
+                    int64_t jmax_opt, int64_t jmax_cap, int shard_rank, int shard_world, Schedule &out)
 {
     // Type group t occupies slots [O[t], O[t] + P[t]) of the packed array, its atoms the first
     // counts[t]; an I-tile spans `tile` slots, a J-range ends at E[t], the count rounded up to 4
@@ -301,6 +302,28 @@ void build_schedule(const int *counts, int T, int64_t batch, int tile, int n_chu
                     }
                 }
             }
+    if (shard_world > 1) {   // keep this shard's items: contiguous runs of the canonical order, balanced by work
+        int64_t total = 0;
+        for (const Item &it : canon) total += it.work;
+        std::vector<Item> keep;
+        std::vector<int> keep_group;
+        int64_t before = 0;
+        out.pair_slots = 0;
+        out.jlen_max = 0;
+        for (size_t k = 0; k < canon.size(); ++k) {
+            const int64_t mid2 = 2 * before + canon[k].work;   // twice the item's midpoint
+            const int owner = (int)std::min<int64_t>(mid2 * shard_world / (2 * std::max<int64_t>(total, 1)),
+                                                     shard_world - 1);
+            before += canon[k].work;
+            if (owner != shard_rank) continue;
+            keep.push_back(canon[k]);
+            keep_group.push_back(canon_group[k]);
+            out.pair_slots += canon[k].work;
+            out.jlen_max = std::max(out.jlen_max, canon[k].jlen);
+        }
+        canon.swap(keep);
+        canon_group.swap(keep_group);
+    }
     const int n = (int)canon.size();
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
@@ -378,10 +401,13 @@ sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32
     key.push_back(grid_cap);
     key.push_back(n_chunks);
     key.push_back(jmax_cap);
+    key.push_back(ctx->opt_shard_rank);
+    key.push_back(ctx->opt_shard_world);
     if (key != ctx->sched_key) {
         Schedule sc;
         const int64_t jm = ctx->opt_jmax > 0 ? std::min(ctx->opt_jmax, jmax_cap) : 0;
-        build_schedule(ctx->h_meta, T, batch, tile, n_chunks, grid_cap, jm, jmax_cap, sc);
+        build_schedule(ctx->h_meta, T, batch, tile, n_chunks, grid_cap, jm, jmax_cap, ctx->opt_shard_rank,
+                       ctx->opt_shard_world, sc);
         const int ni = (int)sc.items.size();
         const int ng = (int)sc.group_off.size() - 1;
         ctx->sched_key.clear();   // invalid until the upload succeeded
@@ -486,7 +512,7 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
                                  ctx->group_items.as<int>(), ctx->group_off.as<int>(), ctx->n_groups,
                                  ctx->qc, ctx->S.as<double>(), s));
     CUDA_TRY(launch_assemble(ctx->S.as<double>(), ctx->F.as<double>(), ctx->meta.as<int>(), T, batch,
-                             ctx->qc, I_dev, s));
+                             ctx->qc, ctx->opt_shard_rank == 0, I_dev, s));
     launches += 3;
     ctx->last_batch = batch;
     ctx->have_partials = true;
@@ -782,6 +808,14 @@ sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value)
         if (value <= 0) return fail(SAS_ERR_INVALID_ARG, "timeout must be positive");
         ctx->opt_timeout_ms = value;
         return SAS_OK;
+    case SAS_OPT_SHARD: {
+        const int64_t world = value >> 16, rank = value & 0xFFFF;
+        if (world < 1 || world > 65535 || rank >= world)
+            return fail(SAS_ERR_INVALID_ARG, "SHARD must be world * 65536 + rank with 1 <= world and rank < world");
+        ctx->opt_shard_world = (int)world;
+        ctx->opt_shard_rank = (int)rank;
+        return SAS_OK;
+    }
     default:
         return fail(SAS_ERR_INVALID_ARG, "unknown option %d", option);
     }
@@ -808,6 +842,9 @@ sas_status sas_profile_grad(sas_ctx *ctx, const float *coords, const int32_t *ty
     sas_status st = check_common(ctx, coords, types, n, batch);
     if (st != SAS_OK) return st;
     if (ctx->flags & SAS_FP64) return fail(SAS_ERR_UNSUPPORTED, "the adjoint needs a SAS_MIXED context");
+    if (ctx->opt_shard_world > 1)
+        return fail(SAS_ERR_UNSUPPORTED, "chi^2 needs the whole profile: use a single shard (or sas_profile_vjp per "
+                                         "shard with the gathered dchi^2/dI)");
     if (batch > 0 && (!target || !weights || !chi2_out || (n > 0 && !grad_out)))
         return fail(SAS_ERR_INVALID_ARG, "null argument");
     if (batch == 0) return SAS_OK;

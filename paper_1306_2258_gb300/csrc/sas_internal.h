@@ -66,8 +66,8 @@ cudaError_t launch_reduce_items(const double *partial, int part_stride, const It
                                 const int *group_items, const int *group_off, int n_groups,
                                 const QChunks &qc, double *S, cudaStream_t s);
 // I[b][k] = sum_t n_t F_t^2 + sum_p 2 F_a F_b (q_k > 0 ? S/q_k : count_p)
-cudaError_t launch_assemble(double *S, const double *F, const int *meta, int n_types,
-                            int64_t batch, const QChunks &qc, double *I, cudaStream_t s);
+cudaError_t launch_assemble(double *S, const double *F, const int *meta, int n_types, int64_t batch,
+                            const QChunks &qc, int whole, double *I, cudaStream_t s);
 
 // ---- pair kernels -------------------------------------------------------------
 // partial [n_items][part_stride] f64: sum over the item's pairs of w_i w_j sin(q r)/r.

@@ -229,7 +229,7 @@ extern "C" sas_status sas_profile_static(const float *coords, const int32_t *typ
     STATIC_TRY(launch_debye_mixed(X, npad, items, ni, qc, 2, reseed, reseed == 0 ? 5 : 1, partial, kQChunk, 0,
                                   kStaticJmax, ticket, s));
     STATIC_TRY(launch_reduce_items(partial, kQChunk, items, group_items, group_off, Pn, qc, S, s));
-    STATIC_TRY(launch_assemble(S, F, meta, T, 1, qc, I_out, s));
+    STATIC_TRY(launch_assemble(S, F, meta, T, 1, qc, 1, I_out, s));
     // the host-side arrays above are gone when this returns: wait until the copies from them are done
     STATIC_TRY(cudaStreamSynchronize(s));
 #undef STATIC_TRY

@@ -44,3 +44,62 @@ def test_two_gloo_ranks_weak_scaling_aggregation():
     assert m0 == m1 == 200.0
     assert v0 == v1 == pytest.approx((pq0 + pq1) * 4 / 0.2)
     assert i0 != i1                                 # independent problems
+
+
+def _share_worker(rank, world, port, out, fail_rank):
+    """Rank r computes the oracle's share of the rows i in its block (I of the suffix from the
+    block's start minus I of the suffix after it), then the shares are combined over gloo."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import datetime
+
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1306_2258_gb300 import workloads as wl
+    from paper_1306_2258_gb300.shard import allreduce_shares
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    mol = wl.random_walk_globule(240, 4, 77)
+    coef = wl.form_factor_coefficients(4, 78)
+    q = wl.q_grid(0.0, 0.8, 33)
+    n = mol.n
+    s, e = rank * n // world, (rank + 1) * n // world
+
+    def suffix(k):
+        return oracle.profile(mol.coords[k:], mol.types[k:], coef, q) if k < n else np.zeros(q.size)
+
+    share = torch.as_tensor(suffix(s) - suffix(e))
+    if rank == fail_rank:   # this rank leaves before the collective
+        out[rank] = ("left", None)
+        return
+    try:
+        total = allreduce_shares(share)
+        out[rank] = ("ok", total.numpy().tolist())
+    except Exception as exc:   # the others learn of the missing rank from the collective's time limit
+        out[rank] = ("error", type(exc).__name__)
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_row_shares_allreduce_to_the_whole_profile(world):
+    import oracle
+    from paper_1306_2258_gb300 import workloads as wl
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_share_worker, args=(world, _free_port(), out, -1), nprocs=world, start_method="spawn",
+                       join=True)
+    mol = wl.random_walk_globule(240, 4, 77)
+    ref = oracle.profile(mol.coords, mol.types, wl.form_factor_coefficients(4, 78), wl.q_grid(0.0, 0.8, 33))
+    assert all(out[r][0] == "ok" for r in range(world))
+    totals = [np.asarray(out[r][1]) for r in range(world)]
+    for t in totals:
+        assert np.array_equal(t, totals[0])            # the same bits on every rank
+        assert np.max(np.abs(t - ref) / ref) <= 1e-11
+
+
+def test_a_rank_that_leaves_makes_the_others_fail_not_hang():
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_share_worker, args=(2, _free_port(), out, 1), nprocs=2, start_method="spawn", join=True)
+    assert out[1][0] == "left"
+    assert out[0][0] == "error"

@@ -113,6 +113,60 @@ def test_automatic_reseed_rule_cases_match_oracle(case):
         assert _rel(I[b], ref) <= TOL_MIXED, b
 
 
+def _shares(mol, coef, q, world, what):
+    from paper_1306_2258_gb300.shard import set_shard
+    x = torch.as_tensor(mol.coords).cuda()
+    t = torch.as_tensor(mol.types).cuda()
+    out = []
+    for rank in range(world):
+        p = Profile(coef, q, "mixed")
+        set_shard(p, rank, world)
+        if what == "profile":
+            out.append((p(x, t).cpu().numpy(), p.partials()))
+        elif what == "histogram":
+            out.append(p.pair_histogram(x, t)[0].cpu().numpy())
+        else:
+            gI = torch.as_tensor(np.linspace(1.0, 2.0, q.size)).cuda()
+            out.append(p.vjp(x, t, gI).cpu().numpy().astype(np.float64))
+        p.close()
+    return out
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 7])
+def test_shards_of_one_molecule_sum_to_the_whole(world):
+    """A molecule's work list split over `world` shards, run one after another on this GPU: the
+    shares of I(q) and of S_ab(q) summed in rank order equal the unsplit call to rounding of the
+    regrouped FP64 item sums; pair histograms add up exactly; VJP shares add up too."""
+    w = wl.c2_globule(10000)
+    whole = _shares(w.mol, w.coef, w.q, 1, "profile")[0]
+    parts = _shares(w.mol, w.coef, w.q, world, "profile")
+    I = sum(pp[0] for pp in parts)
+    S = sum(pp[1] for pp in parts)
+    assert np.max(np.abs(I - whole[0]) / whole[0]) <= 1e-13
+    assert np.max(np.abs(S - whole[1])) <= 1e-13 * np.max(np.abs(whole[1]))
+    h = sum(_shares(w.mol, w.coef, w.q, world, "histogram"))
+    assert np.array_equal(h, _shares(w.mol, w.coef, w.q, 1, "histogram")[0])
+    g = sum(_shares(w.mol, w.coef, w.q, world, "vjp"))
+    g1 = _shares(w.mol, w.coef, w.q, 1, "vjp")[0]
+    assert np.linalg.norm(g - g1) <= 1e-6 * np.linalg.norm(g1)
+
+
+def test_shard_option_validation():
+    from paper_1306_2258_gb300.shard import set_shard
+    w = wl.c1_plain_fp64()
+    p = Profile(w.coef, w.q, "mixed")
+    for bad in (0, 65536 * 2 + 2, 65536 * 3 + 5):
+        with pytest.raises(_lib.SasError):
+            p.set_option(_lib.SAS_OPT_SHARD, bad)
+    set_shard(p, 1, 2)
+    m = w.mol.as_f32()
+    T = np.ones(w.q.size)
+    with pytest.raises(_lib.SasError) as e:
+        p.chi2_grad(torch.as_tensor(m.coords).cuda(), m.types, T, T)
+    assert e.value.status == _lib.SAS_ERR_UNSUPPORTED
+    p.close()
+
+
 def _variant_case(name):
     if name == "globule10k_q201":
         w = wl.c2_globule(10000)
