@@ -121,6 +121,29 @@ def _cpu_oracle_sample(w, seconds_hint=20.0):
                       f"{dt:.1f} s, FP64 double loop with libm sin"}, dt
 
 
+def _cpu_oracle_cases():
+    """Two more oracle timings for scale: the 1,000-atom FP64 configuration in full on every core,
+    and one core on a 2,000-atom subsample of the 50k globule x 201 q."""
+    import oracle
+    from paper_1306_2258_gb300 import workloads as wl
+    out = {}
+    c1 = wl.c1_plain_fp64()
+    t0 = time.perf_counter()
+    oracle.profile(c1.mol.coords, c1.mol.types, c1.coef, c1.q)
+    dt = time.perf_counter() - t0
+    n = c1.mol.n
+    out["c1_1000_atoms_x51q_all_cores"] = {"s": dt, "value": n * (n - 1) / 2 * c1.q.size / dt, "unit": "pair·q/s",
+                                            "cores": oracle.max_threads()}
+    w = wl.c2_globule(N_ATOMS)
+    sub = wl.subsample(w.mol, 2000, wl.seed_for(2, 79))
+    t0 = time.perf_counter()
+    oracle.profile(sub.coords, sub.types, w.coef, w.q, n_threads=1)
+    dt = time.perf_counter() - t0
+    out["globule_2000_atoms_x201q_one_core"] = {"s": dt, "value": 2000 * 1999 / 2 * w.q.size / dt,
+                                                 "unit": "pair·q/s", "cores": 1}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
@@ -415,6 +438,7 @@ def run_ours(args):
         line["rows"] = run_rows(dev, stream)
     if not args.skip_cpu and world == 1:
         line["cpu_baseline"], _ = _cpu_oracle_sample(w, seconds_hint=15.0)
+        line["cpu_baseline"]["cases"] = _cpu_oracle_cases()
     print(json.dumps(line))
     prof.close()
     p64.close()
