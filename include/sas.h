@@ -7,7 +7,7 @@
  *
  *     I(q) = sum_k sum_j f_k(q) f_j(q) sin(q r_jk) / (q r_jk),   sinc(0) = 1,
  *
- * over all N atoms of a molecule, on a uniform grid of q values, with the
+ * over all N atoms of a molecule, on a grid of q values made of uniform runs, with the
  * per-atom form factors f_j(q) taken from a small set of atom types:
  *
  *     f_t(q) = sum_{k=1..4} a_k exp(-b_k (q / 4 pi)^2) + c      (coefficients per type t).
@@ -47,7 +47,7 @@ typedef enum {
     SAS_ERR_INVALID_ARG = 1, /* bad size, null pointer, type out of range, NaN/Inf coordinate */
     SAS_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed */
     SAS_ERR_ALLOC = 3,       /* device or host allocation failed (nothing leaked) */
-    SAS_ERR_UNSUPPORTED = 4, /* non-uniform q grid, too many q values or types */
+    SAS_ERR_UNSUPPORTED = 4, /* q grid of too many uniform runs, too many q values or types */
     SAS_ERR_TIMEOUT = 5      /* a wait on the device exceeded its limit */
 } sas_status;
 
@@ -65,13 +65,16 @@ enum { SAS_COORDS_F32 = 0, SAS_COORDS_F64 = 1 };
 #define SAS_MAX_Q 1664
 
 /*
- * Create a context for n_types atom types and a uniform q grid.
+ * Create a context for n_types atom types and a q grid.
  *   ff_coef  [n_types][9] host, (a1..a4, b1..b4, c) per type; copied.
- *   q        [n_q] host, uniform ascending, q[0] >= 0 (relative spacing deviation <= 1e-9); copied.
+ *   q        [n_q] host, strictly ascending, q[0] >= 0; copied.  The grid is taken as maximal runs
+ *            of uniform spacing (every point within 1e-9 max|q| of its run's line; a uniform grid
+ *            is one run, an irregular one runs of two points), each run computed from its own
+ *            start and step; at most 64 runs after cutting each into pieces of <= 208 values.
  *   flags    SAS_MIXED or SAS_FP64.
  * Errors: INVALID_ARG (n_types outside 1..SAS_MAX_TYPES, n_q outside 1..SAS_MAX_Q,
- * null pointer, negative or non-finite q or coefficient), UNSUPPORTED (non-uniform q),
- * ALLOC, CUDA.  *out is set only on success.
+ * null pointer, negative or non-finite q or coefficient), UNSUPPORTED (q not strictly ascending,
+ * more than 64 runs), ALLOC, CUDA.  *out is set only on success.
  */
 sas_status sas_create(int n_types, const double *ff_coef, const double *q, int n_q, unsigned flags,
                       sas_ctx **out);

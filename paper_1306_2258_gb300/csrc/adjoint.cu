@@ -247,11 +247,11 @@ __global__ void __launch_bounds__(kTile, 4)
         const int jmask = item.diag ? tid : -1;   // pairs with j <= i are not pairs of i<j
         float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
         if (zero_start)
-            run_adj2<NV, true>(sxy, szw, sh, gj, jpairs, xi, item, tid, lane, jmask, qs_hi, qs_lo, bc(qc.dq_hi),
-                               bc(qc.dq_lo), gx, gy, gz);
+            run_adj2<NV, true>(sxy, szw, sh, gj, jpairs, xi, item, tid, lane, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
+                               bc(qc.dq_lo[ch]), gx, gy, gz);
         else
-            run_adj2<NV, false>(sxy, szw, sh, gj, jpairs, xi, item, tid, lane, jmask, qs_hi, qs_lo, bc(qc.dq_hi),
-                                bc(qc.dq_lo), gx, gy, gz);
+            run_adj2<NV, false>(sxy, szw, sh, gj, jpairs, xi, item, tid, lane, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
+                                bc(qc.dq_lo[ch]), gx, gy, gz);
         double *Gb = G + (int64_t)item.batch * npad * 3;
         atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid)], (double)(gx.x + gx.y));
         atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid) + 1], (double)(gy.x + gy.y));
@@ -290,7 +290,7 @@ __global__ void k_adjoint_coef(const double *g, const double *F, int n_types, QC
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t b = blockIdx.y;
     if (k >= qc.n_q) return;
-    const double q = qc.q0 + (double)k * qc.dq;
+    const double q = q_at(qc, k);
     const int P = n_types * (n_types + 1) / 2;
     int p = 0;
     for (int a = 0; a < n_types; ++a)

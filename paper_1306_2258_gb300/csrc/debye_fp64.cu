@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kTile64, 2)
         const double4 xi = Xb[item.i0 + tid];
         const int ch = item.chunk;
         const int qlen = qc.q_len[ch];
-        const double qs = qc.q0 + (double)qc.q_begin[ch] * qc.dq;
+        const double qs = qc.qsd[ch], dq = qc.dqd[ch];
         __syncthreads();   // the previous item's block sum is done with acc
         for (int k = 0; k < qlen; ++k) acc[k * kTile64 + tid] = 0.0;
         const int jmask = item.diag ? tid : -1;
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kTile64, 2)
             const double r = r2 > 0.0 ? sqrt(r2) : 1e-9;   // coincident atoms: sin(q r)/r -> q
             const double scale = w / r;
             double st, ct;
-            sincos(qc.dq * r, &st, &ct);
+            sincos(dq * r, &st, &ct);
             double S = 0.0, C = scale;
             if (qs != 0.0) {
                 double s0, c0;

@@ -322,19 +322,19 @@ __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
         if (P == 3) {
             const int nv = (qlen + 1) >> 1;
             if (zero_start)
-                run_m2_fitted<NB, true>(nv, xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi, qc.dq_lo, acc);
+                run_m2_fitted<NB, true>(nv, xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc);
             else
-                run_m2_fitted<NB, false>(nv, xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi, qc.dq_lo, acc);
+                run_m2_fitted<NB, false>(nv, xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc);
         } else if (P == 4) {
             if (zero_start)
-                run_m2<NB, true>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi, qc.dq_lo, acc);
+                run_m2<NB, true>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc);
             else
-                run_m2<NB, false>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi, qc.dq_lo, acc);
+                run_m2<NB, false>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc);
         } else {
             for (int j = 0; j < item.jlen; ++j) {
                 const float4 xj = sj[j];
                 const float w = (j <= jmask) ? 0.f : xi.w * xj.w;
-                pair_terms<NB, M, KQ>(xi, xj, w, qs_hi, qs_lo, zero_start, qc.dq_hi, qc.dq_lo,
+                pair_terms<NB, M, KQ>(xi, xj, w, qs_hi, qs_lo, zero_start, qc.dq_hi[ch], qc.dq_lo[ch],
                                       pair_hash(item.i0 + tid, item.j0 + j), acc);
             }
         }

@@ -162,11 +162,11 @@ __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
         for (int k = 0; k < 2 * NB; ++k) acc[k] = make_float2(0.f, 0.f);
         const int jmask = item.diag ? tid : -1;   // pairs with j <= i are not pairs of i<j
         if (zero_start)
-            run_pairs2<NB, NV, true>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi),
-                                     bc(qc.dq_lo), acc);
+            run_pairs2<NB, NV, true>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
+                                     bc(qc.dq_lo[ch]), acc);
         else
-            run_pairs2<NB, NV, false>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi),
-                                      bc(qc.dq_lo), acc);
+            run_pairs2<NB, NV, false>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
+                                      bc(qc.dq_lo[ch]), acc);
         flush_warp<NB, 2>(acc, red[warp], lane);
         __syncthreads();
         const int qlen = qc.q_len[ch];

@@ -17,7 +17,7 @@ namespace sas {
 
 namespace {
 
-__device__ __forceinline__ double qval(const QChunks &qc, int k) { return qc.q0 + (double)k * qc.dq; }
+__device__ __forceinline__ double qval(const QChunks &qc, int k) { return q_at(qc, k); }
 
 // f_t(q) = sum_{k<4} a_k exp(-b_k (q/4pi)^2) + c
 __global__ void k_form_factors(const double *coef, int n_types, QChunks qc, double *F)

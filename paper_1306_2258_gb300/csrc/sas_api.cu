@@ -49,6 +49,46 @@ sas_status set_error(sas_status st, const char *msg)
     g_err = msg;
     return st;
 }
+
+// Runs of uniform spacing: a run starting at s extends while every q_k stays within tol of the
+// line through its end points; each run is then cut into passes of at most kQChunk values.
+bool make_chunks(const double *q, int n_q, QChunks &qc)
+{
+    double qmax = 0.0;
+    for (int k = 0; k < n_q; ++k) qmax = std::max(qmax, std::fabs(q[k]));
+    const double tol = 1e-9 * std::max(qmax, 1e-300);
+    qc = QChunks{};
+    qc.n_q = n_q;
+    int nc = 0;
+    int s = 0;
+    while (s < n_q) {
+        int e = std::min(s + 2, n_q);   // run [s, e): one or two points always form a run
+        while (e < n_q) {
+            const double step = (q[e] - q[s]) / (double)(e - s);
+            bool ok = true;
+            for (int k = s + 1; k < e && ok; ++k) ok = std::fabs(q[k] - (q[s] + (k - s) * step)) <= tol;
+            if (!ok) break;
+            ++e;
+        }
+        const double step = e - s > 1 ? (q[e - 1] - q[s]) / (double)(e - s - 1) : 0.0;
+        for (int b = s; b < e; b += kQChunk) {
+            if (nc == kMaxChunks) return false;
+            const double qs = q[s] + (b - s) * step;
+            qc.q_begin[nc] = b;
+            qc.q_len[nc] = std::min(kQChunk, e - b);
+            qc.qsd[nc] = qs;
+            qc.dqd[nc] = step;
+            qc.qs_hi[nc] = (float)qs;
+            qc.qs_lo[nc] = (float)(qs - (double)qc.qs_hi[nc]);
+            qc.dq_hi[nc] = (float)step;
+            qc.dq_lo[nc] = (float)(step - (double)qc.dq_hi[nc]);
+            ++nc;
+        }
+        s = e;
+    }
+    qc.n_chunks = nc;
+    return true;
+}
 }  // namespace sas
 
 namespace {
@@ -673,14 +713,12 @@ sas_status sas_create(int n_types, const double *ff_coef, const double *q, int n
     if (!finite_all(ff_coef, (size_t)9 * n_types)) return fail(SAS_ERR_INVALID_ARG, "non-finite coefficient");
     if (!finite_all(q, (size_t)n_q)) return fail(SAS_ERR_INVALID_ARG, "non-finite q");
     if (q[0] < 0) return fail(SAS_ERR_INVALID_ARG, "negative q");
-    const double q0 = q[0];
-    const double dq = n_q > 1 ? (q[n_q - 1] - q[0]) / (double)(n_q - 1) : 0.0;
-    if (n_q > 1 && !(dq > 0)) return fail(SAS_ERR_UNSUPPORTED, "q grid must be strictly ascending");
-    const double qmax = std::max(std::fabs(q[n_q - 1]), dq);
-    for (int k = 0; k < n_q; ++k)
-        if (std::fabs(q[k] - (q0 + k * dq)) > 1e-9 * qmax)
-            return fail(SAS_ERR_UNSUPPORTED, "q grid is not uniform (q[%d] off by %.3g)", k,
-                        q[k] - (q0 + k * dq));
+    for (int k = 1; k < n_q; ++k)
+        if (!(q[k] > q[k - 1])) return fail(SAS_ERR_UNSUPPORTED, "q grid must be strictly ascending");
+    QChunks qcand{};
+    if (!make_chunks(q, n_q, qcand))
+        return fail(SAS_ERR_UNSUPPORTED, "q grid needs more than %d uniform runs of at most %d values", kMaxChunks,
+                    kQChunk);
     sas_ctx *c = new (std::nothrow) sas_ctx;
     if (!c) return fail(SAS_ERR_ALLOC, "host allocation failed");
     c->n_types = n_types;
@@ -688,20 +726,7 @@ sas_status sas_create(int n_types, const double *ff_coef, const double *q, int n
     c->flags = flags;
     c->coef.assign(ff_coef, ff_coef + 9 * n_types);
     c->q.assign(q, q + n_q);
-    QChunks &qc = c->qc;
-    qc.n_q = n_q;
-    qc.n_chunks = (n_q + kQChunk - 1) / kQChunk;
-    qc.q0 = q0;
-    qc.dq = dq;
-    qc.dq_hi = (float)dq;
-    qc.dq_lo = (float)(dq - (double)qc.dq_hi);
-    for (int ch = 0; ch < qc.n_chunks; ++ch) {
-        qc.q_begin[ch] = ch * kQChunk;
-        qc.q_len[ch] = std::min(kQChunk, n_q - ch * kQChunk);
-        const double qs = q0 + (double)qc.q_begin[ch] * dq;
-        qc.qs_hi[ch] = (float)qs;
-        qc.qs_lo[ch] = (float)(qs - (double)qc.qs_hi[ch]);
-    }
+    c->qc = qcand;
     int dev = 0;
     auto bail = [&](sas_status st) {
         delete c;
@@ -726,7 +751,7 @@ sas_status sas_create(int n_types, const double *ff_coef, const double *q, int n
         return bail(fail(SAS_ERR_ALLOC, "device allocation failed"));
     if (cudaMemcpy(c->coef_d.p, ff_coef, 9 * n_types * sizeof(double), cudaMemcpyHostToDevice) !=
             cudaSuccess ||
-        launch_form_factors(c->coef_d.as<double>(), n_types, qc, c->F.as<double>(), 0) != cudaSuccess ||
+        launch_form_factors(c->coef_d.as<double>(), n_types, c->qc, c->F.as<double>(), 0) != cudaSuccess ||
         cudaStreamSynchronize(0) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(SAS_ERR_CUDA, "form-factor table failed"));

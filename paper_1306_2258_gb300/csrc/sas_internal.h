@@ -11,7 +11,7 @@ namespace sas {
 constexpr int kTile = 128;      // atoms per I-tile of the mixed kernel (= its threads per CTA); group padding
 constexpr int kTile64 = 64;     // atoms per I-tile of the FP64 kernel
 constexpr int kQChunk = 208;    // q values one pass of a pair kernel covers (52 blocks of 4)
-constexpr int kMaxChunks = SAS_MAX_Q / kQChunk;
+constexpr int kMaxChunks = 64;    // passes of one q grid (runs of uniform spacing, split)
 constexpr int kPackThreads = 256;
 
 // One unit of pair work: an I-tile of one type against a contiguous J-range of
@@ -28,7 +28,9 @@ struct Item {
     int work;    // jlen * tile (for scheduling)
 };
 
-// The uniform q grid split into passes of at most kQChunk values.
+// The q grid as runs of uniform spacing (one run for a uniform grid), each run split into passes
+// of at most kQChunk values: chunk c holds q_k = qsd[c] + (k - q_begin[c]) dqd[c] for
+// q_begin[c] <= k < q_begin[c] + q_len[c].
 struct QChunks {
     int n_q;
     int n_chunks;
@@ -36,9 +38,23 @@ struct QChunks {
     int q_len[kMaxChunks];
     float qs_hi[kMaxChunks];   // first q of the chunk as a float32 pair (hi + lo)
     float qs_lo[kMaxChunks];
-    float dq_hi, dq_lo;        // grid step as a float32 pair
-    double q0, dq;             // the grid in FP64: q_k = q0 + k*dq
+    float dq_hi[kMaxChunks];   // step of the chunk as a float32 pair
+    float dq_lo[kMaxChunks];
+    double qsd[kMaxChunks];    // the same in FP64
+    double dqd[kMaxChunks];
 };
+
+// q_k of the grid (a short scan over the chunks).
+__host__ __device__ inline double q_at(const QChunks &qc, int k)
+{
+    int c = 0;
+    while (c + 1 < qc.n_chunks && qc.q_begin[c + 1] <= k) ++c;
+    return qc.qsd[c] + (double)(k - qc.q_begin[c]) * qc.dqd[c];
+}
+
+// Fill qc for q[0..n_q): maximal runs of uniform spacing (deviation <= tol * max|q|), split into
+// passes of at most kQChunk values.  False if the grid needs more than kMaxChunks passes.
+bool make_chunks(const double *q, int n_q, QChunks &qc);
 
 // ---- packing (pack.cu) -------------------------------------------------------
 // meta layout (int32): [0,T) real counts, [T, 2T+1) padded group offsets, [2T+1] error bits

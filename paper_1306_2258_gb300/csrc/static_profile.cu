@@ -154,10 +154,10 @@ extern "C" sas_status sas_profile_static(const float *coords, const int32_t *typ
     QChunks qc{};
     qc.n_q = n_q;
     qc.n_chunks = 1;
-    qc.q0 = q0;
-    qc.dq = dq;
-    qc.dq_hi = (float)dq;
-    qc.dq_lo = (float)(dq - (double)qc.dq_hi);
+    qc.qsd[0] = q0;
+    qc.dqd[0] = dq;
+    qc.dq_hi[0] = (float)dq;
+    qc.dq_lo[0] = (float)(dq - (double)qc.dq_hi[0]);
     qc.q_begin[0] = 0;
     qc.q_len[0] = n_q;
     qc.qs_hi[0] = (float)q0;

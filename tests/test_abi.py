@@ -49,10 +49,9 @@ def test_create_rejects_bad_sizes(n_types, nq, code):
     assert st == code and not h.value
 
 
-def test_create_rejects_nonuniform_and_bad_grids():
+def test_create_rejects_grids_beyond_64_uniform_runs_and_bad_grids():
     coef = np.ones((2, 9))
-    q = np.linspace(0, 1, 51)
-    q[7] += 1e-4
+    q = np.cumsum(np.random.default_rng(3).uniform(0.001, 0.01, 300))   # no three points in line: 150 runs
     with pytest.raises(_lib.SasError) as e:
         _lib.sas_create(2, coef, q)
     assert e.value.status == _lib.SAS_ERR_UNSUPPORTED

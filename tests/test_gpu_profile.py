@@ -167,6 +167,48 @@ def test_shard_option_validation():
     p.close()
 
 
+def _grid(name):
+    if name == "saxs_two_steps":      # fine steps at low q, coarse beyond
+        return np.concatenate([np.linspace(0.0, 0.3, 61), np.linspace(0.32, 1.0, 35)])
+    if name == "waxs_0_3":            # one uniform run to 3/A, split into two passes
+        return np.linspace(0.0, 3.0, 301)
+    if name == "scattered":           # irregular points: runs of two
+        return np.array([0.011, 0.05, 0.052, 0.2, 0.21, 0.22, 0.23, 0.5, 0.77, 0.9])
+    if name == "three_runs_offset":   # three runs, none starting at q = 0
+        return np.concatenate([np.linspace(0.02, 0.1, 17), np.linspace(0.11, 0.5, 14), np.linspace(0.6, 2.0, 8)])
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("grid", ["saxs_two_steps", "waxs_0_3", "scattered", "three_runs_offset"])
+@pytest.mark.parametrize("precision,tol", [("mixed", TOL_MIXED), ("fp64", TOL_FP64)])
+def test_piecewise_uniform_and_irregular_q_grids_match_oracle(grid, precision, tol):
+    """q grids made of uniform runs (each run computed from its own start and step): the oracle
+    takes the same q values directly."""
+    q = _grid(grid)
+    m = wl.random_walk_globule(2000, 5, 95)
+    m32 = m.as_f32()
+    coef = wl.form_factor_coefficients(5, 96)
+    ref = oracle.profile(m32.coords, m32.types, coef, q)
+    I = _gpu(m32, coef, q, precision)
+    assert _rel(I, ref) <= tol
+
+
+def test_chi2_gradient_on_a_piecewise_uniform_grid():
+    q = _grid("three_runs_offset")
+    base = wl.random_walk_globule(1200, 5, 97)
+    coef = wl.form_factor_coefficients(5, 98)
+    T = oracle.profile(wl.perturbed(base, 1.0, 99).coords, base.types, coef, q)
+    w = 1.0 / T ** 2
+    x = wl.perturbed(base, 1.0, 100).coords.astype(np.float32)
+    p = Profile(coef, q, "mixed")
+    chi2, g, _ = p.chi2_grad(torch.as_tensor(x).cuda(), base.types, T, w)
+    chi2_ref, g_ref, _ = oracle.chi2_grad(x, base.types, coef, q, T, w)
+    p.close()
+    assert abs(float(chi2) - chi2_ref) <= 1e-4 * chi2_ref
+    g = g.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
+
+
 def _variant_case(name):
     if name == "globule10k_q201":
         w = wl.c2_globule(10000)
