@@ -117,7 +117,7 @@ def test_vjp_batch_host_buffers():
 
 # ---------------------------------------------------------------- histogram
 
-@pytest.mark.parametrize("n,seed,T", [(2000, 501, 5), (129, 502, 3), (1, 503, 2), (3000, 504, 1)])
+@pytest.mark.parametrize("n,seed,T", [(2000, 501, 5), (129, 502, 3), (1, 503, 2), (3000, 504, 1), (2500, 505, 16)])
 def test_histogram_exact(n, seed, T):
     mol = wl.random_walk_globule(n, T, seed).as_f32()
     p = Profile(wl.form_factor_coefficients(T, 1), wl.q_grid(0, 0.5, 11))

@@ -294,6 +294,34 @@ def test_small_and_ragged_sizes(n, precision):
     assert _rel(_gpu(mol, coef, q, precision), ref) <= tol
 
 
+@pytest.mark.parametrize("precision,tol", [("mixed", TOL_MIXED), ("fp64", TOL_FP64)])
+def test_maximum_types_and_q_values_with_absent_types(precision, tol):
+    """SAS_MAX_TYPES = 16 types of which three never occur, and SAS_MAX_Q = 1664 q values (eight
+    passes of 208)."""
+    m = wl.random_walk_globule(1500, 13, 121).as_f32()
+    remap = np.array([0, 1, 2, 4, 5, 6, 7, 8, 10, 11, 12, 13, 15], dtype=np.int32)   # 3, 9, 14 unused
+    types = remap[m.types]
+    coef = wl.form_factor_coefficients(16, 122)
+    q = wl.q_grid(0.0, 2.0, _lib.SAS_MAX_Q)
+    ref = oracle.profile(m.coords, types, coef, q)
+    mol = wl.Molecule(m.coords, types, 16)
+    assert _rel(_gpu(mol, coef, q, precision), ref) <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", TOL_MIXED), ("fp64", TOL_FP64)])
+def test_many_coincident_atoms(precision, tol):
+    """400 atoms at one point (every pair among them has r = 0: sinc = 1) and 100 elsewhere."""
+    rng = np.random.default_rng(123)
+    x = np.concatenate([np.tile(np.array([[3.0, -2.0, 1.5]]), (400, 1)), rng.uniform(-20, 20, (100, 3))])
+    x = x.astype(np.float32)
+    types = rng.integers(0, 3, 500).astype(np.int32)
+    coef = wl.form_factor_coefficients(3, 124)
+    q = wl.q_grid(0.0, 0.6, 61)
+    ref = oracle.profile(x, types, coef, q)
+    mol = wl.Molecule(x, types, 3)
+    assert _rel(_gpu(mol, coef, q, precision), ref) <= tol
+
+
 def test_empty_molecule_gives_zero():
     p = Profile(wl.form_factor_coefficients(3, 1), wl.q_grid(0, 1, 11))
     I = p(torch.zeros((0, 3), device="cuda"), torch.zeros(0, dtype=torch.int32, device="cuda"))
