@@ -11,6 +11,11 @@
 // chains).  The J atoms are staged in shared memory already transposed into lane pairs:
 // (x_j, x_j+1, y_j, y_j+1) and (z_j, z_j+1, w_j, w_j+1).
 //
+// The set-up is split in two: its head (shared-memory loads, distance by the hardware reciprocal
+// square root and a Newton step, weights) holds the long latencies and is issued for the next two
+// pairs before the current recurrences, which hide it; the tail (sin/cos, seeds, coefficient)
+// stays in sequence (issuing it ahead too raised the register count and ran slower).
+//
 // Every operation matches the one-pair kernel lane by lane, and each accumulator receives pair
 // j before pair j+1, so the partial sums are the same bit for bit.
 #include "mixed_common.cuh"
@@ -32,11 +37,15 @@ struct PairState2 {
     float2 CpA, CnA, CpB, CnB;
 };
 
-template <bool ZERO_START>
-__device__ __forceinline__ void setup2(const float4 pxy, const float4 pzw, const float2 nX, const float2 nY,
-                                       const float2 nZ, const float2 wi, bool keepA, bool keepB, float2 qs_hi,
-                                       float2 qs_lo, float2 dq_hi, float2 dq_lo, unsigned hA, unsigned hB,
-                                       PairState2 &o)
+// First part of the set-up of two pairs: distance (reciprocal square root and one Newton step)
+// and weight.  It holds the long latencies (shared-memory loads, MUFU), so the pair loop issues it
+// one step ahead, next to the previous recurrences.
+struct PairHead2 {
+    float2 y, r, w;   // 1/r (hardware), r, w_i w_j (0: no pair)
+};
+
+__device__ __forceinline__ void setup2_head(const float4 pxy, const float4 pzw, const float2 nX, const float2 nY,
+                                            const float2 nZ, const float2 wi, bool keepA, bool keepB, PairHead2 &h)
 {
     // x_j - x_i (the negated difference: its square is the same)
     const float2 dx = f2add(make_float2(pxy.x, pxy.y), nX);
@@ -45,14 +54,22 @@ __device__ __forceinline__ void setup2(const float4 pxy, const float4 pzw, const
     float2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
     r2.x = fmaxf(r2.x, 1e-12f);   // coincident atoms: r = 1e-6 A
     r2.y = fmaxf(r2.y, 1e-12f);
-    const float2 y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-    const float2 r0 = f2mul(r2, y);
+    h.y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 r0 = f2mul(r2, h.y);
     // r = r0 + (y/2)(r2 - r0^2), as (-y/2)(r0^2 - r2) + r0
-    const float2 r = f2fma(f2mul(y, bc(-0.5f)), f2fma(r0, r0, f2mul(r2, bc(-1.f))), r0);
-    float2 w = f2mul(wi, make_float2(pzw.z, pzw.w));
-    if (!keepA) w.x = 0.f;
-    if (!keepB) w.y = 0.f;
-    const float2 scale = f2mul(w, y);
+    h.r = f2fma(f2mul(h.y, bc(-0.5f)), f2fma(r0, r0, f2mul(r2, bc(-1.f))), r0);
+    h.w = f2mul(wi, make_float2(pzw.z, pzw.w));
+    if (!keepA) h.w.x = 0.f;
+    if (!keepB) h.w.y = 0.f;
+}
+
+// Second part: sin t, cos t of t = dq r, the seeds of the first two blocks and the coefficient.
+template <bool ZERO_START>
+__device__ __forceinline__ void setup2_tail(const PairHead2 &h, float2 qs_hi, float2 qs_lo, float2 dq_hi,
+                                            float2 dq_lo, unsigned hA, unsigned hB, PairState2 &o)
+{
+    const float2 r = h.r;
+    const float2 scale = f2mul(h.w, h.y);
     const float2 t = f2fma(dq_hi, r, f2mul(dq_lo, r));
     const SinCos2 b1 = sincos2_f32(t);
     const float2 s1 = b1.s, c1 = b1.c;
@@ -118,11 +135,19 @@ __device__ __forceinline__ void run_pairs2(const float4 *sxy, const float4 *szw,
 {
     const float2 nX = bc(-xi.x), nY = bc(-xi.y), nZ = bc(-xi.z), wi = bc(xi.w);
     const unsigned ih = item.i0 + tid;
+    if (jpairs <= 0) return;
+    PairHead2 head;
+    setup2_head(sxy[0], szw[0], nX, nY, nZ, wi, 0 > jmask, 1 > jmask, head);
     for (int k = 0; k < jpairs; ++k) {
         const int j = 2 * k;
         PairState2 p;
-        setup2<ZERO_START>(sxy[k], szw[k], nX, nY, nZ, wi, j > jmask, j + 1 > jmask, qs_hi, qs_lo, dq_hi, dq_lo,
-                           pair_hash(ih, item.j0 + j), pair_hash(ih, item.j0 + j + 1), p);
+        setup2_tail<ZERO_START>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
+                                pair_hash(ih, item.j0 + j + 1), p);
+        // the next two pairs' distances, issued ahead of this step's recurrences (the last step
+        // reads its own slot again and discards the result)
+        const bool more = k + 1 < jpairs;
+        const int kn = more ? k + 1 : k;
+        setup2_head(sxy[kn], szw[kn], nX, nY, nZ, wi, more && j + 2 > jmask, more && j + 3 > jmask, head);
         core2<NB, NV>(p, acc);
     }
 }
