@@ -36,29 +36,41 @@ __device__ __forceinline__ float2 bc(float v) { return make_float2(v, v); }
 struct AdjPair2 {
     float2 eA0, eA1, oA0, oA1, eB0, eB1, oB0, oB1;   // (cos, sin) at q blocks 0, 1 of the even/odd chains
     float2 CpA, CnA, CpB, CnB;                       // (C, C) and (-C, -C), C = 2cos(2t)
-    float2 y;                                        // 1/r per lane
-    float2 w;                                        // pair weights w_i w_j (0: no pair)
-    float2 dx, dy, dz;                               // x_j - x_i per lane
 };
 
-template <bool ZERO_START>
-__device__ __forceinline__ void setup_adj2(const float4 pxy, const float4 pzw, const float2 nX, const float2 nY,
-                                           const float2 nZ, const float2 wi, bool keepA, bool keepB,
-                                           float2 qs_hi, float2 qs_lo, float2 dq_hi, float2 dq_lo, unsigned hA,
-                                           unsigned hB, AdjPair2 &o)
+// First part of the set-up: distance (hardware reciprocal square root and a Newton step) and
+// weights.  It holds the long latencies (shared-memory loads, MUFU), so the pair loop issues it
+// for the next two pairs ahead of the current recurrences.
+struct AdjHead2 {
+    float2 y, r, w;   // 1/r (hardware), r, w_i w_j (0: no pair)
+};
+
+__device__ __forceinline__ float2 jdiff(float2 xj, float2 nxi) { return f2add(xj, nxi); }   // x_j - x_i
+
+__device__ __forceinline__ void setup_adj2_head(const float4 pxy, const float4 pzw, const float2 nX,
+                                                const float2 nY, const float2 nZ, const float2 wi, bool keepA,
+                                                bool keepB, AdjHead2 &h)
 {
-    o.dx = f2add(make_float2(pxy.x, pxy.y), nX);
-    o.dy = f2add(make_float2(pxy.z, pxy.w), nY);
-    o.dz = f2add(make_float2(pzw.x, pzw.y), nZ);
-    float2 r2 = f2fma(o.dz, o.dz, f2fma(o.dy, o.dy, f2mul(o.dx, o.dx)));
+    const float2 dx = jdiff(make_float2(pxy.x, pxy.y), nX);
+    const float2 dy = jdiff(make_float2(pxy.z, pxy.w), nY);
+    const float2 dz = jdiff(make_float2(pzw.x, pzw.y), nZ);
+    float2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
     r2.x = fmaxf(r2.x, 1e-12f);
     r2.y = fmaxf(r2.y, 1e-12f);
-    o.y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-    const float2 r0 = f2mul(r2, o.y);
-    const float2 r = f2fma(f2mul(o.y, bc(-0.5f)), f2fma(r0, r0, f2mul(r2, bc(-1.f))), r0);
-    o.w = f2mul(wi, make_float2(pzw.z, pzw.w));
-    if (!keepA) o.w.x = 0.f;
-    if (!keepB) o.w.y = 0.f;
+    h.y = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 r0 = f2mul(r2, h.y);
+    h.r = f2fma(f2mul(h.y, bc(-0.5f)), f2fma(r0, r0, f2mul(r2, bc(-1.f))), r0);
+    h.w = f2mul(wi, make_float2(pzw.z, pzw.w));
+    if (!keepA) h.w.x = 0.f;
+    if (!keepB) h.w.y = 0.f;
+}
+
+// Second part: sin t, cos t, the chains' first two blocks and the coefficient.
+template <bool ZERO_START>
+__device__ __forceinline__ void setup_adj2_tail(const AdjHead2 &h, float2 qs_hi, float2 qs_lo, float2 dq_hi,
+                                                float2 dq_lo, unsigned hA, unsigned hB, AdjPair2 &o)
+{
+    const float2 r = h.r;
     const float2 t = f2fma(dq_hi, r, f2mul(dq_lo, r));
     const SinCos2 b1 = sincos2_f32(t);
     const float2 s1 = b1.s, c1 = b1.c;
@@ -182,22 +194,34 @@ __device__ __forceinline__ void run_adj2(const float4 *sxy, const float4 *szw, c
     const float2 nX = bc(-xi.x), nY = bc(-xi.y), nZ = bc(-xi.z), wi = bc(xi.w);
     const unsigned ih = item.i0 + tid;
     const int kslot = lane >> 2;   // the value this lane adds after the reduce-scatter
+    if (jpairs <= 0) return;
+    AdjHead2 head;
+    setup_adj2_head(sxy[0], szw[0], nX, nY, nZ, wi, 0 > jmask, 1 > jmask, head);
     for (int k = 0; k < jpairs; ++k) {
         const int j = 2 * k;
         AdjPair2 p;
-        setup_adj2<ZERO_START>(sxy[k], szw[k], nX, nY, nZ, wi, j > jmask, j + 1 > jmask, qs_hi, qs_lo, dq_hi, dq_lo,
-                               pair_hash(ih, item.j0 + j), pair_hash(ih, item.j0 + j + 1), p);
+        setup_adj2_tail<ZERO_START>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
+                                    pair_hash(ih, item.j0 + j + 1), p);
+        const float2 y = head.y, w = head.w;
+        // the next two pairs' distances, issued ahead of this step's recurrences (the last step
+        // reads its own slot again and discards the result)
+        const bool more = k + 1 < jpairs;
+        const int kn = more ? k + 1 : k;
+        setup_adj2_head(sxy[kn], szw[kn], nX, nY, nZ, wi, more && j + 2 > jmask, more && j + 3 > jmask, head);
         float2 abA, abB;
         core_adj2<NV>(p, sh, abA, abB);
         // -W_ij = w (2/r^2) (B/r - A), per lane; G_i += -W_ij (x_j - x_i)
         const float2 A = make_float2(abA.x, abB.x), B = make_float2(abA.y, abB.y);
-        const float2 y2 = f2mul(p.y, p.y);
-        const float2 nW = f2mul(f2mul(p.w, f2add(y2, y2)), f2fma(B, p.y, f2mul(A, bc(-1.f))));
-        gx = f2fma(nW, p.dx, gx);
-        gy = f2fma(nW, p.dy, gy);
-        gz = f2fma(nW, p.dz, gz);
-        // atoms j, j+1 receive +W_ij (x_j - x_i)... = -(-W_ij)(x_j - x_i)
-        const float2 fx = f2mul(nW, p.dx), fy = f2mul(nW, p.dy), fz = f2mul(nW, p.dz);
+        const float2 y2 = f2mul(y, y);
+        const float2 nW = f2mul(f2mul(w, f2add(y2, y2)), f2fma(B, y, f2mul(A, bc(-1.f))));
+        const float4 pxy = sxy[k], pzw = szw[k];   // x_j - x_i again (cheaper than keeping it)
+        const float2 dx = jdiff(make_float2(pxy.x, pxy.y), nX), dy = jdiff(make_float2(pxy.z, pxy.w), nY),
+                     dz = jdiff(make_float2(pzw.x, pzw.y), nZ);
+        gx = f2fma(nW, dx, gx);
+        gy = f2fma(nW, dy, gy);
+        gz = f2fma(nW, dz, gz);
+        // atoms j, j+1 receive +W_ij (x_j - x_i) = -(-W_ij)(x_j - x_i)
+        const float2 fx = f2mul(nW, dx), fy = f2mul(nW, dy), fz = f2mul(nW, dz);
         const float v[8] = {-fx.x, -fy.x, -fz.x, -fx.y, -fy.y, -fz.y, 0.f, 0.f};
         const float tot = reduce_scatter8(v, lane);
         if ((lane & 3) == 0 && kslot < 6) atomicAdd(&gj[3 * j + kslot], tot);
