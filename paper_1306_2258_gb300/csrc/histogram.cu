@@ -19,23 +19,28 @@ constexpr int kWarps = kTile / 32;
 
 // Bin of r2 under the rule above: max{k : e_k^2 <= r2} with e_k^2 = fl(fl(k w)^2), capped at
 // n_bins.  The first guess comes from the hardware reciprocal square root; the edge comparisons
-// (the rule's own float32 roundings) decide.
+// (the rule's own float32 roundings) decide: straight-line when the guess is right (almost
+// always), a short walk otherwise.
 __device__ __forceinline__ int bin_of(float r2, float w, float inv_w, int n_bins)
 {
     const float nb = (float)n_bins;
-    float k = fminf(floorf(r2 * rsqrtf(fmaxf(r2, 1e-30f)) * inv_w), nb);
-    k = fmaxf(k, 0.f);
-    for (int guard = 0; guard < 8 && k > 0.f; ++guard) {   // never more than a step or two
-        const float ek = __fmul_rn(k, w);
-        if (__fmul_rn(ek, ek) <= r2) break;
-        k -= 1.f;
+    float k = fminf(fmaxf(floorf(r2 * rsqrtf(fmaxf(r2, 1e-30f)) * inv_w), 0.f), nb);
+    const float elo = __fmul_rn(k, w), ehi = __fmul_rn(k + 1.f, w);
+    const bool lo_ok = k == 0.f || __fmul_rn(elo, elo) <= r2;
+    const bool hi_ok = k == nb || __fmul_rn(ehi, ehi) > r2;
+    if (!(lo_ok && hi_ok)) {
+        for (int guard = 0; guard < 8 && k > 0.f; ++guard) {   // never more than a step or two
+            const float ek = __fmul_rn(k, w);
+            if (__fmul_rn(ek, ek) <= r2) break;
+            k -= 1.f;
+        }
+        for (int guard = 0; guard < 8 && k < nb; ++guard) {
+            const float ek = __fmul_rn(k + 1.f, w);
+            if (__fmul_rn(ek, ek) > r2) break;
+            k += 1.f;
+        }
     }
-    for (int guard = 0; guard < 8 && k < nb; ++guard) {
-        const float ek = __fmul_rn(k + 1.f, w);
-        if (__fmul_rn(ek, ek) > r2) break;
-        k += 1.f;
-    }
-    return (int)k;
+    return __float_as_int(k + 8388608.f) - 0x4B000000;   // k < 2^23: its integer value
 }
 
 // One work item per CTA at a time.  Warp v takes the real rows i = v, v+4, ... of the I-tile (the
@@ -51,7 +56,7 @@ __global__ void __launch_bounds__(kTile)
     float4 *sj = smem;                                            // [jcap]
     float4 *si = sj + jcap;                                       // [kTile]
     int *wh = reinterpret_cast<int *>(si + kTile);                // [kWarps][n_bins]
-    __shared__ int next_item;
+    __shared__ int next_item, jreal;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float w = __fdiv_rn(r_max, (float)n_bins);
     const float inv_w = __fdiv_rn(1.0f, w);
@@ -60,21 +65,33 @@ __global__ void __launch_bounds__(kTile)
         const Item item = items[it];
         const float4 *Xb = X + (int64_t)item.batch * npad;
         __syncthreads();   // the previous item is done with the staging, histograms and next_item
-        if (tid == 0) next_item = (int)gridDim.x + atomicAdd(ticket, 1);
-        for (int j = tid; j < item.jlen; j += kTile) sj[j] = Xb[item.j0 + j];
+        if (tid == 0) {
+            next_item = (int)gridDim.x + atomicAdd(ticket, 1);
+            jreal = 0;
+        }
+        __syncthreads();   // jreal is zero before the staging adds to it
+        int real = 0;
+        for (int j = tid; j < item.jlen; j += kTile) {
+            const float4 x = Xb[item.j0 + j];
+            sj[j] = x;
+            real += x.w != 0.f;
+        }
         for (int k = tid; k < kWarps * n_bins; k += kTile) wh[k] = 0;
         const float4 xt = Xb[item.i0 + tid];
         si[tid] = xt;
-        // real atoms are a prefix of the tile (padding sits at the end of each type group)
+        if (real) atomicAdd(&jreal, real);
+        // real atoms are a prefix of the tile and of the J-range (padding sits at the end of each
+        // type group)
         const int ilen = __syncthreads_count(xt.w != 0.f);
+        const int jlen = jreal;
         int *h = wh + warp * n_bins;
         unsigned drop = 0;
         for (int i = warp; i < ilen; i += kWarps) {
             const float4 xi = si[i];
             const int jstart = item.diag ? i + 1 : 0;   // pairs with j <= i are not pairs of i<j
-            for (int j = jstart + lane; j < item.jlen; j += 32) {
+#pragma unroll 2
+            for (int j = jstart + lane; j < jlen; j += 32) {
                 const float4 xj = sj[j];
-                if (xj.w == 0.f) continue;
                 const float dx = __fsub_rn(xi.x, xj.x), dy = __fsub_rn(xi.y, xj.y), dz = __fsub_rn(xi.z, xj.z);
                 const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
                 const int k = bin_of(r2, w, inv_w, n_bins);
