@@ -128,8 +128,8 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 
-// S shared-memory stages: 3 for 128-column tiles and 4 for 64-column ones (about 97 KB either way,
-// so two CTAs share an SM and one's epilogue overlaps the other's main loop).
+// S shared-memory stages (launch_bn chooses: a deep ring for grids that leave SMs idle, else about
+// 97 KB so that two CTAs share an SM and one's epilogue overlaps the other's main loop).
 template <int BN, int S>
 __global__ void __launch_bounds__(128, 2)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
@@ -271,19 +271,38 @@ bool make_map(CUtensorMap &map, const void *base, int rows, int K, int ld, int b
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
-cudaError_t launch_bn(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias, float *C,
+template <int BN, int S>
+cudaError_t launch_bs(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias, float *C,
                       int ldc, void *D, int ldd, int gelu, cudaStream_t s)
 {
     CUtensorMap ta, tb;
     if (!make_map(ta, A, M, K, lda, kTcM) || !make_map(tb, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
-    constexpr int S = BN == 128 ? 3 : 4;
     const size_t smem = (size_t)S * (kABytes + BN * kTcK * 2) + 1024;
     cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + kTcM - 1) / kTcM));
     k_gemm_tc<BN, S><<<grid, 128, smem, s>>>(ta, tb, M, N, K, bias, C, ldc, static_cast<bf16 *>(D), ldd, gelu);
     return cudaGetLastError();
+}
+
+// Stages: with a grid that leaves SMs idle, one CTA per SM with a deep ring (8 stages of 24 KB for
+// 64-column tiles, 5 of 32 KB for 128-column ones) keeps more TMA loads in flight; otherwise about
+// 97 KB per CTA so that two CTAs share an SM.
+template <int BN>
+cudaError_t launch_bn(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias, float *C,
+                      int ldc, void *D, int ldd, int gelu, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess)
+        return cudaErrorInvalidDevice;
+    const int64_t ctas = (int64_t)((N + BN - 1) / BN) * ((M + kTcM - 1) / kTcM);
+    const bool deep = ctas <= sms;
+    if (BN == 64)
+        return deep ? launch_bs<64, 8>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s)
+                    : launch_bs<64, 4>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s);
+    return deep ? launch_bs<128, 5>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s)
+                : launch_bs<128, 3>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s);
 }
 
 }  // namespace

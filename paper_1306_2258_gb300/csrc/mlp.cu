@@ -9,9 +9,9 @@
 //                  FP32 accumulation with mma.sync m16n8k16 (64x64 CTA tile, four 32x32 warp
 //                  tiles); epilogue writes FP32 and/or bfloat16 of the value or of GELU(value).
 //   k_transpose    bfloat16 [R][C] -> [C][R] (the backward GEMMs' operands)
-//   k_mse          dY = 2 (Y - T) / (B Q) and the loss (one block, fixed order)
+//   k_mse_rows, k_mse_total  dY = 2 (Y - T) / (B Q) and the loss (per-row sums, then their sum; fixed order)
 //   k_gelu_bwd     dZ = dA * GELU'(Z), as FP32 and bfloat16
-//   k_colsum       bias gradients (fixed order over rows)
+//   k_colsum       bias gradients (8 row groups per column, then their sum; fixed order)
 //   k_adam         Adam on the FP32 masters, refreshing their bfloat16 copies
 // Every GEMM operand is rounded to bfloat16 exactly where the FP64 reference rounds it.
 #include <cuda_bf16.h>
@@ -140,14 +140,17 @@ __global__ void k_transpose(int R, int Rpad, int C, const bf16 *__restrict__ in,
 }
 
 // dY = 2 (Y - T) / (B Q) on the valid [B][Q] block (zero in the padding), loss = mean square
-__global__ void k_mse(int B, int Bpad, int Q, int Qpad, const float *__restrict__ Y, const float *__restrict__ T,
-                      float *__restrict__ dY, bf16 *__restrict__ dYb, float *__restrict__ loss)
+// One block per padded row b: dY, its bfloat16 copy, and the row's squared error (FP64, fixed
+// tree order).
+__global__ void k_mse_rows(int B, int Q, int Qpad, const float *__restrict__ Y, const float *__restrict__ T,
+                           float *__restrict__ dY, bf16 *__restrict__ dYb, double *__restrict__ rows)
 {
-    __shared__ double red[256];
+    __shared__ double red[128];
+    const int b = blockIdx.x;
     const double scale = 2.0 / ((double)B * Q);
     double s = 0.0;
-    for (int64_t i = threadIdx.x; i < (int64_t)Bpad * Qpad; i += blockDim.x) {
-        const int b = (int)(i / Qpad), q = (int)(i % Qpad);
+    for (int q = threadIdx.x; q < Qpad; q += blockDim.x) {
+        const int64_t i = (int64_t)b * Qpad + q;
         float d = 0.f;
         if (b < B && q < Q) {
             const double e = (double)Y[i] - (double)T[(int64_t)b * Q + q];
@@ -157,6 +160,21 @@ __global__ void k_mse(int B, int Bpad, int Q, int Qpad, const float *__restrict_
         dY[i] = d;
         dYb[i] = __float2bfloat16_rn(d);
     }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) rows[b] = red[0];
+}
+
+// loss = (sum of the row sums, fixed tree order) / (B Q)
+__global__ void k_mse_total(int B, int Q, int Bpad, const double *__restrict__ rows, float *__restrict__ loss)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < Bpad; b += blockDim.x) s += rows[b];
     red[threadIdx.x] = s;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -177,13 +195,23 @@ __global__ void k_gelu_bwd(int64_t n, const float *__restrict__ dA, const float 
 }
 
 // out[c] = sum_r in[r][c] over r < R, in fixed order
+// out[c] = sum over rows of in[r][c]: 32 columns per block, 8 row groups (rows r = g, g+8, ...),
+// then the 8 partial sums in a fixed order.
 __global__ void k_colsum(int R, int C, const float *__restrict__ in, int ld, float *__restrict__ out)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
+    __shared__ float part[8][33];
+    const int c = blockIdx.x * 32 + threadIdx.x, g = threadIdx.y;
     float s = 0.f;
-    for (int r = 0; r < R; ++r) s += in[(size_t)r * ld + c];
-    out[c] = s;
+    if (c < C)
+        for (int r = g; r < R; r += 8) s += in[(size_t)r * ld + c];
+    part[g][threadIdx.x] = s;
+    __syncthreads();
+    if (g == 0 && c < C) {
+        float t = part[0][threadIdx.x];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) t += part[k][threadIdx.x];
+        out[c] = t;
+    }
 }
 
 __global__ void k_adam(int64_t n, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
@@ -233,9 +261,11 @@ cudaError_t launch_transpose_bf16(int R, int Rpad, int C, const void *in, int ld
 }
 
 cudaError_t launch_mse(int B, int Bpad, int Q, int Qpad, const float *Y, const float *T, float *dY, void *dYb,
-                       float *loss, cudaStream_t s)
+                       double *rows, float *loss, cudaStream_t s)
 {
-    k_mse<<<1, 256, 0, s>>>(B, Bpad, Q, Qpad, Y, T, dY, static_cast<bf16 *>(dYb), loss);
+    if (Bpad <= 0) return cudaSuccess;
+    k_mse_rows<<<Bpad, 128, 0, s>>>(B, Q, Qpad, Y, T, dY, static_cast<bf16 *>(dYb), rows);
+    k_mse_total<<<1, 256, 0, s>>>(B, Q, Bpad, rows, loss);
     return cudaGetLastError();
 }
 
@@ -249,7 +279,7 @@ cudaError_t launch_gelu_bwd(int64_t n, const float *dA, const float *Z, float *d
 cudaError_t launch_colsum(int R, int C, const float *in, int ld, float *out, cudaStream_t s)
 {
     if (C <= 0) return cudaSuccess;
-    k_colsum<<<blocks_for(C, 128), 128, 0, s>>>(R, C, in, ld, out);
+    k_colsum<<<(C + 31) / 32, dim3(32, 8), 0, s>>>(R, C, in, ld, out);
     return cudaGetLastError();
 }
 

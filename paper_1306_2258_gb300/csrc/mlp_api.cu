@@ -66,6 +66,7 @@ struct sas_mlp {
     bf16 *W2t = nullptr, *W3t = nullptr;
     float *Xf = nullptr, *Tf = nullptr, *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dY = nullptr, *dA2 = nullptr,
           *dZ2 = nullptr, *dA1 = nullptr, *dZ1 = nullptr, *loss = nullptr;
+    double *rowloss = nullptr;   // per-row squared-error sums of the MSE
     bf16 *Xb = nullptr, *Xt = nullptr, *A1b = nullptr, *A1t = nullptr, *A2b = nullptr, *A2t = nullptr, *dYb = nullptr,
          *dYt = nullptr, *dZ2b = nullptr, *dZ2t = nullptr, *dZ1b = nullptr, *dZ1t = nullptr;
     std::vector<void *> owned;
@@ -122,7 +123,7 @@ sas_status mlp_forward(sas_mlp *m, const float *x, const float *t, int B, cudaSt
 sas_status mlp_backward(sas_mlp *m, int B, cudaStream_t s)
 {
     const int Bp = round16(B), h = m->h, Qp = m->n_outp;
-    MLP_TRY(launch_mse(B, Bp, m->n_out, Qp, m->Y, m->Tf, m->dY, m->dYb, m->loss, s));
+    MLP_TRY(launch_mse(B, Bp, m->n_out, Qp, m->Y, m->Tf, m->dY, m->dYb, m->rowloss, m->loss, s));
     // layer 3
     MLP_TRY(launch_transpose_bf16(Bp, Bp, Qp, m->dYb, Qp, m->dYt, Bp, s));
     MLP_TRY(launch_transpose_bf16(B, Bp, h, m->A2b, h, m->A2t, Bp, s));
@@ -212,7 +213,7 @@ sas_status sas_mlp_create(int n_in, int n_hidden, int n_out, int max_batch, sas_
               mlp_alloc(m, m->W3t, h * Qp) && mlp_alloc(m, m->Xf, Bp * n_in) && mlp_alloc(m, m->Tf, Bp * n_out) &&
               mlp_alloc(m, m->Z1, Bp * h) && mlp_alloc(m, m->Z2, Bp * h) && mlp_alloc(m, m->Y, Bp * Qp) &&
               mlp_alloc(m, m->dY, Bp * Qp) && mlp_alloc(m, m->dA2, Bp * h) && mlp_alloc(m, m->dZ2, Bp * h) &&
-              mlp_alloc(m, m->dA1, Bp * h) && mlp_alloc(m, m->dZ1, Bp * h) && mlp_alloc(m, m->loss, 1) &&
+              mlp_alloc(m, m->dA1, Bp * h) && mlp_alloc(m, m->dZ1, Bp * h) && mlp_alloc(m, m->loss, 1) && mlp_alloc(m, m->rowloss, Bp) &&
               mlp_alloc(m, m->Xb, Bp * n_in) && mlp_alloc(m, m->Xt, Bp * n_in) && mlp_alloc(m, m->A1b, Bp * h) &&
               mlp_alloc(m, m->A1t, Bp * h) && mlp_alloc(m, m->A2b, Bp * h) && mlp_alloc(m, m->A2t, Bp * h) &&
               mlp_alloc(m, m->dYb, Bp * Qp) && mlp_alloc(m, m->dYt, Bp * Qp) && mlp_alloc(m, m->dZ2b, Bp * h) &&

@@ -149,7 +149,7 @@ cudaError_t launch_to_bf16(int64_t n, const float *x, void *y, cudaStream_t s);
 cudaError_t launch_transpose_bf16(int R, int Rpad, int C, const void *in, int ldin, void *out, int ldout,
                                   cudaStream_t s);
 cudaError_t launch_mse(int B, int Bpad, int Q, int Qpad, const float *Y, const float *T, float *dY, void *dYb,
-                       float *loss, cudaStream_t s);
+                       double *rows, float *loss, cudaStream_t s);
 cudaError_t launch_gelu_bwd(int64_t n, const float *dA, const float *Z, float *dZ, void *dZb, cudaStream_t s);
 cudaError_t launch_colsum(int R, int C, const float *in, int ld, float *out, cudaStream_t s);
 cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,
