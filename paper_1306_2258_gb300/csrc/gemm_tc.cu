@@ -13,11 +13,12 @@
 //    stage's MMAs to its "empty" mbarrier; a last commit signals "done";
 //  * then every warp reads its 32 accumulator lanes (rows) with tcgen05.ld and applies the
 //    epilogue.
-// Every mbarrier wait has an iteration limit; a wait that runs out sets the error word and the
-// kernel still frees its tensor memory.
+// Every mbarrier wait gives up after 2 s (or an iteration limit); a wait that gives up sets the
+// error word, the other roles stop at their next wait, and the kernel still frees its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "sas_internal.h"
@@ -30,6 +31,7 @@ using bf16 = __nv_bfloat16;
 constexpr int kTcM = 128;                 // tile rows: the M of one tcgen05.mma
 constexpr int kTcK = 64;                  // K per stage: 64 bfloat16 = one 128-byte swizzle row
 constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s: far beyond any wait of a correct run
 constexpr uint32_t kABytes = kTcM * kTcK * 2;
 
 __device__ int g_tc_error;   // set when a wait ran out of iterations (never reset by the kernels)
@@ -46,10 +48,19 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
 }
 
-// Wait until the phase of parity `parity` has completed; false if the iteration limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity)
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait until the phase of parity `parity` has completed; false after kWaitNs of waiting (or the
+// iteration limit), or, with `fail` given, as soon as another role has set *fail.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, const volatile int *fail = nullptr)
 {
     const uint32_t a = smem_u32(b);
+    const uint64_t t0 = global_ns();
     for (uint32_t i = 0; i < kSpinLimit; ++i) {
         uint32_t ok;
         asm volatile(
@@ -62,6 +73,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity)
             : "r"(a), "r"(parity)
             : "memory");
         if (ok) return true;
+        if ((i & 255u) == 255u) {
+            if (fail && *fail) return false;
+            if (global_ns() - t0 > kWaitNs) return false;
+        }
     }
     return false;
 }
@@ -236,6 +251,156 @@ __global__ void __launch_bounds__(128, 2)
     }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+// Persistent form for grids of at least one tile per SM: one CTA per SM walks tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (M fastest, so neighbouring CTAs share B tiles in L2).  Warp 0 lane 0
+// streams A and B slices with TMA into S stages; warp 1 lane 0 issues the MMAs into one of two
+// accumulators in tensor memory (tile i uses accumulator i & 1) and commits "full" when a tile is
+// done; warps 2-5 (tensor-memory lane quarters 2, 3, 0, 1) read the finished accumulator, apply the
+// epilogue and release it, so the epilogue of one tile runs under the main loop of the next.
+template <int BN, int S>
+__global__ void __launch_bounds__(192, 1)
+    k_gemm_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
+               const float *__restrict__ bias, float *__restrict__ C, int ldc, bf16 *__restrict__ D, int ldd, int gelu)
+{
+    constexpr uint32_t kBBytes = BN * kTcK * 2;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = smem_raw + (((smem_u32(smem_raw) + 1023u) & ~1023u) - smem_u32(smem_raw));
+    uint8_t *sA = smem;                 // [S][128 rows][128 B]
+    uint8_t *sB = smem + S * kABytes;   // [S][BN rows][128 B]
+    __shared__ __align__(8) uint64_t full[S], empty[S], tfull[2], tempty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int fail;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = (M + kTcM - 1) / kTcM, nt = (N + BN - 1) / BN, tiles = mt * nt;
+    const int ksteps = (K + kTcK - 1) / kTcK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);   // one arrival per epilogue warp
+        }
+        fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (warp == 0) {   // two accumulators of BN columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"((uint32_t)(2 * BN))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {   // TMA producer
+            int it = 0, issued = 0;
+            for (int t = blockIdx.x; t < tiles && !fail; t += gridDim.x) {
+                const int m0 = (t % mt) * kTcM, n0 = (t / mt) * BN;
+                for (int ks = 0; ks < ksteps; ++ks, ++it) {
+                    const int s = it % S;
+                    if (it >= S && !mbar_wait(&empty[s], (uint32_t)((it / S) - 1) & 1u, &fail)) {
+                        fail = 1;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], kABytes + kBBytes);
+                    tma_load_2d(sA + s * kABytes, &tmA, &full[s], ks * kTcK, m0);
+                    tma_load_2d(sB + s * kBBytes, &tmB, &full[s], ks * kTcK, n0);
+                    issued = it + 1;
+                }
+            }
+            // copies still in flight (normally all were consumed): the last phase of each used stage
+            for (int k = issued > S ? issued - S : 0; k < issued; ++k)
+                if (!mbar_wait(&full[k % S], (uint32_t)(k / S) & 1u)) fail = 1;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            const uint32_t idesc = idesc_bf16(kTcM, BN);
+            int it = 0, i = 0;
+            for (int t = blockIdx.x; t < tiles && !fail; t += gridDim.x, ++i) {
+                const int acc = i & 1;
+                if (i >= 2 && !mbar_wait(&tempty[acc], (uint32_t)((i / 2) - 1) & 1u, &fail)) {
+                    fail = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t td = tmem + (uint32_t)(acc * BN);
+                for (int ks = 0; ks < ksteps; ++ks, ++it) {
+                    const int s = it % S;
+                    if (!mbar_wait(&full[s], (uint32_t)(it / S) & 1u, &fail)) {
+                        fail = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
+#pragma unroll
+                    for (int kk = 0; kk < kTcK / 16; ++kk)
+                        umma_bf16(td, sw128_desc(a0 + 32u * kk), sw128_desc(b0 + 32u * kk), idesc,
+                                  (ks > 0 || kk > 0) ? 1u : 0u);
+                    umma_commit(&empty[s]);
+                }
+                umma_commit(&tfull[acc]);   // arrives when this tile's MMAs have completed
+            }
+        }
+    } else {   // epilogue warps
+        const int quarter = warp & 3;   // the tensor-memory lanes this warp may read
+        int i = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+            const int acc = i & 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(&tfull[acc], (uint32_t)(i / 2) & 1u, &fail) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) fail = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m0 = (t % mt) * kTcM, n0 = (t / mt) * BN;
+            const int row = m0 + quarter * 32 + lane;
+            const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 8) {
+                float v[8];
+                tmem_ld8(trow + (uint32_t)c0, v);
+                if (row < M) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int col = n0 + c0 + k;
+                        if (col >= N) break;
+                        float x = ksteps > 0 ? v[k] : 0.f;
+                        if (bias) x += bias[col];
+                        if (C) C[(size_t)row * ldc + col] = x;
+                        if (D) D[(size_t)row * ldd + col] = __float2bfloat16_rn(gelu ? gelu_f(x) : x);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+        }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && fail) atomicExch(&g_tc_error, 1);
+    __syncwarp();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
+                     : "memory");
+    }
+}
+
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -285,6 +450,21 @@ cudaError_t launch_bs(int M, int N, int K, const void *A, int lda, const void *B
     return cudaGetLastError();
 }
 
+template <int BN, int S>
+cudaError_t launch_persistent(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
+                              float *C, int ldc, void *D, int ldd, int gelu, int sms, cudaStream_t s)
+{
+    CUtensorMap ta, tb;
+    if (!make_map(ta, A, M, K, lda, kTcM) || !make_map(tb, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)S * (kABytes + BN * kTcK * 2) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tcp<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int tiles = ((M + kTcM - 1) / kTcM) * ((N + BN - 1) / BN);
+    k_gemm_tcp<BN, S><<<std::min(tiles, sms), 192, smem, s>>>(ta, tb, M, N, K, bias, C, ldc, static_cast<bf16 *>(D),
+                                                               ldd, gelu);
+    return cudaGetLastError();
+}
+
 // Stages: with a grid that leaves SMs idle, one CTA per SM with a deep ring (8 stages of 24 KB for
 // 64-column tiles, 5 of 32 KB for 128-column ones) keeps more TMA loads in flight; otherwise about
 // 97 KB per CTA so that two CTAs share an SM.
@@ -317,8 +497,16 @@ cudaError_t launch_gemm_tc(int M, int N, int K, const void *A, int lda, const vo
                            float *C, int ldc, void *D, int ldd, int gelu, cudaStream_t s)
 {
     if (M <= 0 || N <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaErrorInvalidDevice;
+    // large problems: the persistent kernel with 128 x 256 tiles when every SM gets several
+    const int mt = (M + kTcM - 1) / kTcM;
+    if (N >= 256 && mt * ((N + 255) / 256) >= 2 * sms)
+        return launch_persistent<256, 4>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, sms, s);
     // 64-column tiles when 128-column ones would leave most SMs idle
-    const int tiles128 = ((M + kTcM - 1) / kTcM) * ((N + 127) / 128);
+    const int tiles128 = mt * ((N + 127) / 128);
     if (N <= 64 || tiles128 < 64) return launch_bn<64>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s);
     return launch_bn<128>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s);
 }

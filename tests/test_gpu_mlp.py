@@ -37,6 +37,29 @@ def test_gemm_bf16_matches_fp64(M, N, K):
     assert np.all(np.abs(C.double().cpu().numpy() - expect) <= 1e-6 * bound)
 
 
+@pytest.mark.parametrize("M,N,K", [(8192, 2048, 320), (8000, 2000, 208)])
+def test_gemm_bf16_large_persistent_path(M, N, K):
+    """Problems with several 128 x 256 tiles per SM take the persistent kernel (two tensor-memory
+    accumulators, epilogue overlapped with the next tile); K = 208 ends in a partial 64-wide slice and
+    8000 x 2000 leaves partial tiles in both M and N.
+    Checked on row blocks from every part of C against FP64 products of the same inputs."""
+    rng = np.random.default_rng(M + N + K)
+    A = torch.from_numpy(rng.standard_normal((M, K)).astype(np.float32)).to(torch.bfloat16).cuda()
+    B = torch.from_numpy(rng.standard_normal((N, K)).astype(np.float32)).to(torch.bfloat16).cuda()
+    bias = torch.from_numpy(rng.standard_normal(N).astype(np.float32)).cuda()
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    _lib.sas_gemm_bf16(M, N, K, A, K, B, K, bias, C, N)
+    Bd = B.double().cpu().numpy()
+    rows = np.concatenate([np.arange(0, 130), np.arange(M // 2 - 70, M // 2 + 70), np.arange(M - 130, M),
+                           rng.integers(0, M, 64)])
+    Ad = A[torch.as_tensor(rows).cuda()].double().cpu().numpy()
+    expect = Ad @ Bd.T + bias.double().cpu().numpy()
+    got = C[torch.as_tensor(rows).cuda()].double().cpu().numpy()
+    bound = np.abs(Ad) @ np.abs(Bd).T + 1.0
+    assert not np.isnan(got).any()
+    assert np.all(np.abs(got - expect) <= 1e-6 * bound)
+
+
 def _net_and_data(n_in=64, h=48, n_out=13, B=40, seed=7):
     net = SurrogateMLP(n_in, h, n_out, max_batch=64, seed=seed)
     rng = np.random.default_rng(seed)
