@@ -13,6 +13,9 @@
 //    stage's MMAs to its "empty" mbarrier; a last commit signals "done";
 //  * then every warp reads its 32 accumulator lanes (rows) with tcgen05.ld and applies the
 //    epilogue.
+// Problems of at least two 128 x 256 tiles per SM take the persistent form k_gemm_tcp instead: one
+// CTA per SM walks its tiles with warp-specialized roles (producer, MMA issuer, four epilogue warps)
+// and two accumulators in tensor memory, so a tile's epilogue runs under the next tile's main loop.
 // Every mbarrier wait gives up after 2 s (or an iteration limit); a wait that gives up sets the
 // error word, the other roles stop at their next wait, and the kernel still frees its tensor memory.
 #include <cuda.h>
@@ -262,10 +265,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b)
 // accumulators in tensor memory (tile i uses accumulator i & 1) and commits "full" when a tile is
 // done; warps 2-5 (tensor-memory lane quarters 2, 3, 0, 1) read the finished accumulator, apply the
 // epilogue and release it, so the epilogue of one tile runs under the main loop of the next.
+// Tile t of the persistent walk: groups of `group` row tiles, each group covering every column tile
+// before the next starts (rows fastest inside a group), so the CTAs in flight share both A and B
+// tiles in L2.
+__device__ __forceinline__ void tile_of(int t, int mt, int nt, int group, int &m0, int &n0, int bn)
+{
+    const int per = group * nt, g = t / per, local = t - g * per;
+    const int gm = min(group, mt - g * group);
+    m0 = (g * group + local % gm) * kTcM;
+    n0 = (local / gm) * bn;
+}
+
 template <int BN, int S>
 __global__ void __launch_bounds__(192, 1)
     k_gemm_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
-               const float *__restrict__ bias, float *__restrict__ C, int ldc, bf16 *__restrict__ D, int ldd, int gelu)
+               const float *__restrict__ bias, float *__restrict__ C, int ldc, bf16 *__restrict__ D, int ldd, int gelu,
+               int group)
 {
     constexpr uint32_t kBBytes = BN * kTcK * 2;
     extern __shared__ uint8_t smem_raw[];
@@ -306,7 +321,8 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {   // TMA producer
             int it = 0, issued = 0;
             for (int t = blockIdx.x; t < tiles && !fail; t += gridDim.x) {
-                const int m0 = (t % mt) * kTcM, n0 = (t / mt) * BN;
+                int m0, n0;
+                tile_of(t, mt, nt, group, m0, n0, BN);
                 for (int ks = 0; ks < ksteps; ++ks, ++it) {
                     const int s = it % S;
                     if (it >= S && !mbar_wait(&empty[s], (uint32_t)((it / S) - 1) & 1u, &fail)) {
@@ -365,7 +381,8 @@ __global__ void __launch_bounds__(192, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int m0 = (t % mt) * kTcM, n0 = (t / mt) * BN;
+            int m0, n0;
+            tile_of(t, mt, nt, group, m0, n0, BN);
             const int row = m0 + quarter * 32 + lane;
             const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
@@ -460,8 +477,9 @@ cudaError_t launch_persistent(int M, int N, int K, const void *A, int lda, const
     cudaError_t e = cudaFuncSetAttribute(k_gemm_tcp<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int tiles = ((M + kTcM - 1) / kTcM) * ((N + BN - 1) / BN);
+    const int group = 16;   // 8192^3: 1234 TFLOP/s with rows fastest over all of M, 1336 with groups of 16
     k_gemm_tcp<BN, S><<<std::min(tiles, sms), 192, smem, s>>>(ta, tb, M, N, K, bias, C, ldc, static_cast<bf16 *>(D),
-                                                               ldd, gelu);
+                                                               ldd, gelu, group);
     return cudaGetLastError();
 }
 
