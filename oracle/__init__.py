@@ -42,12 +42,13 @@ def _configure(lib):
     lib.oracle_form_factors.argtypes = [_i64, _ip, _i32, _dp, _i32, _dp, _dp]
     lib.oracle_profile.argtypes = [_i64, _dp, _ip, _i32, _dp, _i32, _dp, _i32, _dp, _dp]
     lib.oracle_profile_full.argtypes = [_i64, _dp, _ip, _i32, _dp, _i32, _dp, _dp]
+    lib.oracle_profile_atomic.argtypes = [_i64, _dp, _dp, _i32, _dp, _i32, _dp, _dp]
     lib.oracle_pair_sums.argtypes = [_i64, _dp, _ip, _i32, _i32, _dp, _i32, _dp]
     lib.oracle_vjp.argtypes = [_i64, _dp, _ip, _i32, _dp, _i32, _dp, _dp, _i32, _dp]
     lib.oracle_chi2_grad.argtypes = [_i64, _dp, _ip, _i32, _dp, _i32, _dp, _dp, _dp, _i32,
                                      _dp, _dp, _dp]
     lib.oracle_pair_histogram.argtypes = [_i64, _fp, _ip, _i32, _i32, ctypes.c_float, _ip, _lp]
-    for f in ("oracle_form_factors", "oracle_profile", "oracle_profile_full",
+    for f in ("oracle_form_factors", "oracle_profile", "oracle_profile_full", "oracle_profile_atomic",
               "oracle_pair_sums", "oracle_vjp", "oracle_chi2_grad", "oracle_pair_histogram"):
         getattr(lib, f).restype = _i32
     return lib
@@ -107,6 +108,19 @@ def profile(coords, types, coef, q, n_threads: int = 0, with_kappa: bool = False
     kap = np.empty(qq.size)
     _check(lib.oracle_profile(x.shape[0], xp, tp, c.shape[0], cp, qq.size, qp, n_threads,
                               I.ctypes.data_as(_dp), kap.ctypes.data_as(_dp)), "profile")
+    return (I, kap) if with_kappa else I
+
+
+def profile_atomic(coords, ff, q, n_threads: int = 0, with_kappa: bool = False):
+    """I(q) by Eq. 2 with per-atom form factors ff[k, i] = f_i(q_k) (shape [n_q, n]), float64."""
+    lib = _load()
+    x, xp = _d(np.asarray(coords).reshape(-1, 3))
+    qq, qp = _d(q)
+    f, fp = _d(np.asarray(ff).reshape(qq.size, x.shape[0]))
+    I = np.empty(qq.size)
+    kap = np.empty(qq.size)
+    _check(lib.oracle_profile_atomic(x.shape[0], xp, fp, qq.size, qp, n_threads,
+                                     I.ctypes.data_as(_dp), kap.ctypes.data_as(_dp)), "profile_atomic")
     return (I, kap) if with_kappa else I
 
 

@@ -11,7 +11,8 @@
  * Everything here is the plain definition, written out with no blocking,
  * type factoring, recurrence or reordering beyond what the definition needs:
  *
- *   f_j(q)  = sum_{k=1..4} a_k exp(-b_k (q/4pi)^2) + c         (per atom, from its type)
+ *   f_j(q)  = sum_{k=1..4} a_k exp(-b_k (q/4pi)^2) + c         (per atom, from its type;
+ *             or given per atom and q directly, oracle_profile_atomic)
  *   I(q)    = sum_k sum_j f_k(q) f_j(q) sin(q r_jk)/(q r_jk)   (Section I-A, Eq. 2)
  *           = sum_i f_i^2 + 2 sum_{i<j} f_i f_j sinc(q r_ij)   (only j <= k, Section II)
  *
@@ -134,12 +135,47 @@ static inline double dist(const double *a, const double *b)
  * kappa_out[k] = (sum_i f_i^2 + 2 sum_{i<j} |f_i f_j sinc|) / |I(q_k)|  (conditioning; may be NULL)
  * Returns 0, -1 on a type out of range, -2 on allocation failure.
  */
+static int profile_core(int64_t n, const double *xyz, const double *f, int n_q, const double *q,
+                        int n_threads, double *I_out, double *kappa_out);
+
 int oracle_profile(int64_t n, const double *xyz, const int32_t *types, int n_types,
                    const double *coef, int n_q, const double *q, int n_threads,
                    double *I_out, double *kappa_out)
 {
     if (check_types(n, types, n_types))
         return -1;
+    double *f = atom_form_factors(n, types, coef, n_q, q);
+    if (!f)
+        return -2;
+    int rc = profile_core(n, xyz, f, n_q, q, n_threads, I_out, kappa_out);
+    free(f);
+    return rc;
+}
+
+/*
+ * The same sum with every atom's form factor given directly, with no types: ff[k * n + i] =
+ * f_i(q_k), one row of N values per q (Section II keeps, for each q value, one form factor per
+ * atom; Section I-A: with a hydration layer the products f_k f_j do not reduce to a few types).
+ * Returns 0 or -2 on allocation failure.
+ */
+int oracle_profile_atomic(int64_t n, const double *xyz, const double *ff, int n_q, const double *q,
+                          int n_threads, double *I_out, double *kappa_out)
+{
+    double *f = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)n_q);
+    if (!f)
+        return -2;
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < n_q; ++k)
+            f[i * n_q + k] = ff[(int64_t)k * n + i];
+    int rc = profile_core(n, xyz, f, n_q, q, n_threads, I_out, kappa_out);
+    free(f);
+    return rc;
+}
+
+/* f[i * n_q + k] = f_i(q_k), atom-major. */
+static int profile_core(int64_t n, const double *xyz, const double *f, int n_q, const double *q,
+                        int n_threads, double *I_out, double *kappa_out)
+{
     if (n == 0) {
         for (int k = 0; k < n_q; ++k) {
             I_out[k] = 0.0;
@@ -148,11 +184,9 @@ int oracle_profile(int64_t n, const double *xyz, const int32_t *types, int n_typ
         }
         return 0;
     }
-    double *f = atom_form_factors(n, types, coef, n_q, q);
     double *row = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n_q);
     double *rowabs = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n_q);
-    if (!f || !row || !rowabs) {
-        free(f);
+    if (!row || !rowabs) {
         free(row);
         free(rowabs);
         return -2;
@@ -209,7 +243,6 @@ int oracle_profile(int64_t n, const double *xyz, const int32_t *types, int n_typ
                 kappa_out[k] = I_out[k] != 0.0 ? mag / fabs(I_out[k]) : INFINITY;
         }
     }
-    free(f);
     free(row);
     free(rowabs);
     return fail ? -2 : 0;

@@ -4,9 +4,11 @@ The paper measured "randomly generated proteins" of 1k-100k atoms (Section III,
 Table 1) and argued for the direct sum on elongated DNA/RNA-like structures and
 sparse pseudo-atom models (Abstract; Section I-A).  None of its molecules ship,
 so these generators stand in for them.  They draw positions, atom types,
-form-factor coefficients and q grids only: nothing here evaluates a form
-factor, a distance or a sinc, so the CPU oracle and the CUDA library can both
-be fed from this module without sharing any of the method's arithmetic.
+form-factor coefficients, q grids and per-atom form-factor tables (an input of
+their own, drawn from a recipe stated below, not from the type coefficients):
+nothing here evaluates the method's type form factor, a distance or a sinc, so
+the CPU oracle and the CUDA library can both be fed from this module without
+sharing any of the method's arithmetic.
 
 Every generator takes an explicit integer seed and uses NumPy's PCG64
 (``np.random.default_rng``), so a (generator, seed) pair names an input
@@ -63,6 +65,25 @@ def form_factor_coefficients(n_types: int, seed: int) -> np.ndarray:
         out[t, 4:8] = rng.uniform(0.5, 40.0, size=4)
         out[t, 8] = rng.uniform(0.0, 0.5)
     return out
+
+
+def atomic_form_factor_table(n: int, q: np.ndarray, seed: int, shell_fraction: float = 0.3) -> np.ndarray:
+    """Per-atom form factors ff[k, i] = f_i(q_k), shape [n_q, n], for the per-atom path (no types).
+
+    Stand-in for vacuum form factors corrected for excluded volume plus a hydration shell, the
+    case where the products f_k f_j do not reduce to a few types (Section I-A, after Eq. 2): each
+    atom draws its own shape a_i exp(-b_i q^2) + c_i with a_i in U[1, 8], b_i in U[0.02, 0.5] Å^2,
+    c_i in U[-0.3, 0.3]; a fraction ``shell_fraction`` of the atoms (the surface, in a water
+    layer) add d_i exp(-0.6 q^2) with d_i in U[-1, 1.5].  Drawn in the order a, b, c, shell mask, d.
+    """
+    rng = np.random.default_rng(seed)
+    qq = np.asarray(q, dtype=np.float64)[:, None]
+    a = rng.uniform(1.0, 8.0, size=n)
+    b = rng.uniform(0.02, 0.5, size=n)
+    c = rng.uniform(-0.3, 0.3, size=n)
+    shell = rng.uniform(size=n) < shell_fraction
+    d = np.where(shell, rng.uniform(-1.0, 1.5, size=n), 0.0)
+    return np.ascontiguousarray(a * np.exp(-b * qq * qq) + c + d * np.exp(-0.6 * qq * qq))
 
 
 def q_grid(lo: float, hi: float, n: int) -> np.ndarray:

@@ -191,6 +191,56 @@ def test_pair_sums_assemble_profile_and_count_pairs():
     np.testing.assert_allclose(I, oracle.profile(mol.coords, mol.types, coef, q), rtol=1e-13)
 
 
+# ---------------------------------------------------------------- per-atom form factors
+
+@pytest.mark.parametrize("seed", [61, 62])
+def test_atomic_eq2_matches_eq1_orientation_average(seed):
+    """Per-atom f_i(q) of arbitrary sign and shape (no types): Eq. 2 against the orientation
+    average of Eq. 1 by quadrature, an independent route."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(3, 12))
+    xyz = rng.uniform(-8, 8, size=(n, 3))
+    q = wl.q_grid(0.0, 0.5, 7)
+    ff = rng.uniform(-2.0, 6.0, size=(q.size, n))      # [n_q, n]: any value at any q
+    I2 = oracle.profile_atomic(xyz, ff, q)
+    I1 = _eq1_quadrature(xyz, ff.T.copy(), q)
+    np.testing.assert_allclose(I2, I1, rtol=1e-12, atol=1e-12 * np.max(np.abs(I1)))
+
+
+def test_atomic_two_atoms_closed_form():
+    """I = f1^2 + f2^2 + 2 f1 f2 sin(q r)/(q r) with different f1(q), f2(q) at every q."""
+    q = np.array([0.0, 0.13, 0.4, 0.77, 1.5])
+    ff = np.array([[3.0, -1.25], [2.5, 0.5], [1.75, 2.0], [-0.5, 4.0], [0.25, 0.125]])
+    r = 4.3
+    xyz = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+    x = q * r
+    sinc = np.where(x == 0, 1.0, np.sin(x) / np.where(x == 0, 1.0, x))
+    expect = ff[:, 0] ** 2 + ff[:, 1] ** 2 + 2 * ff[:, 0] * ff[:, 1] * sinc
+    np.testing.assert_allclose(oracle.profile_atomic(xyz, ff, q), expect, rtol=1e-14)
+
+
+def test_atomic_zero_q_is_square_of_total():
+    mol = wl.random_walk_globule(200, 1, 63)
+    q = wl.q_grid(0.0, 0.3, 4)
+    ff = wl.atomic_form_factor_table(mol.n, q, 64)
+    I = oracle.profile_atomic(mol.coords, ff, q)
+    assert math.isclose(I[0], math.fsum(ff[0]) ** 2, rel_tol=1e-14)
+
+
+def test_atomic_quadratic_in_shell_weight_and_types_limit():
+    """f_i(q) = f_type(i)(q) + lam g_i(q): I(lam) is a quadratic in lam (equal second
+    differences), and at lam = 0 it is the typed profile."""
+    mol = wl.random_walk_globule(160, 3, 65)
+    coef = wl.form_factor_coefficients(3, 66)
+    q = wl.q_grid(0.0, 1.0, 11)
+    f0 = oracle.form_factors(mol.types, coef, q).T.copy()          # [n_q, n]
+    g = wl.atomic_form_factor_table(mol.n, q, 67) - 4.0
+    I = {lam: oracle.profile_atomic(mol.coords, f0 + lam * g, q) for lam in (-1, 0, 1, 2)}
+    np.testing.assert_allclose(I[2] - 2 * I[1] + I[0], I[1] - 2 * I[0] + I[-1],
+                               rtol=1e-9, atol=1e-9 * np.max(np.abs(I[1])))
+    np.testing.assert_allclose(I[0], oracle.profile(mol.coords, mol.types, coef, q), rtol=1e-14)
+
+
 # ---------------------------------------------------------------- invariances
 
 def _mol_case(n=250, seed=51):
