@@ -130,6 +130,25 @@ sas_status sas_profile_vjp(sas_ctx *ctx, const float *coords, const int32_t *typ
 sas_status sas_partials(sas_ctx *ctx, double *S_out, int64_t capacity, void *stream);
 
 /*
+ * I(q) with a form factor per atom and q, no types (Section I-A, Eq. 2 as written: with a hydration
+ * layer the products f_k f_j do not reduce to a few types; Section II keeps, for every q value, one
+ * form factor per atom).  The context supplies the q grid, precision and options; its type
+ * coefficients are not used.
+ *   coords [batch][n_atoms][3] float or double (coords_type), device or host.
+ *   ff     [batch][n_q][n_atoms] double, f_i(q_k) at ff[(b * n_q + k) * n_atoms + i], device or host.
+ *   I_out  [batch][n_q] double: sum_i f_i(q)^2 + 2 sum_{i<j} f_i(q) f_j(q) sinc(q r_ij), and at
+ *          q = 0 exactly (sum_i f_i(0))^2.
+ * The mixed path weights each FP32 recurrence term by f_j(q) in FP32 and each atom's sums by
+ * f_i(q) in FP32 before the FP64 reduction; the diagonal and q = 0 are FP64.  Small molecules
+ * (the automatic re-seed rule of SAS_OPT_RESEED) run the q grid in passes of the re-seed interval.
+ * Errors: INVALID_ARG (null pointer, bad coords_type, non-finite coordinate or form factor),
+ * UNSUPPORTED (sharded context, batch > 65535, q grid needing more than 64 passes), ALLOC, CUDA,
+ * TIMEOUT.  sas_partials is not available after this call.
+ */
+sas_status sas_profile_atomic(sas_ctx *ctx, const void *coords, int coords_type, int64_t n_atoms, int64_t batch,
+                              const double *ff, double *I_out, void *stream);
+
+/*
  * Exact integer histogram of unordered pair distances by type pair.
  *   coords [batch][n_atoms][3] float; types [n_atoms]; hist_out [batch][T(T+1)/2][n_bins] int32;
  *   dropped_out [batch] int64 (pairs beyond the last edge) or NULL.

@@ -29,7 +29,7 @@ EXPORTS = (
     "sas_profile_vjp", "sas_partials", "sas_pair_histogram", "sas_set_option", "sas_last_stats",
     "sas_last_error", "sas_version", "sas_profile_static", "sas_mlp_create", "sas_mlp_destroy",
     "sas_mlp_param_count", "sas_mlp_set_state", "sas_mlp_get_state", "sas_mlp_forward", "sas_mlp_train_step",
-    "sas_mlp_grads", "sas_gemm_bf16", "sas_screen_select", "sas_gather_rows",
+    "sas_mlp_grads", "sas_gemm_bf16", "sas_screen_select", "sas_gather_rows", "sas_profile_atomic",
 )
 
 
@@ -77,6 +77,7 @@ def load():
                 "sas_gemm_bf16": [_int, _int, _int, _vp, _int, _vp, _int, _vp, _vp, _int, _vp],
                 "sas_screen_select": [_int, _int, _vp, _int, _vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _vp],
                 "sas_gather_rows": [_vp, _i64, _vp, _i64, _vp, _vp],
+                "sas_profile_atomic": [_vp, _vp, _int, _i64, _i64, _vp, _vp, _vp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -162,6 +163,11 @@ def sas_profile_grad(ctx, coords, types, n_atoms, batch, target, weights, chi2_o
 def sas_profile_vjp(ctx, coords, types, n_atoms, batch, grad_I, grad_out, stream=None):
     check(load().sas_profile_vjp(ctx, ptr(coords), ptr(types), int(n_atoms), int(batch), ptr(grad_I),
                                  ptr(grad_out), stream_handle(stream)))
+
+
+def sas_profile_atomic(ctx, coords, coords_type, n_atoms, batch, ff, I_out, stream=None):
+    check(load().sas_profile_atomic(ctx, ptr(coords), int(coords_type), int(n_atoms), int(batch), ptr(ff),
+                                    ptr(I_out), stream_handle(stream)))
 
 
 def sas_partials(ctx, S_out, capacity, stream=None):

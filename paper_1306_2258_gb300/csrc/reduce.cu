@@ -50,6 +50,40 @@ __global__ void k_reduce_items(const double *partial, int part_stride, const Ite
     S[(int64_t)g * qc.n_q + k] = q > 0.0 ? s / q : 0.0;
 }
 
+// Two-level form for groups of many items (one type pair over a long work list): block (seg, g)
+// sums items [seg * kSegItems, ...) of group g in list order for every q (threads along q, so the
+// partials are read coalesced); k_reduce_finish adds the segments in order.  A group of at most
+// kSegItems items gets exactly the single-level result.
+__global__ void k_reduce_segments(const double *partial, int part_stride, const Item *items, const int *group_items,
+                                  const int *group_off, QChunks qc, int max_seg, double *seg_out)
+{
+    const int g = blockIdx.y, seg = blockIdx.x;
+    const int b = group_off[g] + seg * kSegItems, e = min(group_off[g + 1], b + kSegItems);
+    if (b >= e) return;
+    for (int k = threadIdx.x; k < qc.n_q; k += blockDim.x) {
+        double s = 0.0;
+        for (int idx = b; idx < e; ++idx) {
+            const int it = group_items[idx];
+            const int ch = items[it].chunk;
+            const int kk = k - qc.q_begin[ch];
+            if (kk >= 0 && kk < qc.q_len[ch]) s += partial[(int64_t)it * part_stride + kk];
+        }
+        seg_out[((int64_t)g * max_seg + seg) * qc.n_q + k] = s;
+    }
+}
+
+__global__ void k_reduce_finish(const double *seg_out, const int *group_off, QChunks qc, int max_seg, double *S)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.y;
+    if (k >= qc.n_q) return;
+    const int nseg = (group_off[g + 1] - group_off[g] + kSegItems - 1) / kSegItems;
+    double s = 0.0;
+    for (int seg = 0; seg < nseg; ++seg) s += seg_out[((int64_t)g * max_seg + seg) * qc.n_q + k];
+    const double q = qval(qc, k);
+    S[(int64_t)g * qc.n_q + k] = q > 0.0 ? s / q : 0.0;
+}
+
 // whole = 0 (a shard other than the first of a split work list): no diagonal, and S(0) = 0, since
 // the first shard carries the exact pair counts at q = 0.
 __global__ void k_assemble(double *S, const double *F, const int *meta, int n_types, QChunks qc, int whole,
@@ -95,6 +129,24 @@ cudaError_t launch_reduce_items(const double *partial, int part_stride, const It
     if (n_groups == 0) return cudaSuccess;
     dim3 grid((qc.n_q + 127) / 128, n_groups);
     k_reduce_items<<<grid, 128, 0, s>>>(partial, part_stride, items, group_items, group_off, qc, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_items_seg(const double *partial, int part_stride, const Item *items,
+                                    const int *group_items, const int *group_off, int n_groups, int max_group,
+                                    const QChunks &qc, double *seg_out, double *S, cudaStream_t s)
+{
+    if (n_groups == 0) return cudaSuccess;
+    if (max_group <= kSegItems)
+        return launch_reduce_items(partial, part_stride, items, group_items, group_off, n_groups, qc, S, s);
+    const int max_seg = (max_group + kSegItems - 1) / kSegItems;
+    k_reduce_segments<<<dim3((unsigned)max_seg, (unsigned)n_groups), 256, 0, s>>>(partial, part_stride, items,
+                                                                                  group_items, group_off, qc,
+                                                                                  max_seg, seg_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_finish<<<dim3((unsigned)((qc.n_q + 127) / 128), (unsigned)n_groups), 128, 0, s>>>(seg_out, group_off, qc,
+                                                                                               max_seg, S);
     return cudaGetLastError();
 }
 

@@ -52,7 +52,7 @@ sas_status set_error(sas_status st, const char *msg)
 
 // Runs of uniform spacing: a run starting at s extends while every q_k stays within tol of the
 // line through its end points; each run is then cut into passes of at most kQChunk values.
-bool make_chunks(const double *q, int n_q, QChunks &qc)
+bool make_chunks(const double *q, int n_q, QChunks &qc, int max_len)
 {
     double qmax = 0.0;
     for (int k = 0; k < n_q; ++k) qmax = std::max(qmax, std::fabs(q[k]));
@@ -71,11 +71,11 @@ bool make_chunks(const double *q, int n_q, QChunks &qc)
             ++e;
         }
         const double step = e - s > 1 ? (q[e - 1] - q[s]) / (double)(e - s - 1) : 0.0;
-        for (int b = s; b < e; b += kQChunk) {
+        for (int b = s; b < e; b += max_len) {
             if (nc == kMaxChunks) return false;
             const double qs = q[s] + (b - s) * step;
             qc.q_begin[nc] = b;
-            qc.q_len[nc] = std::min(kQChunk, e - b);
+            qc.q_len[nc] = std::min(max_len, e - b);
             qc.qsd[nc] = qs;
             qc.dqd[nc] = step;
             qc.qs_hi[nc] = (float)qs;
@@ -215,11 +215,11 @@ struct sas_ctx {
     int64_t opt_timeout_ms = 600000;
     DevBuf coef_d, F, meta, blockcounts, blockoffs, centroid, X, slot_of, items, group_items,
         group_off, partial, ticket, S, in_coords, in_types, out_buf, Ibuf, gbuf, chi2buf, H, G, gout, tgt, wts,
-        hist, dropped;
+        hist, dropped, in_ff, zero_types, FJ, FI, F64t, D2, segbuf;
     int *h_meta = nullptr;   // pinned
     // schedule cache
     std::vector<int64_t> sched_key;
-    int n_items = 0, n_groups = 0, jmax_used = 0, jlen_max = 0;
+    int n_items = 0, n_groups = 0, jmax_used = 0, jlen_max = 0, max_group = 0;
     int64_t pair_slots = 0;
     int64_t last_batch = 0;
     bool have_partials = false;
@@ -303,7 +303,7 @@ void build_schedule(const int *counts, int T, int64_t batch, int tile, int n_chu
     int64_t jmax = jmax_opt;
     if (jmax <= 0) {
         const int64_t cands[] = {4096, 2048, 1024, 512, 256, 128};
-        jmax = 128;
+        jmax = std::min<int64_t>(128, jmax_cap);
         for (int64_t c : cands)
             if (c <= jmax_cap && n_items_for(c) >= 4 * (int64_t)grid) {
                 jmax = c;
@@ -393,11 +393,12 @@ bool finite_all(const double *v, size_t n)
 
 // Shared front half of every pair computation: stage, validate, count, schedule, pack.
 // On success the context holds X (packed), slot_of, meta (counts/offsets) and the item list.
+// T: the types of this call (1 for per-atom form factors, whose table ff_check [ff_count] is
+// validated with the coordinates).
 sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32_t *types, int64_t n,
                    int64_t batch, bool out_f64, bool center, int tile, int n_chunks, int64_t jmax_cap,
-                   cudaStream_t s, int &launches)
+                   cudaStream_t s, int &launches, int T, const double *ff_check = nullptr, int64_t ff_count = 0)
 {
-    const int T = ctx->n_types;
     const size_t esz = coords_f64 ? sizeof(double) : sizeof(float);
     const void *cd = coords;
     const int32_t *td = types;
@@ -423,6 +424,10 @@ sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32
     CUDA_TRY(launch_scan_counts(ctx->blockcounts.as<int>(), nblk, T, kTile, ctx->blockoffs.as<int>(),
                                 ctx->meta.as<int>(), s));
     launches += 2;
+    if (ff_check) {
+        CUDA_TRY(launch_check_finite(ff_check, ff_count, ctx->meta.as<int>() + 2 * T + 1, s));
+        launches += 1;
+    }
     CUDA_TRY(cudaMemcpyAsync(ctx->h_meta, ctx->meta.p, (size_t)(2 * T + 2) * sizeof(int),
                              cudaMemcpyDeviceToHost, s));
     sas_status st = wait_stream(ctx, s);
@@ -430,6 +435,7 @@ sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32
     const int err = ctx->h_meta[2 * T + 1];
     if (err & kErrBadType) return fail(SAS_ERR_INVALID_ARG, "atom type outside [0, %d)", T);
     if (err & kErrNonFinite) return fail(SAS_ERR_INVALID_ARG, "non-finite coordinate");
+    if (err & kErrNonFiniteFF) return fail(SAS_ERR_INVALID_ARG, "non-finite form factor");
     const int64_t npad = ctx->h_meta[2 * T];
     // schedule (cached while counts, batch, tile and options are unchanged)
     const int grid_per_sm = ctx->opt_grid > 0 ? ctx->opt_grid : 2;
@@ -464,6 +470,8 @@ sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32
                                  cudaMemcpyHostToDevice, s));
         ctx->n_items = ni;
         ctx->n_groups = ng;
+        ctx->max_group = 0;
+        for (int g = 0; g < ng; ++g) ctx->max_group = std::max(ctx->max_group, sc.group_off[g + 1] - sc.group_off[g]);
         ctx->jmax_used = sc.jmax;
         ctx->jlen_max = sc.jlen_max;
         ctx->pair_slots = sc.pair_slots;
@@ -515,6 +523,18 @@ sas_status zero_out(void *out, size_t bytes, cudaStream_t s)
     return SAS_OK;
 }
 
+// The items' partials -> S (fixed order; segmented for long groups).
+sas_status reduce_items(sas_ctx *ctx, const QChunks &qc, cudaStream_t s)
+{
+    if (ctx->max_group > kSegItems)
+        ALLOC_TRY(ctx->segbuf,
+                  (size_t)ctx->n_groups * ((ctx->max_group + kSegItems - 1) / kSegItems) * qc.n_q * sizeof(double));
+    CUDA_TRY(launch_reduce_items_seg(ctx->partial.as<double>(), kQChunk, ctx->items.as<Item>(),
+                                     ctx->group_items.as<int>(), ctx->group_off.as<int>(), ctx->n_groups,
+                                     ctx->max_group, qc, ctx->segbuf.as<double>(), ctx->S.as<double>(), s));
+    return SAS_OK;
+}
+
 // I(q) of `batch` conformers into the device buffer I_dev (all steps on stream s).
 sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types, int64_t n,
                    int64_t batch, double *I_dev, int64_t jmax_cap, cudaStream_t s, int &launches)
@@ -524,7 +544,7 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
     const int tile = fp64 ? kTile64 : kTile;
     sas_status st = prepare(ctx, coords, coords_type, types, n, batch, fp64,
                             !fp64 && coords_type == SAS_COORDS_F64, tile, ctx->qc.n_chunks, jmax_cap, s,
-                            launches);
+                            launches, T);
     if (st != SAS_OK) return st;
     const int64_t npad = ctx->h_meta[2 * T];
     ALLOC_TRY(ctx->partial, (size_t)std::max(ctx->n_items, 1) * kQChunk * sizeof(double));
@@ -548,9 +568,8 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
     CUDA_TRY(cudaEventRecord(ctx->ev1, s));
     ctx->ev_pending = true;
     ALLOC_TRY(ctx->S, (size_t)batch * Pn * Q * sizeof(double));
-    CUDA_TRY(launch_reduce_items(ctx->partial.as<double>(), kQChunk, ctx->items.as<Item>(),
-                                 ctx->group_items.as<int>(), ctx->group_off.as<int>(), ctx->n_groups,
-                                 ctx->qc, ctx->S.as<double>(), s));
+    st = reduce_items(ctx, ctx->qc, s);
+    if (st != SAS_OK) return st;
     CUDA_TRY(launch_assemble(ctx->S.as<double>(), ctx->F.as<double>(), ctx->meta.as<int>(), T, batch,
                              ctx->qc, ctx->opt_shard_rank == 0, I_dev, s));
     launches += 3;
@@ -786,6 +805,106 @@ sas_status sas_profile_batch(sas_ctx *ctx, const void *coords, int coords_type, 
     return run_profile(ctx, coords, coords_type, types, n_atoms, batch, I_out, (cudaStream_t)stream);
 }
 
+sas_status sas_profile_atomic(sas_ctx *ctx, const void *coords, int coords_type, int64_t n_atoms, int64_t batch,
+                              const double *ff, double *I_out, void *stream)
+{
+    if (!ctx) return fail(SAS_ERR_INVALID_ARG, "null context");
+    const int64_t n = n_atoms;
+    if (n < 0 || batch < 0) return fail(SAS_ERR_INVALID_ARG, "negative size");
+    if (coords_type != SAS_COORDS_F32 && coords_type != SAS_COORDS_F64)
+        return fail(SAS_ERR_INVALID_ARG, "coords_type must be SAS_COORDS_F32 or SAS_COORDS_F64");
+    if (n > (int64_t)1 << 28) return fail(SAS_ERR_UNSUPPORTED, "more than 2^28 atoms");
+    if (batch > 65535) return fail(SAS_ERR_UNSUPPORTED, "more than 65535 conformers");
+    if (batch * (n + kTile) > ((int64_t)1 << 31)) return fail(SAS_ERR_UNSUPPORTED, "batch * atoms too large");
+    if (batch > 0 && !I_out) return fail(SAS_ERR_INVALID_ARG, "null output");
+    if (batch > 0 && n > 0 && (!coords || !ff)) return fail(SAS_ERR_INVALID_ARG, "null input");
+    if (ctx->opt_shard_world > 1) return fail(SAS_ERR_UNSUPPORTED, "per-atom form factors run as a single shard");
+    ctx->have_partials = false;
+    if (batch == 0) return SAS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int Q = ctx->n_q;
+    if (n == 0) {
+        ctx->stats[0] = ctx->stats[1] = ctx->stats[2] = 0;
+        return zero_out(I_out, (size_t)batch * Q * sizeof(double), s);
+    }
+    const bool fp64 = (ctx->flags & SAS_FP64) != 0;
+    // q passes: the context's, or passes of the re-seed interval (a pass restarts the recurrence
+    // from exact seeds, so this is the re-seeding of the typed kernels)
+    QChunks qf = ctx->qc;
+    const int reseed = fp64 ? 0 : reseed_for(ctx->opt_reseed, n, std::min(Q, kQChunk));
+    if (reseed > 0 && !make_chunks(ctx->q.data(), Q, qf, std::max(2, std::min(reseed, kQChunk))))
+        return fail(SAS_ERR_UNSUPPORTED, "the q grid needs more than %d passes at a re-seed interval of %d",
+                    kMaxChunks, reseed);
+    int launches = 0;
+    const void *ffd = nullptr;
+    const size_t ffbytes = (size_t)batch * Q * n * sizeof(double);
+    sas_status st = stage_in(ctx->in_ff, ff, ffbytes, s, ffd);
+    if (st != SAS_OK) return st;
+    const double *F = static_cast<const double *>(ffd);
+    ALLOC_TRY(ctx->zero_types, (size_t)n * sizeof(int32_t));
+    CUDA_TRY(cudaMemsetAsync(ctx->zero_types.p, 0, (size_t)n * sizeof(int32_t), s));
+    const int tile = fp64 ? kTile64 : kTile;
+    const int64_t jcap = fp64 ? 8192 : atomic_jmax(qf);
+    st = prepare(ctx, coords, coords_type == SAS_COORDS_F64, ctx->zero_types.as<int32_t>(), n, batch, fp64,
+                 !fp64 && coords_type == SAS_COORDS_F64, tile, qf.n_chunks, jcap, s, launches, 1, F,
+                 (int64_t)batch * Q * n);
+    if (st != SAS_OK) return st;
+    const int64_t npad = ctx->h_meta[2];
+    const int nv = atomic_slots(qf);
+    if (fp64) {
+        ALLOC_TRY(ctx->F64t, (size_t)batch * npad * Q * sizeof(double));
+        CUDA_TRY(cudaMemsetAsync(ctx->F64t.p, 0, (size_t)batch * npad * Q * sizeof(double), s));
+        CUDA_TRY(launch_atomic_table64(F, ctx->slot_of.as<int>(), n, npad, batch, Q, ctx->F64t.as<double>(), s));
+    } else {
+        const size_t fj = (size_t)batch * qf.n_chunks * (npad / 2) * nv * sizeof(float4);
+        const size_t fi = (size_t)batch * qf.n_chunks * nv * npad * sizeof(float2);
+        ALLOC_TRY(ctx->FJ, fj);
+        ALLOC_TRY(ctx->FI, fi);
+        CUDA_TRY(cudaMemsetAsync(ctx->FJ.p, 0, fj, s));
+        CUDA_TRY(cudaMemsetAsync(ctx->FI.p, 0, fi, s));
+        CUDA_TRY(launch_atomic_tables(F, ctx->slot_of.as<int>(), n, npad, batch, qf, nv, ctx->FJ.as<float4>(),
+                                      ctx->FI.as<float2>(), s));
+    }
+    ALLOC_TRY(ctx->D2, (size_t)batch * Q * sizeof(double2));
+    CUDA_TRY(launch_atomic_diag(F, n, batch, Q, ctx->D2.as<double2>(), s));
+    ALLOC_TRY(ctx->partial, (size_t)std::max(ctx->n_items, 1) * kQChunk * sizeof(double));
+    const int grid_per_sm = ctx->opt_grid > 0 ? ctx->opt_grid : 2;
+    CUDA_TRY(cudaEventRecord(ctx->ev0, s));
+    if (fp64) {
+        const int grid = std::max(1, std::min(ctx->n_items, grid_per_sm * ctx->sms));
+        CUDA_TRY(launch_debye_fp64_atomic(ctx->X.as<double4>(), npad, ctx->items.as<Item>(), ctx->n_items, qf,
+                                          ctx->F64t.as<double>(), ctx->partial.as<double>(), kQChunk, grid, s));
+    } else {
+        ALLOC_TRY(ctx->ticket, sizeof(int));
+        CUDA_TRY(cudaMemsetAsync(ctx->ticket.p, 0, sizeof(int), s));
+        CUDA_TRY(launch_debye_atomic_pairs2(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, qf,
+                                            ctx->FJ.as<float4>(), ctx->FI.as<float2>(), ctx->partial.as<double>(),
+                                            kQChunk, ctx->opt_grid > 0 ? ctx->opt_grid * ctx->sms : 0,
+                                            ctx->jmax_used, ctx->ticket.as<int>(), s));
+    }
+    CUDA_TRY(cudaEventRecord(ctx->ev1, s));
+    ctx->ev_pending = true;
+    ALLOC_TRY(ctx->S, (size_t)batch * Q * sizeof(double));
+    st = reduce_items(ctx, qf, s);
+    if (st != SAS_OK) return st;
+    const bool host_out = !on_device(I_out);
+    double *Id = I_out;
+    if (host_out) {
+        ALLOC_TRY(ctx->out_buf, (size_t)batch * Q * sizeof(double));
+        Id = ctx->out_buf.as<double>();
+    }
+    CUDA_TRY(launch_assemble_atomic(ctx->S.as<double>(), ctx->D2.as<double2>(), qf, batch, Id, s));
+    launches += 5;
+    if (host_out) {
+        HostCopies hc;
+        st = out_copy(hc, I_out, Id, (size_t)batch * Q * sizeof(double), s);
+        if (st == SAS_OK) st = finish_copies(ctx, hc, s);
+        if (st != SAS_OK) return st;
+    }
+    ctx->stats[5] = launches;
+    return SAS_OK;
+}
+
 sas_status sas_partials(sas_ctx *ctx, double *S_out, int64_t capacity, void *stream)
 {
     if (!ctx || !S_out) return fail(SAS_ERR_INVALID_ARG, "null argument");
@@ -923,7 +1042,7 @@ sas_status sas_profile_vjp(sas_ctx *ctx, const float *coords, const int32_t *typ
     if (st != SAS_OK) return st;
     // the adjoint needs the packed coordinates and items: pack without the pair kernel
     st = prepare(ctx, coords, SAS_COORDS_F32, types, n, batch, false, false, kTile, ctx->qc.n_chunks, 2048,
-                 s, launches);
+                 s, launches, ctx->n_types);
     if (st != SAS_OK) return st;
     (void)T;
     st = adjoint(ctx, n, batch, (const double *)gI, grad_out, s, launches, hc);
@@ -952,7 +1071,8 @@ sas_status sas_pair_histogram(sas_ctx *ctx, const float *coords, const int32_t *
     }
     int launches = 0;
     const int64_t jcap = 4096;
-    st = prepare(ctx, coords, SAS_COORDS_F32, types, n, batch, false, false, kTile, 1, jcap, s, launches);
+    st = prepare(ctx, coords, SAS_COORDS_F32, types, n, batch, false, false, kTile, 1, jcap, s, launches,
+                 ctx->n_types);
     if (st != SAS_OK) return st;
     const int64_t npad = ctx->h_meta[2 * T];
     ALLOC_TRY(ctx->hist, hbytes);

@@ -53,12 +53,12 @@ __host__ __device__ inline double q_at(const QChunks &qc, int k)
 }
 
 // Fill qc for q[0..n_q): maximal runs of uniform spacing (deviation <= tol * max|q|), split into
-// passes of at most kQChunk values.  False if the grid needs more than kMaxChunks passes.
-bool make_chunks(const double *q, int n_q, QChunks &qc);
+// passes of at most max_len (<= kQChunk) values.  False if the grid needs more than kMaxChunks passes.
+bool make_chunks(const double *q, int n_q, QChunks &qc, int max_len = kQChunk);
 
 // ---- packing (pack.cu) -------------------------------------------------------
 // meta layout (int32): [0,T) real counts, [T, 2T+1) padded group offsets, [2T+1] error bits
-enum { kErrBadType = 1, kErrNonFinite = 2 };
+enum { kErrBadType = 1, kErrNonFinite = 2, kErrNonFiniteFF = 4 };
 
 cudaError_t launch_count_types(const void *coords, int coords_f64, const int32_t *types, int64_t n,
                                int64_t batch, int n_types, int *blockcounts, int *errword,
@@ -81,6 +81,13 @@ cudaError_t launch_form_factors(const double *coef, int n_types, const QChunks &
 cudaError_t launch_reduce_items(const double *partial, int part_stride, const Item *items,
                                 const int *group_items, const int *group_off, int n_groups,
                                 const QChunks &qc, double *S, cudaStream_t s);
+// The same sums for groups of any size: groups of more than kSegItems items are summed as
+// segments of kSegItems (in list order) and then the segments in order; seg_out holds
+// n_groups * ceil(max_group / kSegItems) * n_q doubles.
+constexpr int kSegItems = 256;
+cudaError_t launch_reduce_items_seg(const double *partial, int part_stride, const Item *items,
+                                    const int *group_items, const int *group_off, int n_groups, int max_group,
+                                    const QChunks &qc, double *seg_out, double *S, cudaStream_t s);
 // I[b][k] = sum_t n_t F_t^2 + sum_p 2 F_a F_b (q_k > 0 ? S/q_k : count_p)
 cudaError_t launch_assemble(double *S, const double *F, const int *meta, int n_types, int64_t batch,
                             const QChunks &qc, int whole, double *I, cudaStream_t s);
@@ -157,5 +164,23 @@ cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v,
 
 // the calling thread's error message (sas_last_error)
 sas_status set_error(sas_status st, const char *msg);
+
+// ---- per-atom form factors (atomic.cu, atomic_pairs2.cu) -------------------------------------
+int atomic_slots(const QChunks &qc);
+int atomic_jmax(const QChunks &qc);
+cudaError_t launch_check_finite(const double *v, int64_t count, int *err, cudaStream_t s);
+cudaError_t launch_atomic_tables(const double *ff, const int *slot_of, int64_t n, int64_t npad, int64_t batch,
+                                 const QChunks &qc, int nv, float4 *FJ, float2 *FI, cudaStream_t s);
+cudaError_t launch_atomic_table64(const double *ff, const int *slot_of, int64_t n, int64_t npad, int64_t batch,
+                                  int n_q, double *F64, cudaStream_t s);
+cudaError_t launch_atomic_diag(const double *ff, int64_t n, int64_t batch, int n_q, double2 *D, cudaStream_t s);
+cudaError_t launch_assemble_atomic(const double *S, const double2 *D, const QChunks &qc, int64_t batch, double *I,
+                                   cudaStream_t s);
+cudaError_t launch_debye_atomic_pairs2(const float4 *X, int64_t npad, const Item *items, int n_items,
+                                       const QChunks &qc, const float4 *FJ, const float2 *FI, double *partial,
+                                       int part_stride, int grid, int jmax, int *ticket, cudaStream_t s);
+cudaError_t launch_debye_fp64_atomic(const double4 *X, int64_t npad, const Item *items, int n_items,
+                                     const QChunks &qc, const double *F64, double *partial, int part_stride,
+                                     int grid, cudaStream_t s);
 
 }  // namespace sas

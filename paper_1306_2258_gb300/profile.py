@@ -81,6 +81,27 @@ class Profile:
         self._last_batch = B
         return out[0] if single else out
 
+    def atomic(self, coords, ff, stream=None):
+        """I(q) with per-atom form factors ff [n_q, n] (or [B, n_q, n]), f_i(q_k) at ff[..., k, i]:
+        Eq. 2 without types (the context's type coefficients are unused).  Returns float64 [Q]
+        or [B, Q] on the coordinates' device."""
+        single = coords.ndim == 2
+        x = coords if isinstance(coords, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(coords))
+        if single:
+            x = x.unsqueeze(0)
+        x = x.contiguous()
+        if x.dtype not in (torch.float32, torch.float64):
+            x = x.float()
+        B, n = int(x.shape[0]), int(x.shape[1])
+        f = _as_tensor_like(ff, torch.float64).reshape(B, self.n_q, n)
+        if x.is_cuda and not f.is_cuda:
+            f = f.to(x.device)
+        ctype = _lib.SAS_COORDS_F64 if x.dtype == torch.float64 else _lib.SAS_COORDS_F32
+        out = torch.empty((B, self.n_q), dtype=torch.float64, device=x.device)
+        _lib.sas_profile_atomic(self._ctx, x, ctype, n, B, f, out, stream)
+        self._last_batch = 0
+        return out[0] if single else out
+
     def partials(self):
         """Type-pair sinc sums S[b, p, q] of the last call (float64, host)."""
         S = np.empty((self._last_batch, self.n_pairs_types, self.n_q))

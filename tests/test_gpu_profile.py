@@ -427,3 +427,20 @@ def test_invalid_inputs_leave_output_untouched():
     _lib.sas_profile_batch(p._ctx, x, 0, t, 300, 1, out)    # the context is still usable
     assert torch.all(torch.isfinite(out))
     p.close()
+
+
+def test_single_type_long_group_segmented_reduction():
+    """One atom type, 30,000 atoms: all items fall in one type-pair group (more than 256 of them), which
+    is summed in segments of 256 items and then across segments; three sampled q against the oracle
+    evaluated at those q alone."""
+    mol = wl.random_walk_globule(30000, 1, 780)
+    coef = wl.form_factor_coefficients(1, 781)
+    q = wl.q_grid(0.0, 1.0, 201)
+    p = Profile(coef, q)
+    I = p(torch.as_tensor(mol.coords).cuda(), torch.as_tensor(mol.types).cuda()).cpu().numpy()
+    n_items = int(p.stats()[0])
+    p.close()
+    assert n_items > 256
+    ks = [0, 77, 190]
+    ref = oracle.profile(mol.coords, mol.types, coef, q[ks])
+    assert _rel(I[ks], ref) <= TOL_MIXED
