@@ -246,6 +246,19 @@ def run_rows(dev, stream):
                       "unit": "pair·q/s"}
         p.close()
 
+    # per-atom form factors (no types, a hydration-shell-like table) on the 50,000-atom globule
+    w = wl.c2_globule(50000)
+    p = Profile(w.coef, w.q, "mixed")
+    x = torch.as_tensor(w.mol.coords, device=dev)
+    ffa = torch.as_tensor(wl.atomic_form_factor_table(w.mol.n, w.q, 770), device=dev)
+    ms = _timed(lambda: p.atomic(x, ffa, stream), stream)
+    pq = pairs(w.mol.n) * w.q.size
+    rows["profile_atomic_ff_globule50k"] = {"workload": f"{w.mol.n} atoms x {w.q.size} q, per-atom form factors",
+                                            "ms": ms, "value": pq / (ms / 1e3), "unit": "pair·q/s",
+                                            "pair_kernel_ms": int(p.stats()[4]) / 1e6}
+    p.close()
+    del ffa
+
     # refinement (configuration 4): chi^2 and its gradient for 64 conformers of 5,000 atoms
     c4 = wl.c4_refinement()
     p = Profile(c4["coef"], c4["q"], "mixed")

@@ -4,6 +4,7 @@ capture can skip the first):
   pair histogram   512 conformers x 2,000 atoms of the ensemble workload, 256 bins
   chi^2 gradient   16 conformers x 5,000 atoms x 101 q of the refinement workload
   tcgen05 GEMM     4096 x 4096 x 4096 bfloat16 -> float32
+  per-atom f(q)    20,000-atom globule x 201 q with a per-atom form-factor table
 
   python -m paper_1306_2258_gb300.profile_cases
 """
@@ -38,9 +39,18 @@ def main():
     for _ in range(2):
         _lib.sas_gemm_bf16(G, G, G, gA, G, gB, G, None, gC, G)
     torch.cuda.synchronize()
-    print("profile cases: histogram pairs", int(h.sum()), "dropped", int(d.sum()), "gemm", G)
+    w = wl.c2_globule(20000)
+    pa = Profile(w.coef, w.q)
+    xa = torch.as_tensor(w.mol.coords).cuda()
+    ffa = torch.as_tensor(wl.atomic_form_factor_table(w.mol.n, w.q, 770)).cuda()
+    for _ in range(2):
+        Ia = pa.atomic(xa, ffa)
+    torch.cuda.synchronize()
+    print("profile cases: histogram pairs", int(h.sum()), "dropped", int(d.sum()), "gemm", G,
+          "per-atom I(0)", float(Ia[0]))
     p.close()
     p4.close()
+    pa.close()
 
 
 if __name__ == "__main__":
