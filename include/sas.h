@@ -149,6 +149,16 @@ sas_status sas_profile_atomic(sas_ctx *ctx, const void *coords, int coords_type,
                               const double *ff, double *I_out, void *stream);
 
 /*
+ * Peak microbenchmarks of the current device (the denominators of the pair kernels' rooflines):
+ * out[0] FP32 FMA lane operations/s (scalar FFMA), out[1] the same with packed f32x2 FMA (2 per
+ * instruction and lane), out[2] MUFU sine operations/s (__sinf), out[3] FP64 FMA lane
+ * operations/s, out[4] the SM clock (MHz) seen during the FFMA run (clock64 against the global
+ * timer).  Each kernel runs about 10 ms on `stream`; the call waits for them.  out is host memory
+ * of n_out >= 5 doubles.  Errors: INVALID_ARG, CUDA.
+ */
+sas_status sas_measure_peaks(double *out, int n_out, void *stream);
+
+/*
  * Exact integer histogram of unordered pair distances by type pair.
  *   coords [batch][n_atoms][3] float; types [n_atoms]; hist_out [batch][T(T+1)/2][n_bins] int32;
  *   dropped_out [batch] int64 (pairs beyond the last edge) or NULL.

@@ -30,6 +30,7 @@ EXPORTS = (
     "sas_last_error", "sas_version", "sas_profile_static", "sas_mlp_create", "sas_mlp_destroy",
     "sas_mlp_param_count", "sas_mlp_set_state", "sas_mlp_get_state", "sas_mlp_forward", "sas_mlp_train_step",
     "sas_mlp_grads", "sas_gemm_bf16", "sas_screen_select", "sas_gather_rows", "sas_profile_atomic",
+    "sas_measure_peaks",
 )
 
 
@@ -78,6 +79,7 @@ def load():
                 "sas_screen_select": [_int, _int, _vp, _int, _vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _vp],
                 "sas_gather_rows": [_vp, _i64, _vp, _i64, _vp, _vp],
                 "sas_profile_atomic": [_vp, _vp, _int, _i64, _i64, _vp, _vp, _vp],
+                "sas_measure_peaks": [_vp, _int, _vp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -250,6 +252,15 @@ def sas_screen_select(n_conf, n_q, z, ld, mean, stdv, target, weights, k, top_id
 
 def sas_gather_rows(src, row_bytes, idx, n_idx, dst, stream=None):
     check(load().sas_gather_rows(ptr(src), int(row_bytes), ptr(idx), int(n_idx), ptr(dst), stream_handle(stream)))
+
+
+def sas_measure_peaks(stream=None) -> dict:
+    """Measured peaks of the current device: FP32 FMA and packed-FMA lane-ops/s, MUFU sine ops/s,
+    FP64 FMA lane-ops/s and the SM clock (MHz) of the FMA run."""
+    out = np.zeros(5)
+    check(load().sas_measure_peaks(out.ctypes.data, 5, stream_handle(stream)))
+    return {"ffma": float(out[0]), "ffma2": float(out[1]), "mufu_sin": float(out[2]), "dfma": float(out[3]),
+            "sm_mhz": float(out[4])}
 
 
 def sas_last_error() -> str:

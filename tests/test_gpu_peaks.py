@@ -1,0 +1,21 @@
+"""The peak microbenchmarks (roofline denominators) through the C ABI: each rate is positive and
+bounded by what the device's units and the clock the run reports allow."""
+import pytest
+import torch
+
+from paper_1306_2258_gb300 import _lib
+
+pytestmark = pytest.mark.gpu
+
+
+def test_measured_peaks_are_physical():
+    assert torch.cuda.is_available()
+    m = _lib.sas_measure_peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = m["sm_mhz"]
+    assert 500.0 < mhz < 2500.0
+    lanes = sms * 128 * mhz * 1e6                    # FP32 lanes x clock
+    for k in ("ffma", "ffma2"):
+        assert 0.5 * lanes < m[k] <= 1.05 * lanes, (k, m[k], lanes)
+    assert 0.0 < m["mufu_sin"] <= 0.3 * lanes        # MUFU: a fraction of the FP32 rate
+    assert 0.0 < m["dfma"] <= 0.1 * lanes            # FP64 is a small fraction on this part
