@@ -184,7 +184,7 @@ enum {
     SAS_OPT_VARIANT = 7,     /* mixed kernel form for step 2 without re-seed: 0 auto, 1 general,
                                 2 set-up of the next pair overlapped, 3 pairs in sequence,
                                 4 two pairs per step on packed FP32 (same result bit for bit as 2 and 3) */
-    SAS_OPT_SHARD = 8        /* world * 65536 + rank (default 1 * 65536 + 0): later calls compute shard
+    SAS_OPT_SHARD = 8,       /* world * 65536 + rank (default 1 * 65536 + 0): later calls compute shard
                                 `rank` of a work list split into `world` contiguous parts of equal pair
                                 work.  sas_profile / sas_profile_batch then return that shard's share
                                 of I(q) (the diagonal and the exact q = 0 pair counts go to rank 0),
@@ -192,13 +192,23 @@ enum {
                                 sas_profile_vjp and sas_pair_histogram likewise return additive
                                 shares; sas_profile_grad needs the whole profile and returns
                                 UNSUPPORTED while world > 1. */
+    SAS_OPT_METHOD = 9       /* sas_profile / sas_profile_batch on a SAS_MIXED context: 0 the direct sum
+                                (default); 1 hybrid: the orientation average of Eq. 1 by spherical
+                                quadrature (Gauss-Legendre x uniform azimuth, degree from the spherical
+                                Bessel tail at q R, R the largest distance from the centroid) on the low-q
+                                prefix of the grid where it is cheaper than the pair count, the direct sum
+                                on the rest; 2 quadrature on every q.  The quadrature error is kept below
+                                1e-10 of the amplitude terms; sas_partials is not available after 1 or 2;
+                                sas_last_stats entry 6 gives the q values computed by quadrature and
+                                entry 7 its directions */
 };
 sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value);
 
 /*
  * Statistics of the last call: [0] work items, [1] pair slots (incl. padding),
  * [2] unordered real pairs, [3] q values, [4] pair-kernel time in nanoseconds
- * (CUDA events on the call's stream; this call waits for them), [5] kernels launched.
+ * (CUDA events on the call's stream; this call waits for them), [5] kernels launched,
+ * [6] q values computed by quadrature (SAS_OPT_METHOD), [7] quadrature directions.  n <= 8.
  */
 sas_status sas_last_stats(sas_ctx *ctx, int64_t *stats_out, int n);
 

@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "ALLOC", 4: "UNSUPPORTE
 SAS_MIXED, SAS_FP64 = 0, 1
 SAS_COORDS_F32, SAS_COORDS_F64 = 0, 1
 SAS_OPT_JMAX, SAS_OPT_RESEED, SAS_OPT_VALIDATE, SAS_OPT_GRID, SAS_OPT_TIMEOUT_MS, SAS_OPT_STEP, SAS_OPT_VARIANT = 1, 2, 3, 4, 5, 6, 7
-SAS_OPT_SHARD = 8
+SAS_OPT_SHARD, SAS_OPT_METHOD = 8, 9
 SAS_MAX_TYPES, SAS_MAX_Q = 16, 1664
 
 # every symbol include/sas.h declares (checked by the test suite)
@@ -187,8 +187,8 @@ def sas_set_option(ctx, option: int, value: int):
 
 
 def sas_last_stats(ctx):
-    out = np.zeros(6, dtype=np.int64)
-    check(load().sas_last_stats(ctx, out.ctypes.data, 6))
+    out = np.zeros(8, dtype=np.int64)
+    check(load().sas_last_stats(ctx, out.ctypes.data, 8))
     return out
 
 

@@ -31,15 +31,20 @@ __device__ __forceinline__ void load_xyz(const void *coords, int f64, int64_t id
     }
 }
 
-// Per block of kPackThreads atoms: count of each type; validation of types and coordinates.
+// Per block of kPackThreads atoms: count of each type; validation of types and coordinates; and
+// the largest squared distance from each conformer's first atom (as float bits in *extent2, which
+// orders like the value for non-negative floats): the diameter D of every conformer is at most
+// twice its square root.
 __global__ void k_count_types(const void *coords, int coords_f64, const int32_t *types, int64_t n,
-                              int64_t batch, int n_types, int *blockcounts, int *errword)
+                              int64_t batch, int n_types, int *blockcounts, int *errword, unsigned *extent2)
 {
     __shared__ int cnt[SAS_MAX_TYPES];
+    __shared__ float wmax[kPackThreads / 32];
     if (threadIdx.x < SAS_MAX_TYPES) cnt[threadIdx.x] = 0;
     __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int err = 0;
+    float d2max = 0.f;
     if (i < n) {
         int t = types[i];
         if (t < 0 || t >= n_types)
@@ -47,14 +52,26 @@ __global__ void k_count_types(const void *coords, int coords_f64, const int32_t 
         else
             atomicAdd(&cnt[t], 1);
         for (int64_t b = 0; b < batch; ++b) {
-            double x, y, z;
+            double x, y, z, x0, y0, z0;
             load_xyz(coords, coords_f64, b * n + i, x, y, z);
             if (!isfinite(x) || !isfinite(y) || !isfinite(z)) err |= kErrNonFinite;
+            load_xyz(coords, coords_f64, b * n, x0, y0, z0);
+            const double d2 = (x - x0) * (x - x0) + (y - y0) * (y - y0) + (z - z0) * (z - z0);
+            if (d2 == d2) d2max = fmaxf(d2max, __double2float_ru(d2));
         }
     }
     if (err) atomicOr(errword, err);
+    if (extent2) {
+        for (int o = 16; o > 0; o >>= 1) d2max = fmaxf(d2max, __shfl_xor_sync(0xffffffffu, d2max, o));
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = d2max;
+    }
     __syncthreads();
     if (threadIdx.x < n_types) blockcounts[(int64_t)blockIdx.x * n_types + threadIdx.x] = cnt[threadIdx.x];
+    if (extent2 && threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < kPackThreads / 32; ++w) m = fmaxf(m, wmax[w]);
+        atomicMax(extent2, __float_as_uint(m));
+    }
 }
 
 // One block: exclusive scan of the per-block counts for each type; totals and padded offsets.
@@ -152,12 +169,12 @@ __global__ void k_scatter(const void *coords, int coords_f64, const int32_t *typ
 
 cudaError_t launch_count_types(const void *coords, int coords_f64, const int32_t *types, int64_t n,
                                int64_t batch, int n_types, int *blockcounts, int *errword,
-                               cudaStream_t s)
+                               unsigned *extent2, cudaStream_t s)
 {
     int nblk = (int)((n + kPackThreads - 1) / kPackThreads);
     if (nblk == 0) return cudaSuccess;
     k_count_types<<<nblk, kPackThreads, 0, s>>>(coords, coords_f64, types, n, batch, n_types,
-                                                blockcounts, errword);
+                                                blockcounts, errword, extent2);
     return cudaGetLastError();
 }
 

@@ -89,6 +89,28 @@ bool make_chunks(const double *q, int n_q, QChunks &qc, int max_len)
     qc.n_chunks = nc;
     return true;
 }
+// Re-seed interval of the mixed kernel.  The drift of the FP32 recurrence for near pairs is
+// random across pairs, so its effect on I(q) shrinks as the molecule grows, and it grows with the
+// number of recurrence steps, i.e. with the q values of a chunk.  Measured with the 2-step
+// recurrence and no re-seeding (max over q and six seeded globules each): 201 q (0..1/A):
+// 2.5e-5 at 600 atoms, 1.0e-5 at 3,000, 6.4e-6 at 8,000, 2.7e-6 at 50,000; 101 q (0..0.5/A):
+// 8.1e-6 at 600, 4.1e-6 at 1,000, 2.8e-6 at 2,000, 1.2e-6 at 5,000 atoms.  Automatic: no
+// re-seeding from 8,192 atoms, or from 2,000 atoms when a chunk holds at most 104 q values;
+// otherwise every 32 q values (at most 3.5e-6 in the same study).
+// The recurrence with coefficient 2cos(M t), t = dq r, is ill-conditioned where M t nears pi
+// (its error grows like 1/sin(M t) per step): the 200,000-atom globule (diameter 350 A, 201 q
+// on 0..1/A, M t up to 3.5) reached 6.2e-5 at q = 0.975 without re-seeding and 1.3e-6 with a
+// re-seed every 64 q, while the 100,000-atom one (278 A, M t below 2.8) stayed at 1.3e-6.  So
+// once M dq D can reach 0.9 pi (D bounded by twice the largest distance from the first atom),
+// chunks longer than 64 q are re-seeded every 64 q.
+int reseed_auto(int64_t n_atoms, int n_q_chunk, double step_phase_max)
+{
+    const bool ill = step_phase_max >= 0.9 * 3.14159265358979323846 && n_q_chunk > 64;
+    if (n_atoms >= 8192) return ill ? 64 : 0;
+    if (n_q_chunk <= 104 && n_atoms >= 2000) return ill ? 64 : 0;
+    return 32;
+}
+
 }  // namespace sas
 
 namespace {
@@ -164,20 +186,10 @@ bool on_device(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Re-seed interval of the mixed kernel.  The drift of the FP32 recurrence for near pairs is
-// random across pairs, so its effect on I(q) shrinks as the molecule grows, and it grows with the
-// number of recurrence steps, i.e. with the q values of a chunk.  Measured with the 2-step
-// recurrence and no re-seeding (max over q and six seeded globules each): 201 q (0..1/A):
-// 2.5e-5 at 600 atoms, 1.0e-5 at 3,000, 6.4e-6 at 8,000, 2.7e-6 at 50,000; 101 q (0..0.5/A):
-// 8.1e-6 at 600, 4.1e-6 at 1,000, 2.8e-6 at 2,000, 1.2e-6 at 5,000 atoms.  Automatic: no
-// re-seeding from 8,192 atoms, or from 2,000 atoms when a chunk holds at most 104 q values;
-// otherwise every 32 q values (at most 3.5e-6 in the same study).
-int reseed_for(int opt, int64_t n_atoms, int n_q_chunk)
+int reseed_for(int opt, int64_t n_atoms, int n_q_chunk, double step_phase_max)
 {
     if (opt >= 0) return opt;
-    if (n_atoms >= 8192) return 0;
-    if (n_q_chunk <= 104 && n_atoms >= 2000) return 0;
-    return 32;
+    return reseed_auto(n_atoms, n_q_chunk, step_phase_max);
 }
 
 // SAS_OPT_VARIANT (0 auto, 1 general, 2 pipelined, 3 sequential, 4 two pairs per step) -> kernel
@@ -212,10 +224,12 @@ struct sas_ctx {
     int opt_variant = 0;
     int opt_grid = 0;
     int opt_shard_rank = 0, opt_shard_world = 1;   // this call computes shard rank of world
+    int opt_method = 0;                             // 0 direct sum, 1 hybrid by qD and N, 2 quadrature
+    double diam = 0.0;                              // bound on the diameter of the last call's conformers
     int64_t opt_timeout_ms = 600000;
     DevBuf coef_d, F, meta, blockcounts, blockoffs, centroid, X, slot_of, items, group_items,
         group_off, partial, ticket, S, in_coords, in_types, out_buf, Ibuf, gbuf, chi2buf, H, G, gout, tgt, wts,
-        hist, dropped, in_ff, zero_types, FJ, FI, F64t, D2, segbuf;
+        hist, dropped, in_ff, zero_types, FJ, FI, F64t, D2, segbuf, cen, qdirs, qwts, type_off, Apart, Fsub, Itmp, qplan;
     int *h_meta = nullptr;   // pinned
     // schedule cache
     std::vector<int64_t> sched_key;
@@ -223,14 +237,25 @@ struct sas_ctx {
     int64_t pair_slots = 0;
     int64_t last_batch = 0;
     bool have_partials = false;
-    int64_t stats[6] = {0, 0, 0, 0, 0, 0};
+    int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the last pair-kernel launch
     bool ev_pending = false;
+    double4 *h_cen = nullptr;   // pinned: centroid and radius per conformer (quadrature method)
+    int64_t h_cen_cap = 0;
     void *h_stage = nullptr;   // pinned staging of host outputs
     size_t h_stage_cap = 0;
 };
 
 namespace {
+
+// Largest phase step M dq D of the mixed recurrence over the passes of qc (D from the last
+// validation read-back).
+double step_phase(const sas_ctx *ctx, const QChunks &qc)
+{
+    double dq = 0.0;
+    for (int c = 0; c < qc.n_chunks; ++c) dq = std::max(dq, std::fabs(qc.dqd[c]));
+    return ctx->opt_step * dq * ctx->diam;
+}
 
 // Wait for the work queued on `s` so far, giving up after the context's time limit.
 sas_status wait_stream(sas_ctx *ctx, cudaStream_t s)
@@ -391,53 +416,10 @@ bool finite_all(const double *v, size_t n)
     return true;
 }
 
-// Shared front half of every pair computation: stage, validate, count, schedule, pack.
-// On success the context holds X (packed), slot_of, meta (counts/offsets) and the item list.
-// T: the types of this call (1 for per-atom form factors, whose table ff_check [ff_count] is
-// validated with the coordinates).
-sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32_t *types, int64_t n,
-                   int64_t batch, bool out_f64, bool center, int tile, int n_chunks, int64_t jmax_cap,
-                   cudaStream_t s, int &launches, int T, const double *ff_check = nullptr, int64_t ff_count = 0)
+// The work list of the packed layout in ctx->h_meta (counts of T types) for `n_chunks` q passes
+// (cached while counts, batch, tile and options are unchanged).
+sas_status schedule_for(sas_ctx *ctx, int T, int64_t batch, int tile, int n_chunks, int64_t jmax_cap, cudaStream_t s)
 {
-    const size_t esz = coords_f64 ? sizeof(double) : sizeof(float);
-    const void *cd = coords;
-    const int32_t *td = types;
-    if (!on_device(coords)) {
-        ALLOC_TRY(ctx->in_coords, (size_t)batch * n * 3 * esz);
-        CUDA_TRY(cudaMemcpyAsync(ctx->in_coords.p, coords, (size_t)batch * n * 3 * esz,
-                                 cudaMemcpyHostToDevice, s));
-        cd = ctx->in_coords.p;
-    }
-    if (!on_device(types)) {
-        ALLOC_TRY(ctx->in_types, (size_t)n * sizeof(int32_t));
-        CUDA_TRY(cudaMemcpyAsync(ctx->in_types.p, types, (size_t)n * sizeof(int32_t),
-                                 cudaMemcpyHostToDevice, s));
-        td = ctx->in_types.as<int32_t>();
-    }
-    const int nblk = (int)((n + kPackThreads - 1) / kPackThreads);
-    ALLOC_TRY(ctx->blockcounts, (size_t)nblk * T * sizeof(int));
-    ALLOC_TRY(ctx->blockoffs, (size_t)nblk * T * sizeof(int));
-    ALLOC_TRY(ctx->meta, (size_t)(2 * T + 2) * sizeof(int));
-    CUDA_TRY(cudaMemsetAsync(ctx->meta.p, 0, (size_t)(2 * T + 2) * sizeof(int), s));
-    CUDA_TRY(launch_count_types(cd, coords_f64, td, n, batch, T, ctx->blockcounts.as<int>(),
-                                ctx->meta.as<int>() + 2 * T + 1, s));
-    CUDA_TRY(launch_scan_counts(ctx->blockcounts.as<int>(), nblk, T, kTile, ctx->blockoffs.as<int>(),
-                                ctx->meta.as<int>(), s));
-    launches += 2;
-    if (ff_check) {
-        CUDA_TRY(launch_check_finite(ff_check, ff_count, ctx->meta.as<int>() + 2 * T + 1, s));
-        launches += 1;
-    }
-    CUDA_TRY(cudaMemcpyAsync(ctx->h_meta, ctx->meta.p, (size_t)(2 * T + 2) * sizeof(int),
-                             cudaMemcpyDeviceToHost, s));
-    sas_status st = wait_stream(ctx, s);
-    if (st != SAS_OK) return st;
-    const int err = ctx->h_meta[2 * T + 1];
-    if (err & kErrBadType) return fail(SAS_ERR_INVALID_ARG, "atom type outside [0, %d)", T);
-    if (err & kErrNonFinite) return fail(SAS_ERR_INVALID_ARG, "non-finite coordinate");
-    if (err & kErrNonFiniteFF) return fail(SAS_ERR_INVALID_ARG, "non-finite form factor");
-    const int64_t npad = ctx->h_meta[2 * T];
-    // schedule (cached while counts, batch, tile and options are unchanged)
     const int grid_per_sm = ctx->opt_grid > 0 ? ctx->opt_grid : 2;
     const int grid_cap = grid_per_sm * ctx->sms;
     std::vector<int64_t> key(ctx->h_meta, ctx->h_meta + T);
@@ -477,6 +459,66 @@ sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32
         ctx->pair_slots = sc.pair_slots;
         ctx->sched_key = key;
     }
+    ctx->stats[0] = ctx->n_items;
+    ctx->stats[1] = ctx->pair_slots;
+    return SAS_OK;
+}
+
+// Shared front half of every pair computation: stage, validate, count, schedule, pack.
+// On success the context holds X (packed), slot_of, meta (counts/offsets) and the item list.
+// T: the types of this call (1 for per-atom form factors, whose table ff_check [ff_count] is
+// validated with the coordinates).
+sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32_t *types, int64_t n,
+                   int64_t batch, bool out_f64, bool center, int tile, int n_chunks, int64_t jmax_cap,
+                   cudaStream_t s, int &launches, int T, const double *ff_check = nullptr, int64_t ff_count = 0)
+{
+    const size_t esz = coords_f64 ? sizeof(double) : sizeof(float);
+    const void *cd = coords;
+    const int32_t *td = types;
+    if (!on_device(coords)) {
+        ALLOC_TRY(ctx->in_coords, (size_t)batch * n * 3 * esz);
+        CUDA_TRY(cudaMemcpyAsync(ctx->in_coords.p, coords, (size_t)batch * n * 3 * esz,
+                                 cudaMemcpyHostToDevice, s));
+        cd = ctx->in_coords.p;
+    }
+    if (!on_device(types)) {
+        ALLOC_TRY(ctx->in_types, (size_t)n * sizeof(int32_t));
+        CUDA_TRY(cudaMemcpyAsync(ctx->in_types.p, types, (size_t)n * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, s));
+        td = ctx->in_types.as<int32_t>();
+    }
+    const int nblk = (int)((n + kPackThreads - 1) / kPackThreads);
+    ALLOC_TRY(ctx->blockcounts, (size_t)nblk * T * sizeof(int));
+    ALLOC_TRY(ctx->blockoffs, (size_t)nblk * T * sizeof(int));
+    ALLOC_TRY(ctx->meta, (size_t)(2 * T + 3) * sizeof(int));
+    CUDA_TRY(cudaMemsetAsync(ctx->meta.p, 0, (size_t)(2 * T + 3) * sizeof(int), s));
+    CUDA_TRY(launch_count_types(cd, coords_f64, td, n, batch, T, ctx->blockcounts.as<int>(),
+                                ctx->meta.as<int>() + 2 * T + 1,
+                                reinterpret_cast<unsigned *>(ctx->meta.as<int>() + 2 * T + 2), s));
+    CUDA_TRY(launch_scan_counts(ctx->blockcounts.as<int>(), nblk, T, kTile, ctx->blockoffs.as<int>(),
+                                ctx->meta.as<int>(), s));
+    launches += 2;
+    if (ff_check) {
+        CUDA_TRY(launch_check_finite(ff_check, ff_count, ctx->meta.as<int>() + 2 * T + 1, s));
+        launches += 1;
+    }
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_meta, ctx->meta.p, (size_t)(2 * T + 3) * sizeof(int),
+                             cudaMemcpyDeviceToHost, s));
+    sas_status st = wait_stream(ctx, s);
+    if (st != SAS_OK) return st;
+    const int err = ctx->h_meta[2 * T + 1];
+    if (err & kErrBadType) return fail(SAS_ERR_INVALID_ARG, "atom type outside [0, %d)", T);
+    if (err & kErrNonFinite) return fail(SAS_ERR_INVALID_ARG, "non-finite coordinate");
+    if (err & kErrNonFiniteFF) return fail(SAS_ERR_INVALID_ARG, "non-finite form factor");
+    const int64_t npad = ctx->h_meta[2 * T];
+    {
+        float r2;
+        const unsigned bits = (unsigned)ctx->h_meta[2 * T + 2];
+        std::memcpy(&r2, &bits, sizeof r2);
+        ctx->diam = 2.0 * std::sqrt((double)r2);
+    }
+    st = schedule_for(ctx, T, batch, tile, n_chunks, jmax_cap, s);
+    if (st != SAS_OK) return st;
     // pack
     const size_t xsz = out_f64 ? sizeof(double4) : sizeof(float4);
     ALLOC_TRY(ctx->X, (size_t)batch * npad * xsz);
@@ -536,11 +578,18 @@ sas_status reduce_items(sas_ctx *ctx, const QChunks &qc, cudaStream_t s)
 }
 
 // I(q) of `batch` conformers into the device buffer I_dev (all steps on stream s).
+sas_status forward_hybrid(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types, int64_t n,
+                          int64_t batch, double *I_dev, int64_t jmax_cap, cudaStream_t s, int &launches);
+
 sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types, int64_t n,
-                   int64_t batch, double *I_dev, int64_t jmax_cap, cudaStream_t s, int &launches)
+                   int64_t batch, double *I_dev, int64_t jmax_cap, cudaStream_t s, int &launches,
+                   bool hybrid_ok = false)
 {
     const int T = ctx->n_types, Q = ctx->n_q, Pn = T * (T + 1) / 2;
     const bool fp64 = (ctx->flags & SAS_FP64) != 0;
+    ctx->stats[6] = ctx->stats[7] = 0;
+    if (hybrid_ok && !fp64 && ctx->opt_method != 0)
+        return forward_hybrid(ctx, coords, coords_type, types, n, batch, I_dev, jmax_cap, s, launches);
     const int tile = fp64 ? kTile64 : kTile;
     sas_status st = prepare(ctx, coords, coords_type, types, n, batch, fp64,
                             !fp64 && coords_type == SAS_COORDS_F64, tile, ctx->qc.n_chunks, jmax_cap, s,
@@ -560,7 +609,8 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
                                    ctx->qc, ctx->partial.as<double>(), kQChunk, grid, s));
     } else {
         CUDA_TRY(launch_debye_mixed(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items,
-                                    ctx->qc, ctx->opt_step, reseed_for(ctx->opt_reseed, n, std::min(ctx->n_q, kQChunk)),
+                                    ctx->qc, ctx->opt_step,
+                                    reseed_for(ctx->opt_reseed, n, std::min(ctx->n_q, kQChunk), step_phase(ctx, ctx->qc)),
                                     mixed_variant(ctx->opt_variant, std::min(ctx->n_q, kQChunk)), ctx->partial.as<double>(),
                                     kQChunk, ctx->opt_grid > 0 ? ctx->opt_grid * ctx->sms : 0, ctx->jmax_used,
                                     ctx->ticket.as<int>(), s));
@@ -575,6 +625,180 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
     launches += 3;
     ctx->last_batch = batch;
     ctx->have_partials = true;
+    return SAS_OK;
+}
+
+// Cost model of the hybrid split: a pair costs 2 NV + kDirectSetup units per pass of the direct
+// kernel (NV the float2 slots it computes, fitted to the pass or its block capacity; the set-up
+// from the 30,000-atom rod at 101 q against the 50,000-atom globule at 201 q: 9.0 and 13.0 ps per
+// pair), a (direction, atom) pair of the quadrature kQuadStepCost units per q of its 32-value
+// pass (2.5e13 direct units/s against 4.3e12 quadrature steps/s, both measured on GB300).
+constexpr double kDirectSetup = 120.0;
+constexpr double kQuadStepCost = 5.8;
+constexpr double kQuadTol = 1e-10;                  // (2l+1)|j_l(qR)| below this past the degree L
+constexpr size_t kQuadAmpBytes = (size_t)4 << 30;   // partial amplitudes held at once
+int quad_dirs_for(int L)
+{
+    int nt = L + 1;
+    nt += nt & 1;
+    return (nt / 2) * (2 * L + 1);
+}
+
+// I(q) by the orientation average of Eq. 1 on a prefix of the q grid and by the direct sum on
+// the rest.  Method 1 (hybrid) ends the prefix at the first q where the quadrature's directions
+// times atoms, weighted by its relative cost, reach the pair count; method 2 takes every q.
+sas_status forward_hybrid(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types, int64_t n,
+                          int64_t batch, double *I_dev, int64_t jmax_cap, cudaStream_t s, int &launches)
+{
+    const int T = ctx->n_types, Q = ctx->n_q, Pn = T * (T + 1) / 2;
+    if (ctx->opt_shard_world > 1) return fail(SAS_ERR_UNSUPPORTED, "the quadrature method runs as a single shard");
+    sas_status st = prepare(ctx, coords, coords_type, types, n, batch, false, coords_type == SAS_COORDS_F64, kTile,
+                            ctx->qc.n_chunks, jmax_cap, s, launches, T);
+    if (st != SAS_OK) return st;
+    const int64_t npad = ctx->h_meta[2 * T];
+    ctx->have_partials = false;
+    // centroid and radius of every conformer
+    ALLOC_TRY(ctx->cen, (size_t)batch * sizeof(double4));
+    CUDA_TRY(launch_packed_geometry(ctx->X.as<float4>(), npad, batch, ctx->cen.as<double4>(), s));
+    launches += 2;
+    if (ctx->h_cen_cap < batch) {
+        if (ctx->h_cen) cudaFreeHost(ctx->h_cen);
+        ctx->h_cen = nullptr;
+        ctx->h_cen_cap = 0;
+        if (cudaMallocHost((void **)&ctx->h_cen, (size_t)batch * sizeof(double4)) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->h_cen = nullptr;
+            return fail(SAS_ERR_ALLOC, "pinned host allocation failed");
+        }
+        ctx->h_cen_cap = batch;
+    }
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_cen, ctx->cen.p, (size_t)batch * sizeof(double4), cudaMemcpyDeviceToHost, s));
+    st = wait_stream(ctx, s);
+    if (st != SAS_OK) return st;
+    double R = 0.0;
+    for (int64_t b = 0; b < batch; ++b) R = std::max(R, ctx->h_cen[b].w);
+    // the split: the quadrature on whole 32-value passes from q[0], the direct sum on the rest,
+    // at the least modelled cost
+    int k_split = 0;
+    if (ctx->opt_method == 2) {
+        k_split = Q;
+    } else {
+        const double pairs = 0.5 * (double)n * (double)(n - 1);
+        auto direct_cost = [&](int Qd) {
+            double c = 0.0;
+            for (int b = 0; b < Qd; b += kQChunk) {
+                const int len = std::min(kQChunk, Qd - b), nb = mixed_blocks_for(len), nv = (len + 1) / 2;
+                c += pairs * (2.0 * ((2 * nb - nv <= 3) ? nv : 2 * nb) + kDirectSetup);
+            }
+            return c;
+        };
+        double best = direct_cost(Q), quad = 0.0;
+        for (int s0 = 0; s0 < Q; s0 += kQuadChunk) {
+            const int e = std::min(Q, s0 + kQuadChunk);
+            quad += kQuadStepCost * (double)n * kQuadChunk * quad_dirs_for(quad_degree(ctx->q[e - 1] * R, kQuadTol));
+            if (quad > best) break;
+            const double total = quad + direct_cost(Q - e);
+            if (total < best) {
+                best = total;
+                k_split = e;
+            }
+        }
+    }
+    int64_t n_dirs = 0;
+    CUDA_TRY(cudaEventRecord(ctx->ev0, s));
+    if (k_split > 0) {   // quadrature on q[0, k_split)
+        QChunks qq{};
+        if (!make_chunks(ctx->q.data(), k_split, qq, kQuadChunk))
+            return fail(SAS_ERR_UNSUPPORTED, "the quadrature range needs more than %d passes", kMaxChunks);
+        QuadPlan pl{};
+        std::vector<float4> dirs, d;
+        std::vector<double> wts, w;
+        int ctas = 0;
+        int64_t amp = 0;
+        for (int c = 0; c < qq.n_chunks; ++c) {
+            const double qmax = ctx->q[qq.q_begin[c] + qq.q_len[c] - 1];
+            quad_directions(quad_degree(qmax * R, kQuadTol), d, w);
+            const int M = (int)d.size();
+            const int dblk = (M + quad_threads_per_cta() - 1) / quad_threads_per_cta();
+            const int64_t tiles = npad / 256 + 1;
+            int nseg = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (3 * ctx->sms + dblk * batch - 1) / (dblk * batch)));
+            const int64_t seg_len = ((npad + nseg - 1) / nseg + 255) / 256 * 256;
+            nseg = (int)((npad + seg_len - 1) / seg_len);
+            pl.q_begin[c] = qq.q_begin[c];
+            pl.q_len[c] = qq.q_len[c];
+            pl.qs_hi[c] = qq.qs_hi[c];
+            pl.qs_lo[c] = qq.qs_lo[c];
+            pl.dq_hi[c] = qq.dq_hi[c];
+            pl.dq_lo[c] = qq.dq_lo[c];
+            pl.dir_off[c] = (int)dirs.size();
+            pl.n_dir[c] = M;
+            pl.n_seg[c] = nseg;
+            pl.seg_len[c] = (int)seg_len;
+            pl.cta_off[c] = ctas;
+            pl.amp_off[c] = amp;
+            ctas += dblk * nseg;
+            amp += (int64_t)nseg * kQuadChunk * M;
+            dirs.insert(dirs.end(), d.begin(), d.end());
+            wts.insert(wts.end(), w.begin(), w.end());
+        }
+        pl.n_chunks = qq.n_chunks;
+        pl.cta_off[qq.n_chunks] = ctas;
+        pl.amp_stride = amp;
+        n_dirs = (int64_t)dirs.size();
+        std::vector<int> toff(T + 1, 0);
+        for (int t = 0; t < T; ++t) toff[t + 1] = toff[t] + (ctx->h_meta[t] + kTile - 1) / kTile * kTile;
+        ALLOC_TRY(ctx->qdirs, dirs.size() * sizeof(float4));
+        ALLOC_TRY(ctx->qwts, wts.size() * sizeof(double));
+        ALLOC_TRY(ctx->type_off, (T + 1) * sizeof(int));
+        ALLOC_TRY(ctx->qplan, sizeof(QuadPlan));
+        CUDA_TRY(cudaMemcpyAsync(ctx->qplan.p, &pl, sizeof(QuadPlan), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(ctx->qdirs.p, dirs.data(), dirs.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(ctx->qwts.p, wts.data(), wts.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(ctx->type_off.p, toff.data(), (T + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+        const int64_t group = std::max<int64_t>(1, std::min<int64_t>(batch, (int64_t)(kQuadAmpBytes / (amp * sizeof(double2)))));
+        ALLOC_TRY(ctx->Apart, (size_t)group * amp * sizeof(double2));
+        for (int64_t b0 = 0; b0 < batch; b0 += group) {
+            const int64_t nb = std::min(group, batch - b0);
+            CUDA_TRY(launch_quad(ctx->X.as<float4>() + b0 * npad, npad, nb, ctx->type_off.as<int>(), T,
+                                 ctx->cen.as<double4>() + b0, ctx->F.as<double>(), Q, pl, ctx->qplan.as<QuadPlan>(),
+                                 ctx->qdirs.as<float4>(),
+                                 ctx->qwts.as<double>(), ctx->Apart.as<double2>(), I_dev + b0 * Q, s));
+            launches += 2;
+        }
+        // (copies from pageable host memory have read their source when cudaMemcpyAsync returns)
+    }
+    if (k_split < Q) {   // the direct sum on q[k_split, Q)
+        const int Qd = Q - k_split;
+        QChunks qd{};
+        if (!make_chunks(ctx->q.data() + k_split, Qd, qd))
+            return fail(SAS_ERR_UNSUPPORTED, "the direct range needs more than %d passes", kMaxChunks);
+        st = schedule_for(ctx, T, batch, kTile, qd.n_chunks, jmax_cap, s);
+        if (st != SAS_OK) return st;
+        ALLOC_TRY(ctx->Fsub, (size_t)T * Qd * sizeof(double));
+        CUDA_TRY(launch_form_factors(ctx->coef_d.as<double>(), T, qd, ctx->Fsub.as<double>(), s));
+        ALLOC_TRY(ctx->partial, (size_t)std::max(ctx->n_items, 1) * kQChunk * sizeof(double));
+        ALLOC_TRY(ctx->ticket, sizeof(int));
+        CUDA_TRY(cudaMemsetAsync(ctx->ticket.p, 0, sizeof(int), s));
+        CUDA_TRY(launch_debye_mixed(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, qd, ctx->opt_step,
+                                    reseed_for(ctx->opt_reseed, n, std::min(Qd, kQChunk), step_phase(ctx, qd)),
+                                    mixed_variant(ctx->opt_variant, std::min(Qd, kQChunk)), ctx->partial.as<double>(),
+                                    kQChunk, ctx->opt_grid > 0 ? ctx->opt_grid * ctx->sms : 0, ctx->jmax_used,
+                                    ctx->ticket.as<int>(), s));
+        ALLOC_TRY(ctx->S, (size_t)batch * Pn * Qd * sizeof(double));
+        st = reduce_items(ctx, qd, s);
+        if (st != SAS_OK) return st;
+        ALLOC_TRY(ctx->Itmp, (size_t)batch * Qd * sizeof(double));
+        CUDA_TRY(launch_assemble(ctx->S.as<double>(), ctx->Fsub.as<double>(), ctx->meta.as<int>(), T, batch, qd, 1,
+                                 ctx->Itmp.as<double>(), s));
+        CUDA_TRY(cudaMemcpy2DAsync(I_dev + k_split, (size_t)Q * sizeof(double), ctx->Itmp.p, (size_t)Qd * sizeof(double),
+                                   (size_t)Qd * sizeof(double), (size_t)batch, cudaMemcpyDeviceToDevice, s));
+        launches += 4;
+    }
+    CUDA_TRY(cudaEventRecord(ctx->ev1, s));
+    ctx->ev_pending = true;
+    ctx->stats[6] = k_split;
+    ctx->stats[7] = n_dirs;
+    ctx->last_batch = batch;
     return SAS_OK;
 }
 
@@ -673,7 +897,7 @@ sas_status run_profile(sas_ctx *ctx, const void *coords, int coords_type, const 
         ALLOC_TRY(ctx->out_buf, (size_t)batch * Q * sizeof(double));
         Id = ctx->out_buf.as<double>();
     }
-    st = forward(ctx, coords, coords_type, types, n, batch, Id, 8192, s, launches);
+    st = forward(ctx, coords, coords_type, types, n, batch, Id, 8192, s, launches, true);
     if (st != SAS_OK) return st;
     if (host_out) {
         HostCopies hc;
@@ -760,7 +984,7 @@ sas_status sas_create(int n_types, const double *ff_coef, const double *q, int n
         cudaGetLastError();
         return bail(fail(SAS_ERR_CUDA, "event creation failed"));
     }
-    if (cudaMallocHost((void **)&c->h_meta, (2 * SAS_MAX_TYPES + 2) * sizeof(int)) != cudaSuccess) {
+    if (cudaMallocHost((void **)&c->h_meta, (2 * SAS_MAX_TYPES + 3) * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         c->h_meta = nullptr;
         return bail(fail(SAS_ERR_ALLOC, "pinned allocation failed"));
@@ -783,6 +1007,7 @@ sas_status sas_destroy(sas_ctx *ctx)
 {
     if (!ctx) return SAS_OK;
     if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
+    if (ctx->h_cen) cudaFreeHost(ctx->h_cen);
     if (ctx->h_stage) {
         cudaDeviceSynchronize();   // copies of a call that timed out may still target it
         cudaFreeHost(ctx->h_stage);
@@ -830,8 +1055,9 @@ sas_status sas_profile_atomic(sas_ctx *ctx, const void *coords, int coords_type,
     const bool fp64 = (ctx->flags & SAS_FP64) != 0;
     // q passes: the context's, or passes of the re-seed interval (a pass restarts the recurrence
     // from exact seeds, so this is the re-seeding of the typed kernels)
+    // (re-seeded from the diameter bound below, once the validation read-back has it)
     QChunks qf = ctx->qc;
-    const int reseed = fp64 ? 0 : reseed_for(ctx->opt_reseed, n, std::min(Q, kQChunk));
+    int reseed = fp64 ? 0 : reseed_for(ctx->opt_reseed, n, std::min(Q, kQChunk), 0.0);
     if (reseed > 0 && !make_chunks(ctx->q.data(), Q, qf, std::max(2, std::min(reseed, kQChunk))))
         return fail(SAS_ERR_UNSUPPORTED, "the q grid needs more than %d passes at a re-seed interval of %d",
                     kMaxChunks, reseed);
@@ -850,6 +1076,15 @@ sas_status sas_profile_atomic(sas_ctx *ctx, const void *coords, int coords_type,
                  (int64_t)batch * Q * n);
     if (st != SAS_OK) return st;
     const int64_t npad = ctx->h_meta[2];
+    if (!fp64 && reseed == 0 && reseed_for(ctx->opt_reseed, n, std::min(Q, kQChunk), step_phase(ctx, qf)) > 0) {
+        // an ill-conditioned phase step: passes of 32 q (exact slots of the 52-q form), rescheduled
+        reseed = 32;
+        if (!make_chunks(ctx->q.data(), Q, qf, reseed))
+            return fail(SAS_ERR_UNSUPPORTED, "the q grid needs more than %d passes at a re-seed interval of %d",
+                        kMaxChunks, reseed);
+        st = schedule_for(ctx, 1, batch, kTile, qf.n_chunks, atomic_jmax(qf), s);
+        if (st != SAS_OK) return st;
+    }
     const int nv = atomic_slots(qf);
     if (fp64) {
         ALLOC_TRY(ctx->F64t, (size_t)batch * npad * Q * sizeof(double));
@@ -952,6 +1187,10 @@ sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value)
         if (value <= 0) return fail(SAS_ERR_INVALID_ARG, "timeout must be positive");
         ctx->opt_timeout_ms = value;
         return SAS_OK;
+    case SAS_OPT_METHOD:
+        if (value < 0 || value > 2) return fail(SAS_ERR_INVALID_ARG, "METHOD must be 0, 1 or 2");
+        ctx->opt_method = (int)value;
+        return SAS_OK;
     case SAS_OPT_SHARD: {
         const int64_t world = value >> 16, rank = value & 0xFFFF;
         if (world < 1 || world > 65535 || rank >= world)
@@ -975,7 +1214,7 @@ sas_status sas_last_stats(sas_ctx *ctx, int64_t *stats_out, int n)
         ctx->stats[4] = (int64_t)((double)ms * 1.0e6);
         ctx->ev_pending = false;
     }
-    for (int i = 0; i < n && i < 6; ++i) stats_out[i] = ctx->stats[i];
+    for (int i = 0; i < n && i < 8; ++i) stats_out[i] = ctx->stats[i];
     return SAS_OK;
 }
 

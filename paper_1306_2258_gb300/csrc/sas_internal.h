@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "sas.h"
 
 namespace sas {
@@ -60,9 +62,11 @@ bool make_chunks(const double *q, int n_q, QChunks &qc, int max_len = kQChunk);
 // meta layout (int32): [0,T) real counts, [T, 2T+1) padded group offsets, [2T+1] error bits
 enum { kErrBadType = 1, kErrNonFinite = 2, kErrNonFiniteFF = 4 };
 
+// extent2 (may be NULL): max over conformers and atoms of the squared distance from the
+// conformer's first atom, as float bits (atomicMax; zero it first)
 cudaError_t launch_count_types(const void *coords, int coords_f64, const int32_t *types, int64_t n,
                                int64_t batch, int n_types, int *blockcounts, int *errword,
-                               cudaStream_t s);
+                               unsigned *extent2, cudaStream_t s);
 cudaError_t launch_scan_counts(const int *blockcounts, int nblk, int n_types, int tile,
                                int *blockoffs, int *meta, cudaStream_t s);
 cudaError_t launch_centroid(const void *coords, int coords_f64, int64_t n, int64_t batch,
@@ -107,6 +111,9 @@ cudaError_t launch_debye_fp64(const double4 *X, int64_t npad, const Item *items,
                               cudaStream_t s);
 // q capacity (in blocks of four q) of the mixed-precision kernels for a chunk of qlen_max values
 int mixed_blocks_for(int qlen_max);
+// Automatic re-seed interval of the mixed recurrence (0: none) for a molecule of n_atoms, passes
+// of up to n_q_chunk q values and a largest phase step M dq D (radians).
+int reseed_auto(int64_t n_atoms, int n_q_chunk, double step_phase_max);
 
 // ---- adjoint (adjoint.cu) -------------------------------------------------------
 // g[b][k] = 2 w_k (I_bk - T_k), chi2[b] = sum_k w_k (I_bk - T_k)^2 (chi2 may be null)
@@ -182,5 +189,30 @@ cudaError_t launch_debye_atomic_pairs2(const float4 *X, int64_t npad, const Item
 cudaError_t launch_debye_fp64_atomic(const double4 *X, int64_t npad, const Item *items, int n_items,
                                      const QChunks &qc, const double *F64, double *partial, int part_stride,
                                      int grid, cudaStream_t s);
+
+// ---- orientation average by quadrature (quadrature.cu) --------------------------------------
+constexpr int kQuadChunk = 32;   // q values of one quadrature pass
+// The launch plan of the quadrature method: per q chunk its q run, its direction set (an offset
+// into the direction array), its split of the packed atoms into segments over CTAs, and the
+// offset of its partial amplitudes ([segment][kQuadChunk][direction] double2 per conformer).
+struct QuadPlan {
+    int n_chunks;
+    int q_begin[kMaxChunks], q_len[kMaxChunks];
+    float qs_hi[kMaxChunks], qs_lo[kMaxChunks], dq_hi[kMaxChunks], dq_lo[kMaxChunks];
+    int dir_off[kMaxChunks], n_dir[kMaxChunks], n_seg[kMaxChunks], seg_len[kMaxChunks];
+    int64_t amp_off[kMaxChunks];
+    int cta_off[kMaxChunks + 1];
+    int64_t amp_stride;   // double2 per conformer
+};
+int quad_degree(double x, double tol);
+void quad_directions(int L, std::vector<float4> &dirs, std::vector<double> &wts);
+int quad_threads_per_cta();
+// cen[b] = (FP64 centroid of the real atoms of conformer b, largest distance from it)
+cudaError_t launch_packed_geometry(const float4 *X, int64_t npad, int64_t batch, double4 *cen, cudaStream_t s);
+// I[b][q_begin[c] + k] for every chunk of the plan (F: [n_types][n_q] form factors of the full grid)
+// (pl on the host for the launch shape, pl_dev its device copy for the kernels)
+cudaError_t launch_quad(const float4 *X, int64_t npad, int64_t batch, const int *type_off, int n_types,
+                        const double4 *cen, const double *F, int n_q, const QuadPlan &pl, const QuadPlan *pl_dev,
+                        const float4 *dirs, const double *wts, double2 *Apart, double *I, cudaStream_t s);
 
 }  // namespace sas

@@ -42,7 +42,7 @@ constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t kOffX = 0;
 constexpr size_t kOffSlot = kOffX + align256(sizeof(float4) * kStaticNpad);
 constexpr size_t kOffMeta = kOffSlot + align256(sizeof(int) * SAS_STATIC_MAX_ATOMS);
-constexpr size_t kOffCounts = kOffMeta + align256(sizeof(int) * (2 * kStaticTypes + 2));
+constexpr size_t kOffCounts = kOffMeta + align256(sizeof(int) * (2 * kStaticTypes + 3));
 constexpr size_t kOffOffs = kOffCounts + align256(sizeof(int) * kStaticBlocks * kStaticTypes);
 constexpr size_t kOffItems = kOffOffs + align256(sizeof(int) * kStaticBlocks * kStaticTypes);
 constexpr size_t kOffGroupItems = kOffItems + align256(sizeof(Item) * kStaticItems);
@@ -168,11 +168,12 @@ extern "C" sas_status sas_profile_static(const float *coords, const int32_t *typ
     const int nblk = (int)((n + kPackThreads - 1) / kPackThreads);
     STATIC_TRY(cudaMemcpyAsync(coef, ff_coef, sizeof(double) * 9 * T, cudaMemcpyHostToDevice, s));
     STATIC_TRY(launch_form_factors(coef, T, qc, F, s));
-    STATIC_TRY(cudaMemsetAsync(meta, 0, sizeof(int) * (2 * T + 2), s));
-    STATIC_TRY(launch_count_types(coords, 0, types, n, 1, T, blockcounts, meta + 2 * T + 1, s));
+    STATIC_TRY(cudaMemsetAsync(meta, 0, sizeof(int) * (2 * T + 3), s));
+    STATIC_TRY(launch_count_types(coords, 0, types, n, 1, T, blockcounts, meta + 2 * T + 1,
+                                  reinterpret_cast<unsigned *>(meta + 2 * T + 2), s));
     STATIC_TRY(launch_scan_counts(blockcounts, nblk, T, kTile, blockoffs, meta, s));
-    int h_meta[2 * kStaticTypes + 2];
-    STATIC_TRY(cudaMemcpyAsync(h_meta, meta, sizeof(int) * (2 * T + 2), cudaMemcpyDeviceToHost, s));
+    int h_meta[2 * kStaticTypes + 3];
+    STATIC_TRY(cudaMemcpyAsync(h_meta, meta, sizeof(int) * (2 * T + 3), cudaMemcpyDeviceToHost, s));
     STATIC_TRY(cudaStreamSynchronize(s));
     if (h_meta[2 * T + 1] & kErrBadType) return static_fail(SAS_ERR_INVALID_ARG, "atom type outside [0, n_types)");
     if (h_meta[2 * T + 1] & kErrNonFinite) return static_fail(SAS_ERR_INVALID_ARG, "non-finite coordinate");
@@ -224,7 +225,10 @@ extern "C" sas_status sas_profile_static(const float *coords, const int32_t *typ
     STATIC_TRY(launch_scatter(coords, 0, types, n, 1, T, blockoffs, meta, nullptr, 0, X, npad, slot_of, s));
     // the automatic re-seed rule of sas_profile (no re-seeding from 8,192 atoms, or from 2,000 atoms
     // when the chunk holds at most 104 q values)
-    const int reseed = (n >= 8192 || (std::min(n_q, kQChunk) <= 104 && n >= 2000)) ? 0 : 32;
+    float r2;
+    const unsigned bits = (unsigned)h_meta[2 * T + 2];
+    std::memcpy(&r2, &bits, sizeof r2);
+    const int reseed = reseed_auto(n, std::min(n_q, kQChunk), 2.0 * std::fabs(dq) * 2.0 * std::sqrt((double)r2));
     STATIC_TRY(cudaMemsetAsync(ticket, 0, sizeof(int), s));
     STATIC_TRY(launch_debye_mixed(X, npad, items, ni, qc, 2, reseed, reseed == 0 ? 5 : 1, partial, kQChunk, 0,
                                   kStaticJmax, ticket, s));
