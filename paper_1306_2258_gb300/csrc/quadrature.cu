@@ -13,10 +13,11 @@
 // n_phi >= 2L + 1.  L is taken from the spherical Bessel functions at x = q R (R the largest
 // distance of an atom from the centroid): the smallest L with (2l+1)|j_l(x)| < 1e-10 for all l > L.
 //
-// Device work (per q chunk of at most 32 values and conformer): thread = one direction, one atom
-// per step with (cos, sin) of q u.(r - c) on the two lanes of a packed f32x2 value, following the
-// three-term recurrence x_{k+1} = 2cos(dq p) x_k - x_{k-1} from seeds at the chunk's first two q
-// (the sign pattern of the pair kernels keeps every step a packed multiply-add); per-type FP32 sums
+// Device work (per q chunk of at most 32 values and conformer): thread = one direction, two atoms
+// per step in lockstep, each with (cos, sin) of q u.(r - c) on the two lanes of a packed f32x2
+// value, following the three-term recurrence x_{k+1} = 2cos(dq p) x_k - x_{k-1} from seeds at the
+// chunk's first two q (the sign pattern of the pair kernels keeps every step a packed
+// multiply-add); per-type FP32 sums
 // over at most 512 atoms are folded, weighted by f_t(q), into amplitudes kept as FP32 hi/lo pairs
 // (exact two-sum) in shared memory; atoms are split into segments over CTAs, and a second kernel
 // sums segments and directions in FP64 in a fixed order.
@@ -208,16 +209,13 @@ __device__ __forceinline__ void sincos_mufu(float x, float &s, float &c)
     __sincosf(r, &s, &c);
 }
 
-// One atom (weight w, position d relative to the centroid), one direction u: add cos and sin of
-// q_k u.d for the chunk's q values into acc[k] = (re, im), with the sign pattern (+, +, -, -) over
-// k carried by the accumulators (block_negative) and the coefficient (odd steps take -C).
-template <int QC>
-__device__ __forceinline__ void atom1(float dx, float dy, float dz, float w, float4 u, float qs_hi, float qs_lo,
-                                      float dq_hi, float dq_lo, bool zero_start, float2 (&acc)[QC])
+// Seeds of one atom (weight w, position d relative to the centroid) for one direction u: the
+// first two (cos, sin) values of q_k u.d over the chunk and the recurrence coefficient 2cos(dq p)
+// to full relative accuracy in 2 - C (the phase velocity for small steps): C = 2 - 4 sin^2(t/2).
+__device__ __forceinline__ void seeds(float dx, float dy, float dz, float w, float4 u, float qs_hi, float qs_lo,
+                                      float dq_hi, float dq_lo, bool zero_start, float2 &v0, float2 &v1, float &C)
 {
     const float p = fmaf(u.z, dz, fmaf(u.y, dy, u.x * dx));
-    // the rotation by t = dq p to full relative accuracy in 2 - C (the recurrence's phase velocity
-    // for small t): C = 2cos t = 2 - 4 sin^2(t/2), sin t = 2 sin(t/2) cos(t/2)
     const SinCos h = sincos_f32(0.5f * fmaf(dq_hi, p, dq_lo * p));
     const float st = 2.f * h.s * h.c, ct = fmaf(-2.f * h.s, h.s, 1.f);
     float c0 = w, s0 = 0.f;
@@ -227,19 +225,36 @@ __device__ __forceinline__ void atom1(float dx, float dy, float dz, float w, flo
         c0 = w * cp;
         s0 = w * sp;
     }
-    const float2 v0 = make_float2(c0, s0);
-    const float2 v1 = make_float2(fmaf(c0, ct, -s0 * st), fmaf(s0, ct, c0 * st));
-    const float C1 = fmaf(-4.f * h.s, h.s, 2.f);
-    const float2 C = bc2(C1), Cn = bc2(-C1);
-    acc[0] = f2add(acc[0], v0);
-    acc[1] = f2add(acc[1], v1);
-    float2 vp = v0, vc = v1;
+    v0 = make_float2(c0, s0);
+    v1 = make_float2(fmaf(c0, ct, -s0 * st), fmaf(s0, ct, c0 * st));
+    C = fmaf(-4.f * h.s, h.s, 2.f);
+}
+
+// Two atoms A, B in lockstep (two independent recurrence chains): add cos and sin of q_k u.d into
+// acc[k] = (re, im) for the chunk's first qlen q values, with the sign pattern (+, +, -, -) over k
+// carried by the accumulators (block_negative) and the coefficient (odd steps take -C).
+template <int QC>
+__device__ __forceinline__ void atoms2(const float4 A, const float4 B, float4 u, float qs_hi, float qs_lo,
+                                       float dq_hi, float dq_lo, bool zero_start, int qlen, float2 (&acc)[QC])
+{
+    float2 a0, a1, b0, b1;
+    float cA, cB;
+    seeds(A.x, A.y, A.z, A.w, u, qs_hi, qs_lo, dq_hi, dq_lo, zero_start, a0, a1, cA);
+    seeds(B.x, B.y, B.z, B.w, u, qs_hi, qs_lo, dq_hi, dq_lo, zero_start, b0, b1, cB);
+    const float2 CA = bc2(cA), CAn = bc2(-cA), CB = bc2(cB), CBn = bc2(-cB);
+    acc[0] = f2add(f2add(acc[0], a0), b0);
+    acc[1] = f2add(f2add(acc[1], a1), b1);
+    float2 ap = a0, ac = a1, bp = b0, bcur = b1;
 #pragma unroll
     for (int k = 1; k + 1 < QC; ++k) {   // W_{k+1} = (k odd ? -C : C) W_k + W_{k-1}
-        const float2 vn = f2fma((k & 1) ? Cn : C, vc, vp);
-        acc[k + 1] = f2add(acc[k + 1], vn);
-        vp = vc;
-        vc = vn;
+        if (k + 1 >= qlen) break;
+        const float2 an = f2fma((k & 1) ? CAn : CA, ac, ap);
+        const float2 bn = f2fma((k & 1) ? CBn : CB, bcur, bp);
+        acc[k + 1] = f2add(f2add(acc[k + 1], an), bn);
+        ap = ac;
+        ac = an;
+        bp = bcur;
+        bcur = bn;
     }
 }
 
@@ -311,16 +326,16 @@ __global__ void __launch_bounds__(kQuadThreads, 3)
             sx[i] = a;
         }
         __syncthreads();
-        for (int i = 0; i < cnt; ++i) {
+        for (int i = 0; i < cnt; i += 2) {   // groups and segments start on even slots
             const int64_t slot = base + i;
             if (slot >= type_off[t + 1]) {   // type change (groups start on whole tiles)
                 fold<QC>(acc, amp, F + (int64_t)t * n_q + q_begin, qlen, tid);
                 since = 0;
                 while (t + 1 < n_types && slot >= type_off[t + 1]) ++t;
             }
-            const float4 A = sx[i];
-            atom1<QC>(A.x, A.y, A.z, A.w, u, qs_hi, qs_lo, dq_hi, dq_lo, zero_start, acc);
-            if (++since >= kFoldAtoms) {
+            atoms2<QC>(sx[i], sx[i + 1], u, qs_hi, qs_lo, dq_hi, dq_lo, zero_start, qlen, acc);
+            since += 2;
+            if (since >= kFoldAtoms) {
                 fold<QC>(acc, amp, F + (int64_t)t * n_q + q_begin, qlen, tid);
                 since = 0;
             }

@@ -5,6 +5,7 @@ capture can skip the first):
   chi^2 gradient   16 conformers x 5,000 atoms x 101 q of the refinement workload
   tcgen05 GEMM     4096 x 4096 x 4096 bfloat16 -> float32
   per-atom f(q)    20,000-atom globule x 201 q with a per-atom form-factor table
+  quadrature       20,000-atom globule x 65 q (0..0.32/A), orientation average of Eq. 1 on every q
 
   python -m paper_1306_2258_gb300.profile_cases
 """
@@ -46,8 +47,14 @@ def main():
     for _ in range(2):
         Ia = pa.atomic(xa, ffa)
     torch.cuda.synchronize()
+    pq = Profile(w.coef, wl.q_grid(0.0, 0.32, 65))
+    pq.set_option(_lib.SAS_OPT_METHOD, 2)
+    for _ in range(2):
+        Iq = pq(xa, torch.as_tensor(w.mol.types).cuda())
+    torch.cuda.synchronize()
+    pq.close()
     print("profile cases: histogram pairs", int(h.sum()), "dropped", int(d.sum()), "gemm", G,
-          "per-atom I(0)", float(Ia[0]))
+          "per-atom I(0)", float(Ia[0]), "quadrature I(0)", float(Iq[0]))
     p.close()
     p4.close()
     pa.close()
