@@ -495,6 +495,72 @@ def run_ours(args):
     return 0
 
 
+def run_strong(args):
+    """One molecule split over the ranks (strong scaling): each rank computes its shard of the work
+    list (SAS_OPT_SHARD) and the Q-vector shares are all-gathered over NCCL and summed in rank
+    order; a step is the whole profile on every rank.  Timed like the default mode (barriers,
+    CUDA events, the maximum over ranks)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1306_2258_gb300 import _lib, workloads as wl
+    from paper_1306_2258_gb300.profile import Profile
+    from paper_1306_2258_gb300.shard import allreduce_shares, set_shard
+
+    rank, world, local = _dist()
+    if "MASTER_ADDR" not in os.environ:   # a plain single-process run: a group of one
+        os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": "29561", "RANK": "0", "WORLD_SIZE": "1"})
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    w = wl.c2_globule(N_ATOMS)
+    n, Q = w.mol.n, w.q.size
+    pq = n * (n - 1) // 2 * Q
+    prof = Profile(w.coef, w.q, "mixed")
+    set_shard(prof, rank, world)
+    x = torch.as_tensor(w.mol.coords, device=dev)
+    t = torch.as_tensor(w.mol.types, device=dev)
+    share = torch.empty((1, Q), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    result = {}
+
+    def step():
+        _lib.sas_profile_batch(prof._ctx, x, _lib.SAS_COORDS_F32, t, n, 1, share, stream)
+        result["I"] = allreduce_shares(share[0])
+
+    for _ in range(args.warmup):
+        step()
+    dist.barrier()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = torch.tensor([a.elapsed_time(b) / args.steps], dtype=torch.float64, device=dev)
+    dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+    whole = Profile(w.coef, w.q, "mixed")   # unsharded, untimed: the shares must sum to it
+    ref = whole(x, t).cpu().numpy()
+    whole.close()
+    I = result["I"].cpu().numpy()
+    if rank == 0:
+        t_s = float(ms.item()) / 1e3
+        print(json.dumps({
+            "metric": METRIC, "value": pq / t_s, "unit": "pair·q/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_s * 1e3, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "globule 50,000 atoms x 201 q, one molecule split over the ranks "
+                                   "(shards of equal pair work, NCCL all-gather of the Q-vector shares)",
+                       "n_atoms": n, "n_q": Q, "parallelism": f"shards{world}"},
+            "rel_diff_vs_unsharded": float(np.max(np.abs(I - ref) / np.abs(ref))),
+        }))
+    prof.close()
+    dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -506,9 +572,13 @@ def main():
                     help="leave out the timings of the other path steps (rod, sparse chain, gradient, ensemble)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the mixed path only (no e2e, FP64 or CPU legs; for profiler runs)")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="weak (default): one molecule per rank; strong: one molecule split over the ranks")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.scaling == "strong":
+        return run_strong(args)
     return run_ours(args)
 
 
