@@ -7,6 +7,7 @@
 // by type makes every tile type-homogeneous, so each tile pair belongs to one
 // type pair (a, b) and f_a(q) f_b(q) multiplies a whole partial sum instead of
 // every pair term.
+#include <algorithm>
 #include <cmath>
 
 #include "sas_internal.h"
@@ -31,33 +32,38 @@ __device__ __forceinline__ void load_xyz(const void *coords, int f64, int64_t id
     }
 }
 
-// Per block of kPackThreads atoms: count of each type; validation of types and coordinates; and
-// the largest squared distance from each conformer's first atom (as float bits in *extent2, which
-// orders like the value for non-negative floats): the diameter D of every conformer is at most
+// Per block of kPackThreads atoms (blockIdx.x) and slice of the conformers (blockIdx.y, every
+// gridDim.y-th): validation of types (slice 0, which also counts them) and coordinates, and the
+// largest squared distance from each conformer's first atom (FP32, as float bits in *extent2,
+// which order like the values for non-negative floats): every conformer's diameter is at most
 // twice its square root.
-__global__ void k_count_types(const void *coords, int coords_f64, const int32_t *types, int64_t n,
-                              int64_t batch, int n_types, int *blockcounts, int *errword, unsigned *extent2)
+template <typename Real>
+__global__ void k_count_types(const Real *coords, const int32_t *types, int64_t n, int64_t batch, int n_types,
+                              int *blockcounts, int *errword, unsigned *extent2)
 {
     __shared__ int cnt[SAS_MAX_TYPES];
     __shared__ float wmax[kPackThreads / 32];
-    if (threadIdx.x < SAS_MAX_TYPES) cnt[threadIdx.x] = 0;
+    const bool counter = blockIdx.y == 0;
+    if (counter && threadIdx.x < SAS_MAX_TYPES) cnt[threadIdx.x] = 0;
     __syncthreads();
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int err = 0;
     float d2max = 0.f;
     if (i < n) {
-        int t = types[i];
-        if (t < 0 || t >= n_types)
-            err |= kErrBadType;
-        else
-            atomicAdd(&cnt[t], 1);
-        for (int64_t b = 0; b < batch; ++b) {
-            double x, y, z, x0, y0, z0;
-            load_xyz(coords, coords_f64, b * n + i, x, y, z);
+        if (counter) {
+            const int t = types[i];
+            if (t < 0 || t >= n_types)
+                err |= kErrBadType;
+            else
+                atomicAdd(&cnt[t], 1);
+        }
+        for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+            const Real *c = coords + 3 * (b * n + i), *c0 = coords + 3 * (b * n);
+            const Real x = c[0], y = c[1], z = c[2];
             if (!isfinite(x) || !isfinite(y) || !isfinite(z)) err |= kErrNonFinite;
-            load_xyz(coords, coords_f64, b * n, x0, y0, z0);
-            const double d2 = (x - x0) * (x - x0) + (y - y0) * (y - y0) + (z - z0) * (z - z0);
-            if (d2 == d2) d2max = fmaxf(d2max, __double2float_ru(d2));
+            const float dx = (float)(x - c0[0]), dy = (float)(y - c0[1]), dz = (float)(z - c0[2]);
+            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (d2 == d2) d2max = fmaxf(d2max, d2 * 1.000001f);   // a little over: rounding
         }
     }
     if (err) atomicOr(errword, err);
@@ -66,7 +72,7 @@ __global__ void k_count_types(const void *coords, int coords_f64, const int32_t 
         if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = d2max;
     }
     __syncthreads();
-    if (threadIdx.x < n_types) blockcounts[(int64_t)blockIdx.x * n_types + threadIdx.x] = cnt[threadIdx.x];
+    if (counter && threadIdx.x < n_types) blockcounts[(int64_t)blockIdx.x * n_types + threadIdx.x] = cnt[threadIdx.x];
     if (extent2 && threadIdx.x == 0) {
         float m = 0.f;
         for (int w = 0; w < kPackThreads / 32; ++w) m = fmaxf(m, wmax[w]);
@@ -173,8 +179,15 @@ cudaError_t launch_count_types(const void *coords, int coords_f64, const int32_t
 {
     int nblk = (int)((n + kPackThreads - 1) / kPackThreads);
     if (nblk == 0) return cudaSuccess;
-    k_count_types<<<nblk, kPackThreads, 0, s>>>(coords, coords_f64, types, n, batch, n_types,
-                                                blockcounts, errword, extent2);
+    // conformer slices: enough CTAs to fill the device for large batches of small molecules
+    const unsigned ys = (unsigned)std::max<int64_t>(1, std::min<int64_t>(batch, (1216 + nblk - 1) / nblk));
+    const dim3 grid((unsigned)nblk, ys);
+    if (coords_f64)
+        k_count_types<double><<<grid, kPackThreads, 0, s>>>(static_cast<const double *>(coords), types, n, batch,
+                                                          n_types, blockcounts, errword, extent2);
+    else
+        k_count_types<float><<<grid, kPackThreads, 0, s>>>(static_cast<const float *>(coords), types, n, batch,
+                                                         n_types, blockcounts, errword, extent2);
     return cudaGetLastError();
 }
 

@@ -98,14 +98,16 @@ bool make_chunks(const double *q, int n_q, QChunks &qc, int max_len)
 // re-seeding from 8,192 atoms, or from 2,000 atoms when a chunk holds at most 104 q values;
 // otherwise every 32 q values (at most 3.5e-6 in the same study).
 // The recurrence with coefficient 2cos(M t), t = dq r, is ill-conditioned where M t nears pi
-// (its error grows like 1/sin(M t) per step): the 200,000-atom globule (diameter 350 A, 201 q
-// on 0..1/A, M t up to 3.5) reached 6.2e-5 at q = 0.975 without re-seeding and 1.3e-6 with a
-// re-seed every 64 q, while the 100,000-atom one (278 A, M t below 2.8) stayed at 1.3e-6.  So
-// once M dq D can reach 0.9 pi (D bounded by twice the largest distance from the first atom),
-// chunks longer than 64 q are re-seeded every 64 q.
+// (its error grows like 1/sin(M t) per step, and with the number of steps): the 200,000-atom
+// globule (diameter 350 A, 201 q on 0..1/A, M t up to 3.5) reached 6.2e-5 at q = 0.975 without
+// re-seeding and 1.3e-6 with a re-seed every 64 q; with passes of at most 101 q the same globule
+// (0..0.5/A), the 30,000-atom rod and the 200,000-bead chain (M t far beyond pi) stayed at
+// <= 2.1e-6 without, and so did the 150,000-atom globule at 201 q (318 A).  So once M dq D can
+// reach 0.9 pi (D bounded by twice the largest distance from the first atom), passes longer
+// than 128 q are re-seeded every 64 q.
 int reseed_auto(int64_t n_atoms, int n_q_chunk, double step_phase_max)
 {
-    const bool ill = step_phase_max >= 0.9 * 3.14159265358979323846 && n_q_chunk > 64;
+    const bool ill = step_phase_max >= 0.9 * 3.14159265358979323846 && n_q_chunk > 128;
     if (n_atoms >= 8192) return ill ? 64 : 0;
     if (n_q_chunk <= 104 && n_atoms >= 2000) return ill ? 64 : 0;
     return 32;
