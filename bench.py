@@ -3,13 +3,16 @@
 plain kernel on the same GB300 and the CPU oracle on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--scaling weak|strong]
 
 One step = one full profile call through the C ABI with device-resident inputs:
 count/validate, scan, schedule read-back, pack, pair kernel, item reduction and
 assembly.  Under torchrun every rank computes its own molecule (independent
 problems, weak scaling, no data-path collective); rank 0 prints one JSON line.
-`--impl reference` times the CPU oracle (the reference arm of this build) on a
-bounded subsample of the same workload.
+`--scaling strong` splits one molecule over the ranks instead (NCCL all-gather of
+the Q-vector shares).  `--impl reference` times the CPU oracle (the paper ships no
+program to run, so the FP64 oracle is the reference arm) on a bounded subsample
+of the same workload.
 """
 from __future__ import annotations
 
