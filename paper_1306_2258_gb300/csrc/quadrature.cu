@@ -209,6 +209,26 @@ __device__ __forceinline__ void sincos_mufu(float x, float &s, float &c)
     __sincosf(r, &s, &c);
 }
 
+// sin and cos of |x| <= pi/4 by the Taylor polynomials of sincos_f32 without its quadrant
+// reduction (truncation below 2e-9 relative); larger |x| take the full routine.
+__device__ __forceinline__ SinCos sincos_quarter(float x)
+{
+    using namespace sc;
+    if (!(fabsf(x) <= 0.78539816f)) return sincos_f32(x);
+    const float x2 = x * x;
+    float ps = fmaf(x2, kS9, kS7);
+    ps = fmaf(ps, x2, kS5);
+    ps = fmaf(ps, x2, kS3);
+    float pc = fmaf(x2, kC10, kC8);
+    pc = fmaf(pc, x2, kC6);
+    pc = fmaf(pc, x2, kC4);
+    pc = fmaf(pc, x2, kC2);
+    SinCos r;
+    r.s = fmaf(ps * x2, x, x);
+    r.c = fmaf(pc, x2, 1.0f);
+    return r;
+}
+
 // Seeds of one atom (weight w, position d relative to the centroid) for one direction u: the
 // first two (cos, sin) values of q_k u.d over the chunk and the recurrence coefficient 2cos(dq p)
 // to full relative accuracy in 2 - C (the phase velocity for small steps): C = 2 - 4 sin^2(t/2).
@@ -216,7 +236,7 @@ __device__ __forceinline__ void seeds(float dx, float dy, float dz, float w, flo
                                       float dq_hi, float dq_lo, bool zero_start, float2 &v0, float2 &v1, float &C)
 {
     const float p = fmaf(u.z, dz, fmaf(u.y, dy, u.x * dx));
-    const SinCos h = sincos_f32(0.5f * fmaf(dq_hi, p, dq_lo * p));
+    const SinCos h = sincos_quarter(0.5f * fmaf(dq_hi, p, dq_lo * p));
     const float st = 2.f * h.s * h.c, ct = fmaf(-2.f * h.s, h.s, 1.f);
     float c0 = w, s0 = 0.f;
     if (!zero_start) {
@@ -233,7 +253,7 @@ __device__ __forceinline__ void seeds(float dx, float dy, float dz, float w, flo
 // Two atoms A, B in lockstep (two independent recurrence chains): add cos and sin of q_k u.d into
 // acc[k] = (re, im) for the chunk's first qlen q values, with the sign pattern (+, +, -, -) over k
 // carried by the accumulators (block_negative) and the coefficient (odd steps take -C).
-template <int QC>
+template <int QC, bool FULL>
 __device__ __forceinline__ void atoms2(const float4 A, const float4 B, float4 u, float qs_hi, float qs_lo,
                                        float dq_hi, float dq_lo, bool zero_start, int qlen, float2 (&acc)[QC])
 {
@@ -247,7 +267,7 @@ __device__ __forceinline__ void atoms2(const float4 A, const float4 B, float4 u,
     float2 ap = a0, ac = a1, bp = b0, bcur = b1;
 #pragma unroll
     for (int k = 1; k + 1 < QC; ++k) {   // W_{k+1} = (k odd ? -C : C) W_k + W_{k-1}
-        if (k + 1 >= qlen) break;
+        if (!FULL && k + 1 >= qlen) break;   // a pass shorter than QC (the grid's last)
         const float2 an = f2fma((k & 1) ? CAn : CA, ac, ap);
         const float2 bn = f2fma((k & 1) ? CBn : CB, bcur, bp);
         acc[k + 1] = f2add(f2add(acc[k + 1], an), bn);
@@ -333,7 +353,10 @@ __global__ void __launch_bounds__(kQuadThreads, 3)
                 since = 0;
                 while (t + 1 < n_types && slot >= type_off[t + 1]) ++t;
             }
-            atoms2<QC>(sx[i], sx[i + 1], u, qs_hi, qs_lo, dq_hi, dq_lo, zero_start, qlen, acc);
+            if (qlen == QC)
+                atoms2<QC, true>(sx[i], sx[i + 1], u, qs_hi, qs_lo, dq_hi, dq_lo, zero_start, qlen, acc);
+            else
+                atoms2<QC, false>(sx[i], sx[i + 1], u, qs_hi, qs_lo, dq_hi, dq_lo, zero_start, qlen, acc);
             since += 2;
             if (since >= kFoldAtoms) {
                 fold<QC>(acc, amp, F + (int64_t)t * n_q + q_begin, qlen, tid);

@@ -634,9 +634,9 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
 // kernel (NV the float2 slots it computes, fitted to the pass or its block capacity; the set-up
 // from the 30,000-atom rod at 101 q against the 50,000-atom globule at 201 q: 9.0 and 13.0 ps per
 // pair), a (direction, atom) pair of the quadrature kQuadStepCost units per q of its 32-value
-// pass (2.5e13 direct units/s against 4.3e12 quadrature steps/s, both measured on GB300).
+// pass (2.5e13 direct units/s against 5.6e12 quadrature steps/s, both measured on GB300).
 constexpr double kDirectSetup = 120.0;
-constexpr double kQuadStepCost = 5.8;
+constexpr double kQuadStepCost = 4.5;
 constexpr double kQuadTol = 1e-10;                  // (2l+1)|j_l(qR)| below this past the degree L
 constexpr size_t kQuadAmpBytes = (size_t)4 << 30;   // partial amplitudes held at once
 int quad_dirs_for(int L)
