@@ -42,6 +42,23 @@ PAIR_KERNEL = "k_debye_mixed_pairs2<52,101>"
 MIXED_KERNEL_DRAM_BYTES = 990_720
 
 
+# The paper's own timings (Table 1: 50-point profiles on 0 < q <= 1, single-precision OpenCL; pair·q
+# counted as N(N+1)/2 pairs x 50 q, the j <= k form of Section II) with their hardware: context for
+# the line, not its target.
+def _table1(n, seconds):
+    return {"atoms": n, "s": seconds, "pair_q_per_s": n * (n + 1) / 2 * 50 / seconds}
+
+
+PAPER_CONTEXT = {
+    "source": "Table 1 (50-point profiles, 0 < q <= 1 A^-1, FP32 OpenCL GPU, parallel Java CPU)",
+    "gtx295_gpu_40k": _table1(40000, 3.94),
+    "gtx295_gpu_100k": _table1(100000, 22.5),
+    "gt330m_gpu_100k": _table1(100000, 121.0),
+    "xeon_2x4core_java_100k": _table1(100000, 806.0),
+    "note": "other hardware, precision and q grid; not comparable as a ratio",
+}
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -482,6 +499,7 @@ def run_ours(args):
                                   "sm_mhz": meas["sm_mhz"],
                                   "basis": "sas_measure_peaks microbenchmarks, same process, after the timed region"}},
         "e2e": e2e,
+        "paper_context": PAPER_CONTEXT,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
