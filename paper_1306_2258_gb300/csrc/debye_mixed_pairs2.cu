@@ -73,8 +73,10 @@ __device__ __forceinline__ void run_pairs2(const float4 *sxy, const float4 *szw,
     }
 }
 
-template <int NB, int NV>
-__global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
+// TILE: the I-tile (= threads per CTA), 128, or 64 for small molecules whose type groups padded to
+// 128 would waste slots.
+template <int NB, int NV, int TILE>
+__global__ void __launch_bounds__(TILE, mixed_ctas_per_sm(NB) * (kTile / TILE))
     k_debye_mixed_pairs2(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items,
                          int n_items, QChunks qc, double *__restrict__ partial, int part_stride, int jmax,
                          int *__restrict__ ticket)
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
     extern __shared__ float4 smem[];
     float4 *sxy = smem;              // [jmax / 2]: (x_j, x_j+1, y_j, y_j+1)
     float4 *szw = smem + jmax / 2;   // [jmax / 2]: (z_j, z_j+1, w_j, w_j+1)
-    __shared__ double red[kTile / 32][4 * NB];
+    __shared__ double red[TILE / 32][4 * NB];
     __shared__ int next_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int it = blockIdx.x;   // first item: the CTA's index; then tickets (items sorted by work)
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
         __syncthreads();   // the previous item is done with the staging, red and next_item
         if (tid == 0) next_item = (int)gridDim.x + atomicAdd(ticket, 1);
         const int jpairs = (item.jlen + 1) >> 1;
-        for (int k = tid; k < jpairs; k += kTile) {
+        for (int k = tid; k < jpairs; k += TILE) {
             const float4 a = Xb[item.j0 + 2 * k];
             const float4 b = (2 * k + 1 < item.jlen) ? Xb[item.j0 + 2 * k + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
             sxy[k] = make_float4(a.x, b.x, a.y, b.y);
@@ -116,52 +118,55 @@ __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
         flush_warp<NB, 2>(acc, red[warp], lane);
         __syncthreads();
         const int qlen = qc.q_len[ch];
-        for (int k = tid; k < qlen; k += kTile) {
+        for (int k = tid; k < qlen; k += TILE) {
             double s = red[0][k];
 #pragma unroll
-            for (int w = 1; w < kTile / 32; ++w) s += red[w][k];
+            for (int w = 1; w < TILE / 32; ++w) s += red[w][k];
             partial[(int64_t)it * part_stride + k] = s;
         }
         it = next_item;
     }
 }
 
-template <int NB, int NV>
+template <int NB, int NV, int TILE>
 cudaError_t launch_nv(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
                       double *partial, int part_stride, int grid, int jmax, int *ticket, cudaStream_t s)
 {
     const size_t smem = (size_t)jmax * sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(k_debye_mixed_pairs2<NB, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_debye_mixed_pairs2<NB, NV, TILE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (grid <= 0) {   // persistent grid: every resident CTA slot of every SM
         int occ = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_mixed_pairs2<NB, NV>, kTile, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_mixed_pairs2<NB, NV, TILE>, TILE, smem);
         if (e != cudaSuccess) return e;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         grid = (occ > 0 ? occ : 1) * sms;
     }
     if (grid > n_items) grid = n_items;
-    k_debye_mixed_pairs2<NB, NV><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, partial, part_stride, jmax,
-                                                           ticket);
+    k_debye_mixed_pairs2<NB, NV, TILE><<<grid, TILE, smem, s>>>(X, npad, items, n_items, qc, partial, part_stride,
+                                                                 jmax, ticket);
     return cudaGetLastError();
 }
 
 // NV: the slots of the longest chunk when within 3 of the capacity 2*NB, else the capacity.
-template <int NB>
+template <int NB, int TILE>
 cudaError_t launch_nb2(int nv, const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
                        double *partial, int part_stride, int grid, int jmax, int *ticket, cudaStream_t s)
 {
     switch (2 * NB - nv) {
     case 1:
-        return launch_nv<NB, 2 * NB - 1>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+        return launch_nv<NB, 2 * NB - 1, TILE>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket,
+                                               s);
     case 2:
-        return launch_nv<NB, 2 * NB - 2>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+        return launch_nv<NB, 2 * NB - 2, TILE>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket,
+                                               s);
     case 3:
-        return launch_nv<NB, 2 * NB - 3>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+        return launch_nv<NB, 2 * NB - 3, TILE>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket,
+                                               s);
     default:
-        return launch_nv<NB, 2 * NB>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+        return launch_nv<NB, 2 * NB, TILE>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
     }
 }
 
@@ -169,20 +174,27 @@ cudaError_t launch_nb2(int nv, const float4 *X, int64_t npad, const Item *items,
 
 cudaError_t launch_debye_mixed_pairs2(const float4 *X, int64_t npad, const Item *items, int n_items,
                                       const QChunks &qc, double *partial, int part_stride, int grid, int jmax,
-                                      int *ticket, cudaStream_t s)
+                                      int *ticket, cudaStream_t s, int tile)
 {
     if (n_items == 0) return cudaSuccess;
     if (jmax % 2 != 0) return cudaErrorInvalidValue;
     int qmax = 0;
     for (int c = 0; c < qc.n_chunks; ++c) qmax = qc.q_len[c] > qmax ? qc.q_len[c] : qmax;
     const int nv = (qmax + 1) / 2;
-    switch (mixed_blocks_for(qmax)) {
+    const int nb = mixed_blocks_for(qmax);
+    if (tile == 64) {   // small molecules: the 52- and 104-q forms only
+        if (nb == 13) return launch_nb2<13, 64>(nv, X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+        if (nb == 26) return launch_nb2<26, 64>(nv, X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+        return cudaErrorInvalidValue;
+    }
+    if (tile != kTile) return cudaErrorInvalidValue;
+    switch (nb) {
     case 13:
-        return launch_nb2<13>(nv, X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+        return launch_nb2<13, kTile>(nv, X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
     case 26:
-        return launch_nb2<26>(nv, X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+        return launch_nb2<26, kTile>(nv, X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
     default:
-        return launch_nb2<52>(nv, X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+        return launch_nb2<52, kTile>(nv, X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
     }
 }
 

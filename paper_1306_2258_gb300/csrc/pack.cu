@@ -132,9 +132,13 @@ __global__ void k_centroid(const void *coords, int coords_f64, int64_t n, double
 }
 
 // Stable scatter: slot = group offset + (atoms of the same type before this one).
-__global__ void k_scatter(const void *coords, int coords_f64, const int32_t *types, int64_t n,
-                          int64_t batch, int n_types, const int *blockoffs, const int *meta,
-                          const double *centroid, int out_f64, void *X, int64_t npad, int *slot_of)
+// Slot of every atom (stable by type) and its packed coordinates for the conformers of slice
+// blockIdx.y (every gridDim.y-th): FP32 inputs are copied as they are, FP64 inputs centred on the
+// conformer's FP64 centroid (when given) before the FP32 or FP64 store.
+template <typename Real>
+__global__ void k_scatter(const Real *coords, const int32_t *types, int64_t n, int64_t batch, int n_types,
+                          const int *blockoffs, const int *meta, const double *centroid, int out_f64, void *X,
+                          int64_t npad, int *slot_of)
 {
     __shared__ int wcnt[kPackThreads / 32][SAS_MAX_TYPES];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -153,20 +157,17 @@ __global__ void k_scatter(const void *coords, int coords_f64, const int32_t *typ
     for (int w = 0; w < warp; ++w) before += wcnt[w][t];
     int rank = blockoffs[(int64_t)blockIdx.x * n_types + t] + before + rank_in_warp;
     int slot = meta[n_types + t] + rank;
-    slot_of[i] = slot;
-    for (int64_t b = 0; b < batch; ++b) {
-        double x, y, z;
-        load_xyz(coords, coords_f64, b * n + i, x, y, z);
+    if (blockIdx.y == 0) slot_of[i] = slot;
+    for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+        const Real *c = coords + 3 * (b * n + i);
         if (out_f64) {
-            static_cast<double4 *>(X)[b * npad + slot] = make_double4(x, y, z, 1.0);
-        } else {
-            if (centroid) {
-                x -= centroid[3 * b];
-                y -= centroid[3 * b + 1];
-                z -= centroid[3 * b + 2];
-            }
+            static_cast<double4 *>(X)[b * npad + slot] = make_double4(c[0], c[1], c[2], 1.0);
+        } else if (centroid) {
             static_cast<float4 *>(X)[b * npad + slot] =
-                make_float4((float)x, (float)y, (float)z, 1.0f);
+                make_float4((float)((double)c[0] - centroid[3 * b]), (float)((double)c[1] - centroid[3 * b + 1]),
+                            (float)((double)c[2] - centroid[3 * b + 2]), 1.0f);
+        } else {
+            static_cast<float4 *>(X)[b * npad + slot] = make_float4((float)c[0], (float)c[1], (float)c[2], 1.0f);
         }
     }
 }
@@ -213,8 +214,14 @@ cudaError_t launch_scatter(const void *coords, int coords_f64, const int32_t *ty
 {
     int nblk = (int)((n + kPackThreads - 1) / kPackThreads);
     if (nblk == 0) return cudaSuccess;
-    k_scatter<<<nblk, kPackThreads, 0, s>>>(coords, coords_f64, types, n, batch, n_types, blockoffs,
-                                            meta, centroid, out_f64, X, npad, slot_of);
+    const unsigned ys = (unsigned)std::max<int64_t>(1, std::min<int64_t>(batch, (1216 + nblk - 1) / nblk));
+    const dim3 grid((unsigned)nblk, ys);
+    if (coords_f64)
+        k_scatter<double><<<grid, kPackThreads, 0, s>>>(static_cast<const double *>(coords), types, n, batch, n_types,
+                                                        blockoffs, meta, centroid, out_f64, X, npad, slot_of);
+    else
+        k_scatter<float><<<grid, kPackThreads, 0, s>>>(static_cast<const float *>(coords), types, n, batch, n_types,
+                                                       blockoffs, meta, centroid, out_f64, X, npad, slot_of);
     return cudaGetLastError();
 }
 

@@ -228,6 +228,7 @@ struct sas_ctx {
     int opt_shard_rank = 0, opt_shard_world = 1;   // this call computes shard rank of world
     int opt_method = 0;                             // 0 direct sum, 1 hybrid by qD and N, 2 quadrature
     double diam = 0.0;                              // bound on the diameter of the last call's conformers
+    int pad = kTile, tile_used = kTile;             // type-group padding and I-tile of the last packing
     int64_t opt_timeout_ms = 600000;
     DevBuf coef_d, F, meta, blockcounts, blockoffs, centroid, X, slot_of, items, group_items,
         group_off, partial, ticket, S, in_coords, in_types, out_buf, Ibuf, gbuf, chi2buf, H, G, gout, tgt, wts,
@@ -301,16 +302,16 @@ struct Schedule {
 };
 
 // Items of one conformer-independent layout; `counts` are the real atoms per type.
-void build_schedule(const int *counts, int T, int64_t batch, int tile, int n_chunks, int grid,
+void build_schedule(const int *counts, int T, int64_t batch, int tile, int pad, int n_chunks, int grid,
                     int64_t jmax_opt, int64_t jmax_cap, int shard_rank, int shard_world, Schedule &out)
 {
-    // Type group t occupies slots [O[t], O[t] + P[t]) of the packed array, its atoms the first
-    // counts[t]; an I-tile spans `tile` slots, a J-range ends at E[t], the count rounded up to 4
-    // (the slots past the count hold zero-weight padding).
+    // Type group t occupies slots [O[t], O[t] + P[t]) of the packed array (its count padded to a
+    // multiple of `pad`), its atoms the first counts[t]; an I-tile spans `tile` slots, a J-range
+    // ends at E[t], the count rounded up to 4 (the slots past the count hold zero-weight padding).
     std::vector<int64_t> P(T), O(T), E(T);
     int64_t off = 0;
     for (int t = 0; t < T; ++t) {
-        P[t] = (counts[t] + kTile - 1) / kTile * kTile;
+        P[t] = (counts[t] + pad - 1) / pad * pad;
         O[t] = off;
         E[t] = off + std::min<int64_t>(P[t], (counts[t] + 3) / 4 * 4);
         off += P[t];
@@ -433,10 +434,11 @@ sas_status schedule_for(sas_ctx *ctx, int T, int64_t batch, int tile, int n_chun
     key.push_back(jmax_cap);
     key.push_back(ctx->opt_shard_rank);
     key.push_back(ctx->opt_shard_world);
+    key.push_back(ctx->pad);
     if (key != ctx->sched_key) {
         Schedule sc;
         const int64_t jm = ctx->opt_jmax > 0 ? std::min(ctx->opt_jmax, jmax_cap) : 0;
-        build_schedule(ctx->h_meta, T, batch, tile, n_chunks, grid_cap, jm, jmax_cap, ctx->opt_shard_rank,
+        build_schedule(ctx->h_meta, T, batch, tile, ctx->pad, n_chunks, grid_cap, jm, jmax_cap, ctx->opt_shard_rank,
                        ctx->opt_shard_world, sc);
         const int ni = (int)sc.items.size();
         const int ng = (int)sc.group_off.size() - 1;
@@ -469,7 +471,8 @@ sas_status schedule_for(sas_ctx *ctx, int T, int64_t batch, int tile, int n_chun
 // Shared front half of every pair computation: stage, validate, count, schedule, pack.
 // On success the context holds X (packed), slot_of, meta (counts/offsets) and the item list.
 // T: the types of this call (1 for per-atom form factors, whose table ff_check [ff_count] is
-// validated with the coordinates).
+// validated with the coordinates).  tile 0: the mixed typed path chooses its I-tile after the
+// read-back (see the choice below); otherwise the given tile and groups padded to 128 slots.
 sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32_t *types, int64_t n,
                    int64_t batch, bool out_f64, bool center, int tile, int n_chunks, int64_t jmax_cap,
                    cudaStream_t s, int &launches, int T, const double *ff_check = nullptr, int64_t ff_count = 0)
@@ -512,13 +515,45 @@ sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32
     if (err & kErrBadType) return fail(SAS_ERR_INVALID_ARG, "atom type outside [0, %d)", T);
     if (err & kErrNonFinite) return fail(SAS_ERR_INVALID_ARG, "non-finite coordinate");
     if (err & kErrNonFiniteFF) return fail(SAS_ERR_INVALID_ARG, "non-finite form factor");
-    const int64_t npad = ctx->h_meta[2 * T];
     {
         float r2;
         const unsigned bits = (unsigned)ctx->h_meta[2 * T + 2];
         std::memcpy(&r2, &bits, sizeof r2);
         ctx->diam = 2.0 * std::sqrt((double)r2);
     }
+    ctx->pad = kTile;
+    if (tile == 0) {
+        // Tiles of 64 atoms where the automatic kernel form is the two-pair kernel (no re-seeding,
+        // passes of at most 104 q; an explicit SAS_OPT_VARIANT keeps the 128-slot layout, whose
+        // variants agree bit for bit) and type groups padded to 128 slots would waste more than 5 %
+        // of them (small molecules:
+        // 2,000 atoms of 5 types pad to 2,560 slots, against 2,240 in groups of 64).  The scan ran
+        // with 128; the group offsets are redone here and written back before the packing.
+        tile = kTile;
+        int qmax = 0;
+        for (int c = 0; c < ctx->qc.n_chunks; ++c) qmax = std::max(qmax, ctx->qc.q_len[c]);
+        int64_t p128 = 0, p64 = 0;
+        for (int t = 0; t < T; ++t) {
+            p128 += ((int64_t)ctx->h_meta[t] + 127) / 128 * 128;
+            p64 += ((int64_t)ctx->h_meta[t] + 63) / 64 * 64;
+        }
+        if (ctx->opt_variant == 0 && ctx->opt_step == 2 && mixed_blocks_for(qmax) <= 26 &&
+            reseed_for(ctx->opt_reseed, n, qmax, step_phase(ctx, ctx->qc)) == 0 && ctx->opt_shard_world == 1 &&
+            (double)p128 > 1.05 * (double)p64) {
+            tile = 64;
+            ctx->pad = 64;
+            int off = 0;
+            for (int t = 0; t < T; ++t) {
+                ctx->h_meta[T + t] = off;
+                off += (ctx->h_meta[t] + 63) / 64 * 64;
+            }
+            ctx->h_meta[2 * T] = off;
+            CUDA_TRY(cudaMemcpyAsync(ctx->meta.as<int>() + T, ctx->h_meta + T, (size_t)(T + 1) * sizeof(int),
+                                     cudaMemcpyHostToDevice, s));
+        }
+    }
+    ctx->tile_used = tile;
+    const int64_t npad = ctx->h_meta[2 * T];
     st = schedule_for(ctx, T, batch, tile, n_chunks, jmax_cap, s);
     if (st != SAS_OK) return st;
     // pack
@@ -592,7 +627,9 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
     ctx->stats[6] = ctx->stats[7] = 0;
     if (hybrid_ok && !fp64 && ctx->opt_method != 0)
         return forward_hybrid(ctx, coords, coords_type, types, n, batch, I_dev, jmax_cap, s, launches);
-    const int tile = fp64 ? kTile64 : kTile;
+    // plain profile calls may take 64-atom tiles (chosen in prepare); the gradient's adjoint kernel
+    // reuses the forward's packing with 128-atom tiles
+    const int tile = fp64 ? kTile64 : (hybrid_ok ? 0 : kTile);
     sas_status st = prepare(ctx, coords, coords_type, types, n, batch, fp64,
                             !fp64 && coords_type == SAS_COORDS_F64, tile, ctx->qc.n_chunks, jmax_cap, s,
                             launches, T);
@@ -609,6 +646,12 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
     if (fp64) {
         CUDA_TRY(launch_debye_fp64(ctx->X.as<double4>(), npad, ctx->items.as<Item>(), ctx->n_items,
                                    ctx->qc, ctx->partial.as<double>(), kQChunk, grid, s));
+    } else if (ctx->tile_used != kTile) {   // the two-pair kernel on 64-atom tiles (chosen in prepare)
+        CUDA_TRY(launch_debye_mixed_pairs2(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, ctx->qc,
+                                           ctx->partial.as<double>(), kQChunk,
+                                           ctx->opt_grid > 0 ? ctx->opt_grid * ctx->sms : 0,
+                                           std::min(ctx->jmax_used, ctx->jlen_max + (ctx->jlen_max & 1)),
+                                           ctx->ticket.as<int>(), s, ctx->tile_used));
     } else {
         CUDA_TRY(launch_debye_mixed(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items,
                                     ctx->qc, ctx->opt_step,

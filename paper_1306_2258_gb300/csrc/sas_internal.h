@@ -105,7 +105,7 @@ cudaError_t launch_debye_mixed(const float4 *X, int64_t npad, const Item *items,
 // The two-pairs-per-step form of the 2-step kernel without re-seeding (same arguments and result).
 cudaError_t launch_debye_mixed_pairs2(const float4 *X, int64_t npad, const Item *items, int n_items,
                                       const QChunks &qc, double *partial, int part_stride, int grid, int jmax,
-                                      int *ticket, cudaStream_t s);
+                                      int *ticket, cudaStream_t s, int tile = kTile);
 cudaError_t launch_debye_fp64(const double4 *X, int64_t npad, const Item *items, int n_items,
                               const QChunks &qc, double *partial, int part_stride, int grid,
                               cudaStream_t s);
