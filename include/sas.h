@@ -10,7 +10,9 @@
  * over all N atoms of a molecule, on a grid of q values made of uniform runs, with the
  * per-atom form factors f_j(q) taken from a small set of atom types:
  *
- *     f_t(q) = sum_{k=1..4} a_k exp(-b_k (q / 4 pi)^2) + c      (coefficients per type t).
+ *     f_t(q) = sum_{k=1..4} a_k exp(-b_k (q / 4 pi)^2) + c      (coefficients per type t),
+ *
+ * or given per atom and q (sas_profile_atomic).
  *
  * Conventions for every entry point
  *  - Every function returns a sas_status; nothing throws across the ABI.
@@ -22,10 +24,12 @@
  *    output returns only after the result has been copied back.
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
  *  - Validation (n < 0, null pointers, type out of range, non-finite
- *    coordinate) happens before any output is written: on an error the
- *    outputs are untouched.  Device-resident inputs are validated by a kernel
- *    whose verdict the host reads back, so these calls synchronize on the
- *    stream once, after packing and before the pair kernel.
+ *    coordinate or form factor) happens before any output is written: on an
+ *    error the outputs are untouched.  Device-resident inputs are validated by
+ *    a kernel whose verdict (with the type counts) the host reads back, so
+ *    these calls synchronize on the stream once, before packing (the
+ *    quadrature method of SAS_OPT_METHOD reads back the molecule's radius
+ *    once more, after packing).
  *  - A context is not thread-safe: use one context per host thread.
  *  - Layouts are C order (row-major): coords [batch][n][3], outputs [batch][...].
  *  - Atom pairs are counted as unordered distinct pairs i<j (Section II: only
