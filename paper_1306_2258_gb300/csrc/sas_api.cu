@@ -22,11 +22,14 @@
 #include <thread>
 #include <vector>
 
+#include "api_internal.h"
 #include "sas_internal.h"
 
 using namespace sas;
+using namespace sas::api;
 
-namespace {
+namespace sas {
+namespace api {
 
 thread_local std::string g_err;
 
@@ -41,7 +44,8 @@ sas_status fail(sas_status st, const char *fmt, ...)
     return st;
 }
 
-}  // namespace
+}  // namespace api
+}  // namespace sas
 
 namespace sas {
 sas_status set_error(sas_status st, const char *msg)
@@ -115,16 +119,9 @@ int reseed_auto(int64_t n_atoms, int n_q_chunk, double step_phase_max)
 
 }  // namespace sas
 
-namespace {
+namespace sas {
+namespace api {
 
-#define CUDA_TRY(call)                                                                       \
-    do {                                                                                     \
-        cudaError_t e_ = (call);                                                             \
-        if (e_ != cudaSuccess) {                                                             \
-            cudaGetLastError();                                                              \
-            return fail(SAS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));              \
-        }                                                                                    \
-    } while (0)
 
 // Test hook: SAS_TEST_FAIL_ALLOC=k makes the k-th device allocation (1-based) fail.
 long g_alloc_count = 0;
@@ -137,46 +134,6 @@ long alloc_fail_at()
     return v;
 }
 
-struct DevBuf {
-    void *p = nullptr;
-    size_t cap = 0;
-    DevBuf() = default;
-    DevBuf(const DevBuf &) = delete;
-    DevBuf &operator=(const DevBuf &) = delete;
-    ~DevBuf() { release(); }
-    void release()
-    {
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-    }
-    // Grow to at least `bytes`.  Returns false (and leaves the buffer empty) on failure.
-    bool ensure(size_t bytes)
-    {
-        if (bytes <= cap && p) return true;
-        release();
-        ++g_alloc_count;
-        if (alloc_fail_at() > 0 && g_alloc_count == alloc_fail_at()) return false;
-        if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
-            cudaGetLastError();
-            p = nullptr;
-            return false;
-        }
-        cap = bytes;
-        return true;
-    }
-    template <class T>
-    T *as() const
-    {
-        return static_cast<T *>(p);
-    }
-};
-
-#define ALLOC_TRY(buf, bytes)                                                                \
-    do {                                                                                     \
-        if (!(buf).ensure(bytes))                                                            \
-            return fail(SAS_ERR_ALLOC, "device allocation of %zu bytes failed", (size_t)(bytes)); \
-    } while (0)
 
 bool on_device(const void *p)
 {
@@ -212,44 +169,12 @@ int pair_index(int a, int b, int T)
     return a * T - a * (a - 1) / 2 + (b - a);
 }
 
-}  // namespace
+}  // namespace api
+}  // namespace sas
 
-struct sas_ctx {
-    int n_types = 0, n_q = 0;
-    unsigned flags = 0;
-    std::vector<double> coef, q;
-    QChunks qc{};
-    int sms = 1;
-    int64_t opt_jmax = 0;
-    int opt_reseed = -1;   // -1: automatic (see reseed_for)
-    int opt_step = 2;
-    int opt_variant = 0;
-    int opt_grid = 0;
-    int opt_shard_rank = 0, opt_shard_world = 1;   // this call computes shard rank of world
-    int opt_method = 0;                             // 0 direct sum, 1 hybrid by qD and N, 2 quadrature
-    double diam = 0.0;                              // bound on the diameter of the last call's conformers
-    int pad = kTile, tile_used = kTile;             // type-group padding and I-tile of the last packing
-    int64_t opt_timeout_ms = 600000;
-    DevBuf coef_d, F, meta, blockcounts, blockoffs, centroid, X, slot_of, items, group_items,
-        group_off, partial, ticket, S, in_coords, in_types, out_buf, Ibuf, gbuf, chi2buf, H, G, gout, tgt, wts,
-        hist, dropped, in_ff, zero_types, FJ, FI, F64t, D2, segbuf, cen, qdirs, qwts, type_off, Apart, Fsub, Itmp, qplan;
-    int *h_meta = nullptr;   // pinned
-    // schedule cache
-    std::vector<int64_t> sched_key;
-    int n_items = 0, n_groups = 0, jmax_used = 0, jlen_max = 0, max_group = 0;
-    int64_t pair_slots = 0;
-    int64_t last_batch = 0;
-    bool have_partials = false;
-    int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the last pair-kernel launch
-    bool ev_pending = false;
-    double4 *h_cen = nullptr;   // pinned: centroid and radius per conformer (quadrature method)
-    int64_t h_cen_cap = 0;
-    void *h_stage = nullptr;   // pinned staging of host outputs
-    size_t h_stage_cap = 0;
-};
 
-namespace {
+namespace sas {
+namespace api {
 
 // Largest phase step M dq D of the mixed recurrence over the passes of qc (D from the last
 // validation read-back).
@@ -475,7 +400,7 @@ sas_status schedule_for(sas_ctx *ctx, int T, int64_t batch, int tile, int n_chun
 // read-back (see the choice below); otherwise the given tile and groups padded to 128 slots.
 sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32_t *types, int64_t n,
                    int64_t batch, bool out_f64, bool center, int tile, int n_chunks, int64_t jmax_cap,
-                   cudaStream_t s, int &launches, int T, const double *ff_check = nullptr, int64_t ff_count = 0)
+                   cudaStream_t s, int &launches, int T, const double *ff_check, int64_t ff_count)
 {
     const size_t esz = coords_f64 ? sizeof(double) : sizeof(float);
     const void *cd = coords;
@@ -615,9 +540,6 @@ sas_status reduce_items(sas_ctx *ctx, const QChunks &qc, cudaStream_t s)
 }
 
 // I(q) of `batch` conformers into the device buffer I_dev (all steps on stream s).
-sas_status forward_hybrid(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types, int64_t n,
-                          int64_t batch, double *I_dev, int64_t jmax_cap, cudaStream_t s, int &launches);
-
 sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types, int64_t n,
                    int64_t batch, double *I_dev, int64_t jmax_cap, cudaStream_t s, int &launches,
                    bool hybrid_ok = false)
@@ -673,189 +595,10 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
     return SAS_OK;
 }
 
-// Cost model of the hybrid split: a pair costs 2 NV + kDirectSetup units per pass of the direct
-// kernel (NV the float2 slots it computes, fitted to the pass or its block capacity; the set-up
-// from the 30,000-atom rod at 101 q against the 50,000-atom globule at 201 q: 9.0 and 13.0 ps per
-// pair), a (direction, atom) pair of the quadrature kQuadStepCost units per q of its 32-value
-// pass (2.5e13 direct units/s against 5.6e12 quadrature steps/s, both measured on GB300).
-constexpr double kDirectSetup = 120.0;
-constexpr double kQuadStepCost = 4.5;
-constexpr double kQuadTol = 1e-10;                  // (2l+1)|j_l(qR)| below this past the degree L
-constexpr size_t kQuadAmpBytes = (size_t)4 << 30;   // partial amplitudes held at once
-int quad_dirs_for(int L)
-{
-    int nt = L + 1;
-    nt += nt & 1;
-    return (nt / 2) * (2 * L + 1);
-}
-
-// I(q) by the orientation average of Eq. 1 on a prefix of the q grid and by the direct sum on
-// the rest.  Method 1 (hybrid) ends the prefix at the first q where the quadrature's directions
-// times atoms, weighted by its relative cost, reach the pair count; method 2 takes every q.
-sas_status forward_hybrid(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types, int64_t n,
-                          int64_t batch, double *I_dev, int64_t jmax_cap, cudaStream_t s, int &launches)
-{
-    const int T = ctx->n_types, Q = ctx->n_q, Pn = T * (T + 1) / 2;
-    if (ctx->opt_shard_world > 1) return fail(SAS_ERR_UNSUPPORTED, "the quadrature method runs as a single shard");
-    sas_status st = prepare(ctx, coords, coords_type, types, n, batch, false, coords_type == SAS_COORDS_F64, kTile,
-                            ctx->qc.n_chunks, jmax_cap, s, launches, T);
-    if (st != SAS_OK) return st;
-    const int64_t npad = ctx->h_meta[2 * T];
-    ctx->have_partials = false;
-    // centroid and radius of every conformer
-    ALLOC_TRY(ctx->cen, (size_t)batch * sizeof(double4));
-    CUDA_TRY(launch_packed_geometry(ctx->X.as<float4>(), npad, batch, ctx->cen.as<double4>(), s));
-    launches += 2;
-    if (ctx->h_cen_cap < batch) {
-        if (ctx->h_cen) cudaFreeHost(ctx->h_cen);
-        ctx->h_cen = nullptr;
-        ctx->h_cen_cap = 0;
-        if (cudaMallocHost((void **)&ctx->h_cen, (size_t)batch * sizeof(double4)) != cudaSuccess) {
-            cudaGetLastError();
-            ctx->h_cen = nullptr;
-            return fail(SAS_ERR_ALLOC, "pinned host allocation failed");
-        }
-        ctx->h_cen_cap = batch;
-    }
-    CUDA_TRY(cudaMemcpyAsync(ctx->h_cen, ctx->cen.p, (size_t)batch * sizeof(double4), cudaMemcpyDeviceToHost, s));
-    st = wait_stream(ctx, s);
-    if (st != SAS_OK) return st;
-    double R = 0.0;
-    for (int64_t b = 0; b < batch; ++b) R = std::max(R, ctx->h_cen[b].w);
-    // the split: the quadrature on whole 32-value passes from q[0], the direct sum on the rest,
-    // at the least modelled cost
-    int k_split = 0;
-    if (ctx->opt_method == 2) {
-        k_split = Q;
-    } else {
-        const double pairs = 0.5 * (double)n * (double)(n - 1);
-        auto direct_cost = [&](int Qd) {
-            double c = 0.0;
-            for (int b = 0; b < Qd; b += kQChunk) {
-                const int len = std::min(kQChunk, Qd - b), nb = mixed_blocks_for(len), nv = (len + 1) / 2;
-                c += pairs * (2.0 * ((2 * nb - nv <= 3) ? nv : 2 * nb) + kDirectSetup);
-            }
-            return c;
-        };
-        double best = direct_cost(Q), quad = 0.0;
-        for (int s0 = 0; s0 < Q; s0 += kQuadChunk) {
-            const int e = std::min(Q, s0 + kQuadChunk);
-            quad += kQuadStepCost * (double)n * kQuadChunk * quad_dirs_for(quad_degree(ctx->q[e - 1] * R, kQuadTol));
-            if (quad > best) break;
-            const double total = quad + direct_cost(Q - e);
-            if (total < best) {
-                best = total;
-                k_split = e;
-            }
-        }
-    }
-    int64_t n_dirs = 0;
-    CUDA_TRY(cudaEventRecord(ctx->ev0, s));
-    if (k_split > 0) {   // quadrature on q[0, k_split)
-        QChunks qq{};
-        if (!make_chunks(ctx->q.data(), k_split, qq, kQuadChunk))
-            return fail(SAS_ERR_UNSUPPORTED, "the quadrature range needs more than %d passes", kMaxChunks);
-        QuadPlan pl{};
-        std::vector<float4> dirs, d;
-        std::vector<double> wts, w;
-        int ctas = 0;
-        int64_t amp = 0;
-        for (int c = 0; c < qq.n_chunks; ++c) {
-            const double qmax = ctx->q[qq.q_begin[c] + qq.q_len[c] - 1];
-            quad_directions(quad_degree(qmax * R, kQuadTol), d, w);
-            const int M = (int)d.size();
-            const int dblk = (M + quad_threads_per_cta() - 1) / quad_threads_per_cta();
-            const int64_t tiles = npad / 256 + 1;
-            int nseg = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (3 * ctx->sms + dblk * batch - 1) / (dblk * batch)));
-            const int64_t seg_len = ((npad + nseg - 1) / nseg + 255) / 256 * 256;
-            nseg = (int)((npad + seg_len - 1) / seg_len);
-            pl.q_begin[c] = qq.q_begin[c];
-            pl.q_len[c] = qq.q_len[c];
-            pl.qs_hi[c] = qq.qs_hi[c];
-            pl.qs_lo[c] = qq.qs_lo[c];
-            pl.dq_hi[c] = qq.dq_hi[c];
-            pl.dq_lo[c] = qq.dq_lo[c];
-            pl.dir_off[c] = (int)dirs.size();
-            pl.n_dir[c] = M;
-            pl.n_seg[c] = nseg;
-            pl.seg_len[c] = (int)seg_len;
-            pl.cta_off[c] = ctas;
-            pl.amp_off[c] = amp;
-            ctas += dblk * nseg;
-            amp += (int64_t)nseg * kQuadChunk * M;
-            dirs.insert(dirs.end(), d.begin(), d.end());
-            wts.insert(wts.end(), w.begin(), w.end());
-        }
-        pl.n_chunks = qq.n_chunks;
-        pl.cta_off[qq.n_chunks] = ctas;
-        pl.amp_stride = amp;
-        n_dirs = (int64_t)dirs.size();
-        std::vector<int> toff(T + 1, 0);
-        for (int t = 0; t < T; ++t) toff[t + 1] = toff[t] + (ctx->h_meta[t] + kTile - 1) / kTile * kTile;
-        ALLOC_TRY(ctx->qdirs, dirs.size() * sizeof(float4));
-        ALLOC_TRY(ctx->qwts, wts.size() * sizeof(double));
-        ALLOC_TRY(ctx->type_off, (T + 1) * sizeof(int));
-        ALLOC_TRY(ctx->qplan, sizeof(QuadPlan));
-        CUDA_TRY(cudaMemcpyAsync(ctx->qplan.p, &pl, sizeof(QuadPlan), cudaMemcpyHostToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(ctx->qdirs.p, dirs.data(), dirs.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(ctx->qwts.p, wts.data(), wts.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-        CUDA_TRY(cudaMemcpyAsync(ctx->type_off.p, toff.data(), (T + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-        const int64_t group = std::max<int64_t>(1, std::min<int64_t>(batch, (int64_t)(kQuadAmpBytes / (amp * sizeof(double2)))));
-        ALLOC_TRY(ctx->Apart, (size_t)group * amp * sizeof(double2));
-        for (int64_t b0 = 0; b0 < batch; b0 += group) {
-            const int64_t nb = std::min(group, batch - b0);
-            CUDA_TRY(launch_quad(ctx->X.as<float4>() + b0 * npad, npad, nb, ctx->type_off.as<int>(), T,
-                                 ctx->cen.as<double4>() + b0, ctx->F.as<double>(), Q, pl, ctx->qplan.as<QuadPlan>(),
-                                 ctx->qdirs.as<float4>(),
-                                 ctx->qwts.as<double>(), ctx->Apart.as<double2>(), I_dev + b0 * Q, s));
-            launches += 2;
-        }
-        // (copies from pageable host memory have read their source when cudaMemcpyAsync returns)
-    }
-    if (k_split < Q) {   // the direct sum on q[k_split, Q)
-        const int Qd = Q - k_split;
-        QChunks qd{};
-        if (!make_chunks(ctx->q.data() + k_split, Qd, qd))
-            return fail(SAS_ERR_UNSUPPORTED, "the direct range needs more than %d passes", kMaxChunks);
-        st = schedule_for(ctx, T, batch, kTile, qd.n_chunks, jmax_cap, s);
-        if (st != SAS_OK) return st;
-        ALLOC_TRY(ctx->Fsub, (size_t)T * Qd * sizeof(double));
-        CUDA_TRY(launch_form_factors(ctx->coef_d.as<double>(), T, qd, ctx->Fsub.as<double>(), s));
-        ALLOC_TRY(ctx->partial, (size_t)std::max(ctx->n_items, 1) * kQChunk * sizeof(double));
-        ALLOC_TRY(ctx->ticket, sizeof(int));
-        CUDA_TRY(cudaMemsetAsync(ctx->ticket.p, 0, sizeof(int), s));
-        CUDA_TRY(launch_debye_mixed(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, qd, ctx->opt_step,
-                                    reseed_for(ctx->opt_reseed, n, std::min(Qd, kQChunk), step_phase(ctx, qd)),
-                                    mixed_variant(ctx->opt_variant, std::min(Qd, kQChunk)), ctx->partial.as<double>(),
-                                    kQChunk, ctx->opt_grid > 0 ? ctx->opt_grid * ctx->sms : 0, ctx->jmax_used,
-                                    ctx->ticket.as<int>(), s));
-        ALLOC_TRY(ctx->S, (size_t)batch * Pn * Qd * sizeof(double));
-        st = reduce_items(ctx, qd, s);
-        if (st != SAS_OK) return st;
-        ALLOC_TRY(ctx->Itmp, (size_t)batch * Qd * sizeof(double));
-        CUDA_TRY(launch_assemble(ctx->S.as<double>(), ctx->Fsub.as<double>(), ctx->meta.as<int>(), T, batch, qd, 1,
-                                 ctx->Itmp.as<double>(), s));
-        CUDA_TRY(cudaMemcpy2DAsync(I_dev + k_split, (size_t)Q * sizeof(double), ctx->Itmp.p, (size_t)Qd * sizeof(double),
-                                   (size_t)Qd * sizeof(double), (size_t)batch, cudaMemcpyDeviceToDevice, s));
-        launches += 4;
-    }
-    CUDA_TRY(cudaEventRecord(ctx->ev1, s));
-    ctx->ev_pending = true;
-    ctx->stats[6] = k_split;
-    ctx->stats[7] = n_dirs;
-    ctx->last_batch = batch;
-    return SAS_OK;
-}
 
 // Outputs of one call: device destinations are copied at once on the stream; host destinations
 // are staged through pinned memory, so that the wait for them obeys the context's time limit
 // (a copy into pageable memory would block inside cudaMemcpyAsync instead).
-struct HostCopies {
-    void *dst[4];
-    const void *src[4];
-    size_t bytes[4];
-    int n = 0;
-};
 
 sas_status out_copy(HostCopies &hc, void *dst, const void *src, size_t bytes, cudaStream_t s)
 {
@@ -981,7 +724,8 @@ sas_status adjoint(sas_ctx *ctx, int64_t n, int64_t batch, const double *g_dev, 
     return SAS_OK;
 }
 
-}  // namespace
+}  // namespace api
+}  // namespace sas
 
 extern "C" {
 
@@ -1075,115 +819,6 @@ sas_status sas_profile_batch(sas_ctx *ctx, const void *coords, int coords_type, 
     return run_profile(ctx, coords, coords_type, types, n_atoms, batch, I_out, (cudaStream_t)stream);
 }
 
-sas_status sas_profile_atomic(sas_ctx *ctx, const void *coords, int coords_type, int64_t n_atoms, int64_t batch,
-                              const double *ff, double *I_out, void *stream)
-{
-    if (!ctx) return fail(SAS_ERR_INVALID_ARG, "null context");
-    const int64_t n = n_atoms;
-    if (n < 0 || batch < 0) return fail(SAS_ERR_INVALID_ARG, "negative size");
-    if (coords_type != SAS_COORDS_F32 && coords_type != SAS_COORDS_F64)
-        return fail(SAS_ERR_INVALID_ARG, "coords_type must be SAS_COORDS_F32 or SAS_COORDS_F64");
-    if (n > (int64_t)1 << 28) return fail(SAS_ERR_UNSUPPORTED, "more than 2^28 atoms");
-    if (batch > 65535) return fail(SAS_ERR_UNSUPPORTED, "more than 65535 conformers");
-    if (batch * (n + kTile) > ((int64_t)1 << 31)) return fail(SAS_ERR_UNSUPPORTED, "batch * atoms too large");
-    if (batch > 0 && !I_out) return fail(SAS_ERR_INVALID_ARG, "null output");
-    if (batch > 0 && n > 0 && (!coords || !ff)) return fail(SAS_ERR_INVALID_ARG, "null input");
-    if (ctx->opt_shard_world > 1) return fail(SAS_ERR_UNSUPPORTED, "per-atom form factors run as a single shard");
-    ctx->have_partials = false;
-    if (batch == 0) return SAS_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int Q = ctx->n_q;
-    if (n == 0) {
-        ctx->stats[0] = ctx->stats[1] = ctx->stats[2] = 0;
-        return zero_out(I_out, (size_t)batch * Q * sizeof(double), s);
-    }
-    const bool fp64 = (ctx->flags & SAS_FP64) != 0;
-    // q passes: the context's, or passes of the re-seed interval (a pass restarts the recurrence
-    // from exact seeds, so this is the re-seeding of the typed kernels)
-    // (re-seeded from the diameter bound below, once the validation read-back has it)
-    QChunks qf = ctx->qc;
-    int reseed = fp64 ? 0 : reseed_for(ctx->opt_reseed, n, std::min(Q, kQChunk), 0.0);
-    if (reseed > 0 && !make_chunks(ctx->q.data(), Q, qf, std::max(2, std::min(reseed, kQChunk))))
-        return fail(SAS_ERR_UNSUPPORTED, "the q grid needs more than %d passes at a re-seed interval of %d",
-                    kMaxChunks, reseed);
-    int launches = 0;
-    const void *ffd = nullptr;
-    const size_t ffbytes = (size_t)batch * Q * n * sizeof(double);
-    sas_status st = stage_in(ctx->in_ff, ff, ffbytes, s, ffd);
-    if (st != SAS_OK) return st;
-    const double *F = static_cast<const double *>(ffd);
-    ALLOC_TRY(ctx->zero_types, (size_t)n * sizeof(int32_t));
-    CUDA_TRY(cudaMemsetAsync(ctx->zero_types.p, 0, (size_t)n * sizeof(int32_t), s));
-    const int tile = fp64 ? kTile64 : kTile;
-    const int64_t jcap = fp64 ? 8192 : atomic_jmax(qf);
-    st = prepare(ctx, coords, coords_type == SAS_COORDS_F64, ctx->zero_types.as<int32_t>(), n, batch, fp64,
-                 !fp64 && coords_type == SAS_COORDS_F64, tile, qf.n_chunks, jcap, s, launches, 1, F,
-                 (int64_t)batch * Q * n);
-    if (st != SAS_OK) return st;
-    const int64_t npad = ctx->h_meta[2];
-    if (!fp64 && reseed == 0 && reseed_for(ctx->opt_reseed, n, std::min(Q, kQChunk), step_phase(ctx, qf)) > 0) {
-        // an ill-conditioned phase step: passes of 32 q (exact slots of the 52-q form), rescheduled
-        reseed = 32;
-        if (!make_chunks(ctx->q.data(), Q, qf, reseed))
-            return fail(SAS_ERR_UNSUPPORTED, "the q grid needs more than %d passes at a re-seed interval of %d",
-                        kMaxChunks, reseed);
-        st = schedule_for(ctx, 1, batch, kTile, qf.n_chunks, atomic_jmax(qf), s);
-        if (st != SAS_OK) return st;
-    }
-    const int nv = atomic_slots(qf);
-    if (fp64) {
-        ALLOC_TRY(ctx->F64t, (size_t)batch * npad * Q * sizeof(double));
-        CUDA_TRY(cudaMemsetAsync(ctx->F64t.p, 0, (size_t)batch * npad * Q * sizeof(double), s));
-        CUDA_TRY(launch_atomic_table64(F, ctx->slot_of.as<int>(), n, npad, batch, Q, ctx->F64t.as<double>(), s));
-    } else {
-        const size_t fj = (size_t)batch * qf.n_chunks * (npad / 2) * nv * sizeof(float4);
-        const size_t fi = (size_t)batch * qf.n_chunks * nv * npad * sizeof(float2);
-        ALLOC_TRY(ctx->FJ, fj);
-        ALLOC_TRY(ctx->FI, fi);
-        CUDA_TRY(cudaMemsetAsync(ctx->FJ.p, 0, fj, s));
-        CUDA_TRY(cudaMemsetAsync(ctx->FI.p, 0, fi, s));
-        CUDA_TRY(launch_atomic_tables(F, ctx->slot_of.as<int>(), n, npad, batch, qf, nv, ctx->FJ.as<float4>(),
-                                      ctx->FI.as<float2>(), s));
-    }
-    ALLOC_TRY(ctx->D2, (size_t)batch * Q * sizeof(double2));
-    CUDA_TRY(launch_atomic_diag(F, n, batch, Q, ctx->D2.as<double2>(), s));
-    ALLOC_TRY(ctx->partial, (size_t)std::max(ctx->n_items, 1) * kQChunk * sizeof(double));
-    const int grid_per_sm = ctx->opt_grid > 0 ? ctx->opt_grid : 2;
-    CUDA_TRY(cudaEventRecord(ctx->ev0, s));
-    if (fp64) {
-        const int grid = std::max(1, std::min(ctx->n_items, grid_per_sm * ctx->sms));
-        CUDA_TRY(launch_debye_fp64_atomic(ctx->X.as<double4>(), npad, ctx->items.as<Item>(), ctx->n_items, qf,
-                                          ctx->F64t.as<double>(), ctx->partial.as<double>(), kQChunk, grid, s));
-    } else {
-        ALLOC_TRY(ctx->ticket, sizeof(int));
-        CUDA_TRY(cudaMemsetAsync(ctx->ticket.p, 0, sizeof(int), s));
-        CUDA_TRY(launch_debye_atomic_pairs2(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, qf,
-                                            ctx->FJ.as<float4>(), ctx->FI.as<float2>(), ctx->partial.as<double>(),
-                                            kQChunk, ctx->opt_grid > 0 ? ctx->opt_grid * ctx->sms : 0,
-                                            ctx->jmax_used, ctx->ticket.as<int>(), s));
-    }
-    CUDA_TRY(cudaEventRecord(ctx->ev1, s));
-    ctx->ev_pending = true;
-    ALLOC_TRY(ctx->S, (size_t)batch * Q * sizeof(double));
-    st = reduce_items(ctx, qf, s);
-    if (st != SAS_OK) return st;
-    const bool host_out = !on_device(I_out);
-    double *Id = I_out;
-    if (host_out) {
-        ALLOC_TRY(ctx->out_buf, (size_t)batch * Q * sizeof(double));
-        Id = ctx->out_buf.as<double>();
-    }
-    CUDA_TRY(launch_assemble_atomic(ctx->S.as<double>(), ctx->D2.as<double2>(), qf, batch, Id, s));
-    launches += 5;
-    if (host_out) {
-        HostCopies hc;
-        st = out_copy(hc, I_out, Id, (size_t)batch * Q * sizeof(double), s);
-        if (st == SAS_OK) st = finish_copies(ctx, hc, s);
-        if (st != SAS_OK) return st;
-    }
-    ctx->stats[5] = launches;
-    return SAS_OK;
-}
 
 sas_status sas_partials(sas_ctx *ctx, double *S_out, int64_t capacity, void *stream)
 {
