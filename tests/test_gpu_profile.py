@@ -444,3 +444,24 @@ def test_single_type_long_group_segmented_reduction():
     ks = [0, 77, 190]
     ref = oracle.profile(mol.coords, mol.types, coef, q[ks])
     assert _rel(I[ks], ref) <= TOL_MIXED
+
+
+def test_small_molecule_64_atom_tiles_with_ragged_and_empty_groups():
+    """2,000 atoms of 16 types (one absent, one with a single atom, fourteen of ~143) at 101 q: the
+    automatic two-pair form takes 64-atom tiles (groups padded to 128 would take 3,584 slots, to
+    64 about 2,700); mixed against the oracle, single conformer and a batch."""
+    rng = np.random.default_rng(790)
+    mol = wl.random_walk_globule(2000, 16, 791).as_f32()
+    t = rng.integers(0, 14, size=mol.n).astype(np.int32)
+    t[7] = 14                                   # a one-atom group; type 15 stays empty
+    mol.types = t
+    coef = wl.form_factor_coefficients(16, 792)
+    q = wl.q_grid(0.0, 0.5, 101)
+    ref = oracle.profile(mol.coords, mol.types, coef, q)
+    assert _rel(_gpu(mol, coef, q, "mixed"), ref) <= TOL_MIXED
+    X = np.stack([wl.perturbed(mol, 0.5, 793 + b).coords for b in range(3)]).astype(np.float32)
+    p = Profile(coef, q, "mixed")
+    I = p(torch.as_tensor(X).cuda(), torch.as_tensor(mol.types).cuda()).cpu().numpy()
+    p.close()
+    for b in range(3):
+        assert _rel(I[b], oracle.profile(X[b], mol.types, coef, q)) <= TOL_MIXED
