@@ -212,7 +212,8 @@ sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value);
  * Statistics of the last call: [0] work items, [1] pair slots (incl. padding),
  * [2] unordered real pairs, [3] q values, [4] pair-kernel time in nanoseconds
  * (CUDA events on the call's stream; this call waits for them), [5] kernels launched,
- * [6] q values computed by quadrature (SAS_OPT_METHOD), [7] quadrature directions.  n <= 8.
+ * [6] q values computed by quadrature (SAS_OPT_METHOD), [7] quadrature directions, [8] atoms per
+ * I-tile of the last packing (128, or 64 for small molecules on the two-pair kernel).  n <= 9.
  */
 sas_status sas_last_stats(sas_ctx *ctx, int64_t *stats_out, int n);
 

@@ -187,8 +187,8 @@ def sas_set_option(ctx, option: int, value: int):
 
 
 def sas_last_stats(ctx):
-    out = np.zeros(8, dtype=np.int64)
-    check(load().sas_last_stats(ctx, out.ctypes.data, 8))
+    out = np.zeros(9, dtype=np.int64)
+    check(load().sas_last_stats(ctx, out.ctypes.data, 9))
     return out
 
 

@@ -101,7 +101,7 @@ struct sas_ctx {
     int64_t pair_slots = 0;
     int64_t last_batch = 0;
     bool have_partials = false;
-    int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t stats[9] = {0, 0, 0, 0, 0, 0, 0, 0, 128};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the last pair-kernel launch
     bool ev_pending = false;
     double4 *h_cen = nullptr;   // pinned: centroid and radius per conformer (quadrature method)

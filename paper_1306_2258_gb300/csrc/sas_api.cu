@@ -478,6 +478,7 @@ sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32
         }
     }
     ctx->tile_used = tile;
+    ctx->stats[8] = tile;
     const int64_t npad = ctx->h_meta[2 * T];
     st = schedule_for(ctx, T, batch, tile, n_chunks, jmax_cap, s);
     if (st != SAS_OK) return st;
@@ -894,7 +895,7 @@ sas_status sas_last_stats(sas_ctx *ctx, int64_t *stats_out, int n)
         ctx->stats[4] = (int64_t)((double)ms * 1.0e6);
         ctx->ev_pending = false;
     }
-    for (int i = 0; i < n && i < 8; ++i) stats_out[i] = ctx->stats[i];
+    for (int i = 0; i < n && i < 9; ++i) stats_out[i] = ctx->stats[i];
     return SAS_OK;
 }
 

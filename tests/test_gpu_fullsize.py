@@ -69,6 +69,7 @@ def test_c5_full_ensemble_profiles_and_histograms_on_sampled_conformers():
     types = c5["base"].types
     p = Profile(c5["coef"], c5["q"])
     I = p(X, torch.as_tensor(types).cuda()).cpu().numpy()
+    assert p.stats()[8] == 64   # five groups of ~400 atoms: 64-atom tiles
     h, d = p.pair_histogram(X, types)
     h = h.cpu().numpy()
     d = d.cpu().numpy()

@@ -458,10 +458,13 @@ def test_small_molecule_64_atom_tiles_with_ragged_and_empty_groups():
     coef = wl.form_factor_coefficients(16, 792)
     q = wl.q_grid(0.0, 0.5, 101)
     ref = oracle.profile(mol.coords, mol.types, coef, q)
-    assert _rel(_gpu(mol, coef, q, "mixed"), ref) <= TOL_MIXED
-    X = np.stack([wl.perturbed(mol, 0.5, 793 + b).coords for b in range(3)]).astype(np.float32)
     p = Profile(coef, q, "mixed")
+    I1 = p(torch.as_tensor(mol.coords).cuda(), torch.as_tensor(mol.types).cuda()).cpu().numpy()
+    assert p.stats()[8] == 64
+    assert _rel(I1, ref) <= TOL_MIXED
+    X = np.stack([wl.perturbed(mol, 0.5, 793 + b).coords for b in range(3)]).astype(np.float32)
     I = p(torch.as_tensor(X).cuda(), torch.as_tensor(mol.types).cuda()).cpu().numpy()
+    assert p.stats()[8] == 64
     p.close()
     for b in range(3):
         assert _rel(I[b], oracle.profile(X[b], mol.types, coef, q)) <= TOL_MIXED
