@@ -180,7 +180,10 @@ enum {
     SAS_OPT_JMAX = 1,        /* longest J-range of one work item, atoms (multiple of 128 up to 8192; 0 = automatic) */
     SAS_OPT_RESEED = 2,      /* re-seed interval of the q recurrence in q steps: -1 automatic (default:
                                 none from 8,192 atoms, or from 2,000 atoms when a q chunk holds at most
-                                104 values; otherwise 32), 0, 32 or 64 */
+                                104 values, except every 64 when a chunk holds more than 128 values and
+                                the phase step M dq D reaches 0.9 pi, M the q steps per recurrence step
+                                (SAS_OPT_STEP) and D twice the largest distance from the first atom of a
+                                conformer; otherwise 32), 0, 32 or 64 */
     SAS_OPT_VALIDATE = 3,    /* must stay 1: the device-side validation verdict is always read back */
     SAS_OPT_GRID = 4,        /* persistent CTAs per SM for the pair kernels (0 = automatic) */
     SAS_OPT_TIMEOUT_MS = 5,  /* limit of every host-side wait for device work (default 600000) */
