@@ -61,6 +61,19 @@ enum {
     SAS_FP64 = 1   /* every step in FP64 (the plain form) */
 };
 
+/*
+ * SAS_DETERMINISTIC (sas_create flag, ORed with the precision): every output of the context is the
+ * same bit for bit on every call with the same inputs, options and device.  The profiles, partials,
+ * histograms and quadrature sums are so on every context (each work item writes its own partial
+ * sums, which are added in a fixed order); the flag changes the adjoint (sas_profile_grad,
+ * sas_profile_vjp), whose per-atom gradient sums otherwise use FP64 atomics in whatever order the
+ * items finish.  With it, every work item writes its gradient totals to a buffer of its own
+ * (12 * (128 + J) bytes per item, J the longest J-range of the call, at most 512 atoms) and a
+ * further kernel adds them per atom in a fixed order.  Results differ from a context without the
+ * flag by the FP32 and FP64 rounding of the regrouped sums.
+ */
+#define SAS_DETERMINISTIC 16
+
 /* coordinate element type (per call) */
 enum { SAS_COORDS_F32 = 0, SAS_COORDS_F64 = 1 };
 
@@ -75,7 +88,7 @@ enum { SAS_COORDS_F32 = 0, SAS_COORDS_F64 = 1 };
  *            of uniform spacing (every point within 1e-9 max|q| of its run's line; a uniform grid
  *            is one run, an irregular one runs of two points), each run computed from its own
  *            start and step; at most 64 runs after cutting each into pieces of <= 208 values.
- *   flags    SAS_MIXED or SAS_FP64.
+ *   flags    SAS_MIXED or SAS_FP64, optionally | SAS_DETERMINISTIC.
  * Errors: INVALID_ARG (n_types outside 1..SAS_MAX_TYPES, n_q outside 1..SAS_MAX_Q,
  * null pointer, negative or non-finite q or coefficient), UNSUPPORTED (q not strictly ascending,
  * more than 64 runs), ALLOC, CUDA.  *out is set only on success.

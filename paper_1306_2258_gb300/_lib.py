@@ -18,6 +18,7 @@ from . import build as _build
 SAS_OK, SAS_ERR_INVALID_ARG, SAS_ERR_CUDA, SAS_ERR_ALLOC, SAS_ERR_UNSUPPORTED, SAS_ERR_TIMEOUT = range(6)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "ALLOC", 4: "UNSUPPORTED", 5: "TIMEOUT"}
 SAS_MIXED, SAS_FP64 = 0, 1
+SAS_DETERMINISTIC = 16
 SAS_COORDS_F32, SAS_COORDS_F64 = 0, 1
 SAS_OPT_JMAX, SAS_OPT_RESEED, SAS_OPT_VALIDATE, SAS_OPT_GRID, SAS_OPT_TIMEOUT_MS, SAS_OPT_STEP, SAS_OPT_VARIANT = 1, 2, 3, 4, 5, 6, 7
 SAS_OPT_SHARD, SAS_OPT_METHOD = 8, 9

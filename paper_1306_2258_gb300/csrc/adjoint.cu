@@ -19,7 +19,8 @@
 // W_ij is applied at once: the thread's own G_i accumulates in registers, and -W_ij (x_i - x_j)
 // for atoms j and j+1 (six values) is reduce-scattered over the warp with shuffles and added to
 // shared memory by six lanes.  Item totals go to a [batch][slot][3] FP64 array with FP64
-// atomics.
+// atomics, or, on a deterministic context, to per-item buffers (each warp with its own copy of the
+// J-range sums) that k_adjoint_gather adds up per atom in a fixed order.
 #include "mixed_common.cuh"
 #include "sas_internal.h"
 #include "sincos_f32.cuh"
@@ -185,7 +186,7 @@ __device__ __forceinline__ float reduce_scatter8(const float (&v)[8], int lane)
     return c;
 }
 
-template <int NV, bool ZERO_START>
+template <int NV, bool ZERO_START, bool DET>
 __device__ __forceinline__ void run_adj2(const float4 *sxy, const float4 *szw, const float4 *sh, float *gj,
                                          int jpairs, const float4 xi, const Item &item, int tid, int lane, int jmask,
                                          float2 qs_hi, float2 qs_lo, float2 dq_hi, float2 dq_lo, float2 &gx,
@@ -224,21 +225,30 @@ __device__ __forceinline__ void run_adj2(const float4 *sxy, const float4 *szw, c
         const float2 fx = f2mul(nW, dx), fy = f2mul(nW, dy), fz = f2mul(nW, dz);
         const float v[8] = {-fx.x, -fy.x, -fz.x, -fx.y, -fy.y, -fz.y, 0.f, 0.f};
         const float tot = reduce_scatter8(v, lane);
-        if ((lane & 3) == 0 && kslot < 6) atomicAdd(&gj[3 * j + kslot], tot);
+        if ((lane & 3) == 0 && kslot < 6) {
+            if (DET)
+                gj[3 * j + kslot] += tot;   // this warp's own copy: one writer per value
+            else
+                atomicAdd(&gj[3 * j + kslot], tot);
+        }
     }
 }
 
-template <int NV>
+constexpr int kAdjWarps = kTile / 32;
+
+// DET: item `it` writes its I-tile totals to PI[it][tid][3] and its J-range totals (the warps'
+// copies added in warp order) to PJ[it][j][3], j < jlen; G is not touched.
+template <int NV, bool DET>
 __global__ void __launch_bounds__(kTile, 4)
     k_debye_adjoint(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items, int n_items,
                     QChunks qc, const float2 *__restrict__ H, int n_pairs, int hstride, double *__restrict__ G,
-                    int jcap, int *__restrict__ ticket)
+                    int jcap, int *__restrict__ ticket, float *__restrict__ PI, float *__restrict__ PJ)
 {
     extern __shared__ float4 smem[];
     float4 *sxy = smem;                                   // [jcap / 2]: (x_j, x_j+1, y_j, y_j+1)
     float4 *szw = smem + jcap / 2;                        // [jcap / 2]: (z_j, z_j+1, w_j, w_j+1)
     float4 *sh = smem + jcap;                             // [NV]: signed (h, h/q) for q 2v and 2v+1
-    float *gj = reinterpret_cast<float *>(sh + NV);       // [jcap][3]
+    float *gj = reinterpret_cast<float *>(sh + NV);       // [DET ? kAdjWarps : 1][jcap][3]
     __shared__ int next_item;
     const int tid = threadIdx.x, lane = tid & 31;
     int it = blockIdx.x;
@@ -255,7 +265,11 @@ __global__ void __launch_bounds__(kTile, 4)
             sxy[k] = make_float4(a.x, b.x, a.y, b.y);
             szw[k] = make_float4(a.z, b.z, a.w, b.w);
         }
-        for (int k = tid; k < 6 * jpairs; k += kTile) gj[k] = 0.f;
+        if (DET) {
+            for (int k = tid; k < kAdjWarps * 3 * jcap; k += kTile) gj[k] = 0.f;
+        } else {
+            for (int k = tid; k < 6 * jpairs; k += kTile) gj[k] = 0.f;
+        }
         const float2 *Hc = H + ((int64_t)item.batch * n_pairs + item.pair) * hstride + qc.q_begin[ch];
         const int qlen = qc.q_len[ch];
         for (int v = tid; v < NV; v += kTile) {   // zero beyond the chunk's q values
@@ -270,19 +284,68 @@ __global__ void __launch_bounds__(kTile, 4)
         const bool zero_start = (qs_hi.x == 0.f) && (qs_lo.x == 0.f);
         const int jmask = item.diag ? tid : -1;   // pairs with j <= i are not pairs of i<j
         float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
+        float *gw = DET ? gj + (tid >> 5) * 3 * jcap : gj;
         if (zero_start)
-            run_adj2<NV, true>(sxy, szw, sh, gj, jpairs, xi, item, tid, lane, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
-                               bc(qc.dq_lo[ch]), gx, gy, gz);
+            run_adj2<NV, true, DET>(sxy, szw, sh, gw, jpairs, xi, item, tid, lane, jmask, qs_hi, qs_lo,
+                                    bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), gx, gy, gz);
         else
-            run_adj2<NV, false>(sxy, szw, sh, gj, jpairs, xi, item, tid, lane, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
-                                bc(qc.dq_lo[ch]), gx, gy, gz);
-        double *Gb = G + (int64_t)item.batch * npad * 3;
-        atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid)], (double)(gx.x + gx.y));
-        atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid) + 1], (double)(gy.x + gy.y));
-        atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid) + 2], (double)(gz.x + gz.y));
-        __syncthreads();
-        for (int k = tid; k < 3 * item.jlen; k += kTile) atomicAdd(&Gb[3 * (int64_t)item.j0 + k], (double)gj[k]);
+            run_adj2<NV, false, DET>(sxy, szw, sh, gw, jpairs, xi, item, tid, lane, jmask, qs_hi, qs_lo,
+                                     bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), gx, gy, gz);
+        if (DET) {
+            float *pi = PI + ((int64_t)it * kTile + tid) * 3;
+            pi[0] = gx.x + gx.y;
+            pi[1] = gy.x + gy.y;
+            pi[2] = gz.x + gz.y;
+            __syncthreads();
+            float *pj = PJ + (int64_t)it * 3 * jcap;
+            for (int k = tid; k < 3 * item.jlen; k += kTile) {
+                float t = gj[k];
+                for (int w = 1; w < kAdjWarps; ++w) t += gj[w * 3 * jcap + k];
+                pj[k] = t;
+            }
+        } else {
+            double *Gb = G + (int64_t)item.batch * npad * 3;
+            atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid)], (double)(gx.x + gx.y));
+            atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid) + 1], (double)(gy.x + gy.y));
+            atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid) + 2], (double)(gz.x + gz.y));
+            __syncthreads();
+            for (int k = tid; k < 3 * item.jlen; k += kTile)
+                atomicAdd(&Gb[3 * (int64_t)item.j0 + k], (double)gj[k]);
+        }
         it = next_item;
+    }
+}
+
+// G[b][slot][c] (every slot of every I-tile) = the item totals of the items listed for the slot's
+// tile, added in list order in FP64: entry 2e is item e's I-tile, entry 2e+1 its J-range.
+__global__ void k_adjoint_gather(const float *__restrict__ PI, const float *__restrict__ PJ, int jcap,
+                                 const Item *__restrict__ items, const int *__restrict__ tile_off,
+                                 const int *__restrict__ tile_ent, int ntiles, int64_t npad, int64_t batch,
+                                 double *__restrict__ G)
+{
+    const int tau = blockIdx.x, tid = threadIdx.x;
+    const int slot = tau * kTile + tid;
+    for (int64_t b = blockIdx.y; b < batch; b += gridDim.y) {
+        const int64_t l = b * ntiles + tau;
+        double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+        for (int idx = tile_off[l]; idx < tile_off[l + 1]; ++idx) {
+            const int ent = tile_ent[idx], e = ent >> 1;
+            const float *p;
+            if (ent & 1) {
+                const int k = slot - items[e].j0;
+                if (k < 0 || k >= items[e].jlen) continue;
+                p = PJ + ((int64_t)e * jcap + k) * 3;
+            } else {
+                p = PI + ((int64_t)e * kTile + tid) * 3;
+            }
+            g0 += (double)p[0];
+            g1 += (double)p[1];
+            g2 += (double)p[2];
+        }
+        double *g = G + (b * npad + slot) * 3;
+        g[0] = g0;
+        g[1] = g1;
+        g[2] = g2;
     }
 }
 
@@ -335,38 +398,52 @@ __global__ void k_unpermute(const double *G, const int *slot_of, int64_t n, int6
     for (int c = 0; c < 3; ++c) grad_out[3 * idx + c] = (float)G[(b * npad + s) * 3 + c];
 }
 
-template <int NV>
+template <int NV, bool DET>
 cudaError_t launch_nv(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
-                      const float2 *H, int n_pairs, int hstride, double *G, int jcap, int *ticket, cudaStream_t s)
+                      const float2 *H, int n_pairs, int hstride, double *G, int jcap, int *ticket, float *PI,
+                      float *PJ, cudaStream_t s)
 {
-    const size_t smem = (size_t)jcap * sizeof(float4) + NV * sizeof(float4) + (size_t)jcap * 3 * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_debye_adjoint<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)jcap * sizeof(float4) + NV * sizeof(float4) +
+                        (size_t)(DET ? kAdjWarps : 1) * jcap * 3 * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_debye_adjoint<NV, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0, dev = 0, sms = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_adjoint<NV>, kTile, smem)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_adjoint<NV, DET>, kTile, smem)) !=
+        cudaSuccess)
         return e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     int grid = (occ > 0 ? occ : 1) * sms;
     if (grid > n_items) grid = n_items;
-    k_debye_adjoint<NV><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket);
+    k_debye_adjoint<NV, DET><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap,
+                                                       ticket, PI, PJ);
     return cudaGetLastError();
 }
 
-// NV: the slots of the longest chunk when within 3 of the capacity 2*NB, else the capacity.
+// NV: the slots of the longest chunk when within 3 of the capacity 2*NB, else the capacity (always
+// the capacity for the deterministic form).
 template <int NB>
 cudaError_t launch_nb(int nv, const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
-                      const float2 *H, int n_pairs, int hstride, double *G, int jcap, int *ticket, cudaStream_t s)
+                      const float2 *H, int n_pairs, int hstride, double *G, int jcap, int *ticket, float *PI,
+                      float *PJ, cudaStream_t s)
 {
+    if (PI)
+        return launch_nv<2 * NB, true>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, PI, PJ,
+                                       s);
     switch (2 * NB - nv) {
     case 1:
-        return launch_nv<2 * NB - 1>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, s);
+        return launch_nv<2 * NB - 1, false>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket,
+                                            nullptr, nullptr, s);
     case 2:
-        return launch_nv<2 * NB - 2>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, s);
+        return launch_nv<2 * NB - 2, false>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket,
+                                            nullptr, nullptr, s);
     case 3:
-        return launch_nv<2 * NB - 3>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, s);
+        return launch_nv<2 * NB - 3, false>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket,
+                                            nullptr, nullptr, s);
     default:
-        return launch_nv<2 * NB>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, s);
+        return launch_nv<2 * NB, false>(X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, nullptr,
+                                        nullptr, s);
     }
 }
 
@@ -391,21 +468,31 @@ cudaError_t launch_adjoint_coef(const double *g, const double *F, int n_types, i
 
 cudaError_t launch_debye_adjoint(const float4 *X, int64_t npad, const Item *items, int n_items,
                                  const QChunks &qc, const float2 *H, int n_pairs, int hstride, double *G,
-                                 int jlen_max, int *ticket, cudaStream_t s)
+                                 int jlen_max, int *ticket, float *PI, float *PJ, cudaStream_t s)
 {
     if (n_items == 0) return cudaSuccess;
-    const int jcap = (jlen_max + 1) / 2 * 2;
+    const int jcap = adjoint_jcap(jlen_max);
     int qmax = 0;
     for (int c = 0; c < qc.n_chunks; ++c) qmax = qc.q_len[c] > qmax ? qc.q_len[c] : qmax;
     const int nv = (qmax + 1) / 2;
     switch (mixed_blocks_for(qmax)) {
     case 13:
-        return launch_nb<13>(nv, X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, s);
+        return launch_nb<13>(nv, X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, PI, PJ, s);
     case 26:
-        return launch_nb<26>(nv, X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, s);
+        return launch_nb<26>(nv, X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, PI, PJ, s);
     default:
-        return launch_nb<52>(nv, X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, s);
+        return launch_nb<52>(nv, X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, PI, PJ, s);
     }
+}
+
+cudaError_t launch_adjoint_gather(const float *PI, const float *PJ, int jcap, const Item *items,
+                                  const int *tile_off, const int *tile_ent, int ntiles, int64_t npad, int64_t batch,
+                                  double *G, cudaStream_t s)
+{
+    if (ntiles == 0 || batch == 0) return cudaSuccess;
+    dim3 grid((unsigned)ntiles, (unsigned)(batch < 65535 ? batch : 65535));
+    k_adjoint_gather<<<grid, kTile, 0, s>>>(PI, PJ, jcap, items, tile_off, tile_ent, ntiles, npad, batch, G);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_unpermute(const double *G, const int *slot_of, int64_t n, int64_t npad, int64_t batch,

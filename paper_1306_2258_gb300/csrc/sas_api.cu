@@ -224,11 +224,16 @@ struct Schedule {
     int jmax = 0;
     int jlen_max = 0;   // longest J-range of the items
     int64_t pair_slots = 0;
+    // For the deterministic adjoint: per conformer and I-tile of the packed array, the items whose
+    // I-tile (entry 2e) or J-range (entry 2e + 1) touches it, in execution order.
+    int ntiles = -1;   // -1: not built
+    std::vector<int> tile_off, tile_ent;
 };
 
 // Items of one conformer-independent layout; `counts` are the real atoms per type.
 void build_schedule(const int *counts, int T, int64_t batch, int tile, int pad, int n_chunks, int grid,
-                    int64_t jmax_opt, int64_t jmax_cap, int shard_rank, int shard_world, Schedule &out)
+                    int64_t jmax_opt, int64_t jmax_cap, int shard_rank, int shard_world, bool tile_lists,
+                    Schedule &out)
 {
     // Type group t occupies slots [O[t], O[t] + P[t]) of the packed array (its count padded to a
     // multiple of `pad`), its atoms the first counts[t]; an I-tile spans `tile` slots, a J-range
@@ -335,6 +340,27 @@ void build_schedule(const int *counts, int T, int64_t batch, int tile, int pad, 
     out.group_items.resize(n);
     std::vector<int> fill(out.group_off.begin(), out.group_off.end() - 1);
     for (int i = 0; i < n; ++i) out.group_items[fill[canon_group[i]]++] = pos[i];
+    if (tile_lists && off % tile == 0) {
+        const int64_t ntiles = off / tile;
+        std::vector<int64_t> cnt(batch * ntiles + 1, 0);
+        auto visit = [&](auto &&f) {
+            for (int e = 0; e < n; ++e) {
+                const Item &it = out.items[e];
+                const int64_t base = (int64_t)it.batch * ntiles;
+                f(base + it.i0 / tile, 2 * e);
+                for (int64_t t = it.j0 / tile; t <= (it.j0 + (int64_t)it.jlen - 1) / tile; ++t) f(base + t, 2 * e + 1);
+            }
+        };
+        visit([&](int64_t l, int) { cnt[l + 1]++; });
+        for (size_t l = 1; l < cnt.size(); ++l) cnt[l] += cnt[l - 1];
+        if (cnt.back() < (int64_t)INT32_MAX) {
+            out.ntiles = (int)ntiles;
+            out.tile_off.assign(cnt.begin(), cnt.end());
+            out.tile_ent.resize((size_t)cnt.back());
+            std::vector<int64_t> at(cnt.begin(), cnt.end() - 1);
+            visit([&](int64_t l, int ent) { out.tile_ent[(size_t)at[l]++] = ent; });
+        }
+    }
 }
 
 bool finite_all(const double *v, size_t n)
@@ -363,8 +389,9 @@ sas_status schedule_for(sas_ctx *ctx, int T, int64_t batch, int tile, int n_chun
     if (key != ctx->sched_key) {
         Schedule sc;
         const int64_t jm = ctx->opt_jmax > 0 ? std::min(ctx->opt_jmax, jmax_cap) : 0;
+        const bool lists = (ctx->flags & SAS_DETERMINISTIC) && tile == kTile;
         build_schedule(ctx->h_meta, T, batch, tile, ctx->pad, n_chunks, grid_cap, jm, jmax_cap, ctx->opt_shard_rank,
-                       ctx->opt_shard_world, sc);
+                       ctx->opt_shard_world, lists, sc);
         const int ni = (int)sc.items.size();
         const int ng = (int)sc.group_off.size() - 1;
         ctx->sched_key.clear();   // invalid until the upload succeeded
@@ -379,6 +406,17 @@ sas_status schedule_for(sas_ctx *ctx, int T, int64_t batch, int tile, int n_chun
         }
         CUDA_TRY(cudaMemcpyAsync(ctx->group_off.p, sc.group_off.data(), (ng + 1) * sizeof(int),
                                  cudaMemcpyHostToDevice, s));
+        ctx->det_ntiles = -1;
+        if (sc.ntiles >= 0) {
+            ALLOC_TRY(ctx->tile_off, sc.tile_off.size() * sizeof(int));
+            ALLOC_TRY(ctx->tile_ent, std::max<size_t>(sc.tile_ent.size(), 1) * sizeof(int));
+            CUDA_TRY(cudaMemcpyAsync(ctx->tile_off.p, sc.tile_off.data(), sc.tile_off.size() * sizeof(int),
+                                     cudaMemcpyHostToDevice, s));
+            if (!sc.tile_ent.empty())
+                CUDA_TRY(cudaMemcpyAsync(ctx->tile_ent.p, sc.tile_ent.data(), sc.tile_ent.size() * sizeof(int),
+                                         cudaMemcpyHostToDevice, s));
+            ctx->det_ntiles = sc.ntiles;
+        }
         ctx->n_items = ni;
         ctx->n_groups = ng;
         ctx->max_group = 0;
@@ -699,6 +737,10 @@ sas_status run_profile(sas_ctx *ctx, const void *coords, int coords_type, const 
 }
 
 // Shared back half of sas_profile_grad / sas_profile_vjp: g [batch][Q] (device) -> gradient.
+// Longest J-range of the adjoint's work items: shorter on a deterministic context, whose kernel keeps
+// one copy of the J-range sums per warp in shared memory.
+int64_t adjoint_jmax_cap(const sas_ctx *ctx) { return (ctx->flags & SAS_DETERMINISTIC) ? 512 : 2048; }
+
 sas_status adjoint(sas_ctx *ctx, int64_t n, int64_t batch, const double *g_dev, float *grad_out,
                    cudaStream_t s, int &launches, HostCopies &hc)
 {
@@ -707,12 +749,30 @@ sas_status adjoint(sas_ctx *ctx, int64_t n, int64_t batch, const double *g_dev, 
     ALLOC_TRY(ctx->H, (size_t)batch * Pn * Q * sizeof(float2));
     CUDA_TRY(launch_adjoint_coef(g_dev, ctx->F.as<double>(), T, batch, ctx->qc, ctx->H.as<float2>(), Q, s));
     ALLOC_TRY(ctx->G, (size_t)batch * npad * 3 * sizeof(double));
-    CUDA_TRY(cudaMemsetAsync(ctx->G.p, 0, (size_t)batch * npad * 3 * sizeof(double), s));
+    const bool det = (ctx->flags & SAS_DETERMINISTIC) != 0;
+    float *PI = nullptr, *PJ = nullptr;
+    const int jcap = adjoint_jcap(ctx->jlen_max);
+    if (det) {   // per-item totals, then a fixed-order sum per atom
+        if (ctx->det_ntiles < 0 || (int64_t)ctx->det_ntiles * kTile != npad)
+            return fail(SAS_ERR_UNSUPPORTED, "deterministic adjoint: work list too long for its tile lists");
+        ALLOC_TRY(ctx->adj_pi, (size_t)std::max(ctx->n_items, 1) * kTile * 3 * sizeof(float));
+        ALLOC_TRY(ctx->adj_pj, (size_t)std::max(ctx->n_items, 1) * jcap * 3 * sizeof(float));
+        PI = ctx->adj_pi.as<float>();
+        PJ = ctx->adj_pj.as<float>();
+    } else {
+        CUDA_TRY(cudaMemsetAsync(ctx->G.p, 0, (size_t)batch * npad * 3 * sizeof(double), s));
+    }
     ALLOC_TRY(ctx->ticket, sizeof(int));
     CUDA_TRY(cudaMemsetAsync(ctx->ticket.p, 0, sizeof(int), s));
     CUDA_TRY(launch_debye_adjoint(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, ctx->qc,
                                   ctx->H.as<float2>(), Pn, Q, ctx->G.as<double>(), ctx->jlen_max,
-                                  ctx->ticket.as<int>(), s));
+                                  ctx->ticket.as<int>(), PI, PJ, s));
+    if (det) {
+        CUDA_TRY(launch_adjoint_gather(PI, PJ, jcap, ctx->items.as<Item>(), ctx->tile_off.as<int>(),
+                                       ctx->tile_ent.as<int>(), ctx->det_ntiles, npad, batch, ctx->G.as<double>(),
+                                       s));
+        launches += 1;
+    }
     float *gd = grad_out;
     const bool h = !on_device(grad_out);
     if (h) {
@@ -742,7 +802,7 @@ sas_status sas_create(int n_types, const double *ff_coef, const double *q, int n
         return fail(SAS_ERR_INVALID_ARG, "n_types must be in [1, %d]", SAS_MAX_TYPES);
     if (n_q < 1 || n_q > SAS_MAX_Q) return fail(SAS_ERR_INVALID_ARG, "n_q must be in [1, %d]", SAS_MAX_Q);
     if (!ff_coef || !q) return fail(SAS_ERR_INVALID_ARG, "null coefficients or q grid");
-    if (flags & ~1u) return fail(SAS_ERR_INVALID_ARG, "unknown flags");
+    if (flags & ~(unsigned)(SAS_FP64 | SAS_DETERMINISTIC)) return fail(SAS_ERR_INVALID_ARG, "unknown flags");
     if (!finite_all(ff_coef, (size_t)9 * n_types)) return fail(SAS_ERR_INVALID_ARG, "non-finite coefficient");
     if (!finite_all(q, (size_t)n_q)) return fail(SAS_ERR_INVALID_ARG, "non-finite q");
     if (q[0] < 0) return fail(SAS_ERR_INVALID_ARG, "negative q");
@@ -925,7 +985,8 @@ sas_status sas_profile_grad(sas_ctx *ctx, const float *coords, const int32_t *ty
     if (n == 0) {
         CUDA_TRY(cudaMemsetAsync(ctx->Ibuf.p, 0, (size_t)batch * Q * sizeof(double), s));
     } else {
-        st = forward(ctx, coords, SAS_COORDS_F32, types, n, batch, ctx->Ibuf.as<double>(), 2048, s, launches);
+        st = forward(ctx, coords, SAS_COORDS_F32, types, n, batch, ctx->Ibuf.as<double>(), adjoint_jmax_cap(ctx), s,
+                     launches);
         if (st != SAS_OK) return st;
     }
     ALLOC_TRY(ctx->gbuf, (size_t)batch * Q * sizeof(double));
@@ -961,8 +1022,8 @@ sas_status sas_profile_vjp(sas_ctx *ctx, const float *coords, const int32_t *typ
     st = stage_in(ctx->gbuf, grad_I, (size_t)batch * Q * sizeof(double), s, gI);
     if (st != SAS_OK) return st;
     // the adjoint needs the packed coordinates and items: pack without the pair kernel
-    st = prepare(ctx, coords, SAS_COORDS_F32, types, n, batch, false, false, kTile, ctx->qc.n_chunks, 2048,
-                 s, launches, ctx->n_types);
+    st = prepare(ctx, coords, SAS_COORDS_F32, types, n, batch, false, false, kTile, ctx->qc.n_chunks,
+                 adjoint_jmax_cap(ctx), s, launches, ctx->n_types);
     if (st != SAS_OK) return st;
     (void)T;
     st = adjoint(ctx, n, batch, (const double *)gI, grad_out, s, launches, hc);

@@ -124,9 +124,18 @@ cudaError_t launch_adjoint_coef(const double *g, const double *F, int n_types, i
                                 const QChunks &qc, float2 *H, int hstride, cudaStream_t s);
 // G[b][slot][3] += d(sum_q g_q I(q)) / dx (G must be zeroed); jlen_max: the longest J-range of
 // the items (sets the shared memory); ticket: one device int, zero when the kernel starts.
+// PI == nullptr: item totals added to G (zeroed by the caller) with FP64 atomics.  Otherwise the
+// deterministic form: item e's totals go to PI [n_items][kTile][3] and PJ [n_items][adjoint_jcap][3]
+// (G untouched), and launch_adjoint_gather adds them up per atom over the tile lists
+// (tile_off [batch * ntiles + 1], tile_ent: 2e for item e's I-tile, 2e + 1 for its J-range, in a
+// fixed order), writing every slot of G.
+inline int adjoint_jcap(int jlen_max) { return (jlen_max + 1) / 2 * 2; }
 cudaError_t launch_debye_adjoint(const float4 *X, int64_t npad, const Item *items, int n_items,
                                  const QChunks &qc, const float2 *H, int n_pairs, int hstride, double *G,
-                                 int jlen_max, int *ticket, cudaStream_t s);
+                                 int jlen_max, int *ticket, float *PI, float *PJ, cudaStream_t s);
+cudaError_t launch_adjoint_gather(const float *PI, const float *PJ, int jcap, const Item *items,
+                                  const int *tile_off, const int *tile_ent, int ntiles, int64_t npad, int64_t batch,
+                                  double *G, cudaStream_t s);
 cudaError_t launch_unpermute(const double *G, const int *slot_of, int64_t n, int64_t npad, int64_t batch,
                              float *grad_out, cudaStream_t s);
 

@@ -20,17 +20,21 @@ def _as_tensor_like(x, dtype):
 class Profile:
     """I(q) by the Debye sum (Section I-A, Eq. 2) for one set of atom types and q grid.
 
-    ``Profile(coef [T,9], q [Q], precision="mixed"|"fp64")``.  Calling it with
-    coordinates [n,3] or [B,n,3] (float32 or float64; CUDA or CPU) and types [n]
-    returns float64 I(q) [Q] or [B,Q] on the coordinates' device.
+    ``Profile(coef [T,9], q [Q], precision="mixed"|"fp64", deterministic=False)``.
+    Calling it with coordinates [n,3] or [B,n,3] (float32 or float64; CUDA or CPU)
+    and types [n] returns float64 I(q) [Q] or [B,Q] on the coordinates' device.
+    ``deterministic=True`` makes the gradients bitwise reproducible as well
+    (SAS_DETERMINISTIC); every other output is on any context.
     """
 
-    def __init__(self, coef, q, precision: str = "mixed"):
+    def __init__(self, coef, q, precision: str = "mixed", deterministic: bool = False):
         coef = np.ascontiguousarray(coef, dtype=np.float64)
         self.q = np.ascontiguousarray(q, dtype=np.float64)
         self.n_types = int(coef.shape[0])
         self.coef = coef
         flags = {"mixed": _lib.SAS_MIXED, "fp64": _lib.SAS_FP64}[precision]
+        if deterministic:
+            flags |= _lib.SAS_DETERMINISTIC
         self.precision = precision
         self._ctx = _lib.sas_create(self.n_types, coef, self.q, flags)
         self._last_batch = 0

@@ -75,3 +75,15 @@ def test_null_context_is_rejected():
     with pytest.raises(_lib.SasError):
         _lib.sas_set_option(None, _lib.SAS_OPT_JMAX, 0)
     _lib.sas_destroy(None)
+
+
+def test_create_flags_constant_and_unknown_bits():
+    text = open(HEADER).read()
+    assert int(re.search(r"#define SAS_DETERMINISTIC (\d+)", text).group(1)) == _lib.SAS_DETERMINISTIC
+    import ctypes
+    coef = np.ones((2, 9))
+    q = np.linspace(0, 1, 11)
+    for bad in (2, 1 << 5, _lib.SAS_DETERMINISTIC | 8):
+        h = ctypes.c_void_p()
+        st = _lib.load().sas_create(2, coef.ctypes.data, q.ctypes.data, 11, bad, ctypes.byref(h))
+        assert st == _lib.SAS_ERR_INVALID_ARG and not h.value, bad

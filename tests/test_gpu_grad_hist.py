@@ -117,6 +117,33 @@ def test_vjp_batch_host_buffers():
 
 # ---------------------------------------------------------------- histogram
 
+@pytest.mark.parametrize("n,batch,seed", [(1500, 3, 421), (6000, 1, 423)])
+def test_deterministic_context_repeats_gradients_bit_for_bit(n, batch, seed):
+    """SAS_DETERMINISTIC: chi^2, gradient, profile and VJP identical bit for bit over repeated calls
+    (the 6,000-atom case has J-ranges of several I-tiles, so an atom's totals come from many items),
+    the gradient within the oracle tolerance, and the VJP within 1e-5 of the default context's."""
+    types, coef, q, T, w, X = _refine_case(n=n, batch=batch, seed=seed)
+    x = torch.as_tensor(X).cuda()
+    gI = torch.as_tensor(np.random.default_rng(seed).standard_normal((batch, q.size))).cuda()
+    p = Profile(coef, q, deterministic=True)
+    runs = [p.chi2_grad(x, types, T, w) for _ in range(3)]
+    vj = [p.vjp(x, types, gI) for _ in range(3)]
+    p.close()
+    for c, g, I in runs[1:]:
+        assert torch.equal(c, runs[0][0]) and torch.equal(g, runs[0][1]) and torch.equal(I, runs[0][2])
+    for v in vj[1:]:
+        assert torch.equal(v, vj[0])
+    c_ref, g_ref, I_ref = oracle.chi2_grad(X[0], types, coef, q, T, w)
+    assert np.max(np.abs(runs[0][2][0].cpu().numpy() - I_ref) / I_ref) <= 1e-5
+    assert abs(runs[0][0][0].item() - c_ref) <= 1e-3 * c_ref
+    _grad_ok(runs[0][1][0].cpu().numpy(), g_ref)
+    p0 = Profile(coef, q)
+    v0 = p0.vjp(x, types, gI)
+    p0.close()
+    for b in range(batch):
+        _grad_ok(vj[0][b].cpu().numpy(), v0[b].cpu().numpy(), 1e-5)
+
+
 @pytest.mark.parametrize("n,seed,T", [(2000, 501, 5), (129, 502, 3), (1, 503, 2), (3000, 504, 1), (2500, 505, 16)])
 def test_histogram_exact(n, seed, T):
     mol = wl.random_walk_globule(n, T, seed).as_f32()

@@ -468,3 +468,30 @@ def test_small_molecule_64_atom_tiles_with_ragged_and_empty_groups():
     p.close()
     for b in range(3):
         assert _rel(I[b], oracle.profile(X[b], mol.types, coef, q)) <= TOL_MIXED
+
+
+def test_profiles_repeat_bit_for_bit_on_any_context():
+    """Every work item writes its own partial sums and they are added in a fixed order, so repeated
+    calls give identical bits whatever order the items finish in: the mixed and FP64 direct sums,
+    the quadrature method and per-atom form factors, with and without SAS_DETERMINISTIC (which
+    changes only the adjoint), on a molecule of many more items than CTAs."""
+    mol = wl.random_walk_globule(12000, 5, 431)
+    coef = wl.form_factor_coefficients(5, 432)
+    q = wl.q_grid(0.0, 1.0, 201)
+    x = torch.as_tensor(mol.coords).cuda()
+    t = torch.as_tensor(mol.types).cuda()
+    ff = torch.as_tensor(wl.atomic_form_factor_table(mol.n, q, 433)).cuda()
+    out = {}
+    for precision, det, method in (("mixed", False, 0), ("fp64", False, 0), ("mixed", False, 2),
+                                   ("mixed", True, 0)):
+        p = Profile(coef, q, precision, deterministic=det)
+        p.set_option(_lib.SAS_OPT_METHOD, method)
+        a, b = p(x, t), p(x, t)
+        assert torch.equal(a, b), (precision, det, method)
+        out[(precision, det, method)] = a.cpu().numpy()
+        if method == 0 and precision == "mixed" and not det:
+            fa, fb = p.atomic(x, ff), p.atomic(x, ff)
+            assert torch.equal(fa, fb)
+        p.close()
+    # the flag leaves the forward kernels as they are
+    assert np.array_equal(out[("mixed", True, 0)], out[("mixed", False, 0)])
