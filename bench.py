@@ -317,6 +317,10 @@ def run_rows(dev, stream):
                                 "ms": ms, "value": pq / (ms / 1e3), "unit": "pair·q/s (forward and adjoint each)",
                                 "gradients_per_s": B4 / (ms / 1e3)}
     p.close()
+    # the same on a SAS_DETERMINISTIC context (fixed-order per-atom gradient sums)
+    p = Profile(c4["coef"], c4["q"], "mixed", deterministic=True)
+    rows["chi2_gradient_c4"]["ms_deterministic"] = _timed(lambda: p.chi2_grad(X4, tt, target, wq, stream), stream)
+    p.close()
 
     # ensemble (configuration 5): exact profiles, pair histograms, surrogate epoch and screen
     c5 = wl.c5_ensemble()
