@@ -171,7 +171,7 @@ sas_status forward_hybrid(sas_ctx *ctx, const void *coords, int coords_type, con
         CUDA_TRY(cudaMemsetAsync(ctx->ticket.p, 0, sizeof(int), s));
         CUDA_TRY(launch_debye_mixed(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, qd, ctx->opt_step,
                                     reseed_for(ctx->opt_reseed, n, std::min(Qd, kQChunk), step_phase(ctx, qd)),
-                                    mixed_variant(ctx->opt_variant, std::min(Qd, kQChunk)), ctx->partial.as<double>(),
+                                    mixed_variant(ctx->opt_variant), ctx->partial.as<double>(),
                                     kQChunk, ctx->opt_grid > 0 ? ctx->opt_grid * ctx->sms : 0, ctx->jmax_used,
                                     ctx->ticket.as<int>(), s));
         ALLOC_TRY(ctx->S, (size_t)batch * Pn * Qd * sizeof(double));

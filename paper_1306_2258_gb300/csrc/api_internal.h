@@ -124,7 +124,7 @@ struct HostCopies {
 
 bool on_device(const void *p);
 int reseed_for(int opt, int64_t n_atoms, int n_q_chunk, double step_phase_max);
-int mixed_variant(int opt, int n_q_max);
+int mixed_variant(int opt);
 double step_phase(const sas_ctx *ctx, const QChunks &qc);
 sas_status wait_stream(sas_ctx *ctx, cudaStream_t s);
 sas_status schedule_for(sas_ctx *ctx, int T, int64_t batch, int tile, int n_chunks, int64_t jmax_cap, cudaStream_t s);

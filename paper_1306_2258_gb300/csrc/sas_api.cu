@@ -154,12 +154,11 @@ int reseed_for(int opt, int64_t n_atoms, int n_q_chunk, double step_phase_max)
 // SAS_OPT_VARIANT (0 auto, 1 general, 2 pipelined, 3 sequential, 4 two pairs per step) -> kernel
 // variant code.  Auto: two pairs per step, the fastest form for every q capacity (measured on the
 // 50,000- and 10,000-atom globules, 201 q, and the 30,000-atom rod, 101 q).
-int mixed_variant(int opt, int n_q_max)
+int mixed_variant(int opt)
 {
     if (opt == 1) return 1;
     if (opt == 2) return 3;
     if (opt == 3) return 4;
-    (void)n_q_max;
     return 5;
 }
 
@@ -617,7 +616,7 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
         CUDA_TRY(launch_debye_mixed(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items,
                                     ctx->qc, ctx->opt_step,
                                     reseed_for(ctx->opt_reseed, n, std::min(ctx->n_q, kQChunk), step_phase(ctx, ctx->qc)),
-                                    mixed_variant(ctx->opt_variant, std::min(ctx->n_q, kQChunk)), ctx->partial.as<double>(),
+                                    mixed_variant(ctx->opt_variant), ctx->partial.as<double>(),
                                     kQChunk, ctx->opt_grid > 0 ? ctx->opt_grid * ctx->sms : 0, ctx->jmax_used,
                                     ctx->ticket.as<int>(), s));
     }
@@ -1015,7 +1014,7 @@ sas_status sas_profile_vjp(sas_ctx *ctx, const float *coords, const int32_t *typ
     if (batch > 0 && n > 0 && (!grad_I || !grad_out)) return fail(SAS_ERR_INVALID_ARG, "null argument");
     if (batch == 0 || n == 0) return SAS_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    const int T = ctx->n_types, Q = ctx->n_q;
+    const int Q = ctx->n_q;
     int launches = 0;
     HostCopies hc;
     const void *gI = nullptr;
@@ -1025,7 +1024,6 @@ sas_status sas_profile_vjp(sas_ctx *ctx, const float *coords, const int32_t *typ
     st = prepare(ctx, coords, SAS_COORDS_F32, types, n, batch, false, false, kTile, ctx->qc.n_chunks,
                  adjoint_jmax_cap(ctx), s, launches, ctx->n_types);
     if (st != SAS_OK) return st;
-    (void)T;
     st = adjoint(ctx, n, batch, (const double *)gI, grad_out, s, launches, hc);
     if (st != SAS_OK) return st;
     ctx->stats[5] = launches;
