@@ -63,14 +63,17 @@ enum {
 
 /*
  * SAS_DETERMINISTIC (sas_create flag, ORed with the precision): every output of the context is the
- * same bit for bit on every call with the same inputs, options and device.  The profiles, partials,
- * histograms and quadrature sums are so on every context (each work item writes its own partial
- * sums, which are added in a fixed order); the flag changes the adjoint (sas_profile_grad,
- * sas_profile_vjp), whose per-atom gradient sums otherwise use FP64 atomics in whatever order the
- * items finish.  With it, every work item writes its gradient totals to a buffer of its own
- * (12 * (128 + J) bytes per item, J the longest J-range of the call, at most 512 atoms) and a
- * further kernel adds them per atom in a fixed order.  Results differ from a context without the
- * flag by the FP32 and FP64 rounding of the regrouped sums.
+ * same bit for bit on every call with the same inputs, options and device, and a profile split
+ * into shards (SAS_OPT_SHARD) can be put back together bit for bit (sas_exact_sums,
+ * sas_assemble_exact).  The profiles, partials, histograms and quadrature sums repeat on every
+ * context (each work item writes its own partial sums, which are added in a fixed order).  The flag
+ * (1) makes the direct profile add the items' partial sums exactly (sas_exact_sums) and keeps its
+ * I-tiles at 128 atoms, and (2) changes the adjoint (sas_profile_grad, sas_profile_vjp), whose
+ * per-atom gradient sums otherwise use FP64 atomics in whatever order the items finish: every work
+ * item writes its gradient totals to a buffer of its own (12 * (128 + J) bytes per item, J the
+ * longest J-range of the call, at most 512 atoms) and a further kernel adds them per atom in a
+ * fixed order.  Results differ from a context without the flag by the rounding of the regrouped
+ * sums.
  */
 #define SAS_DETERMINISTIC 16
 
@@ -145,6 +148,26 @@ sas_status sas_profile_vjp(sas_ctx *ctx, const float *coords, const int32_t *typ
  * Then I(q) = sum_t n_t f_t(q)^2 + sum_p 2 f_a(q) f_b(q) S_p(q).
  */
 sas_status sas_partials(sas_ctx *ctx, double *S_out, int64_t capacity, void *stream);
+
+/*
+ * Exact sums for splitting one molecule over shards (SAS_OPT_SHARD) on SAS_DETERMINISTIC contexts,
+ * whose direct profile calls add the work items' partial sums U_p(q) = sum sin(q r)/r exactly: each
+ * partial v enters as the integer nearest v * 2^60 (v itself for |v| >= 2^-7), held in 128-bit two's
+ * complement, so the sum does not depend on the order or grouping of its terms.
+ *
+ * sas_exact_sums: the last sas_profile / sas_profile_batch call's (direct sum, SAS_OPT_METHOD 0) exact
+ *   sums, U_out[b][p][k][0..1] = (low 64 bits as unsigned, high 64 bits as signed) of U_p(q_k) * 2^60
+ *   (0 at q = 0), batch * T(T+1)/2 * n_q * 2 int64, pair index p as in sas_partials.  On a shard
+ *   these are the shard's own; the 128-bit sums over all shards equal the unsplit call's.
+ * sas_assemble_exact: I(q) of the whole molecule from such sums U (e.g. added over all shards; same
+ *   layout, device or host), with the type counts of the context's last profile call (same molecule,
+ *   batch as then): the arithmetic of an unsplit call after its sums, so the result equals that
+ *   call's bit for bit.
+ * Errors: INVALID_ARG (null pointer, capacity too small, no direct profile since the last other
+ * call, batch differing from the last call's), UNSUPPORTED (context without SAS_DETERMINISTIC), CUDA.
+ */
+sas_status sas_exact_sums(sas_ctx *ctx, int64_t *U_out, int64_t capacity, void *stream);
+sas_status sas_assemble_exact(sas_ctx *ctx, const int64_t *U, int64_t batch, double *I_out, void *stream);
 
 /*
  * I(q) with a form factor per atom and q, no types (Section I-A, Eq. 2 as written: with a hydration

@@ -31,7 +31,7 @@ EXPORTS = (
     "sas_last_error", "sas_version", "sas_profile_static", "sas_mlp_create", "sas_mlp_destroy",
     "sas_mlp_param_count", "sas_mlp_set_state", "sas_mlp_get_state", "sas_mlp_forward", "sas_mlp_train_step",
     "sas_mlp_grads", "sas_gemm_bf16", "sas_screen_select", "sas_gather_rows", "sas_profile_atomic",
-    "sas_measure_peaks",
+    "sas_measure_peaks", "sas_exact_sums", "sas_assemble_exact",
 )
 
 
@@ -81,6 +81,8 @@ def load():
                 "sas_gather_rows": [_vp, _i64, _vp, _i64, _vp, _vp],
                 "sas_profile_atomic": [_vp, _vp, _int, _i64, _i64, _vp, _vp, _vp],
                 "sas_measure_peaks": [_vp, _int, _vp],
+                "sas_exact_sums": [_vp, _vp, _i64, _vp],
+                "sas_assemble_exact": [_vp, _vp, _i64, _vp, _vp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -175,6 +177,14 @@ def sas_profile_atomic(ctx, coords, coords_type, n_atoms, batch, ff, I_out, stre
 
 def sas_partials(ctx, S_out, capacity, stream=None):
     check(load().sas_partials(ctx, ptr(S_out), int(capacity), stream_handle(stream)))
+
+
+def sas_exact_sums(ctx, U_out, capacity, stream=None):
+    check(load().sas_exact_sums(ctx, ptr(U_out), int(capacity), stream_handle(stream)))
+
+
+def sas_assemble_exact(ctx, U, batch, I_out, stream=None):
+    check(load().sas_assemble_exact(ctx, ptr(U), int(batch), ptr(I_out), stream_handle(stream)))
 
 
 def sas_pair_histogram(ctx, coords, types, n_atoms, batch, n_bins, r_max, hist_out, dropped_out=None,

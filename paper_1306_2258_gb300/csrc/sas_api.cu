@@ -487,7 +487,8 @@ sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32
     if (tile == 0) {
         // Tiles of 64 atoms where the automatic kernel form is the two-pair kernel (no re-seeding,
         // passes of at most 104 q; an explicit SAS_OPT_VARIANT keeps the 128-slot layout, whose
-        // variants agree bit for bit) and type groups padded to 128 slots would waste more than 5 %
+        // variants agree bit for bit; so do sharded and deterministic contexts, whose work items
+        // must be those of every shard count) and type groups padded to 128 slots would waste more than 5 %
         // of them (small molecules:
         // 2,000 atoms of 5 types pad to 2,560 slots, against 2,240 in groups of 64).  The scan ran
         // with 128; the group offsets are redone here and written back before the packing.
@@ -501,7 +502,7 @@ sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32
         }
         if (ctx->opt_variant == 0 && ctx->opt_step == 2 && mixed_blocks_for(qmax) <= 26 &&
             reseed_for(ctx->opt_reseed, n, qmax, step_phase(ctx, ctx->qc)) == 0 && ctx->opt_shard_world == 1 &&
-            (double)p128 > 1.05 * (double)p64) {
+            !(ctx->flags & SAS_DETERMINISTIC) && (double)p128 > 1.05 * (double)p64) {
             tile = 64;
             ctx->pad = 64;
             int off = 0;
@@ -568,6 +569,16 @@ sas_status zero_out(void *out, size_t bytes, cudaStream_t s)
 // The items' partials -> S (fixed order; segmented for long groups).
 sas_status reduce_items(sas_ctx *ctx, const QChunks &qc, cudaStream_t s)
 {
+    if (ctx->flags & SAS_DETERMINISTIC) {   // exact sums, kept in Ufix for sas_exact_sums
+        const int max_seg = ctx->max_group > kSegItems ? (ctx->max_group + kSegItems - 1) / kSegItems : 1;
+        ALLOC_TRY(ctx->segfix, (size_t)ctx->n_groups * max_seg * qc.n_q * sizeof(Fix128));
+        ALLOC_TRY(ctx->Ufix, (size_t)ctx->n_groups * qc.n_q * sizeof(Fix128));
+        CUDA_TRY(launch_reduce_items_fix(ctx->partial.as<double>(), kQChunk, ctx->items.as<Item>(),
+                                         ctx->group_items.as<int>(), ctx->group_off.as<int>(), ctx->n_groups,
+                                         ctx->max_group, qc, ctx->segfix.as<Fix128>(), ctx->Ufix.as<Fix128>(),
+                                         ctx->S.as<double>(), s));
+        return SAS_OK;
+    }
     if (ctx->max_group > kSegItems)
         ALLOC_TRY(ctx->segbuf,
                   (size_t)ctx->n_groups * ((ctx->max_group + kSegItems - 1) / kSegItems) * qc.n_q * sizeof(double));
@@ -890,6 +901,51 @@ sas_status sas_partials(sas_ctx *ctx, double *S_out, int64_t capacity, void *str
     cudaStream_t s = (cudaStream_t)stream;
     HostCopies hc;
     sas_status st = out_copy(hc, S_out, ctx->S.p, (size_t)need * sizeof(double), s);
+    if (st != SAS_OK) return st;
+    return finish_copies(ctx, hc, s);
+}
+
+sas_status sas_exact_sums(sas_ctx *ctx, int64_t *U_out, int64_t capacity, void *stream)
+{
+    if (!ctx || !U_out) return fail(SAS_ERR_INVALID_ARG, "null argument");
+    if (!(ctx->flags & SAS_DETERMINISTIC)) return fail(SAS_ERR_UNSUPPORTED, "exact sums need a SAS_DETERMINISTIC context");
+    if (!ctx->have_partials) return fail(SAS_ERR_INVALID_ARG, "no profile computed since the last change");
+    const int Pn = ctx->n_types * (ctx->n_types + 1) / 2;
+    const int64_t need = ctx->last_batch * Pn * ctx->n_q * 2;
+    if (capacity < need) return fail(SAS_ERR_INVALID_ARG, "capacity %lld < %lld", (long long)capacity, (long long)need);
+    cudaStream_t s = (cudaStream_t)stream;
+    HostCopies hc;
+    sas_status st = out_copy(hc, U_out, ctx->Ufix.p, (size_t)need * sizeof(int64_t), s);
+    if (st != SAS_OK) return st;
+    return finish_copies(ctx, hc, s);
+}
+
+sas_status sas_assemble_exact(sas_ctx *ctx, const int64_t *U, int64_t batch, double *I_out, void *stream)
+{
+    if (!ctx || !U || !I_out) return fail(SAS_ERR_INVALID_ARG, "null argument");
+    if (!(ctx->flags & SAS_DETERMINISTIC)) return fail(SAS_ERR_UNSUPPORTED, "exact sums need a SAS_DETERMINISTIC context");
+    if (!ctx->have_partials) return fail(SAS_ERR_INVALID_ARG, "no profile computed since the last change");
+    if (batch != ctx->last_batch)
+        return fail(SAS_ERR_INVALID_ARG, "batch %lld differs from the last call's %lld", (long long)batch,
+                    (long long)ctx->last_batch);
+    const int T = ctx->n_types, Pn = T * (T + 1) / 2, Q = ctx->n_q;
+    const int64_t groups = batch * Pn;
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *Ud = nullptr;
+    sas_status st = stage_in(ctx->Ustage, U, (size_t)groups * Q * sizeof(Fix128), s, Ud);
+    if (st != SAS_OK) return st;
+    ALLOC_TRY(ctx->Sx, (size_t)groups * Q * sizeof(double));
+    CUDA_TRY(launch_fix_to_S(static_cast<const Fix128 *>(Ud), groups, ctx->qc, ctx->Sx.as<double>(), s));
+    const bool host_out = !on_device(I_out);
+    double *Id = I_out;
+    if (host_out) {
+        ALLOC_TRY(ctx->Ix, (size_t)batch * Q * sizeof(double));
+        Id = ctx->Ix.as<double>();
+    }
+    CUDA_TRY(launch_assemble(ctx->Sx.as<double>(), ctx->F.as<double>(), ctx->meta.as<int>(), T, batch, ctx->qc, 1,
+                             Id, s));
+    HostCopies hc;
+    st = out_copy(hc, I_out, Id, (size_t)batch * Q * sizeof(double), s);
     if (st != SAS_OK) return st;
     return finish_copies(ctx, hc, s);
 }

@@ -92,6 +92,22 @@ constexpr int kSegItems = 256;
 cudaError_t launch_reduce_items_seg(const double *partial, int part_stride, const Item *items,
                                     const int *group_items, const int *group_off, int n_groups, int max_group,
                                     const QChunks &qc, double *seg_out, double *S, cudaStream_t s);
+// Exact cross-item sums (deterministic contexts): a partial sum v enters as the integer nearest
+// v * 2^kFixBits (ties to even; v itself when |v| >= 2^-7, whose 53 significant bits then lie above
+// 2^-60), held in 128-bit two's complement, so that a sum of partials does not depend on the order
+// or grouping of its terms.  |v| and every sum stay below 2^67.
+constexpr int kFixBits = 60;
+struct Fix128 {
+    unsigned long long lo;
+    long long hi;
+};
+// U[g][k] = the exact sum of group g's item partials at q_k (segment sums in seg_out
+// [n_groups][max(1, ceil(max_group / kSegItems))][n_q]), then S as launch_fix_to_S.
+cudaError_t launch_reduce_items_fix(const double *partial, int part_stride, const Item *items,
+                                    const int *group_items, const int *group_off, int n_groups, int max_group,
+                                    const QChunks &qc, Fix128 *seg_out, Fix128 *U, double *S, cudaStream_t s);
+// S[g][k] = (q_k > 0 ? double(U[g][k]) 2^-kFixBits / q_k : 0) for n_groups groups.
+cudaError_t launch_fix_to_S(const Fix128 *U, int64_t n_groups, const QChunks &qc, double *S, cudaStream_t s);
 // I[b][k] = sum_t n_t F_t^2 + sum_p 2 F_a F_b (q_k > 0 ? S/q_k : count_p)
 cudaError_t launch_assemble(double *S, const double *F, const int *meta, int n_types, int64_t batch,
                             const QChunks &qc, int whole, double *I, cudaStream_t s);

@@ -112,6 +112,22 @@ class Profile:
         _lib.sas_partials(self._ctx, S, S.size)
         return S
 
+    def exact_sums(self):
+        """The last profile call's exact type-pair sums (SAS_DETERMINISTIC contexts): int64 [B, P, Q, 2],
+        (low, high) 64-bit halves of U_p(q) * 2^60 in two's complement (host)."""
+        U = np.empty((self._last_batch, self.n_pairs_types, self.n_q, 2), dtype=np.int64)
+        _lib.sas_exact_sums(self._ctx, U, U.size)
+        return U
+
+    def assemble_exact(self, U, device=None):
+        """I(q) [B, Q] (float64) of the whole molecule from exact sums U [B, P, Q, 2] (e.g. summed over
+        shards with shard.add_exact), with the type counts of this context's last profile call."""
+        U = np.ascontiguousarray(U, dtype=np.int64)
+        B = int(U.shape[0])
+        out = torch.empty((B, self.n_q), dtype=torch.float64, device=device or "cpu")
+        _lib.sas_assemble_exact(self._ctx, U, B, out)
+        return out
+
     # -- adjoint
     def chi2_grad(self, coords, types, target, weights, stream=None):
         """(chi2 [B], d chi2/dx [B,n,3] float32, I [B,Q]) for float32 coordinates [B,n,3]."""

@@ -103,3 +103,57 @@ def test_a_rank_that_leaves_makes_the_others_fail_not_hang():
     mp.start_processes(_share_worker, args=(2, _free_port(), out, 1), nprocs=2, start_method="spawn", join=True)
     assert out[1][0] == "left"
     assert out[0][0] == "error"
+
+
+def _enc128(v):
+    """A Python integer in [-2^127, 2^127) as int64 (low, high) halves of its two's complement."""
+    v &= (1 << 128) - 1
+    lo, hi = v & ((1 << 64) - 1), v >> 64
+    return [lo - (1 << 64) if lo >= 1 << 63 else lo, hi - (1 << 64) if hi >= 1 << 63 else hi]
+
+
+def _dec128(p):
+    return (int(p[1]) << 64) + (int(p[0]) & ((1 << 64) - 1))
+
+
+def _rank_values(rank, n=12):
+    import random
+    r = random.Random(900 + rank)
+    return [r.randint(-(1 << 110), 1 << 110) for _ in range(n)]
+
+
+def test_add_exact_is_integer_addition():
+    from paper_1306_2258_gb300.shard import add_exact
+    import random
+    r = random.Random(5)
+    for _ in range(50):
+        k = r.randint(1, 9)
+        vals = [[r.choice([r.randint(-(1 << 120), 1 << 120), r.randint(-3, 3), -(1 << 64), (1 << 64) - 1])
+                 for _ in range(6)] for _ in range(k)]
+        tot = add_exact([np.array([_enc128(v) for v in row], dtype=np.int64) for row in vals]).numpy()
+        assert [_dec128(tot[j]) for j in range(6)] == [sum(row[j] for row in vals) for j in range(6)]
+
+
+def _exact_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch
+    import torch.distributed as dist
+
+    from paper_1306_2258_gb300.shard import allreduce_exact
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    U = torch.as_tensor(np.array([_enc128(v) for v in _rank_values(rank)], dtype=np.int64))
+    out[rank] = allreduce_exact(U).numpy().tolist()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_exact_sums_allreduce_over_gloo_ranks(world):
+    """Every rank's 128-bit sums (as a shard's sas_exact_sums) all-reduced as 32-bit limbs: every
+    rank holds the exact integer total."""
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_exact_worker, args=(world, _free_port(), out), nprocs=world, start_method="spawn",
+                       join=True)
+    want = [sum(_rank_values(r)[j] for r in range(world)) for j in range(12)]
+    for r in range(world):
+        assert [_dec128(p) for p in out[r]] == want

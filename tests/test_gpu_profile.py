@@ -151,6 +151,52 @@ def test_shards_of_one_molecule_sum_to_the_whole(world):
     assert np.linalg.norm(g - g1) <= 1e-6 * np.linalg.norm(g1)
 
 
+@pytest.mark.parametrize("precision,world", [("mixed", 2), ("mixed", 3), ("mixed", 7), ("fp64", 3)])
+def test_deterministic_shards_reassemble_bit_for_bit(precision, world):
+    """SAS_DETERMINISTIC: the exact sums of `world` shards of the 10,000-atom globule, run in turn on
+    this GPU and added as 128-bit integers, equal the unsplit call's and assemble to its I(q) bit for
+    bit; the shares of I(q) still add up to it to FP64 rounding, and it agrees with a default
+    context's profile to 1e-13."""
+    from paper_1306_2258_gb300.shard import add_exact, set_shard
+    w = wl.c2_globule(10000)
+    x = torch.as_tensor(w.mol.coords).cuda()
+    t = torch.as_tensor(w.mol.types).cuda()
+    p1 = Profile(w.coef, w.q, precision, deterministic=True)
+    whole = p1(x, t).cpu().numpy()
+    U1 = p1.exact_sums()
+    Us, shares = [], []
+    for rank in range(world):
+        p = Profile(w.coef, w.q, precision, deterministic=True)
+        set_shard(p, rank, world)
+        shares.append(p(x, t).cpu().numpy())
+        Us.append(p.exact_sums())
+        p.close()
+    U = add_exact(Us).numpy()
+    assert np.array_equal(U, U1)
+    assert np.array_equal(p1.assemble_exact(U).numpy()[0], whole)
+    p1.close()
+    assert np.max(np.abs(sum(shares) - whole) / whole) <= 1e-13
+    pd = Profile(w.coef, w.q, precision)
+    ref = pd(x, t).cpu().numpy()
+    pd.close()
+    assert np.max(np.abs(whole - ref) / ref) <= 1e-13
+
+
+def test_exact_sums_need_a_deterministic_context_and_a_profile():
+    w = wl.c1_plain_fp64()
+    p = Profile(w.coef, w.q, "mixed")
+    p(torch.as_tensor(w.mol.coords).cuda(), torch.as_tensor(w.mol.types).cuda())
+    with pytest.raises(_lib.SasError) as e:
+        p.exact_sums()
+    assert e.value.status == _lib.SAS_ERR_UNSUPPORTED
+    p.close()
+    p = Profile(w.coef, w.q, "mixed", deterministic=True)
+    with pytest.raises(_lib.SasError) as e:
+        p.exact_sums()
+    assert e.value.status == _lib.SAS_ERR_INVALID_ARG
+    p.close()
+
+
 def test_shard_option_validation():
     from paper_1306_2258_gb300.shard import set_shard
     w = wl.c1_plain_fp64()
@@ -473,8 +519,8 @@ def test_small_molecule_64_atom_tiles_with_ragged_and_empty_groups():
 def test_profiles_repeat_bit_for_bit_on_any_context():
     """Every work item writes its own partial sums and they are added in a fixed order, so repeated
     calls give identical bits whatever order the items finish in: the mixed and FP64 direct sums,
-    the quadrature method and per-atom form factors, with and without SAS_DETERMINISTIC (which
-    changes only the adjoint), on a molecule of many more items than CTAs."""
+    the quadrature method and per-atom form factors, with and without SAS_DETERMINISTIC, on a
+    molecule of many more items than CTAs."""
     mol = wl.random_walk_globule(12000, 5, 431)
     coef = wl.form_factor_coefficients(5, 432)
     q = wl.q_grid(0.0, 1.0, 201)
@@ -493,5 +539,6 @@ def test_profiles_repeat_bit_for_bit_on_any_context():
             fa, fb = p.atomic(x, ff), p.atomic(x, ff)
             assert torch.equal(fa, fb)
         p.close()
-    # the flag leaves the forward kernels as they are
-    assert np.array_equal(out[("mixed", True, 0)], out[("mixed", False, 0)])
+    # the flag changes only how the items' partial sums are added (exactly)
+    ref = out[("mixed", False, 0)]
+    assert np.max(np.abs(out[("mixed", True, 0)] - ref) / ref) <= 1e-13
