@@ -170,9 +170,7 @@ def run_reference(args):
         return 0
     from paper_1306_2258_gb300 import workloads as wl
     w = wl.c2_globule(N_ATOMS)
-    for _ in range(args.warmup):
-        pass
-    per_step = max(2.0, 120.0 / max(args.steps + args.warmup, 1))
+    per_step = max(0.5, args.ref_seconds / max(args.steps + args.warmup, 1))
     vals, times = [], []
     base = None
     for s in range(args.warmup + args.steps):
@@ -597,6 +595,8 @@ def main():
                     help="leave out the timings of the other path steps (rod, sparse chain, gradient, ensemble)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the mixed path only (no e2e, FP64 or CPU legs; for profiler runs)")
+    ap.add_argument("--ref-seconds", type=float, default=120.0,
+                    help="CPU time of the whole --impl reference run (each step a subsample sized to its share)")
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
                     help="weak (default): one molecule per rank; strong: one molecule split over the ranks")
     args = ap.parse_args()
