@@ -87,3 +87,17 @@ def test_create_flags_constant_and_unknown_bits():
         h = ctypes.c_void_p()
         st = _lib.load().sas_create(2, coef.ctypes.data, q.ctypes.data, 11, bad, ctypes.byref(h))
         assert st == _lib.SAS_ERR_INVALID_ARG and not h.value, bad
+
+
+def test_header_constants_match_binding():
+    """Every SAS_* enumerator and #define of the header has the binding's value."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"#define (SAS_[A-Z0-9_]+) (\d+)\b", text)}
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S) + re.findall(r"typedef enum\s*\{(.*?)\}", text,
+                                                                                 flags=re.S):
+        for k, v in re.findall(r"(SAS_[A-Z0-9_]+)\s*=\s*(\d+)", body):
+            consts[k] = int(v)
+    expected = [k for k in consts if not k.startswith("SAS_STATIC_") and k != "SAS_H"]
+    assert len(expected) >= 20
+    for k in expected:
+        assert getattr(_lib, k) == consts[k], k
