@@ -45,11 +45,12 @@ def _configure(lib):
     lib.oracle_profile_atomic.argtypes = [_i64, _dp, _dp, _i32, _dp, _i32, _dp, _dp]
     lib.oracle_pair_sums.argtypes = [_i64, _dp, _ip, _i32, _i32, _dp, _i32, _dp]
     lib.oracle_vjp.argtypes = [_i64, _dp, _ip, _i32, _dp, _i32, _dp, _dp, _i32, _dp]
+    lib.oracle_vjp_atomic.argtypes = [_i64, _dp, _dp, _i32, _dp, _dp, _i32, _dp]
     lib.oracle_chi2_grad.argtypes = [_i64, _dp, _ip, _i32, _dp, _i32, _dp, _dp, _dp, _i32,
                                      _dp, _dp, _dp]
     lib.oracle_pair_histogram.argtypes = [_i64, _fp, _ip, _i32, _i32, ctypes.c_float, _ip, _lp]
     for f in ("oracle_form_factors", "oracle_profile", "oracle_profile_full", "oracle_profile_atomic",
-              "oracle_pair_sums", "oracle_vjp", "oracle_chi2_grad", "oracle_pair_histogram"):
+              "oracle_pair_sums", "oracle_vjp", "oracle_vjp_atomic", "oracle_chi2_grad", "oracle_pair_histogram"):
         getattr(lib, f).restype = _i32
     return lib
 
@@ -161,6 +162,19 @@ def vjp(coords, types, coef, q, grad_I, n_threads: int = 0) -> np.ndarray:
     out = np.empty_like(x)
     _check(lib.oracle_vjp(x.shape[0], xp, tp, c.shape[0], cp, qq.size, qp, gp, n_threads,
                           out.ctypes.data_as(_dp)), "vjp")
+    return out
+
+
+def vjp_atomic(coords, ff, q, grad_I, n_threads: int = 0) -> np.ndarray:
+    """sum_q grad_I[q] dI(q)/dx [n, 3] with per-atom form factors ff[k, i] = f_i(q_k)."""
+    lib = _load()
+    x, xp = _d(np.asarray(coords).reshape(-1, 3))
+    qq, qp = _d(q)
+    f, fp = _d(np.asarray(ff).reshape(qq.size, x.shape[0]))
+    g, gp = _d(grad_I)
+    out = np.empty_like(x)
+    _check(lib.oracle_vjp_atomic(x.shape[0], xp, fp, qq.size, qp, gp, n_threads, out.ctypes.data_as(_dp)),
+           "vjp_atomic")
     return out
 
 

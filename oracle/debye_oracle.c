@@ -16,6 +16,9 @@
  *   I(q)    = sum_k sum_j f_k(q) f_j(q) sin(q r_jk)/(q r_jk)   (Section I-A, Eq. 2)
  *           = sum_i f_i^2 + 2 sum_{i<j} f_i f_j sinc(q r_ij)   (only j <= k, Section II)
  *
+ * and its derivative with respect to the positions (vector-Jacobian products, with typed or
+ * per-atom form factors), the chi^2 of a profile against a target, and pair-distance counts.
+ *
  * with sinc(0) = 1 (the diagonal, and coincident atoms), r_ij in double,
  * libm sin/cos/exp/sqrt, and Neumaier-compensated sums.  Per-row partial
  * sums are stored and merged in row order, so results do not depend on the
@@ -350,14 +353,10 @@ int oracle_pair_sums(int64_t n, const double *xyz, const int32_t *types, int n_t
  * zero (the bracket vanishes, or x_i - x_j does).  Each row i sums over all j != i, so
  * the result needs no scatter.  Returns 0 / -1 / -2.
  */
-int oracle_vjp(int64_t n, const double *xyz, const int32_t *types, int n_types, const double *coef,
-               int n_q, const double *q, const double *gI, int n_threads, double *grad_out)
+/* f[i * n_q + k] = f_i(q_k), atom-major. */
+static void vjp_core(int64_t n, const double *xyz, const double *f, int n_q, const double *q,
+                     const double *gI, int n_threads, double *grad_out)
 {
-    if (check_types(n, types, n_types))
-        return -1;
-    double *f = atom_form_factors(n, types, coef, n_q, q);
-    if (!f)
-        return -2;
     set_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 8)
     for (int64_t i = 0; i < n; ++i) {
@@ -383,6 +382,35 @@ int oracle_vjp(int64_t n, const double *xyz, const int32_t *types, int n_types, 
         for (int c = 0; c < 3; ++c)
             grad_out[3 * i + c] = nval(&g[c]);
     }
+}
+
+int oracle_vjp(int64_t n, const double *xyz, const int32_t *types, int n_types, const double *coef,
+               int n_q, const double *q, const double *gI, int n_threads, double *grad_out)
+{
+    if (check_types(n, types, n_types))
+        return -1;
+    double *f = atom_form_factors(n, types, coef, n_q, q);
+    if (!f)
+        return -2;
+    vjp_core(n, xyz, f, n_q, q, gI, n_threads, grad_out);
+    free(f);
+    return 0;
+}
+
+/*
+ * The same product with per-atom form factors ff[k * n + i] = f_i(q_k) (no types): the form
+ * factors do not depend on the positions, so the bracket above holds with f_i(q), f_j(q) per atom.
+ */
+int oracle_vjp_atomic(int64_t n, const double *xyz, const double *ff, int n_q, const double *q,
+                      const double *gI, int n_threads, double *grad_out)
+{
+    double *f = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)n_q);
+    if (!f)
+        return -2;
+    for (int k = 0; k < n_q; ++k)
+        for (int64_t i = 0; i < n; ++i)
+            f[i * n_q + k] = ff[i + (int64_t)k * n];
+    vjp_core(n, xyz, f, n_q, q, gI, n_threads, grad_out);
     free(f);
     return 0;
 }

@@ -74,6 +74,35 @@ def test_gradient_zero_q_and_coincident_atoms_are_finite():
 
 # ---------------------------------------------------------------- histogram
 
+def test_atomic_vjp_matches_central_differences_of_atomic_profile():
+    """Per-atom form factors of either sign (a shell-like table): sum_q gI_q dI(q)/dx against
+    central differences of the oracle's per-atom profile, a separate code path."""
+    mol, _, q, _, _ = _refine_case(50, 65)
+    ff = wl.atomic_form_factor_table(mol.n, q, 66)
+    gI = np.random.default_rng(67).standard_normal(q.size)
+    g = oracle.vjp_atomic(mol.coords, ff, q, gI)
+    h = 1e-4
+    scale = np.max(np.abs(g))
+    for i, c in [(0, 0), (3, 2), (11, 1), (24, 0), (49, 2)]:
+        xp = mol.coords.copy(); xp[i, c] += h
+        xm = mol.coords.copy(); xm[i, c] -= h
+        fd = gI @ (oracle.profile_atomic(xp, ff, q) - oracle.profile_atomic(xm, ff, q)) / (2 * h)
+        assert abs(fd - g[i, c]) <= 1e-6 * scale, (i, c, fd, g[i, c])
+
+
+def test_atomic_vjp_rigid_motion_and_typed_limit():
+    """sum_i g_i = 0 and sum_i x_i x g_i = 0 for any per-atom table; with the table of the typed form
+    factors it is the typed product."""
+    mol, coef, q, _, _ = _refine_case(70, 68)
+    gI = np.random.default_rng(69).standard_normal(q.size)
+    g = oracle.vjp_atomic(mol.coords, wl.atomic_form_factor_table(mol.n, q, 70), q, gI)
+    assert np.all(np.abs(g.sum(0)) <= 1e-12 * np.abs(g).sum())
+    assert np.all(np.abs(np.cross(mol.coords, g).sum(0)) <= 1e-11 * np.abs(np.cross(mol.coords, g)).sum())
+    ff_typed = oracle.form_factors(mol.types, coef, q).T          # [n, n_q] -> [n_q, n]
+    np.testing.assert_allclose(oracle.vjp_atomic(mol.coords, ff_typed, q, gI),
+                               oracle.vjp(mol.coords, mol.types, coef, q, gI), rtol=0, atol=1e-13)
+
+
 def _exact_bin(r2: Fraction, n_bins: int, w: Fraction):
     """max{k : (k w)^2 <= r2} in exact rationals (None if >= n_bins)."""
     k = 0

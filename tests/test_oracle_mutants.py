@@ -29,6 +29,7 @@ MUTANTS = {
                      "double br = (cos(x) + sin(x) / x) / (r * r);"),
     "bin_rule": ("if (e2[mid] <= r2)", "if (e2[mid] < r2)"),
     "atomic_layout": ("f[i * n_q + k] = ff[(int64_t)k * n + i];", "f[i * n_q + k] = ff[i * n_q + k];"),
+    "atomic_vjp_layout": ("f[i * n_q + k] = ff[i + (int64_t)k * n];", "f[i * n_q + k] = ff[i * n_q + k];"),
     "pair_index": ("return a * T - a * (a - 1) / 2 + (b - a);",
                    "return (a * T - a * (a - 1) / 2 + (b - a) + 1) % (T * (T + 1) / 2);"),
 }
