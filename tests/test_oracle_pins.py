@@ -291,3 +291,27 @@ def test_golden_globule1000_regression():
     np.testing.assert_array_equal(w.q, ref[:, 0])
     np.testing.assert_allclose(oracle.profile(w.mol.coords, w.mol.types, w.coef, w.q), ref[:, 1],
                                rtol=1e-14)
+
+
+def _golden(name):
+    import os
+    return os.path.join(os.path.dirname(__file__), "golden", name)
+
+
+def test_golden_per_atom_profile_vjp_and_histogram_regression():
+    """The stored per-atom profile, typed and per-atom VJPs and pair histogram of a 300-atom globule
+    (tests/golden/make_golden.py, from the oracle only) still match."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_golden", _golden("make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    mol, coef, q, ff, gI = mg.small_case()
+    ref = np.loadtxt(_golden("globule300_q21_atomic_profile.txt"))
+    np.testing.assert_array_equal(q, ref[:, 0])
+    np.testing.assert_allclose(oracle.profile_atomic(mol.coords, ff, q), ref[:, 1], rtol=1e-14)
+    ref = np.loadtxt(_golden("globule300_q21_vjp.txt"))
+    for got, want in ((oracle.vjp(mol.coords, mol.types, coef, q, gI), ref[:, :3]),
+                      (oracle.vjp_atomic(mol.coords, ff, q, gI), ref[:, 3:])):
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.max(np.abs(want)))
+    h, _ = oracle.pair_histogram(mol.coords.astype(np.float32), mol.types, 4, 64, 40.0)
+    np.testing.assert_array_equal(h, np.loadtxt(_golden("globule300_hist64_r40.txt"), dtype=np.int64))
