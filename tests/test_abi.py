@@ -101,3 +101,21 @@ def test_header_constants_match_binding():
     assert len(expected) >= 20
     for k in expected:
         assert getattr(_lib, k) == consts[k], k
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++17")])
+def test_header_compiles_as_plain_c_and_cpp(tmp_path, lang, std):
+    """include/sas.h is a C header: it compiles on its own as C99 and C++17 with warnings as errors,
+    and every declared entry point can be referenced."""
+    import shutil
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    names = _declared()
+    src = tmp_path / ("probe.c" if lang == "c" else "probe.cpp")
+    src.write_text('#include "sas.h"\nvoid *sas_probe_table[] = {\n' +
+                   "".join(f"    (void *)&{n},\n" for n in names) + "};\n")
+    r = subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "probe.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
