@@ -119,3 +119,44 @@ def test_header_compiles_as_plain_c_and_cpp(tmp_path, lang, std):
                         "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "probe.o")],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+_C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "sas.h"
+
+int main(void)
+{
+    const double coef[9] = {1, 1, 1, 1, 1, 1, 1, 1, 0};
+    const double q[3] = {0.0, 0.1, 0.2};
+    sas_ctx *ctx = NULL;
+    if (strstr(sas_version(), "sm_103a") == NULL) return 1;
+    if (sas_create(0, coef, q, 3, SAS_MIXED, &ctx) != SAS_ERR_INVALID_ARG || ctx) return 2;
+    if (strlen(sas_last_error()) == 0) return 3;
+    if (sas_create(1, coef, q, 3, 1u << 5, &ctx) != SAS_ERR_INVALID_ARG || ctx) return 4;
+    if (sas_destroy(NULL) != SAS_OK) return 5;
+    if (sas_profile(NULL, NULL, SAS_COORDS_F32, NULL, 0, NULL, NULL) != SAS_ERR_INVALID_ARG) return 6;
+    if (sas_exact_sums(NULL, NULL, 0, NULL) != SAS_ERR_INVALID_ARG) return 7;
+    printf("ok\n");
+    return 0;
+}
+"""
+
+
+def test_plain_c_client_links_and_gets_status_codes(tmp_path):
+    """A C program linked against libsas.so (no Python) gets the documented status codes from the
+    argument checks, which need no GPU."""
+    import shutil
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no host compiler")
+    lib = _lib.load()._name
+    src = tmp_path / "client.c"
+    src.write_text(_C_CLIENT)
+    exe = tmp_path / "client"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), lib,
+                        "-Wl,-rpath," + os.path.dirname(lib), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
