@@ -5,17 +5,19 @@
 // hosts that forbid cudaMalloc/cudaFree (which synchronize the device) inside a latency-critical
 // loop.  This entry point serves them: every intermediate buffer (packed coordinates, the
 // type-pair table, the work list, the per-item partial sums, the form-factor table) lives in one
-// file-scope __device__ array of fixed size, and the host side uses only stack memory.  The
-// arithmetic is that of sas_profile on a SAS_MIXED context: the same pack, pair, reduction and
-// assembly kernels, given pointers into the fixed array.
+// file-scope __device__ array of fixed size, and the host side uses fixed static arrays (no heap,
+// a few hundred bytes of stack).  The arithmetic is that of sas_profile on a SAS_MIXED context:
+// the same pack, pair, reduction and assembly kernels, given pointers into the fixed array.
 //
 // Set-up: the address of the array on the current device is taken with cudaGetSymbolAddress by
 // the first call on that device (the host-side name of the array is not a device address) and
 // kept for later calls.  Do that first call outside any stream capture.
+// Synchronization: a call waits for its stream twice, once to read the type counts back (the
+// work list is built from them on the host) and once at the end.
 // Sharing: every call on a device uses the same array, and it keeps the previous call's
 // contents; the calls clear what has to start at zero.  Two calls whose work overlaps on the
-// GPU (different streams, different host threads) race on the array and must be serialized by
-// the caller.
+// GPU race on the array.  Calls from several host threads are serialized by a lock that is held
+// until the call's stream has finished, which also guards the static host-side work list.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -59,8 +61,15 @@ constexpr size_t kStaticBytes = kOffTicket + align256(sizeof(int));
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
+// Held for a whole call: it guards the per-device addresses and the host-side work list below,
+// and keeps calls from different host threads from overlapping on the shared array.
+std::mutex g_static_mutex;
 void *g_scratch_ptr[kMaxDevices] = {nullptr};
+// Host-side work list of the current call (static storage, about 130 KB, rather than the
+// caller's stack, which may be small on worker threads).
+Item g_h_items[kStaticItems];
+int g_h_group_items[kStaticItems];
+int g_h_group_off[kStaticPairs + 1];
 
 // The entry point reports through its status code only (the messages below document the cases).
 sas_status static_fail(sas_status st, const char *msg, const char *detail = "")
@@ -122,16 +131,13 @@ extern "C" sas_status sas_profile_static(const float *coords, const int32_t *typ
     int dev = 0;
     STATIC_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return static_fail(SAS_ERR_UNSUPPORTED, "device ordinal too large");
-    unsigned char *base;
-    {
-        std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_ptr[dev]) {
-            void *p = nullptr;
-            STATIC_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
-            g_scratch_ptr[dev] = p;
-        }
-        base = static_cast<unsigned char *>(g_scratch_ptr[dev]);
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        STATIC_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
+        g_scratch_ptr[dev] = p;
     }
+    unsigned char *base = static_cast<unsigned char *>(g_scratch_ptr[dev]);
     if (n == 0) {
         STATIC_TRY(cudaMemsetAsync(I_out, 0, sizeof(double) * n_q, s));
         return SAS_OK;
@@ -179,10 +185,10 @@ extern "C" sas_status sas_profile_static(const float *coords, const int32_t *typ
     if (h_meta[2 * T + 1] & kErrNonFinite) return static_fail(SAS_ERR_INVALID_ARG, "non-finite coordinate");
     const int64_t npad = h_meta[2 * T];
 
-    // work list in canonical order (groups (a, b) in row-major order), on the host stack
-    Item h_items[kStaticItems];
-    int h_group_items[kStaticItems];
-    int h_group_off[kStaticPairs + 1];
+    // work list in canonical order (groups (a, b) in row-major order), in the static host arrays
+    Item *h_items = g_h_items;
+    int *h_group_items = g_h_group_items;
+    int *h_group_off = g_h_group_off;
     int ni = 0;
     {
         int64_t P[kStaticTypes], O[kStaticTypes], off = 0;
@@ -234,7 +240,7 @@ extern "C" sas_status sas_profile_static(const float *coords, const int32_t *typ
                                   kStaticJmax, ticket, s));
     STATIC_TRY(launch_reduce_items(partial, kQChunk, items, group_items, group_off, Pn, qc, S, s));
     STATIC_TRY(launch_assemble(S, F, meta, T, 1, qc, 1, I_out, s));
-    // the host-side arrays above are gone when this returns: wait until the copies from them are done
+    // the next call reuses the host-side arrays: wait until the copies from them are done
     STATIC_TRY(cudaStreamSynchronize(s));
 #undef STATIC_TRY
     return SAS_OK;
