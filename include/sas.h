@@ -211,6 +211,23 @@ sas_status sas_pair_histogram(sas_ctx *ctx, const float *coords, const int32_t *
                               int64_t batch, int n_bins, float r_max, int32_t *hist_out,
                               int64_t *dropped_out, void *stream);
 
+/*
+ * The Debye sum over pair-distance histograms with every pair at its bin centre: Eq. 2 (Section
+ * I-A) with each pair distance replaced by the centre r_k = (k + 1/2) r_max / n_bins of its
+ * histogram bin, which costs O(T^2 n_bins) per q instead of O(N^2).  Not the paper's method (which
+ * sums every pair exactly); the baseline a learned surrogate must beat.
+ *   I_c(q) = sum_t n_t f_t(q)^2 + sum_{a<=b} 2 f_a(q) f_b(q) sum_k hist_c[p(a,b)][k] sinc(q r_k)
+ * hist [batch][T(T+1)/2][n_bins] int32 (sas_pair_histogram's layout; host or device, counts below
+ * 2^24), type_counts [T] host int64 (atoms of each type, the same for every conformer), I_out
+ * [batch][n_q] double (host or device), with the context's form factors and q grid.  The table of
+ * 2 f_a f_b sinc(q r_k) is built on the first call for an (n_bins, r_max) and kept in the context.
+ * FP32 products summed over 32 bins in FP32, then in FP64.  Asynchronous for device outputs.
+ * Errors: INVALID_ARG (sizes, null pointers, negative counts), UNSUPPORTED (batch > 2^28), ALLOC,
+ * CUDA, TIMEOUT.
+ */
+sas_status sas_binned_profile(sas_ctx *ctx, const int32_t *hist, int64_t batch, int n_bins, float r_max,
+                              const int64_t *type_counts, double *I_out, void *stream);
+
 /* Tuning and diagnostics (values are validated; unknown options give INVALID_ARG). */
 enum {
     SAS_OPT_JMAX = 1,        /* longest J-range of one work item, atoms (multiple of 128 up to 8192; 0 = automatic) */
@@ -235,7 +252,7 @@ enum {
                                 sas_profile_vjp and sas_pair_histogram likewise return additive
                                 shares; sas_profile_grad needs the whole profile and returns
                                 UNSUPPORTED while world > 1. */
-    SAS_OPT_METHOD = 9       /* sas_profile / sas_profile_batch on a SAS_MIXED context: 0 the direct sum
+    SAS_OPT_METHOD = 9,      /* sas_profile / sas_profile_batch on a SAS_MIXED context: 0 the direct sum
                                 (default); 1 hybrid: the orientation average of Eq. 1 by spherical
                                 quadrature (Gauss-Legendre x uniform azimuth, degree from the spherical
                                 Bessel tail at q R, R the largest distance from the centroid) on the low-q
@@ -244,6 +261,12 @@ enum {
                                 1e-10 of the amplitude terms; sas_partials is not available after 1 or 2;
                                 sas_last_stats entry 6 gives the q values computed by quadrature and
                                 entry 7 its directions */
+    SAS_OPT_ADJOINT = 10     /* gradient kernels (sas_profile_grad, sas_profile_vjp): 0 (default) the pair weight
+                                W(r) = 2 sum_q h_q (cos(q r) - sinc(q r)) / r^2, a function of the distance alone
+                                within one conformer and type pair, tabulated on nodes 0.05 / q_max apart up to
+                                the diameter bound and interpolated by cubics (error below 2e-7 of its scale),
+                                falling back to 1 when the tables would exceed 2 GB or 65535 conformer type
+                                pairs; 1 the sums over q by the three-term recurrence for every pair */
 };
 sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value);
 
@@ -267,11 +290,15 @@ sas_status sas_last_stats(sas_ctx *ctx, int64_t *stats_out, int n);
  * array of SAS_STATIC_SCRATCH_BYTES that every GPU loading the library holds until exit.
  * Limits: n_atoms <= SAS_STATIC_MAX_ATOMS, n_q <= 208, n_types <= SAS_MAX_TYPES; larger sizes
  * give SAS_ERR_UNSUPPORTED; device inputs on the host give SAS_ERR_INVALID_ARG.  The call
- * returns when I_out is written (it synchronizes on `stream`).  Errors are reported by the
- * status code only (sas_last_error is not updated).
+ * returns when I_out is written: it waits for `stream` twice, once to read the type counts back
+ * (the work list is built from them on the host) and once at the end.  Errors are reported by
+ * the status code only (sas_last_error is not updated).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls on a device share the array, so
- * calls that overlap on the GPU (other streams or host threads) race: serialize them.
+ * make that first call before any stream capture.  All calls on a device share the array and
+ * it keeps the last call's contents (each call clears what must start at zero); calls that
+ * overlap on the GPU race on it.  The library serializes its own calls from several host
+ * threads with a lock held until the call's stream has finished; the host-side work list
+ * (about 130 KB) is static storage under that lock, not the caller's stack.
  */
 #define SAS_STATIC_MAX_ATOMS 16384
 #define SAS_STATIC_SCRATCH_BYTES (7 << 20)
@@ -314,6 +341,27 @@ sas_status sas_mlp_train_step(sas_mlp *mlp, const float *x, const float *t, int 
 sas_status sas_mlp_grads(sas_mlp *mlp, const float *x, const float *t, int batch, float *grads, float *loss_out,
                          void *stream);
 
+/* Intermediate tensors of the network's last passes, for tests and inspection: the forward pass
+ * of the last sas_mlp_forward, sas_mlp_grads or sas_mlp_train_step call (X .. Y) and the backward
+ * pass of the last sas_mlp_grads or sas_mlp_train_step call (DY .. DZ1B).  Rows [0, batch) of
+ * tensor `which` go to out [batch][width] (float32; bfloat16 tensors are widened exactly; host or
+ * device memory); width is n_in for X, n_out for Y, DY and DYB, n_hidden otherwise, and is stored
+ * to *width_out if that is not NULL.  batch must be in [1, max_batch]; rows beyond the batch of the
+ * pass that wrote the tensor hold stale values.  Synchronizes the device.
+ *   XB   bfloat16(x)                           Z1   XB W1b^T + b1 (FP32)   A1B  bfloat16(GELU(Z1))
+ *   Z2   A1B W2b^T + b2                        A2B  bfloat16(GELU(Z2))     Y    A2B W3b^T + b3
+ *   DY   2 (Y - t) / (batch n_out)             DYB  bfloat16(DY)           DA2  DYB W3b
+ *   DZ2  DA2 GELU'(Z2)    DZ2B bfloat16(DZ2)   DA1  DZ2B W2b               DZ1  DA1 GELU'(Z1)
+ *   DZ1B bfloat16(DZ1)
+ * (W1b, W2b, W3b: the bfloat16 copies of the master weights.) */
+enum {
+    SAS_MLP_BUF_XB = 0, SAS_MLP_BUF_Z1 = 1, SAS_MLP_BUF_A1B = 2, SAS_MLP_BUF_Z2 = 3, SAS_MLP_BUF_A2B = 4,
+    SAS_MLP_BUF_Y = 5, SAS_MLP_BUF_DY = 6, SAS_MLP_BUF_DYB = 7, SAS_MLP_BUF_DA2 = 8, SAS_MLP_BUF_DZ2 = 9,
+    SAS_MLP_BUF_DZ2B = 10, SAS_MLP_BUF_DA1 = 11, SAS_MLP_BUF_DZ1 = 12, SAS_MLP_BUF_DZ1B = 13,
+    SAS_MLP_BUF_COUNT = 14
+};
+sas_status sas_mlp_read_buffer(sas_mlp *mlp, int which, int batch, float *out, int *width_out);
+
 /* C[M][N] = A[M][K] B[N][K]^T (+ bias[N]): bfloat16 A and B (device, K contiguous, 16-byte aligned,
  * K % 16 == 0, lda and ldb multiples of 8), float32 C (device), FP32 accumulation on the tcgen05
  * tensor cores (TMA-fed shared-memory stages, accumulator in tensor memory).  Asynchronous on the
@@ -323,16 +371,19 @@ sas_status sas_gemm_bf16(int M, int N, int K, const void *A, int lda, const void
 
 /*
  * Screening of a conformer ensemble (the high-throughput setting of Section I; not part of the
- * paper's method): chi2_c = sum_q w_q (exp(z_cq stdv_q + mean_q) - target_q)^2 for n_conf
- * standardized log-profiles z (float32, row stride ld), written to chi2_all [n_conf]; then the
- * indices of the k smallest chi2 in increasing order (equal values by index, NaN last) to top_idx
- * [k] and their chi2 to top_chi2 [k] (may be NULL).  Every buffer is device memory; chi2_all is
- * required.  Limits: 1 <= n_conf <= 8192 (one CTA sorts them in shared memory), 1 <= k <= n_conf,
- * ld >= n_q.  Asynchronous on the stream.
+ * paper's method): chi2_c = sum_q w_q (P_cq - target_q)^2 for n_conf predicted profiles
+ *   P_cq = base_cq * exp(z_cq stdv_q + mean_q),
+ * z a standardized log-profile (float32, row stride ld) and base a profile (double, row stride
+ * ld_base) that it multiplies; either may be NULL (factor 1), not both; mean and stdv are needed
+ * with z.  chi2 goes to chi2_all [n_conf]; then the indices of the k smallest chi2 in increasing
+ * order (equal values by index, NaN last) to top_idx [k] and their chi2 to top_chi2 [k] (may be
+ * NULL).  Every buffer is device memory; chi2_all is required.  Limits: 1 <= n_conf <= 8192 (one
+ * CTA sorts them in shared memory), 1 <= k <= n_conf, ld and ld_base >= n_q.  Asynchronous on the
+ * stream.
  */
 sas_status sas_screen_select(int n_conf, int n_q, const float *z, int ld, const double *mean, const double *stdv,
-                             const double *target, const double *weights, int k, int32_t *top_idx, double *top_chi2,
-                             double *chi2_all, void *stream);
+                             const double *base, int ld_base, const double *target, const double *weights, int k,
+                             int32_t *top_idx, double *top_chi2, double *chi2_all, void *stream);
 
 /* dst[r] = src[idx[r]] for r < n_idx, rows of row_bytes bytes (device src, idx, dst; idx values
  * must address rows of src).  Packs selected conformers for the exact kernels. */

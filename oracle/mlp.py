@@ -39,16 +39,43 @@ def gelu_grad(z):
     return 0.5 * (1.0 + _erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
 
 
+# ---- the steps, each at the GPU's rounding points (GEMM operands in bfloat16) ----
+
+def linear(a_b, W, b):
+    """z = a W^T + b for an input already rounded to bfloat16; the weight is rounded here."""
+    return a_b @ bf16(W).T + b
+
+
+def activation(z):
+    """bfloat16(GELU(z)): the next layer's GEMM operand."""
+    return bf16(gelu(z))
+
+
+def mse_grad(y, t):
+    """dL/dy of L = mean over batch and outputs of (y - t)^2."""
+    B, Q = t.shape
+    return 2.0 * (y - t) / (B * Q)
+
+
+def linear_backward(dz, dz_b, a_b, W):
+    """Gradients through z = a W^T + b: (dW, db, da), with dz_b = bfloat16(dz) the GEMM operand and
+    the bias gradient summed from the unrounded dz."""
+    return dz_b.T @ a_b, dz.sum(0), dz_b @ bf16(W)
+
+
+def activation_backward(da, z):
+    """dz = da GELU'(z)."""
+    return da * gelu_grad(z)
+
+
 def forward(params, x):
     """Returns (y, cache).  params: dict W1 [h,n_in], b1, W2 [h,h], b2, W3 [n_out,h], b3 (float32 masters)."""
     xb = bf16(x)
-    z1 = xb @ bf16(params["W1"]).T + params["b1"]
-    a1 = gelu(z1)
-    a1b = bf16(a1)
-    z2 = a1b @ bf16(params["W2"]).T + params["b2"]
-    a2 = gelu(z2)
-    a2b = bf16(a2)
-    y = a2b @ bf16(params["W3"]).T + params["b3"]
+    z1 = linear(xb, params["W1"], params["b1"])
+    a1b = activation(z1)
+    z2 = linear(a1b, params["W2"], params["b2"])
+    a2b = activation(z2)
+    y = linear(a2b, params["W3"], params["b3"])
     return y, dict(xb=xb, z1=z1, a1b=a1b, z2=z2, a2b=a2b)
 
 
@@ -58,30 +85,31 @@ def loss_and_grads(params, x, t):
     B, Q = t.shape
     d = y - t
     loss = float(np.sum(d * d) / (B * Q))
-    dy = 2.0 * d / (B * Q)
-    dyb = bf16(dy)
+    dy = mse_grad(y, t)
     g = {}
-    g["W3"] = dyb.T @ c["a2b"]
-    g["b3"] = dy.sum(0)
-    da2 = dyb @ bf16(params["W3"])
-    dz2 = da2 * gelu_grad(c["z2"])
-    dz2b = bf16(dz2)
-    g["W2"] = dz2b.T @ c["a1b"]
-    g["b2"] = dz2.sum(0)
-    da1 = dz2b @ bf16(params["W2"])
-    dz1 = da1 * gelu_grad(c["z1"])
-    dz1b = bf16(dz1)
-    g["W1"] = dz1b.T @ c["xb"]
-    g["b1"] = dz1.sum(0)
+    g["W3"], g["b3"], da2 = linear_backward(dy, bf16(dy), c["a2b"], params["W3"])
+    dz2 = activation_backward(da2, c["z2"])
+    g["W2"], g["b2"], da1 = linear_backward(dz2, bf16(dz2), c["a1b"], params["W2"])
+    dz1 = activation_backward(da1, c["z1"])
+    g["W1"], g["b1"], _ = linear_backward(dz1, bf16(dz1), c["xb"], params["W1"])
     return loss, g, y
+
+
+def adam_moments(m, v, g, beta1=0.9, beta2=0.999):
+    """Adam's moment estimates after one more gradient g (element-wise, float64)."""
+    return beta1 * m + (1 - beta1) * g, beta2 * v + (1 - beta2) * g ** 2
+
+
+def adam_update(p, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """The parameter after step `step` (counting from 1) given the updated moments m, v."""
+    mh = m / (1 - beta1 ** step)
+    vh = v / (1 - beta2 ** step)
+    return p - lr * mh / (np.sqrt(vh) + eps)
 
 
 def adam_step(params, grads, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update (bias-corrected), in place on float64 copies; `step` counts from 1."""
     for k in params:
-        m[k] = beta1 * m[k] + (1 - beta1) * grads[k]
-        v[k] = beta2 * v[k] + (1 - beta2) * grads[k] ** 2
-        mh = m[k] / (1 - beta1 ** step)
-        vh = v[k] / (1 - beta2 ** step)
-        params[k] = params[k] - lr * mh / (np.sqrt(vh) + eps)
+        m[k], v[k] = adam_moments(m[k], v[k], grads[k], beta1, beta2)
+        params[k] = adam_update(params[k], m[k], v[k], step, lr, beta1, beta2, eps)
     return params, m, v

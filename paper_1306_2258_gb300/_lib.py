@@ -21,8 +21,11 @@ SAS_MIXED, SAS_FP64 = 0, 1
 SAS_DETERMINISTIC = 16
 SAS_COORDS_F32, SAS_COORDS_F64 = 0, 1
 SAS_OPT_JMAX, SAS_OPT_RESEED, SAS_OPT_VALIDATE, SAS_OPT_GRID, SAS_OPT_TIMEOUT_MS, SAS_OPT_STEP, SAS_OPT_VARIANT = 1, 2, 3, 4, 5, 6, 7
-SAS_OPT_SHARD, SAS_OPT_METHOD = 8, 9
+SAS_OPT_SHARD, SAS_OPT_METHOD, SAS_OPT_ADJOINT = 8, 9, 10
 SAS_MAX_TYPES, SAS_MAX_Q = 16, 1664
+(SAS_MLP_BUF_XB, SAS_MLP_BUF_Z1, SAS_MLP_BUF_A1B, SAS_MLP_BUF_Z2, SAS_MLP_BUF_A2B, SAS_MLP_BUF_Y, SAS_MLP_BUF_DY,
+ SAS_MLP_BUF_DYB, SAS_MLP_BUF_DA2, SAS_MLP_BUF_DZ2, SAS_MLP_BUF_DZ2B, SAS_MLP_BUF_DA1, SAS_MLP_BUF_DZ1,
+ SAS_MLP_BUF_DZ1B, SAS_MLP_BUF_COUNT) = range(15)
 
 # every symbol include/sas.h declares (checked by the test suite)
 EXPORTS = (
@@ -31,7 +34,8 @@ EXPORTS = (
     "sas_last_error", "sas_version", "sas_profile_static", "sas_mlp_create", "sas_mlp_destroy",
     "sas_mlp_param_count", "sas_mlp_set_state", "sas_mlp_get_state", "sas_mlp_forward", "sas_mlp_train_step",
     "sas_mlp_grads", "sas_gemm_bf16", "sas_screen_select", "sas_gather_rows", "sas_profile_atomic",
-    "sas_measure_peaks", "sas_exact_sums", "sas_assemble_exact",
+    "sas_measure_peaks", "sas_exact_sums", "sas_assemble_exact", "sas_mlp_read_buffer",
+    "sas_binned_profile",
 )
 
 
@@ -76,13 +80,16 @@ def load():
                 "sas_mlp_forward": [_vp, _vp, _int, _vp, _vp],
                 "sas_mlp_train_step": [_vp, _vp, _vp, _int, ctypes.c_float, _vp, _vp],
                 "sas_mlp_grads": [_vp, _vp, _vp, _int, _vp, _vp, _vp],
+                "sas_mlp_read_buffer": [_vp, _int, _int, _vp, _vp],
                 "sas_gemm_bf16": [_int, _int, _int, _vp, _int, _vp, _int, _vp, _vp, _int, _vp],
-                "sas_screen_select": [_int, _int, _vp, _int, _vp, _vp, _vp, _vp, _int, _vp, _vp, _vp, _vp],
+                "sas_screen_select": [_int, _int, _vp, _int, _vp, _vp, _vp, _int, _vp, _vp, _int, _vp, _vp, _vp,
+                                      _vp],
                 "sas_gather_rows": [_vp, _i64, _vp, _i64, _vp, _vp],
                 "sas_profile_atomic": [_vp, _vp, _int, _i64, _i64, _vp, _vp, _vp],
                 "sas_measure_peaks": [_vp, _int, _vp],
                 "sas_exact_sums": [_vp, _vp, _i64, _vp],
                 "sas_assemble_exact": [_vp, _vp, _i64, _vp, _vp],
+                "sas_binned_profile": [_vp, _vp, _i64, _int, ctypes.c_float, _vp, _vp, _vp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -212,6 +219,13 @@ def sas_profile_static(coords, types, n_atoms, n_types, ff_coef, q0, dq, n_q, I_
         raise SasError(st, "sas_profile_static failed")
 
 
+def sas_binned_profile(ctx, hist, batch, n_bins, r_max, type_counts, I_out, stream=None):
+    """Debye sum over pair-distance histograms at bin centres (hist [batch][P][n_bins] int32)."""
+    tc = np.ascontiguousarray(type_counts, dtype=np.int64)
+    check(load().sas_binned_profile(ctx, ptr(hist), int(batch), int(n_bins), float(r_max), tc.ctypes.data, ptr(I_out),
+                                    stream_handle(stream)))
+
+
 def sas_mlp_create(n_in, n_hidden, n_out, max_batch):
     h = _vp()
     check(load().sas_mlp_create(int(n_in), int(n_hidden), int(n_out), int(max_batch), ctypes.byref(h)))
@@ -249,16 +263,23 @@ def sas_mlp_grads(mlp, x, t, batch, grads, loss_out=None, stream=None):
     check(load().sas_mlp_grads(mlp, ptr(x), ptr(t), int(batch), ptr(grads), ptr(loss_out), stream_handle(stream)))
 
 
+def sas_mlp_read_buffer(mlp, which, batch, out):
+    """Rows [0, batch) of intermediate tensor `which` (SAS_MLP_BUF_*) into out (float32); returns its width."""
+    w = ctypes.c_int(0)
+    check(load().sas_mlp_read_buffer(mlp, int(which), int(batch), ptr(out), ctypes.byref(w)))
+    return int(w.value)
+
+
 def sas_gemm_bf16(M, N, K, A, lda, B, ldb, bias, C, ldc, stream=None):
     check(load().sas_gemm_bf16(int(M), int(N), int(K), ptr(A), int(lda), ptr(B), int(ldb), ptr(bias), ptr(C),
                                int(ldc), stream_handle(stream)))
 
 
-def sas_screen_select(n_conf, n_q, z, ld, mean, stdv, target, weights, k, top_idx, top_chi2, chi2_all,
-                      stream=None):
-    check(load().sas_screen_select(int(n_conf), int(n_q), ptr(z), int(ld), ptr(mean), ptr(stdv), ptr(target),
-                                   ptr(weights), int(k), ptr(top_idx), ptr(top_chi2), ptr(chi2_all),
-                                   stream_handle(stream)))
+def sas_screen_select(n_conf, n_q, z, ld, mean, stdv, base, ld_base, target, weights, k, top_idx, top_chi2,
+                      chi2_all, stream=None):
+    check(load().sas_screen_select(int(n_conf), int(n_q), ptr(z), int(ld), ptr(mean), ptr(stdv), ptr(base),
+                                   int(ld_base), ptr(target), ptr(weights), int(k), ptr(top_idx), ptr(top_chi2),
+                                   ptr(chi2_all), stream_handle(stream)))
 
 
 def sas_gather_rows(src, row_bytes, idx, n_idx, dst, stream=None):

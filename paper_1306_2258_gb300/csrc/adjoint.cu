@@ -21,6 +21,8 @@
 // shared memory by six lanes.  Item totals go to a [batch][slot][3] FP64 array with FP64
 // atomics, or, on a deterministic context, to per-item buffers (each warp with its own copy of the
 // J-range sums) that k_adjoint_gather adds up per atom in a fixed order.
+#include <algorithm>
+
 #include "mixed_common.cuh"
 #include "sas_internal.h"
 #include "sincos_f32.cuh"
@@ -316,6 +318,232 @@ __global__ void __launch_bounds__(kTile, 4)
     }
 }
 
+// ---- the tabulated form (default) ---------------------------------------------------------------
+// Within one work item every pair has the same conformer and type pair, so the pair weight is one
+// function of the distance:  W_ij = W(r_ij),  W(r) = 2 sum_q h_q (cos(q r) - sinc(q r)) / r^2,
+// an entire function of r (W(0) = -(2/3) sum_q h_q q^2) whose fourth derivative is at most about
+// q_max^4 times its scale.  It is tabulated per conformer and type pair on nodes r_m = m D
+// (D = kAdjTabStep / q_max) in FP64 as a contraction of h with the matrix K[k][m] = 2 (cos(q_k r_m) -
+// sinc(q_k r_m)) / r_m^2, and each interval [r_m, r_m+1] holds the cubic through the nodes m-1..m+2
+// (W is even, so node -1 is node 1) as FP32 coefficients.  Four-point cubic interpolation errs by at
+// most (9/16)/24 (q_max D)^4 = 1.5e-7 of the scale at q_max D = 0.05, below the FP32 rounding of
+// the recurrence it replaces.  Per pair: the distance, one float4 load and three packed FMAs in
+// place of two recurrences over the q grid; the forces are applied as in k_debye_adjoint.
+
+// K[k][m] (row stride n_rows) = 2 (cos x - sinc x) / r^2 with x = q_k r, r = m step; for x < 1e-2 the
+// series 2 q^2 (-1/3 + x^2/30 - x^4/840) (its next term is below 1e-13 relative there).
+__global__ void k_adj_kmat(QChunks qc, int n_rows, double step, double *__restrict__ K)
+{
+    const int64_t total = (int64_t)qc.n_q * n_rows;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / n_rows), m = (int)(e % n_rows);
+        const double q = q_at(qc, k), r = m * step, x = q * r;
+        double v;
+        if (x < 1e-2) {
+            const double x2 = x * x;
+            v = 2.0 * q * q * (-1.0 / 3.0 + x2 * (1.0 / 30.0 - x2 / 840.0));
+        } else {
+            double sn, cs;
+            sincos(x, &sn, &cs);
+            v = 2.0 * (cs - sn / x) / (r * r);
+        }
+        K[e] = v;
+    }
+}
+
+// Wn[row][m] = sum_k h_row(q_k) K[k][m], h = g_b(q) f_a(q) f_c(q) for row = b P + p(a, c), FP64.
+__global__ void __launch_bounds__(256)
+    k_adj_wnodes(const double *__restrict__ g, const double *__restrict__ F, int n_types, int n_q,
+                 const double *__restrict__ K, int n_rows, double *__restrict__ Wn)
+{
+    extern __shared__ double hrow[];   // [n_q]
+    const int P = n_types * (n_types + 1) / 2;
+    const int64_t row = blockIdx.y;
+    const int64_t b = row / P;
+    int a = 0, rem = (int)(row % P);
+    while (rem >= n_types - a) {
+        rem -= n_types - a;
+        ++a;
+    }
+    const int c = a + rem;
+    for (int k = threadIdx.x; k < n_q; k += blockDim.x)
+        hrow[k] = g[b * n_q + k] * F[(int64_t)a * n_q + k] * F[(int64_t)c * n_q + k];
+    __syncthreads();
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_rows) return;
+    double acc = 0.0;
+    for (int k = 0; k < n_q; ++k) acc = fma(hrow[k], K[(int64_t)k * n_rows + m], acc);
+    Wn[row * n_rows + m] = acc;
+}
+
+// tab[row][m] = (c0, c1, c2, c3) of the cubic through nodes m-1, m, m+1, m+2 at t = -1, 0, 1, 2
+// (node -1 = node 1), for m < n_int = n_rows - 2.
+__global__ void k_adj_wcoef(const double *__restrict__ Wn, int n_rows, int64_t rows, float4 *__restrict__ tab)
+{
+    const int n_int = n_rows - 2;
+    const int64_t total = rows * n_int;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e / n_int;
+        const int m = (int)(e % n_int);
+        const double *w = Wn + row * n_rows;
+        const double y0 = w[m == 0 ? 1 : m - 1], y1 = w[m], y2 = w[m + 1], y3 = w[m + 2];
+        tab[e] = make_float4((float)y1, (float)(-y0 / 3.0 - 0.5 * y1 + y2 - y3 / 6.0), (float)(0.5 * (y0 + y2) - y1),
+                             (float)((y3 - y0) / 6.0 + 0.5 * (y1 - y2)));
+    }
+}
+
+// The pair loop with W from the item's table row (tab, n_int intervals of width 1 / inv_step).
+template <bool DET>
+__device__ __forceinline__ void run_adj_tab(const float4 *sxy, const float4 *szw, const float4 *__restrict__ tab,
+                                            int n_int, float inv_step, float *gj, int jpairs, const float4 xi,
+                                            int lane, int jmask, float2 &gx, float2 &gy, float2 &gz)
+{
+    const float2 nX = bc(-xi.x), nY = bc(-xi.y), nZ = bc(-xi.z), wi = bc(xi.w);
+    const int kslot = lane >> 2;
+    const float last = (float)(n_int - 1);
+    for (int k = 0; k < jpairs; ++k) {
+        const int j = 2 * k;
+        const float4 pxy = sxy[k], pzw = szw[k];
+        AdjHead2 h;
+        setup_adj2_head(pxy, pzw, nX, nY, nZ, wi, j > jmask, j + 1 > jmask, h);
+        // interval and position: m = floor(r / step) (clamped to the last interval, where t <= 1 keeps
+        // the cubic finite for pairs beyond it, which carry w = 0), t = r / step - m
+        const float2 sv = f2mul(h.r, bc(inv_step));
+        const float ma = fminf(floorf(sv.x), last), mb = fminf(floorf(sv.y), last);
+        const float2 t = make_float2(fminf(sv.x - ma, 1.f), fminf(sv.y - mb, 1.f));
+        const float4 ca = tab[(int)ma], cb = tab[(int)mb];
+        const float2 W = f2fma(f2fma(f2fma(make_float2(ca.w, cb.w), t, make_float2(ca.z, cb.z)), t,
+                                     make_float2(ca.y, cb.y)),
+                               t, make_float2(ca.x, cb.x));
+        const float2 nW = f2mul(f2mul(h.w, bc(-1.f)), W);   // -w_i w_j W(r); G_i += -W (x_j - x_i)
+        const float2 dx = jdiff(make_float2(pxy.x, pxy.y), nX), dy = jdiff(make_float2(pxy.z, pxy.w), nY),
+                     dz = jdiff(make_float2(pzw.x, pzw.y), nZ);
+        gx = f2fma(nW, dx, gx);
+        gy = f2fma(nW, dy, gy);
+        gz = f2fma(nW, dz, gz);
+        const float2 fx = f2mul(nW, dx), fy = f2mul(nW, dy), fz = f2mul(nW, dz);
+        const float v[8] = {-fx.x, -fy.x, -fz.x, -fx.y, -fy.y, -fz.y, 0.f, 0.f};
+        const float tot = reduce_scatter8(v, lane);
+        if ((lane & 3) == 0 && kslot < 6) {
+            if (DET)
+                gj[3 * j + kslot] += tot;
+            else
+                atomicAdd(&gj[3 * j + kslot], tot);
+        }
+    }
+}
+
+// The tabulated form of k_debye_adjoint: same items, tickets, force accumulation and outputs.
+// STAGED: the item's table row is copied to shared memory (rows of at most kAdjTabStaged intervals);
+// otherwise it is read through the L1 cache.
+constexpr int kAdjTabStaged = 2048;
+
+// float4 slots of the J-range force sums gj ([copies][jcap][3] floats), rounded up so that the
+// staged table after them starts on a 16-byte boundary
+__host__ __device__ constexpr int adj_gj_f4(int jcap, bool det) { return ((det ? kAdjWarps : 1) * jcap * 3 + 3) / 4; }
+
+template <bool DET, bool STAGED>
+__global__ void __launch_bounds__(kTile, 4)
+    k_debye_adjoint_tab(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items, int n_items,
+                        const float4 *__restrict__ tab, int n_int, float inv_step, int n_pairs, double *__restrict__ G,
+                        int jcap, int *__restrict__ ticket, float *__restrict__ PI, float *__restrict__ PJ)
+{
+    extern __shared__ float4 smem[];
+    float4 *sxy = smem;                                 // [jcap / 2]
+    float4 *szw = smem + jcap / 2;                      // [jcap / 2]
+    float *gj = reinterpret_cast<float *>(smem + jcap);  // [DET ? kAdjWarps : 1][jcap][3]
+    float4 *stab = smem + jcap + adj_gj_f4(jcap, DET);   // [n_int] when STAGED
+    __shared__ int next_item;
+    const int tid = threadIdx.x, lane = tid & 31;
+    int it = blockIdx.x;
+    while (it < n_items) {
+        const Item item = items[it];
+        const float4 *Xb = X + (int64_t)item.batch * npad;
+        __syncthreads();
+        if (tid == 0) next_item = (int)gridDim.x + atomicAdd(ticket, 1);
+        if (item.chunk != 0) {
+            // the work list repeats every pair once per q pass; the table holds the sum over the
+            // whole grid, so only the items of the first pass contribute (the others give zero)
+            if (DET) {
+                PI[((int64_t)it * kTile + tid) * 3 + 0] = 0.f;
+                PI[((int64_t)it * kTile + tid) * 3 + 1] = 0.f;
+                PI[((int64_t)it * kTile + tid) * 3 + 2] = 0.f;
+                for (int k = tid; k < 3 * item.jlen; k += kTile) PJ[(int64_t)it * 3 * jcap + k] = 0.f;
+            }
+            __syncthreads();   // next_item is written
+            it = next_item;
+            continue;
+        }
+        const int jpairs = (item.jlen + 1) >> 1;
+        for (int k = tid; k < jpairs; k += kTile) {
+            const float4 a = Xb[item.j0 + 2 * k];
+            const float4 b = (2 * k + 1 < item.jlen) ? Xb[item.j0 + 2 * k + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            sxy[k] = make_float4(a.x, b.x, a.y, b.y);
+            szw[k] = make_float4(a.z, b.z, a.w, b.w);
+        }
+        if (DET) {
+            for (int k = tid; k < kAdjWarps * 3 * jcap; k += kTile) gj[k] = 0.f;
+        } else {
+            for (int k = tid; k < 6 * jpairs; k += kTile) gj[k] = 0.f;
+        }
+        const float4 *trow = tab + ((int64_t)item.batch * n_pairs + item.pair) * n_int;
+        if (STAGED)
+            for (int k = tid; k < n_int; k += kTile) stab[k] = trow[k];
+        const float4 xi = Xb[item.i0 + tid];
+        __syncthreads();
+        const int jmask = item.diag ? tid : -1;
+        float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
+        float *gw = DET ? gj + (tid >> 5) * 3 * jcap : gj;
+        run_adj_tab<DET>(sxy, szw, STAGED ? stab : trow, n_int, inv_step, gw, jpairs, xi, lane, jmask, gx, gy, gz);
+        if (DET) {
+            float *pi = PI + ((int64_t)it * kTile + tid) * 3;
+            pi[0] = gx.x + gx.y;
+            pi[1] = gy.x + gy.y;
+            pi[2] = gz.x + gz.y;
+            __syncthreads();
+            float *pj = PJ + (int64_t)it * 3 * jcap;
+            for (int k = tid; k < 3 * item.jlen; k += kTile) {
+                float t = gj[k];
+                for (int w = 1; w < kAdjWarps; ++w) t += gj[w * 3 * jcap + k];
+                pj[k] = t;
+            }
+        } else {
+            double *Gb = G + (int64_t)item.batch * npad * 3;
+            atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid)], (double)(gx.x + gx.y));
+            atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid) + 1], (double)(gy.x + gy.y));
+            atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid) + 2], (double)(gz.x + gz.y));
+            __syncthreads();
+            for (int k = tid; k < 3 * item.jlen; k += kTile)
+                atomicAdd(&Gb[3 * (int64_t)item.j0 + k], (double)gj[k]);
+        }
+        it = next_item;
+    }
+}
+
+template <bool DET, bool STAGED>
+cudaError_t launch_tab(const float4 *X, int64_t npad, const Item *items, int n_items, const float4 *tab, int n_int,
+                       float inv_step, int n_pairs, double *G, int jcap, int *ticket, float *PI, float *PJ,
+                       cudaStream_t s)
+{
+    const size_t smem = ((size_t)jcap + adj_gj_f4(jcap, DET) + (STAGED ? (size_t)n_int : 0)) * sizeof(float4);
+    cudaError_t e = cudaFuncSetAttribute(k_debye_adjoint_tab<DET, STAGED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0, dev = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_adjoint_tab<DET, STAGED>, kTile, smem)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    int grid = (occ > 0 ? occ : 1) * sms;
+    if (grid > n_items) grid = n_items;
+    k_debye_adjoint_tab<DET, STAGED><<<grid, kTile, smem, s>>>(X, npad, items, n_items, tab, n_int, inv_step,
+                                                               n_pairs, G, jcap, ticket, PI, PJ);
+    return cudaGetLastError();
+}
+
 // G[b][slot][c] (every slot of every I-tile) = the item totals of the items listed for the slot's
 // tile, added in list order in FP64: entry 2e is item e's I-tile, entry 2e+1 its J-range.
 __global__ void k_adjoint_gather(const float *__restrict__ PI, const float *__restrict__ PJ, int jcap,
@@ -483,6 +711,48 @@ cudaError_t launch_debye_adjoint(const float4 *X, int64_t npad, const Item *item
     default:
         return launch_nb<52>(nv, X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, PI, PJ, s);
     }
+}
+
+cudaError_t launch_adjoint_kmat(const QChunks &qc, int n_rows, double step, double *K, cudaStream_t s)
+{
+    const int64_t total = (int64_t)qc.n_q * n_rows;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    k_adj_kmat<<<blocks, 256, 0, s>>>(qc, n_rows, step, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_wtab(const double *g, const double *F, int n_types, int64_t batch, int n_q, const double *K,
+                                int n_rows, double *Wn, float4 *tab, cudaStream_t s)
+{
+    const int P = n_types * (n_types + 1) / 2;
+    const int64_t rows = batch * P;
+    if (rows == 0) return cudaSuccess;
+    if (rows > 65535) return cudaErrorInvalidValue;
+    dim3 grid((n_rows + 255) / 256, (unsigned)rows);
+    k_adj_wnodes<<<grid, 256, (size_t)n_q * sizeof(double), s>>>(g, F, n_types, n_q, K, n_rows, Wn);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t total = rows * (n_rows - 2);
+    k_adj_wcoef<<<(int)std::min<int64_t>((total + 255) / 256, 8192), 256, 0, s>>>(Wn, n_rows, rows, tab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debye_adjoint_tab(const float4 *X, int64_t npad, const Item *items, int n_items, const float4 *tab,
+                                     int n_int, float inv_step, int n_pairs, double *G, int jlen_max, int *ticket,
+                                     float *PI, float *PJ, cudaStream_t s)
+{
+    if (n_items == 0) return cudaSuccess;
+    const int jcap = adjoint_jcap(jlen_max);
+    const bool staged = n_int <= kAdjTabStaged;
+    if (PI)
+        return staged ? launch_tab<true, true>(X, npad, items, n_items, tab, n_int, inv_step, n_pairs, G, jcap, ticket,
+                                               PI, PJ, s)
+                      : launch_tab<true, false>(X, npad, items, n_items, tab, n_int, inv_step, n_pairs, G, jcap,
+                                                ticket, PI, PJ, s);
+    return staged ? launch_tab<false, true>(X, npad, items, n_items, tab, n_int, inv_step, n_pairs, G, jcap, ticket,
+                                            nullptr, nullptr, s)
+                  : launch_tab<false, false>(X, npad, items, n_items, tab, n_int, inv_step, n_pairs, G, jcap, ticket,
+                                             nullptr, nullptr, s);
 }
 
 cudaError_t launch_adjoint_gather(const float *PI, const float *PJ, int jcap, const Item *items,

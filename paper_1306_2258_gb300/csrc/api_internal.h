@@ -88,13 +88,16 @@ struct sas_ctx {
     int opt_grid = 0;
     int opt_shard_rank = 0, opt_shard_world = 1;   // this call computes shard rank of world
     int opt_method = 0;                             // 0 direct sum, 1 hybrid by qD and N, 2 quadrature
+    int opt_adjoint = 0;                            // 0 tabulated radial weight (if it fits), 1 q recurrence
     double diam = 0.0;                              // bound on the diameter of the last call's conformers
     int pad = sas::kTile, tile_used = sas::kTile;             // type-group padding and I-tile of the last packing
     int64_t opt_timeout_ms = 600000;
     sas::api::DevBuf coef_d, F, meta, blockcounts, blockoffs, centroid, X, slot_of, items, group_items,
         group_off, partial, ticket, S, in_coords, in_types, out_buf, Ibuf, gbuf, chi2buf, H, G, gout, tgt, wts,
         hist, dropped, in_ff, zero_types, FJ, FI, F64t, D2, segbuf, cen, qdirs, qwts, type_off, Apart, Fsub, Itmp, qplan,
-        tile_off, tile_ent, adj_pi, adj_pj, Ufix, segfix, Ustage, Sx, Ix;
+        tile_off, tile_ent, adj_pi, adj_pj, Ufix, segfix, Ustage, Sx, Ix, btab, bdiag, bhist, bout, adj_k, adj_wn, adj_tab;
+    int btab_bins = 0;        // (n_bins, r_max) of the binned-sum table in btab (0: none)
+    float btab_rmax = 0.f;
     int det_ntiles = -1;   // I-tiles per conformer of the current schedule's tile lists (-1: none built)
     int *h_meta = nullptr;   // pinned
     // schedule cache

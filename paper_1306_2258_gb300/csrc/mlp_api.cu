@@ -336,6 +336,49 @@ sas_status sas_mlp_train_step(sas_mlp *m, const float *x, const float *t, int ba
     return SAS_OK;
 }
 
+sas_status sas_mlp_read_buffer(sas_mlp *m, int which, int batch, float *out, int *width_out)
+{
+    if (!m || !out) return mlp_fail(SAS_ERR_INVALID_ARG, "null argument");
+    if (batch < 1 || batch > m->max_b) return mlp_fail(SAS_ERR_INVALID_ARG, "batch outside [1, max_batch]");
+    const int h = m->h, Qp = m->n_outp;
+    // (buffer, row stride, width, bfloat16?) per SAS_MLP_BUF_* value
+    const void *src = nullptr;
+    int ld = 0, width = 0;
+    bool is_bf16 = false;
+    switch (which) {
+    case SAS_MLP_BUF_XB: src = m->Xb, ld = m->n_in, width = m->n_in, is_bf16 = true; break;
+    case SAS_MLP_BUF_Z1: src = m->Z1, ld = h, width = h; break;
+    case SAS_MLP_BUF_A1B: src = m->A1b, ld = h, width = h, is_bf16 = true; break;
+    case SAS_MLP_BUF_Z2: src = m->Z2, ld = h, width = h; break;
+    case SAS_MLP_BUF_A2B: src = m->A2b, ld = h, width = h, is_bf16 = true; break;
+    case SAS_MLP_BUF_Y: src = m->Y, ld = Qp, width = m->n_out; break;
+    case SAS_MLP_BUF_DY: src = m->dY, ld = Qp, width = m->n_out; break;
+    case SAS_MLP_BUF_DYB: src = m->dYb, ld = Qp, width = m->n_out, is_bf16 = true; break;
+    case SAS_MLP_BUF_DA2: src = m->dA2, ld = h, width = h; break;
+    case SAS_MLP_BUF_DZ2: src = m->dZ2, ld = h, width = h; break;
+    case SAS_MLP_BUF_DZ2B: src = m->dZ2b, ld = h, width = h, is_bf16 = true; break;
+    case SAS_MLP_BUF_DA1: src = m->dA1, ld = h, width = h; break;
+    case SAS_MLP_BUF_DZ1: src = m->dZ1, ld = h, width = h; break;
+    case SAS_MLP_BUF_DZ1B: src = m->dZ1b, ld = h, width = h, is_bf16 = true; break;
+    default: return mlp_fail(SAS_ERR_INVALID_ARG, "unknown buffer");
+    }
+    MLP_TRY(cudaDeviceSynchronize());
+    sas_status st = gemm_check();
+    if (st != SAS_OK) return st;
+    const size_t n = (size_t)batch * width, esz = is_bf16 ? sizeof(bf16) : sizeof(float);
+    std::vector<float> host(n);
+    if (is_bf16) {
+        std::vector<bf16> tmp(n);
+        MLP_TRY(cudaMemcpy2D(tmp.data(), esz * width, src, esz * ld, esz * width, batch, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) host[i] = __bfloat162float(tmp[i]);
+    } else {
+        MLP_TRY(cudaMemcpy2D(host.data(), esz * width, src, esz * ld, esz * width, batch, cudaMemcpyDeviceToHost));
+    }
+    MLP_TRY(cudaMemcpy(out, host.data(), sizeof(float) * n, cudaMemcpyDefault));
+    if (width_out) *width_out = width;
+    return SAS_OK;
+}
+
 sas_status sas_gemm_bf16(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias, float *C,
                          int ldc, void *stream)
 {

@@ -774,9 +774,30 @@ sas_status adjoint(sas_ctx *ctx, int64_t n, int64_t batch, const double *g_dev, 
     }
     ALLOC_TRY(ctx->ticket, sizeof(int));
     CUDA_TRY(cudaMemsetAsync(ctx->ticket.p, 0, sizeof(int), s));
-    CUDA_TRY(launch_debye_adjoint(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, ctx->qc,
-                                  ctx->H.as<float2>(), Pn, Q, ctx->G.as<double>(), ctx->jlen_max,
-                                  ctx->ticket.as<int>(), PI, PJ, s));
+    // The tabulated radial weight W(r) per conformer and type pair (default), on nodes spaced
+    // kAdjTabStep / q_max apart up to the validated diameter bound; the q recurrence when the tables
+    // would be too large or SAS_OPT_ADJOINT asks for it.
+    const double qmax = std::max(ctx->q.back(), 1e-6), step = kAdjTabStep / qmax;
+    const double n_int_d = std::ceil(ctx->diam * (1.0 + 1e-5) / step) + 2.0;
+    const int64_t rows = batch * Pn;
+    const double tab_bytes = (double)Q * (n_int_d + 2) * 8 + (double)rows * (n_int_d + 2) * 8 + (double)rows * n_int_d * 16;
+    if (ctx->opt_adjoint == 0 && rows <= 65535 && n_int_d < 1e8 && tab_bytes <= 2e9) {
+        const int n_int = (int)n_int_d, n_rows = n_int + 2;
+        ALLOC_TRY(ctx->adj_k, (size_t)Q * n_rows * sizeof(double));
+        ALLOC_TRY(ctx->adj_wn, (size_t)rows * n_rows * sizeof(double));
+        ALLOC_TRY(ctx->adj_tab, (size_t)rows * n_int * sizeof(float4));
+        CUDA_TRY(launch_adjoint_kmat(ctx->qc, n_rows, step, ctx->adj_k.as<double>(), s));
+        CUDA_TRY(launch_adjoint_wtab(g_dev, ctx->F.as<double>(), T, batch, Q, ctx->adj_k.as<double>(), n_rows,
+                                     ctx->adj_wn.as<double>(), ctx->adj_tab.as<float4>(), s));
+        CUDA_TRY(launch_debye_adjoint_tab(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items,
+                                          ctx->adj_tab.as<float4>(), n_int, (float)(1.0 / step), Pn,
+                                          ctx->G.as<double>(), ctx->jlen_max, ctx->ticket.as<int>(), PI, PJ, s));
+        launches += 3;
+    } else {
+        CUDA_TRY(launch_debye_adjoint(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, ctx->qc,
+                                      ctx->H.as<float2>(), Pn, Q, ctx->G.as<double>(), ctx->jlen_max,
+                                      ctx->ticket.as<int>(), PI, PJ, s));
+    }
     if (det) {
         CUDA_TRY(launch_adjoint_gather(PI, PJ, jcap, ctx->items.as<Item>(), ctx->tile_off.as<int>(),
                                        ctx->tile_ent.as<int>(), ctx->det_ntiles, npad, batch, ctx->G.as<double>(),
@@ -986,6 +1007,10 @@ sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value)
     case SAS_OPT_METHOD:
         if (value < 0 || value > 2) return fail(SAS_ERR_INVALID_ARG, "METHOD must be 0, 1 or 2");
         ctx->opt_method = (int)value;
+        return SAS_OK;
+    case SAS_OPT_ADJOINT:
+        if (value < 0 || value > 1) return fail(SAS_ERR_INVALID_ARG, "ADJOINT must be 0 or 1");
+        ctx->opt_adjoint = (int)value;
         return SAS_OK;
     case SAS_OPT_SHARD: {
         const int64_t world = value >> 16, rank = value & 0xFFFF;

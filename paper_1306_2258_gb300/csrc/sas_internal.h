@@ -149,6 +149,17 @@ inline int adjoint_jcap(int jlen_max) { return (jlen_max + 1) / 2 * 2; }
 cudaError_t launch_debye_adjoint(const float4 *X, int64_t npad, const Item *items, int n_items,
                                  const QChunks &qc, const float2 *H, int n_pairs, int hstride, double *G,
                                  int jlen_max, int *ticket, float *PI, float *PJ, cudaStream_t s);
+// The tabulated form: K [n_q][n_rows] FP64 (r_m = m step), then per conformer and type pair the FP64
+// nodes Wn [batch P][n_rows] and the cubic coefficients tab [batch P][n_rows - 2] float4 of
+// W(r) = 2 sum_q h_q (cos(q r) - sinc(q r)) / r^2, h_q = g_q f_a(q) f_b(q) (batch P <= 65535), and
+// the pair kernel over the table (same arguments and outputs as launch_debye_adjoint otherwise).
+constexpr double kAdjTabStep = 0.05;   // q_max times the node spacing
+cudaError_t launch_adjoint_kmat(const QChunks &qc, int n_rows, double step, double *K, cudaStream_t s);
+cudaError_t launch_adjoint_wtab(const double *g, const double *F, int n_types, int64_t batch, int n_q, const double *K,
+                                int n_rows, double *Wn, float4 *tab, cudaStream_t s);
+cudaError_t launch_debye_adjoint_tab(const float4 *X, int64_t npad, const Item *items, int n_items, const float4 *tab,
+                                     int n_int, float inv_step, int n_pairs, double *G, int jlen_max, int *ticket,
+                                     float *PI, float *PJ, cudaStream_t s);
 cudaError_t launch_adjoint_gather(const float *PI, const float *PJ, int jcap, const Item *items,
                                   const int *tile_off, const int *tile_ent, int ntiles, int64_t npad, int64_t batch,
                                   double *G, cudaStream_t s);
@@ -177,7 +188,8 @@ cudaError_t gemm_tc_error(int *err);
 // Screening: surrogate chi^2 per conformer, top-k selection (n <= select_max()), row gather.
 int select_max();
 cudaError_t launch_surrogate_chi2(int n_conf, int n_q, const float *z, int ld, const double *mean, const double *stdv,
-                                  const double *target, const double *w, double *chi2, cudaStream_t s);
+                                  const double *base, int ld_base, const double *target, const double *w, double *chi2,
+                                  cudaStream_t s);
 cudaError_t launch_select_topk(int n, const double *chi2, int k, int32_t *top_idx, double *top_chi2, cudaStream_t s);
 cudaError_t launch_gather_rows(const void *src, int64_t row_bytes, const int32_t *idx, int64_t n_idx, void *dst,
                                cudaStream_t s);

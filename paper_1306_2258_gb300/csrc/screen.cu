@@ -2,9 +2,10 @@
 // target profile, keep the best k for exact re-scoring with the Debye kernels (Section I-A, Eq. 2;
 // the paper's high-throughput setting, Section I).  Not part of the paper's method itself.
 //
-//   k_surrogate_chi2  one warp per conformer: chi2_c = sum_q w_q (exp(z_cq s_q + m_q) - T_q)^2, the
-//                     network's standardized log-profile z mapped back by (m, s); FP64, lane-strided
-//                     partial sums reduced in a fixed butterfly order (deterministic)
+//   k_surrogate_chi2  one warp per conformer: chi2_c = sum_q w_q (B_cq exp(z_cq s_q + m_q) - T_q)^2, the
+//                     network's standardized log-profile z mapped back by (m, s) and times a base
+//                     profile B (either factor may be absent); FP64, lane-strided partial sums
+//                     reduced in a fixed butterfly order (deterministic)
 //   k_select_topk     one CTA: bitonic sort of (chi2, index) pairs in shared memory, ties broken by
 //                     the index and NaN ordered last, so the selection is unique; writes the first k
 //   k_gather_rows     dst[r] = src[idx[r]] for rows of a fixed byte size (the selected conformers'
@@ -24,15 +25,18 @@ constexpr int kSelectThreads = 1024;
 
 __global__ void k_surrogate_chi2(int n_conf, int n_q, const float *__restrict__ z, int ld,
                                  const double *__restrict__ mean, const double *__restrict__ stdv,
-                                 const double *__restrict__ target, const double *__restrict__ w,
-                                 double *__restrict__ chi2)
+                                 const double *__restrict__ base, int ld_base, const double *__restrict__ target,
+                                 const double *__restrict__ w, double *__restrict__ chi2)
 {
     const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (warp >= n_conf) return;
-    const float *zc = z + (int64_t)warp * ld;
+    const float *zc = z ? z + (int64_t)warp * ld : nullptr;
+    const double *bc = base ? base + (int64_t)warp * ld_base : nullptr;
     double s = 0.0;
     for (int q = lane; q < n_q; q += 32) {
-        const double d = exp(fma((double)zc[q], stdv[q], mean[q])) - target[q];
+        double I = zc ? exp(fma((double)zc[q], stdv[q], mean[q])) : 1.0;
+        if (bc) I *= bc[q];
+        const double d = I - target[q];
         s = fma(w[q] * d, d, s);
     }
 #pragma unroll
@@ -111,11 +115,13 @@ __global__ void k_gather_rows(const unsigned char *__restrict__ src, int64_t row
 int select_max() { return 8192; }
 
 cudaError_t launch_surrogate_chi2(int n_conf, int n_q, const float *z, int ld, const double *mean, const double *stdv,
-                                  const double *target, const double *w, double *chi2, cudaStream_t s)
+                                  const double *base, int ld_base, const double *target, const double *w, double *chi2,
+                                  cudaStream_t s)
 {
     if (n_conf <= 0) return cudaSuccess;
     const int threads = 256, per = threads / 32;
-    k_surrogate_chi2<<<(n_conf + per - 1) / per, threads, 0, s>>>(n_conf, n_q, z, ld, mean, stdv, target, w, chi2);
+    k_surrogate_chi2<<<(n_conf + per - 1) / per, threads, 0, s>>>(n_conf, n_q, z, ld, mean, stdv, base, ld_base, target,
+                                                                  w, chi2);
     return cudaGetLastError();
 }
 
@@ -176,17 +182,20 @@ sas_status cuda_status(cudaError_t e, const char *what)
 extern "C" {
 
 sas_status sas_screen_select(int n_conf, int n_q, const float *z, int ld, const double *mean, const double *stdv,
-                             const double *target, const double *weights, int k, int32_t *top_idx, double *top_chi2,
-                             double *chi2_all, void *stream)
+                             const double *base, int ld_base, const double *target, const double *weights, int k,
+                             int32_t *top_idx, double *top_chi2, double *chi2_all, void *stream)
 {
     if (n_conf < 1 || n_conf > select_max()) return set_error(SAS_ERR_INVALID_ARG, "n_conf must be in [1, 8192]");
-    if (n_q < 1 || ld < n_q) return set_error(SAS_ERR_INVALID_ARG, "need n_q >= 1 and ld >= n_q");
+    if (n_q < 1) return set_error(SAS_ERR_INVALID_ARG, "need n_q >= 1");
+    if (!z && !base) return set_error(SAS_ERR_INVALID_ARG, "z and base cannot both be NULL");
+    if ((z && ld < n_q) || (base && ld_base < n_q)) return set_error(SAS_ERR_INVALID_ARG, "need ld, ld_base >= n_q");
     if (k < 1 || k > n_conf) return set_error(SAS_ERR_INVALID_ARG, "k must be in [1, n_conf]");
-    if (!dev_ptr(z) || !dev_ptr(mean) || !dev_ptr(stdv) || !dev_ptr(target) || !dev_ptr(weights) ||
-        !dev_ptr(top_idx) || !dev_ptr(chi2_all) || (top_chi2 && !dev_ptr(top_chi2)))
+    if ((z && (!dev_ptr(z) || !dev_ptr(mean) || !dev_ptr(stdv))) || (base && !dev_ptr(base)) || !dev_ptr(target) ||
+        !dev_ptr(weights) || !dev_ptr(top_idx) || !dev_ptr(chi2_all) || (top_chi2 && !dev_ptr(top_chi2)))
         return set_error(SAS_ERR_INVALID_ARG, "every buffer must be device memory (top_chi2 may be NULL)");
     cudaStream_t s = (cudaStream_t)stream;
-    sas_status st = cuda_status(launch_surrogate_chi2(n_conf, n_q, z, ld, mean, stdv, target, weights, chi2_all, s),
+    sas_status st = cuda_status(launch_surrogate_chi2(n_conf, n_q, z, ld, mean, stdv, base, ld_base, target, weights,
+                                                      chi2_all, s),
                                 "surrogate chi2");
     if (st != SAS_OK) return st;
     return cuda_status(launch_select_topk(n_conf, chi2_all, k, top_idx, top_chi2, s), "top-k selection");

@@ -179,6 +179,20 @@ class Profile:
         return (h[0], d[0]) if single else (h, d)
 
 
+    def binned(self, hist, type_counts, n_bins: int = 256, r_max: float = 120.0, stream=None):
+        """Binned Debye profiles [B, n_q] float64 of pair histograms hist [B, P, n_bins] (every pair at
+        its bin centre; sas_binned_profile) of molecules with type_counts[t] atoms of type t."""
+        h = hist if isinstance(hist, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(hist))
+        single = h.ndim == 2
+        if single:
+            h = h.unsqueeze(0)
+        h = h.to(torch.int32).contiguous()
+        B = int(h.shape[0])
+        out = torch.empty((B, self.n_q), dtype=torch.float64, device=h.device)
+        _lib.sas_binned_profile(self._ctx, h, B, n_bins, r_max, np.asarray(type_counts, np.int64), out, stream)
+        return out[0] if single else out
+
+
 class DebyeFunction(torch.autograd.Function):
     """I = DebyeFunction.apply(coords, profile, types): differentiable in coords.
 

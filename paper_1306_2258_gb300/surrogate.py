@@ -9,8 +9,9 @@ drives the loop and keeps checkpoints.
 
     python -m paper_1306_2258_gb300.surrogate [--conformers 4096] [--atoms 2000] [--epochs 60]
 
-prints one JSON report (surrogate error against exact profiles, the binned-sinc baseline
-computed from the same histograms, screen recall and timings).
+prints one JSON report (surrogate error against exact profiles, the binned Debye baseline computed
+from the same histograms, both screens' recall and timings).  By default the network learns the
+residual log I - log I_binned, a correction of the baseline.
 """
 from __future__ import annotations
 
@@ -115,6 +116,14 @@ class SurrogateMLP:
         _lib.sas_mlp_grads(self._h, x, t, int(x.shape[0]), g, loss)
         return float(loss[0]), g
 
+    def read_buffer(self, which: int, batch: int) -> np.ndarray:
+        """Rows [0, batch) of an intermediate tensor of the last passes (_lib.SAS_MLP_BUF_*), float32."""
+        width = {_lib.SAS_MLP_BUF_XB: self.n_in, _lib.SAS_MLP_BUF_Y: self.n_out, _lib.SAS_MLP_BUF_DY: self.n_out,
+                 _lib.SAS_MLP_BUF_DYB: self.n_out}.get(which, self.h)
+        out = np.empty((batch, width), np.float32)
+        _lib.sas_mlp_read_buffer(self._h, which, batch, out)
+        return out
+
     def predict(self, x) -> torch.Tensor:
         xt = torch.as_tensor(x).float().contiguous()
         out = torch.empty((xt.shape[0], self.n_out), dtype=torch.float32, device=xt.device)
@@ -156,27 +165,6 @@ def histogram_features(hist: np.ndarray, totals: np.ndarray) -> np.ndarray:
     return h.reshape(h.shape[0], -1)
 
 
-def binned_sinc_profiles(hist: np.ndarray, types: np.ndarray, coef: np.ndarray, q: np.ndarray,
-                         n_bins: int = N_BINS, r_max: float = R_MAX) -> np.ndarray:
-    """The method without the network: the Debye sum over the histogram with every pair at its bin
-    centre, I(q) ~ sum_t n_t f_t^2 + sum_p 2 f_a f_b sum_k c_pk sinc(q r_k).  Float64, host."""
-    T = coef.shape[0]
-    s = q / (4 * math.pi)
-    F = coef[:, 8][:, None] + np.sum(coef[:, 0:4][:, :, None] * np.exp(-coef[:, 4:8][:, :, None] * s ** 2), axis=1)
-    nt = np.bincount(types, minlength=T).astype(np.float64)
-    diag = np.sum(nt[:, None] * F ** 2, axis=0)
-    rk = (np.arange(n_bins) + 0.5) * (r_max / n_bins)
-    x = q[:, None] * rk[None, :]
-    sinc = np.where(x == 0, 1.0, np.sin(x) / np.where(x == 0, 1.0, x))   # [Q, n_bins]
-    out = np.tile(diag, (hist.shape[0], 1))
-    p = 0
-    for a in range(T):
-        for b in range(a, T):
-            out += 2 * (F[a] * F[b])[None, :] * (hist[:, p, :].astype(np.float64) @ sinc.T)
-            p += 1
-    return out
-
-
 # ----------------------------------------------------------------------------------------------
 # the pipeline
 # ----------------------------------------------------------------------------------------------
@@ -202,18 +190,23 @@ def train(net: SurrogateMLP, X: np.ndarray, Y: np.ndarray, epochs: int, batch: i
     return losses
 
 
-def screen_select(net: "SurrogateMLP", feats: torch.Tensor, ys: "Standardizer", target, weights, k: int):
-    """Rank conformers by the surrogate's chi^2 against `target` (weights w_q) and return (indices of the
-    k best in increasing chi^2, chi^2 of all), both device tensors; the chi^2, ranking and selection run
-    in the library (sas_screen_select)."""
-    dev = feats.device
-    pred = net.predict(feats)
-    n_conf, n_q = int(pred.shape[0]), int(pred.shape[1])
+def screen_select(net: "SurrogateMLP | None", feats: torch.Tensor | None, ys: "Standardizer | None", target,
+                  weights, k: int, base: torch.Tensor | None = None):
+    """Rank conformers by the chi^2 of a predicted profile against `target` (weights w_q) and return
+    (indices of the k best in increasing chi^2, chi^2 of all), both device tensors.  The prediction is
+    base * exp(network) when both are given (a network trained on the residual log I - log base),
+    exp(network) without a base, and the base alone without a network.  The chi^2, ranking and
+    selection run in the library (sas_screen_select)."""
+    pred = net.predict(feats) if net is not None else None
+    ref = pred if pred is not None else base
+    dev = ref.device
+    n_conf, n_q = int(ref.shape[0]), int(ref.shape[1])
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
     chi2 = torch.empty(n_conf, dtype=torch.float64, device=dev)
     top = torch.empty(k, dtype=torch.int32, device=dev)
-    _lib.sas_screen_select(n_conf, n_q, pred, pred.stride(0), d(ys.mean), d(ys.std), d(target), d(weights), k, top,
-                           None, chi2)
+    mean, std = (d(ys.mean), d(ys.std)) if pred is not None else (None, None)
+    _lib.sas_screen_select(n_conf, n_q, pred, pred.stride(0) if pred is not None else 0, mean, std,
+                           base, base.stride(0) if base is not None else 0, d(target), d(weights), k, top, None, chi2)
     return top, chi2
 
 
@@ -224,79 +217,101 @@ def gather_conformers(X: torch.Tensor, idx: torch.Tensor) -> torch.Tensor:
     return out
 
 
+def _rel_err_stats(I, I_exact):
+    e = np.abs(I - I_exact) / I_exact
+    return {"median": float(np.median(e)), "p95": float(np.percentile(e, 95)), "max": float(e.max())}
+
+
+def _screen_report(top, chi, chi_exact, I_top, target, wq):
+    """What a screen found: the selected conformers re-scored exactly, against the exact ranking."""
+    rank_exact = np.argsort(chi_exact)
+    chi_top = np.sum(wq * (I_top - target) ** 2, axis=1)
+    found = int(top[np.argmin(chi_top)])
+    k = top.size
+    return {"top_k": int(k), "found": found, "exact_rank_of_found": int(np.where(rank_exact == found)[0][0]),
+            "recall_of_exact_top10_in_top_k": float(np.mean(np.isin(rank_exact[:10], top))),
+            "recall_of_exact_top_k": float(np.mean(np.isin(rank_exact[:k], top))),
+            "spearman_rank_corr": float(np.corrcoef(np.argsort(np.argsort(chi)),
+                                                    np.argsort(np.argsort(chi_exact)))[0, 1])}
+
+
 def run_screen(n_conf: int = 4096, n_atoms: int = 2000, n_train: int | None = None, epochs: int = 60,
-               batch: int = 256, lr: float = 1e-3, hidden: int = 512, top_frac: float = 0.05, seed: int = 0):
-    """Configuration 5 end to end; returns a report dict."""
+               batch: int = 256, lr: float = 1e-3, hidden: int = 512, top_frac: float = 0.05, seed: int = 0,
+               residual: bool = True):
+    """Configuration 5 end to end; returns a report dict.
+
+    The method without the network is the binned Debye sum over the same histograms
+    (sas_binned_profile).  With `residual` the network learns log I - log I_binned, so its profile is
+    I_binned exp(prediction): a correction of the baseline.  Both screens (network and baseline)
+    rank all conformers against one target and re-score the same number k of them exactly."""
     t0 = time.perf_counter()
     w = wl.c5_ensemble(n_conf=n_conf, n=n_atoms)
     n_train = n_train if n_train is not None else n_conf - n_conf // 8
     types = w["base"].types
     coef, q = w["coef"], w["q"]
     T = coef.shape[0]
+    nt = np.bincount(types, minlength=T)
     X = torch.as_tensor(w["conformers"], device="cuda")
     t_gen = time.perf_counter() - t0
     prof = Profile(coef, q)
     tt = torch.as_tensor(types, device="cuda")
-    # exact profiles and histograms of every conformer (in slices to bound device memory)
+    # exact profiles, histograms and binned profiles of every conformer (slices bound device memory)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     I_exact = torch.cat([prof(X[s:s + 1024], tt) for s in range(0, n_conf, 1024)]).cpu().numpy()
     torch.cuda.synchronize()
     t_exact_all = time.perf_counter() - t1
-    hist = torch.cat([prof.pair_histogram(X[s:s + 1024], tt, N_BINS, R_MAX)[0]
-                      for s in range(0, n_conf, 1024)]).cpu().numpy()
-    feats = histogram_features(hist, pair_totals(types, T))
-    logI = np.log(I_exact)
-    xs = Standardizer(feats[:n_train])
-    ys = Standardizer(logI[:n_train])
-    Xn = xs(feats).astype(np.float32)
-    Yn = ys(logI).astype(np.float32)
-    net = SurrogateMLP(Xn.shape[1], hidden, q.size, max_batch=max(batch, 1024), seed=seed)
+    hist_d = torch.cat([prof.pair_histogram(X[s:s + 1024], tt, N_BINS, R_MAX)[0] for s in range(0, n_conf, 1024)])
+    torch.cuda.synchronize()
     t2 = time.perf_counter()
+    I_bin_d = prof.binned(hist_d, nt, N_BINS, R_MAX)
+    torch.cuda.synchronize()
+    t_binned = time.perf_counter() - t2
+    I_bin = I_bin_d.cpu().numpy()
+    hist = hist_d.cpu().numpy()
+    feats = histogram_features(hist, pair_totals(types, T))
+    logY = np.log(I_exact) - (np.log(I_bin) if residual else 0.0)
+    xs = Standardizer(feats[:n_train])
+    ys = Standardizer(logY[:n_train])
+    Xn = xs(feats).astype(np.float32)
+    Yn = ys(logY).astype(np.float32)
+    net = SurrogateMLP(Xn.shape[1], hidden, q.size, max_batch=max(batch, 1024), seed=seed)
+    t3 = time.perf_counter()
     losses = train(net, Xn[:n_train], Yn[:n_train], epochs, batch, lr, seed)
     torch.cuda.synchronize()
-    t_train = time.perf_counter() - t2
-    # held-out error of the surrogate and of the binned-sinc baseline (same histograms)
+    t_train = time.perf_counter() - t3
+    # held-out error of the network's profile and of the baseline alone
     test = slice(n_train, n_conf)
-    I_sur = np.exp(ys.inverse(net.predict(torch.as_tensor(Xn[test], device="cuda")).double().cpu().numpy()))
-    I_bin = binned_sinc_profiles(hist[test], types, coef, q)
-    err_sur = np.abs(I_sur - I_exact[test]) / I_exact[test]
-    err_bin = np.abs(I_bin - I_exact[test]) / I_exact[test]
-    # screen: rank all conformers by surrogate chi^2 against a target, re-score the best exactly
+    corr = np.exp(ys.inverse(net.predict(torch.as_tensor(Xn[test], device="cuda")).double().cpu().numpy()))
+    I_sur = corr * (I_bin[test] if residual else 1.0)
+    # screens against a target profile: the network's and the baseline's, the same exact budget k
     target = prof(torch.as_tensor(w["target"].coords, device="cuda"), tt).cpu().numpy()
     wq = 1.0 / target ** 2
-    torch.cuda.synchronize()
-    t3 = time.perf_counter()
-    k = max(1, int(round(top_frac * n_conf)))
-    top_t, chi_sur_t = screen_select(net, torch.as_tensor(Xn, device="cuda"), ys, target, wq, k)
-    Xtop = gather_conformers(X, top_t)
-    I_top = prof(Xtop, tt).cpu().numpy()
-    top = top_t.cpu().numpy()
-    chi_sur = chi_sur_t.cpu().numpy()
-    chi_top = np.sum(wq * (I_top - target) ** 2, axis=1)
-    best_screen = int(top[np.argmin(chi_top)])
-    torch.cuda.synchronize()
-    t_screen = time.perf_counter() - t3   # histograms assumed available, as for any candidate pool
     chi_exact = np.sum(wq * (I_exact - target) ** 2, axis=1)
-    rank_exact = np.argsort(chi_exact)
-    true_best = int(rank_exact[0])
-    rank_of_found = int(np.where(rank_exact == best_screen)[0][0])
-    recall10 = float(np.mean(np.isin(rank_exact[:10], top)))
-    sp = np.corrcoef(np.argsort(np.argsort(chi_sur)), np.argsort(np.argsort(chi_exact)))[0, 1]
+    k = max(1, int(round(top_frac * n_conf)))
+    feats_d = torch.as_tensor(Xn, device="cuda")
+    screens, seconds = {}, {}
+    for name, use_net in (("network", True), ("binned_baseline", False)):
+        torch.cuda.synchronize()
+        t4 = time.perf_counter()
+        top_t, chi_t = screen_select(net if use_net else None, feats_d if use_net else None, ys if use_net else None,
+                                     target, wq, k, base=I_bin_d if (residual or not use_net) else None)
+        I_top = prof(gather_conformers(X, top_t), tt).cpu().numpy()
+        torch.cuda.synchronize()
+        seconds[name] = time.perf_counter() - t4   # histograms (and binned profiles) assumed available
+        screens[name] = _screen_report(top_t.cpu().numpy(), chi_t.cpu().numpy(), chi_exact, I_top, target, wq)
     net.close()
     prof.close()
     return {
         "conformers": n_conf, "atoms": n_atoms, "q": int(q.size), "train": n_train, "test": n_conf - n_train,
-        "epochs": epochs, "batch": batch, "lr": lr, "hidden": hidden,
+        "epochs": epochs, "batch": batch, "lr": lr, "hidden": hidden, "residual": residual,
         "final_train_loss": losses[-1], "first_train_loss": losses[0],
-        "surrogate_rel_err": {"median": float(np.median(err_sur)), "p95": float(np.percentile(err_sur, 95)),
-                              "max": float(err_sur.max())},
-        "binned_sinc_rel_err": {"median": float(np.median(err_bin)), "p95": float(np.percentile(err_bin, 95)),
-                                "max": float(err_bin.max())},
-        "screen": {"top_k": k, "true_best": true_best, "found": best_screen, "exact_rank_of_found": rank_of_found,
-                   "recall_of_exact_top10_in_top_k": recall10, "spearman_rank_corr": float(sp),
-                   "exact_evaluations": k, "exact_evaluations_without_surrogate": n_conf},
-        "seconds": {"generate": t_gen, "exact_all": t_exact_all, "train": t_train, "screen": t_screen},
+        "surrogate_rel_err": _rel_err_stats(I_sur, I_exact[test]),
+        "binned_sinc_rel_err": _rel_err_stats(I_bin[test], I_exact[test]),
+        "true_best": int(np.argmin(chi_exact)), "exact_evaluations": k, "exact_evaluations_without_screen": n_conf,
+        "screen": screens,
+        "seconds": {"generate": t_gen, "exact_all": t_exact_all, "binned_all": t_binned, "train": t_train,
+                    "screen_network": seconds["network"], "screen_binned": seconds["binned_baseline"]},
     }
 
 
@@ -306,8 +321,10 @@ def main():
     ap.add_argument("--atoms", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--hidden", type=int, default=512)
+    ap.add_argument("--absolute", action="store_true", help="train on log I itself instead of log I - log I_binned")
     args = ap.parse_args()
-    print(json.dumps(run_screen(args.conformers, args.atoms, epochs=args.epochs, hidden=args.hidden)))
+    print(json.dumps(run_screen(args.conformers, args.atoms, epochs=args.epochs, hidden=args.hidden,
+                                residual=not args.absolute)))
 
 
 if __name__ == "__main__":

@@ -124,12 +124,28 @@ def test_checkpoint_resume_is_bit_exact(tmp_path):
 
 
 def test_screen_finds_good_conformers_with_5_percent_of_exact_evaluations():
-    """What the network buys: ranking the ensemble by the surrogate and re-scoring only its best
-    5% with the exact kernel still lands on a conformer from the exact top 5%, for 1/20 of the
-    exact evaluations; its ranking correlates with the exact one."""
+    """What the screen buys: ranking the ensemble by the network's correction of the binned profiles
+    and re-scoring only its best 5% with the exact kernel still lands on a conformer from the exact top
+    5%, for 1/20 of the exact evaluations; its ranking correlates with the exact one."""
     r = run_screen(n_conf=768, n_atoms=600, epochs=40, hidden=128, batch=64, seed=3)
-    s = r["screen"]
-    assert r["final_train_loss"] < 0.1 * r["first_train_loss"]
+    s = r["screen"]["network"]
+    assert r["final_train_loss"] < 0.5 * r["first_train_loss"]
     assert s["exact_rank_of_found"] < 0.05 * r["conformers"]
     assert s["spearman_rank_corr"] > 0.5
-    assert s["exact_evaluations"] * 20 <= s["exact_evaluations_without_surrogate"] + 20
+    assert r["exact_evaluations"] * 20 <= r["exact_evaluations_without_screen"] + 20
+
+
+def test_network_gains_over_the_binned_debye_sum_at_the_same_exact_budget():
+    """What the trained network gains over the method without it.  The method without the network is
+    the Debye sum over the same exact histograms with every pair at its bin centre
+    (sas_binned_profile).  The network is trained on the residual log I - log I_binned, so it can
+    only correct the baseline.  On held-out conformers its profiles are closer to the exact ones
+    than the baseline's, and at the same budget of exact re-scores (the best 5% by each ranking)
+    its screen recalls at least as much of the exact top 5% and ranks closer to the exact order."""
+    r = run_screen(n_conf=768, n_atoms=600, epochs=40, hidden=128, batch=64, seed=3)
+    net, base = r["screen"]["network"], r["screen"]["binned_baseline"]
+    assert r["surrogate_rel_err"]["median"] <= 0.75 * r["binned_sinc_rel_err"]["median"]
+    assert r["surrogate_rel_err"]["p95"] <= r["binned_sinc_rel_err"]["p95"]
+    assert net["recall_of_exact_top_k"] >= base["recall_of_exact_top_k"]
+    assert net["spearman_rank_corr"] >= base["spearman_rank_corr"]
+    assert net["exact_rank_of_found"] <= base["exact_rank_of_found"]

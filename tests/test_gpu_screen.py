@@ -1,5 +1,6 @@
 """GPU screening kernels (sas_screen_select, sas_gather_rows) against plain NumPy: the surrogate chi^2
-in FP64, the unique (chi^2, index) order with NaN last, and the row gather."""
+in FP64 (a network's log-profile, a base profile, or the base times the network's correction), the
+unique (chi^2, index) order with NaN last, and the row gather."""
 import numpy as np
 import pytest
 import torch
@@ -16,14 +17,15 @@ def _cuda():
     _lib.load()
 
 
-def _select(z, mean, std, target, w, k):
+def _select(z, mean, std, target, w, k, base=None):
     d = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).cuda()
-    zt = torch.as_tensor(z).cuda()
-    chi2 = torch.empty(z.shape[0], dtype=torch.float64, device="cuda")
+    n_conf, n_q = (z if z is not None else base).shape
+    zt = torch.as_tensor(z).cuda() if z is not None else None
+    bt = d(base) if base is not None else None
+    chi2 = torch.empty(n_conf, dtype=torch.float64, device="cuda")
     top = torch.empty(k, dtype=torch.int32, device="cuda")
     topc = torch.empty(k, dtype=torch.float64, device="cuda")
-    _lib.sas_screen_select(z.shape[0], z.shape[1], zt, z.shape[1], d(mean), d(std), d(target), d(w), k, top, topc,
-                           chi2)
+    _lib.sas_screen_select(n_conf, n_q, zt, n_q, d(mean), d(std), bt, n_q, d(target), d(w), k, top, topc, chi2)
     return top.cpu().numpy(), topc.cpu().numpy(), chi2.cpu().numpy()
 
 
@@ -40,6 +42,24 @@ def test_screen_select_matches_numpy(n_conf, n_q, k):
     order = np.lexsort((np.arange(n_conf), chi2))   # by chi2, then index (the kernel's unique order)
     assert np.array_equal(top, order[:k])
     assert np.array_equal(topc, chi2[order[:k]])
+
+
+@pytest.mark.parametrize("with_z", [True, False])
+def test_screen_select_with_a_base_profile_matches_numpy(with_z):
+    """P = base * exp(z s + m) (a correction to a base profile) and P = base alone."""
+    rng = np.random.default_rng(17)
+    n_conf, n_q, k = 3000, 101, 150
+    base = np.exp(rng.uniform(2, 8, n_q) + 0.3 * rng.standard_normal((n_conf, n_q)))
+    z = (0.05 * rng.standard_normal((n_conf, n_q))).astype(np.float32) if with_z else None
+    mean, std = rng.uniform(-0.01, 0.01, n_q), rng.uniform(0.01, 0.1, n_q)
+    target = base[11] * 1.01
+    w = 1.0 / target ** 2
+    top, topc, chi2 = _select(z, mean, std, target, w, k, base=base)
+    P = base * (np.exp(z.astype(np.float64) * std + mean) if with_z else 1.0)
+    ref = np.sum(w * (P - target) ** 2, axis=1)
+    assert np.allclose(chi2, ref, rtol=1e-12, atol=0)
+    order = np.lexsort((np.arange(n_conf), chi2))
+    assert np.array_equal(top, order[:k])
 
 
 def test_screen_select_ties_by_index_and_nan_last():
@@ -64,12 +84,17 @@ def test_select_and_gather_limits():
     d = torch.ones(3, dtype=torch.float64, device="cuda")
     top = torch.empty(2, dtype=torch.int32, device="cuda")
     chi2 = torch.empty(2, dtype=torch.float64, device="cuda")
+    b = torch.ones((2, 3), dtype=torch.float64, device="cuda")
     with pytest.raises(_lib.SasError):   # k > n_conf
-        _lib.sas_screen_select(2, 3, z, 3, d, d, d, d, 3, top, None, chi2)
+        _lib.sas_screen_select(2, 3, z, 3, d, d, None, 0, d, d, 3, top, None, chi2)
     with pytest.raises(_lib.SasError):   # host buffer
-        _lib.sas_screen_select(2, 3, z, 3, d.cpu(), d, d, d, 1, top, None, chi2)
+        _lib.sas_screen_select(2, 3, z, 3, d.cpu(), d, None, 0, d, d, 1, top, None, chi2)
     with pytest.raises(_lib.SasError):   # too many conformers for one CTA
-        _lib.sas_screen_select(8193, 3, z, 3, d, d, d, d, 1, top, None, chi2)
+        _lib.sas_screen_select(8193, 3, z, 3, d, d, None, 0, d, d, 1, top, None, chi2)
+    with pytest.raises(_lib.SasError):   # neither a log-profile nor a base
+        _lib.sas_screen_select(2, 3, None, 0, d, d, None, 0, d, d, 1, top, None, chi2)
+    with pytest.raises(_lib.SasError):   # base row stride too short
+        _lib.sas_screen_select(2, 3, None, 0, None, None, b, 2, d, d, 1, top, None, chi2)
 
 
 @pytest.mark.parametrize("shape", [(50, 2000, 3), (7, 3, 3), (1, 1, 1)])

@@ -64,3 +64,27 @@ def test_first_adam_step_is_minus_lr_sign():
     for k in p:
         step = p1[k] - p0[k]
         np.testing.assert_allclose(step, -1e-3 * g[k] / (np.abs(g[k]) + 1e-8), rtol=1e-12, atol=1e-18)
+
+
+def test_forward_and_gradients_match_a_float64_torch_chain(monkeypatch):
+    """With the bfloat16 rounding switched off, the reference is the plain network: torch's float64
+    linear / exact-erf GELU chain and its autograd gradients, at the surrogate's full width."""
+    import torch.nn.functional as F
+    monkeypatch.setattr(mlp, "bf16", lambda a: np.asarray(a, dtype=np.float64))
+    rng = np.random.default_rng(21)
+    n_in, h, n_out, B = 3840, 512, 101, 16
+    p = {"W1": rng.uniform(-1, 1, (h, n_in)) * math.sqrt(3 / n_in), "b1": rng.standard_normal(h) * 0.1,
+         "W2": rng.uniform(-1, 1, (h, h)) * math.sqrt(3 / h), "b2": rng.standard_normal(h) * 0.1,
+         "W3": rng.uniform(-1, 1, (n_out, h)) * math.sqrt(3 / h), "b3": rng.standard_normal(n_out) * 0.1}
+    x, t = rng.standard_normal((B, n_in)), rng.standard_normal((B, n_out))
+    loss, g, y = mlp.loss_and_grads(p, x, t)
+    tp = {k: torch.tensor(v, dtype=torch.float64, requires_grad=True) for k, v in p.items()}
+    a1 = F.gelu(F.linear(torch.tensor(x), tp["W1"], tp["b1"]), approximate="none")
+    a2 = F.gelu(F.linear(a1, tp["W2"], tp["b2"]), approximate="none")
+    yt = F.linear(a2, tp["W3"], tp["b3"])
+    lt = F.mse_loss(yt, torch.tensor(t))
+    lt.backward()
+    np.testing.assert_allclose(y, yt.detach().numpy(), rtol=1e-12, atol=1e-13)
+    assert loss == pytest.approx(lt.item(), rel=1e-13)
+    for k in p:
+        np.testing.assert_allclose(g[k], tp[k].grad.numpy(), rtol=1e-10, atol=1e-16), k
