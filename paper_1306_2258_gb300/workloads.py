@@ -167,6 +167,31 @@ def double_helix_rod(seed: int, n_steps: int = 1500, rise: float = 3.4,
     return Molecule(xyz, types, n_types, "helix_rod")
 
 
+def cubic_lattice(n_side: int, spacing: float, n_types: int, seed: int) -> Molecule:
+    """Simple cubic lattice of n_side^3 atoms, ``spacing`` Å apart, centred on the origin; types
+    i.i.d. uniform.  Every squared distance is spacing^2 times an integer, so very many pairs
+    share one distance exactly: a crystalline stress case for the FP32 recurrence, where the
+    rounding of equal pairs can add up coherently.  With spacing 6.5 Å the (100) reflection
+    2 pi / spacing = 0.967 Å^-1 falls inside a 0-1 Å^-1 grid."""
+    rng = np.random.default_rng(seed)
+    g = (np.arange(n_side, dtype=np.float64) - 0.5 * (n_side - 1)) * spacing
+    xyz = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3).copy()
+    types = rng.integers(0, n_types, size=xyz.shape[0]).astype(np.int32)
+    return Molecule(xyz, types, n_types, f"lattice{n_side}")
+
+
+def spherical_shell(n: int, radius: float, n_types: int, seed: int) -> Molecule:
+    """``n`` atoms uniformly at random on one sphere of ``radius`` Å (a thin hollow shell, like
+    an empty viral capsid), types i.i.d. uniform.  Its amplitude is close to sum_t n_t f_t
+    sinc(q radius), so I(q) falls by about 1/n at the zeros of sinc(q radius): deep minima where
+    the pair sum cancels almost completely."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((n, 3))
+    xyz = radius * v / np.linalg.norm(v, axis=1, keepdims=True)
+    types = rng.integers(0, n_types, size=n).astype(np.int32)
+    return Molecule(xyz, types, n_types, f"shell{n}")
+
+
 def subsample(mol: Molecule, n: int, seed: int) -> Molecule:
     """Seeded uniform sample of ``n`` atoms without replacement, types kept,
     original order kept."""

@@ -71,3 +71,15 @@ def test_q_grid_endpoints():
     q = wl.q_grid(0.0, 1.0, 201)
     assert q[0] == 0.0 and q[-1] == 1.0 and q.size == 201
     np.testing.assert_allclose(np.diff(q), 0.005, rtol=1e-9)
+
+
+def test_cubic_lattice_and_spherical_shell_shapes():
+    lat = wl.cubic_lattice(5, 6.5, 5, 3)
+    assert lat.n == 125 and lat.types.min() >= 0 and lat.types.max() < 5
+    np.testing.assert_allclose(lat.coords.mean(axis=0), 0.0, atol=1e-12)
+    d2 = np.sum((lat.coords[:, None] - lat.coords[None]) ** 2, axis=-1) / 6.5 ** 2
+    np.testing.assert_allclose(d2, np.round(d2), atol=1e-9)       # squared distances on the integer lattice
+    shell = wl.spherical_shell(2000, 100.0, 5, 4)
+    np.testing.assert_allclose(np.linalg.norm(shell.coords, axis=1), 100.0, rtol=1e-12)
+    assert np.linalg.norm(shell.coords.mean(axis=0)) < 10.0       # uniform over the sphere
+    assert np.array_equal(shell.coords, wl.spherical_shell(2000, 100.0, 5, 4).coords)
