@@ -604,7 +604,7 @@ def run_strong(args):
     return 0
 
 
-PROFILE_CASES = ("histogram", "gradient", "gradient_recurrence", "gemm", "atomic", "quadrature", "binned")
+PROFILE_CASES = ("histogram", "gradient", "gradient_recurrence", "gemm", "atomic", "quadrature", "binned", "rod")
 
 
 def run_profile_case(args):
@@ -616,6 +616,7 @@ def run_profile_case(args):
                    the tabulated pair weight)
       gradient_recurrence  the same with the sums over q by the recurrence (SAS_OPT_ADJOINT 1)
       binned       the Debye sum at bin centres over the histograms of 4,096 ensemble conformers
+      rod          the 30,000-atom double-helix rod x 101 q (the benchmark row's profile)
       gemm         4096 x 4096 x 4096 bfloat16 -> float32 on the tcgen05 GEMM
       atomic       20,000-atom globule x 201 q with a per-atom form-factor table
       quadrature   20,000-atom globule x 65 q (0..0.32 A^-1), orientation average of Eq. 1 on every q
@@ -651,6 +652,15 @@ def run_profile_case(args):
             chi2, _, _ = p4.chi2_grad(X4, tt, T, 1.0 / T ** 2)
         report["chi2_sum_" + case] = float(chi2.sum())
         p4.close()
+    if "rod" in cases:
+        w3 = wl.c3_rod()
+        p = Profile(w3.coef, w3.q)
+        x3 = torch.as_tensor(w3.mol.coords, device=dev)
+        t3 = torch.as_tensor(w3.mol.types, device=dev)
+        for _ in range(2):
+            I3 = p(x3, t3)
+        report["rod_I0"] = float(I3[0])
+        p.close()
     if "binned" in cases:
         c5 = wl.c5_ensemble()
         X5 = torch.as_tensor(c5["conformers"], device=dev)
