@@ -320,6 +320,19 @@ def run_rows(dev, stream):
     rows["chi2_gradient_c4"]["ms_deterministic"] = _timed(lambda: p.chi2_grad(X4, tt, target, wq, stream), stream)
     p.close()
 
+    # the same refinement batch with per-atom form factors (a water-layer table per conformer): the
+    # vector-Jacobian product of the per-atom profile
+    ffa4 = torch.as_tensor(np.stack([wl.atomic_form_factor_table(n4, c4["q"], 780 + b) for b in range(B4)]),
+                           device=dev)
+    gI4 = torch.as_tensor(np.random.default_rng(781).standard_normal((B4, c4["q"].size)), device=dev) / target
+    p = Profile(c4["coef"], c4["q"], "mixed")
+    ms = _timed(lambda: p.vjp_atomic(X4, ffa4, gI4, stream), stream)
+    rows["vjp_atomic_c4"] = {"workload": f"{B4} conformers x {n4} atoms x {c4['q'].size} q, per-atom form factors, "
+                                         "vector-Jacobian product", "ms": ms, "value": pq / (ms / 1e3),
+                             "unit": "pair·q/s", "gradients_per_s": B4 / (ms / 1e3)}
+    p.close()
+    del ffa4
+
     # ensemble (configuration 5): exact profiles, pair histograms, surrogate epoch and screen
     c5 = wl.c5_ensemble()
     X5 = torch.as_tensor(c5["conformers"], device=dev)

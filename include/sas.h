@@ -189,6 +189,21 @@ sas_status sas_profile_atomic(sas_ctx *ctx, const void *coords, int coords_type,
                               const double *ff, double *I_out, void *stream);
 
 /*
+ * Vector-Jacobian product of the per-atom profile (the derivative of Eq. 2 with a form factor per
+ * atom and q, for refinement against data with a hydration layer or excluded volume, Section I-A
+ * after Eq. 2): grad_out[b][i] = sum_q grad_I[b][q] dI_b(q)/dx_i
+ *   = sum_{j != i} W_ij (x_i - x_j),  W_ij = 2 sum_q grad_I[q] f_i(q) f_j(q) (cos(q r) - sinc(q r)) / r^2,
+ * with the form factors held fixed.  coords [batch][n_atoms][3] float, ff [batch][n_q][n_atoms] as in
+ * sas_profile_atomic, grad_I [batch][n_q] double, grad_out [batch][n_atoms][3] float (host or device).
+ * The sums over q run in passes of at most 52 q by the FP32 recurrence with FP64 accumulation of the
+ * atom totals.  A SAS_MIXED, non-deterministic, unsharded context is needed (else UNSUPPORTED).
+ * Errors: INVALID_ARG (sizes, null pointers, non-finite coordinates or form factors), UNSUPPORTED,
+ * ALLOC, CUDA, TIMEOUT.
+ */
+sas_status sas_profile_vjp_atomic(sas_ctx *ctx, const float *coords, int64_t n_atoms, int64_t batch, const double *ff,
+                                  const double *grad_I, float *grad_out, void *stream);
+
+/*
  * Peak microbenchmarks of the current device (the denominators of the pair kernels' rooflines):
  * out[0] FP32 FMA lane operations/s (scalar FFMA), out[1] the same with packed f32x2 FMA (2 per
  * instruction and lane), out[2] MUFU sine operations/s (__sinf), out[3] FP64 FMA lane

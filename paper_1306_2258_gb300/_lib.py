@@ -35,7 +35,7 @@ EXPORTS = (
     "sas_mlp_param_count", "sas_mlp_set_state", "sas_mlp_get_state", "sas_mlp_forward", "sas_mlp_train_step",
     "sas_mlp_grads", "sas_gemm_bf16", "sas_screen_select", "sas_gather_rows", "sas_profile_atomic",
     "sas_measure_peaks", "sas_exact_sums", "sas_assemble_exact", "sas_mlp_read_buffer",
-    "sas_binned_profile",
+    "sas_binned_profile", "sas_profile_vjp_atomic",
 )
 
 
@@ -90,6 +90,7 @@ def load():
                 "sas_exact_sums": [_vp, _vp, _i64, _vp],
                 "sas_assemble_exact": [_vp, _vp, _i64, _vp, _vp],
                 "sas_binned_profile": [_vp, _vp, _i64, _int, ctypes.c_float, _vp, _vp, _vp],
+                "sas_profile_vjp_atomic": [_vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -217,6 +218,11 @@ def sas_profile_static(coords, types, n_atoms, n_types, ff_coef, q0, dq, n_q, I_
                                    float(q0), float(dq), int(n_q), ptr(I_out), stream_handle(stream))
     if st != SAS_OK:
         raise SasError(st, "sas_profile_static failed")
+
+
+def sas_profile_vjp_atomic(ctx, coords, n_atoms, batch, ff, grad_I, grad_out, stream=None):
+    check(load().sas_profile_vjp_atomic(ctx, ptr(coords), int(n_atoms), int(batch), ptr(ff), ptr(grad_I),
+                                        ptr(grad_out), stream_handle(stream)))
 
 
 def sas_binned_profile(ctx, hist, batch, n_bins, r_max, type_counts, I_out, stream=None):

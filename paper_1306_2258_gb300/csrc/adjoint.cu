@@ -318,6 +318,185 @@ __global__ void __launch_bounds__(kTile, 4)
     }
 }
 
+// ---- per-atom form factors ------------------------------------------------------------------------
+// The vector-Jacobian product of Eq. 2 with a form factor per atom and q: the pair weight becomes
+//   W_ij = (2 / r^2) (A - B / r),  A = sum_q a_i(q) f_j(q) cos(q r),  B = sum_q (a_i(q) / q) f_j(q) sin(q r),
+//   a_i(q) = g_q f_i(q),
+// so the per-q weight differs from pair to pair: one more packed multiply per pair and q than the
+// typed form.  Thread i's weights a_i sit in shared memory (AI: per float2 slot v the signed
+// (a(q_2v), a(q_2v)/q_2v, a(q_2v+1), a(q_2v+1)/q_2v+1), zero past the pass and at q = 0); the J pair's
+// form factors are one float4 per slot of the forward per-atom table FJ, which every thread of the
+// CTA reads at the same address (a broadcast through L1).  Passes of at most 52 q keep the weights of
+// a 128-atom tile within 52 KB.
+constexpr int kAtomAdjNV = 26;
+
+template <int NV>
+__device__ __forceinline__ void core_adj2_atomic(const AdjPair2 &p, const float4 *sa, const float4 *__restrict__ fj,
+                                                 float2 &abA, float2 &abB)
+{
+    float2 peA = p.eA0, ceA = p.eA1, poA = p.oA0, coA = p.oA1;
+    float2 peB = p.eB0, ceB = p.eB1, poB = p.oB0, coB = p.oB1;
+    float2 aeA, aoA, aeB, aoB;
+    {
+        const float4 a0 = sa[0], a1 = sa[kTile];
+        const float4 f0 = __ldg(fj), f1 = __ldg(fj + 1);
+        const float2 ae0 = make_float2(a0.x, a0.y), ao0 = make_float2(a0.z, a0.w);
+        const float2 ae1 = make_float2(a1.x, a1.y), ao1 = make_float2(a1.z, a1.w);
+        aeA = f2fma(f2mul(ae1, bc(f1.x)), ceA, f2mul(f2mul(ae0, bc(f0.x)), peA));
+        aoA = f2fma(f2mul(ao1, bc(f1.y)), coA, f2mul(f2mul(ao0, bc(f0.y)), poA));
+        aeB = f2fma(f2mul(ae1, bc(f1.z)), ceB, f2mul(f2mul(ae0, bc(f0.z)), peB));
+        aoB = f2fma(f2mul(ao1, bc(f1.w)), coB, f2mul(f2mul(ao0, bc(f0.w)), poB));
+    }
+#pragma unroll
+    for (int v = 1; v + 1 < NV; ++v) {   // block v+1 = (+/-)C block v + block v-1
+        const float4 a = sa[(v + 1) * kTile];
+        const float4 f = __ldg(fj + v + 1);
+        const float2 ae = make_float2(a.x, a.y), ao = make_float2(a.z, a.w);
+        const float2 CA = step_negative(v) ? p.CnA : p.CpA, CB = step_negative(v) ? p.CnB : p.CpB;
+        const float2 neA = f2fma(CA, ceA, peA), noA = f2fma(CA, coA, poA);
+        const float2 neB = f2fma(CB, ceB, peB), noB = f2fma(CB, coB, poB);
+        aeA = f2fma(f2mul(ae, bc(f.x)), neA, aeA);
+        aoA = f2fma(f2mul(ao, bc(f.y)), noA, aoA);
+        aeB = f2fma(f2mul(ae, bc(f.z)), neB, aeB);
+        aoB = f2fma(f2mul(ao, bc(f.w)), noB, aoB);
+        peA = ceA;
+        ceA = neA;
+        poA = coA;
+        coA = noA;
+        peB = ceB;
+        ceB = neB;
+        poB = coB;
+        coB = noB;
+    }
+    abA = f2add(aeA, aoA);
+    abB = f2add(aeB, aoB);
+}
+
+template <int NV, bool ZERO_START>
+__device__ __forceinline__ void run_adj2_atomic(const float4 *sxy, const float4 *szw, const float4 *sa,
+                                                const float4 *__restrict__ fjrows, float *gj, int jpairs,
+                                                const float4 xi, const Item &item, int tid, int lane, int jmask,
+                                                float2 qs_hi, float2 qs_lo, float2 dq_hi, float2 dq_lo, float2 &gx,
+                                                float2 &gy, float2 &gz)
+{
+    const float2 nX = bc(-xi.x), nY = bc(-xi.y), nZ = bc(-xi.z), wi = bc(xi.w);
+    const unsigned ih = item.i0 + tid;
+    const int kslot = lane >> 2;
+    if (jpairs <= 0) return;
+    AdjHead2 head;
+    setup_adj2_head(sxy[0], szw[0], nX, nY, nZ, wi, 0 > jmask, 1 > jmask, head);
+    for (int k = 0; k < jpairs; ++k) {
+        const int j = 2 * k;
+        AdjPair2 p;
+        setup_adj2_tail<ZERO_START>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
+                                    pair_hash(ih, item.j0 + j + 1), p);
+        const float2 y = head.y, w = head.w;
+        const bool more = k + 1 < jpairs;
+        const int kn = more ? k + 1 : k;
+        setup_adj2_head(sxy[kn], szw[kn], nX, nY, nZ, wi, more && j + 2 > jmask, more && j + 3 > jmask, head);
+        float2 abA, abB;
+        core_adj2_atomic<NV>(p, sa, fjrows + (int64_t)k * NV, abA, abB);
+        const float2 A = make_float2(abA.x, abB.x), B = make_float2(abA.y, abB.y);
+        const float2 y2 = f2mul(y, y);
+        const float2 nW = f2mul(f2mul(w, f2add(y2, y2)), f2fma(B, y, f2mul(A, bc(-1.f))));
+        const float4 pxy = sxy[k], pzw = szw[k];
+        const float2 dx = jdiff(make_float2(pxy.x, pxy.y), nX), dy = jdiff(make_float2(pxy.z, pxy.w), nY),
+                     dz = jdiff(make_float2(pzw.x, pzw.y), nZ);
+        gx = f2fma(nW, dx, gx);
+        gy = f2fma(nW, dy, gy);
+        gz = f2fma(nW, dz, gz);
+        const float2 fx = f2mul(nW, dx), fy = f2mul(nW, dy), fz = f2mul(nW, dz);
+        const float v[8] = {-fx.x, -fy.x, -fz.x, -fx.y, -fy.y, -fz.y, 0.f, 0.f};
+        const float tot = reduce_scatter8(v, lane);
+        if ((lane & 3) == 0 && kslot < 6) atomicAdd(&gj[3 * j + kslot], tot);
+    }
+}
+
+// One work item per CTA at a time (the forward per-atom schedule: one type group, items per pass);
+// totals into G [batch][slot][3] with FP64 atomics as in k_debye_adjoint.
+template <int NV>
+__global__ void __launch_bounds__(kTile, 2)
+    k_debye_adjoint_atomic(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items, int n_items,
+                           QChunks qc, const float4 *__restrict__ AI, const float4 *__restrict__ FJ,
+                           double *__restrict__ G, int jcap, int *__restrict__ ticket)
+{
+    extern __shared__ float4 smem[];
+    float4 *sxy = smem;                                          // [jcap / 2]
+    float4 *szw = smem + jcap / 2;                               // [jcap / 2]
+    float4 *sa = smem + jcap;                                    // [NV][kTile]
+    float *gj = reinterpret_cast<float *>(sa + NV * kTile);      // [jcap][3]
+    __shared__ int next_item;
+    const int tid = threadIdx.x, lane = tid & 31;
+    int it = blockIdx.x;
+    while (it < n_items) {
+        const Item item = items[it];
+        const float4 *Xb = X + (int64_t)item.batch * npad;
+        const int ch = item.chunk;
+        __syncthreads();
+        if (tid == 0) next_item = (int)gridDim.x + atomicAdd(ticket, 1);
+        const int jpairs = (item.jlen + 1) >> 1;
+        for (int k = tid; k < jpairs; k += kTile) {
+            const float4 a = Xb[item.j0 + 2 * k];
+            const float4 b = (2 * k + 1 < item.jlen) ? Xb[item.j0 + 2 * k + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            sxy[k] = make_float4(a.x, b.x, a.y, b.y);
+            szw[k] = make_float4(a.z, b.z, a.w, b.w);
+        }
+        for (int k = tid; k < 6 * jpairs; k += kTile) gj[k] = 0.f;
+        const int64_t tab = (int64_t)item.batch * qc.n_chunks + ch;
+        const float4 *ai = AI + tab * NV * npad + item.i0;
+        for (int e = tid; e < NV * kTile; e += kTile) sa[e] = ai[(int64_t)(e / kTile) * npad + (e % kTile)];
+        const float4 *fjrows = FJ + (tab * (npad / 2) + item.j0 / 2) * NV;
+        const float4 xi = Xb[item.i0 + tid];
+        __syncthreads();
+        const float2 qs_hi = bc(qc.qs_hi[ch]), qs_lo = bc(qc.qs_lo[ch]);
+        const bool zero_start = (qs_hi.x == 0.f) && (qs_lo.x == 0.f);
+        const int jmask = item.diag ? tid : -1;
+        float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
+        if (zero_start)
+            run_adj2_atomic<NV, true>(sxy, szw, sa + tid, fjrows, gj, jpairs, xi, item, tid, lane, jmask, qs_hi, qs_lo,
+                                      bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), gx, gy, gz);
+        else
+            run_adj2_atomic<NV, false>(sxy, szw, sa + tid, fjrows, gj, jpairs, xi, item, tid, lane, jmask, qs_hi,
+                                       qs_lo, bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), gx, gy, gz);
+        double *Gb = G + (int64_t)item.batch * npad * 3;
+        atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid)], (double)(gx.x + gx.y));
+        atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid) + 1], (double)(gy.x + gy.y));
+        atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid) + 2], (double)(gz.x + gz.y));
+        __syncthreads();
+        for (int k = tid; k < 3 * item.jlen; k += kTile) atomicAdd(&Gb[3 * (int64_t)item.j0 + k], (double)gj[k]);
+        it = next_item;
+    }
+}
+
+// AI[b][c][v][slot] = sigma_v (a(q_2v), a(q_2v)/q_2v, a(q_2v+1), a(q_2v+1)/q_2v+1), a(q) = g_b(q) f_i(q), for
+// the atom in `slot`; zero past the pass, at q = 0 and on padding slots (zeroed beforehand).
+__global__ void k_atomic_adj_table(const double *__restrict__ ff, const double *__restrict__ gI,
+                                   const int *__restrict__ slot_of, int64_t n, int64_t npad, QChunks qc, int nv,
+                                   float4 *__restrict__ AI)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * nv) return;
+    const int64_t atom = i % n;
+    const int v = (int)(i / n);
+    const int c = blockIdx.y;
+    const int64_t b = blockIdx.z;
+    const int len = qc.q_len[c];
+    float out[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int h = 0; h < 2; ++h) {
+        const int m = 2 * v + h;
+        if (m >= len) continue;
+        const int k = qc.q_begin[c] + m;
+        const double q = qc.qsd[c] + m * qc.dqd[c];
+        if (!(q > 0.0)) continue;
+        const double a = gI[b * qc.n_q + k] * ff[(b * qc.n_q + k) * n + atom];
+        out[2 * h] = (float)a;
+        out[2 * h + 1] = (float)(a / q);
+    }
+    const float sg = block_negative(v) ? -1.f : 1.f;
+    AI[((b * qc.n_chunks + c) * nv + v) * npad + slot_of[atom]] =
+        make_float4(sg * out[0], sg * out[1], sg * out[2], sg * out[3]);
+}
+
 // ---- the tabulated form (default) ---------------------------------------------------------------
 // Within one work item every pair has the same conformer and type pair, so the pair weight is one
 // function of the distance:  W_ij = W(r_ij),  W(r) = 2 sum_q h_q (cos(q r) - sinc(q r)) / r^2,
@@ -711,6 +890,43 @@ cudaError_t launch_debye_adjoint(const float4 *X, int64_t npad, const Item *item
     default:
         return launch_nb<52>(nv, X, npad, items, n_items, qc, H, n_pairs, hstride, G, jcap, ticket, PI, PJ, s);
     }
+}
+
+int adjoint_atomic_slots() { return kAtomAdjNV; }
+
+cudaError_t launch_atomic_adj_table(const double *ff, const double *gI, const int *slot_of, int64_t n, int64_t npad,
+                                    int64_t batch, const QChunks &qc, float4 *AI, cudaStream_t s)
+{
+    if (n == 0 || batch == 0) return cudaSuccess;
+    const int threads = 256;
+    const dim3 grid((unsigned)((n * kAtomAdjNV + threads - 1) / threads), (unsigned)qc.n_chunks, (unsigned)batch);
+    k_atomic_adj_table<<<grid, threads, 0, s>>>(ff, gI, slot_of, n, npad, qc, kAtomAdjNV, AI);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debye_adjoint_atomic(const float4 *X, int64_t npad, const Item *items, int n_items,
+                                        const QChunks &qc, const float4 *AI, const float4 *FJ, double *G, int jlen_max,
+                                        int *ticket, cudaStream_t s)
+{
+    if (n_items == 0) return cudaSuccess;
+    for (int c = 0; c < qc.n_chunks; ++c)
+        if (qc.q_len[c] > 2 * kAtomAdjNV) return cudaErrorInvalidValue;
+    const int jcap = adjoint_jcap(jlen_max);
+    const size_t smem = (size_t)jcap * sizeof(float4) + (size_t)kAtomAdjNV * kTile * sizeof(float4) +
+                        (size_t)jcap * 3 * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_debye_adjoint_atomic<kAtomAdjNV>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0, dev = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_adjoint_atomic<kAtomAdjNV>, kTile, smem)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    int grid = (occ > 0 ? occ : 1) * sms;
+    if (grid > n_items) grid = n_items;
+    k_debye_adjoint_atomic<kAtomAdjNV><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, AI, FJ, G, jcap, ticket);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_kmat(const QChunks &qc, int n_rows, double step, double *K, cudaStream_t s)

@@ -95,7 +95,7 @@ struct sas_ctx {
     sas::api::DevBuf coef_d, F, meta, blockcounts, blockoffs, centroid, X, slot_of, items, group_items,
         group_off, partial, ticket, S, in_coords, in_types, out_buf, Ibuf, gbuf, chi2buf, H, G, gout, tgt, wts,
         hist, dropped, in_ff, zero_types, FJ, FI, F64t, D2, segbuf, cen, qdirs, qwts, type_off, Apart, Fsub, Itmp, qplan,
-        tile_off, tile_ent, adj_pi, adj_pj, Ufix, segfix, Ustage, Sx, Ix, btab, bdiag, bhist, bout, adj_k, adj_wn, adj_tab;
+        tile_off, tile_ent, adj_pi, adj_pj, Ufix, segfix, Ustage, Sx, Ix, btab, bdiag, bhist, bout, adj_k, adj_wn, adj_tab, adj_ai;
     int btab_bins = 0;        // (n_bins, r_max) of the binned-sum table in btab (0: none)
     float btab_rmax = 0.f;
     int det_ntiles = -1;   // I-tiles per conformer of the current schedule's tile lists (-1: none built)

@@ -144,6 +144,7 @@ using namespace sas::api;
 extern "C" sas_status sas_binned_profile(sas_ctx *ctx, const int32_t *hist, int64_t batch, int n_bins, float r_max,
                                          const int64_t *type_counts, double *I_out, void *stream)
 {
+    sas::NvtxRange nvtx_range("sas_binned_profile");
     if (!ctx) return fail(SAS_ERR_INVALID_ARG, "null context");
     if (batch < 0) return fail(SAS_ERR_INVALID_ARG, "negative batch");
     if (n_bins < 1 || n_bins > 4096) return fail(SAS_ERR_INVALID_ARG, "n_bins must be in [1, 4096]");

@@ -282,6 +282,7 @@ sas_status sas_mlp_get_state(sas_mlp *m, float *params, float *adam_m, float *ad
 
 sas_status sas_mlp_forward(sas_mlp *m, const float *x, int batch, float *y, void *stream)
 {
+    sas::NvtxRange nvtx_range("sas_mlp_forward");
     if (!m || !x || !y) return mlp_fail(SAS_ERR_INVALID_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     sas_status st = mlp_forward(m, x, nullptr, batch, s);
@@ -299,6 +300,7 @@ sas_status sas_mlp_forward(sas_mlp *m, const float *x, int batch, float *y, void
 sas_status sas_mlp_grads(sas_mlp *m, const float *x, const float *t, int batch, float *grads, float *loss_out,
                          void *stream)
 {
+    sas::NvtxRange nvtx_range("sas_mlp_grads");
     if (!m || !x || !t) return mlp_fail(SAS_ERR_INVALID_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     sas_status st = mlp_forward(m, x, t, batch, s);
@@ -314,6 +316,7 @@ sas_status sas_mlp_grads(sas_mlp *m, const float *x, const float *t, int batch, 
 sas_status sas_mlp_train_step(sas_mlp *m, const float *x, const float *t, int batch, float lr, float *loss_out,
                               void *stream)
 {
+    sas::NvtxRange nvtx_range("sas_mlp_train_step");
     if (!m || !x || !t) return mlp_fail(SAS_ERR_INVALID_ARG, "null argument");
     if (!(lr > 0.f) || !std::isfinite(lr)) return mlp_fail(SAS_ERR_INVALID_ARG, "learning rate must be positive");
     cudaStream_t s = (cudaStream_t)stream;

@@ -902,12 +902,14 @@ sas_status sas_destroy(sas_ctx *ctx)
 sas_status sas_profile(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types,
                        int64_t n_atoms, double *I_out, void *stream)
 {
+    sas::NvtxRange nvtx_range("sas_profile");
     return run_profile(ctx, coords, coords_type, types, n_atoms, 1, I_out, (cudaStream_t)stream);
 }
 
 sas_status sas_profile_batch(sas_ctx *ctx, const void *coords, int coords_type, const int32_t *types,
                              int64_t n_atoms, int64_t batch, double *I_out, void *stream)
 {
+    sas::NvtxRange nvtx_range("sas_profile_batch");
     return run_profile(ctx, coords, coords_type, types, n_atoms, batch, I_out, (cudaStream_t)stream);
 }
 
@@ -1043,6 +1045,7 @@ sas_status sas_profile_grad(sas_ctx *ctx, const float *coords, const int32_t *ty
                             int64_t batch, const double *target, const double *weights,
                             double *chi2_out, float *grad_out, double *I_out, void *stream)
 {
+    sas::NvtxRange nvtx_range("sas_profile_grad");
     sas_status st = check_common(ctx, coords, types, n, batch);
     if (st != SAS_OK) return st;
     if (ctx->flags & SAS_FP64) return fail(SAS_ERR_UNSUPPORTED, "the adjoint needs a SAS_MIXED context");
@@ -1089,6 +1092,7 @@ sas_status sas_profile_grad(sas_ctx *ctx, const float *coords, const int32_t *ty
 sas_status sas_profile_vjp(sas_ctx *ctx, const float *coords, const int32_t *types, int64_t n,
                            int64_t batch, const double *grad_I, float *grad_out, void *stream)
 {
+    sas::NvtxRange nvtx_range("sas_profile_vjp");
     sas_status st = check_common(ctx, coords, types, n, batch);
     if (st != SAS_OK) return st;
     if (ctx->flags & SAS_FP64) return fail(SAS_ERR_UNSUPPORTED, "the adjoint needs a SAS_MIXED context");
@@ -1115,6 +1119,7 @@ sas_status sas_pair_histogram(sas_ctx *ctx, const float *coords, const int32_t *
                               int64_t batch, int n_bins, float r_max, int32_t *hist_out,
                               int64_t *dropped_out, void *stream)
 {
+    sas::NvtxRange nvtx_range("sas_pair_histogram");
     sas_status st = check_common(ctx, coords, types, n, batch);
     if (st != SAS_OK) return st;
     if (n_bins < 1 || n_bins > 4096) return fail(SAS_ERR_INVALID_ARG, "n_bins must be in [1, 4096]");

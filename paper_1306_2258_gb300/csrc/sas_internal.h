@@ -6,6 +6,8 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sas.h"
 
 namespace sas {
@@ -160,6 +162,15 @@ cudaError_t launch_adjoint_wtab(const double *g, const double *F, int n_types, i
 cudaError_t launch_debye_adjoint_tab(const float4 *X, int64_t npad, const Item *items, int n_items, const float4 *tab,
                                      int n_int, float inv_step, int n_pairs, double *G, int jlen_max, int *ticket,
                                      float *PI, float *PJ, cudaStream_t s);
+// Per-atom form factors: the weights AI [b][pass][slots][npad] float4 from the caller's ff [b][k][i] and
+// g [b][k], and the pair kernel over them and the forward table FJ [b][pass][npad/2][slots] (passes of
+// at most 2 * adjoint_atomic_slots() q; G as launch_debye_adjoint without PI).
+int adjoint_atomic_slots();
+cudaError_t launch_atomic_adj_table(const double *ff, const double *gI, const int *slot_of, int64_t n, int64_t npad,
+                                    int64_t batch, const QChunks &qc, float4 *AI, cudaStream_t s);
+cudaError_t launch_debye_adjoint_atomic(const float4 *X, int64_t npad, const Item *items, int n_items,
+                                        const QChunks &qc, const float4 *AI, const float4 *FJ, double *G, int jlen_max,
+                                        int *ticket, cudaStream_t s);
 cudaError_t launch_adjoint_gather(const float *PI, const float *PJ, int jcap, const Item *items,
                                   const int *tile_off, const int *tile_ent, int ntiles, int64_t npad, int64_t batch,
                                   double *G, cudaStream_t s);
@@ -208,6 +219,15 @@ cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v,
 
 // the calling thread's error message (sas_last_error)
 sas_status set_error(sas_status st, const char *msg);
+
+// A named NVTX range over one entry point, so that a profiler can select a call's kernels by name
+// (ncu --nvtx --nvtx-include NAME/); without a tool attached the header-only NVTX calls do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ---- per-atom form factors (atomic.cu, atomic_pairs2.cu) -------------------------------------
 int atomic_slots(const QChunks &qc);

@@ -185,6 +185,7 @@ sas_status sas_screen_select(int n_conf, int n_q, const float *z, int ld, const 
                              const double *base, int ld_base, const double *target, const double *weights, int k,
                              int32_t *top_idx, double *top_chi2, double *chi2_all, void *stream)
 {
+    sas::NvtxRange nvtx_range("sas_screen_select");
     if (n_conf < 1 || n_conf > select_max()) return set_error(SAS_ERR_INVALID_ARG, "n_conf must be in [1, 8192]");
     if (n_q < 1) return set_error(SAS_ERR_INVALID_ARG, "need n_q >= 1");
     if (!z && !base) return set_error(SAS_ERR_INVALID_ARG, "z and base cannot both be NULL");

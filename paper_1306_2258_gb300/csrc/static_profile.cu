@@ -106,6 +106,7 @@ extern "C" sas_status sas_profile_static(const float *coords, const int32_t *typ
                                          const double *ff_coef, double q0, double dq, int n_q, double *I_out,
                                          void *stream)
 {
+    sas::NvtxRange nvtx_range("sas_profile_static");
     if (n < 0 || n > SAS_STATIC_MAX_ATOMS)
         return static_fail(SAS_ERR_UNSUPPORTED, "n_atoms must be in [0, SAS_STATIC_MAX_ATOMS]");
     if (n_types < 1 || n_types > kStaticTypes) return static_fail(SAS_ERR_INVALID_ARG, "n_types must be in [1, 16]");

@@ -106,6 +106,21 @@ class Profile:
         self._last_batch = 0
         return out[0] if single else out
 
+    def vjp_atomic(self, coords, ff, grad_I, stream=None):
+        """sum_q grad_I[q] dI(q)/dx [n, 3] (or [B, n, 3]) float32 for the per-atom profile of
+        ff [n_q, n] (or [B, n_q, n]); the form factors are held fixed (sas_profile_vjp_atomic)."""
+        x = coords if isinstance(coords, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(coords))
+        single = x.ndim == 2
+        if single:
+            x = x.unsqueeze(0)
+        x = x.to(torch.float32).contiguous()
+        B, n = int(x.shape[0]), int(x.shape[1])
+        f = _as_tensor_like(ff, torch.float64).reshape(B, self.n_q, n).to(x.device)
+        gI = _as_tensor_like(grad_I, torch.float64).reshape(B, self.n_q).to(x.device)
+        g = torch.empty((B, n, 3), dtype=torch.float32, device=x.device)
+        _lib.sas_profile_vjp_atomic(self._ctx, x, n, B, f, gI, g, stream)
+        return g[0] if single else g
+
     def partials(self):
         """Type-pair sinc sums S[b, p, q] of the last call (float64, host)."""
         S = np.empty((self._last_batch, self.n_pairs_types, self.n_q))

@@ -178,3 +178,92 @@ def test_atomic_globule50k_sampled_q():
     ref = oracle.profile_atomic(w.mol.coords.astype(np.float32).astype(np.float64), ff[ks], q[ks])
     assert _rel(I[ks], ref) <= TOL_MIXED
     assert abs(I[0] - np.sum(ff[0]) ** 2) <= 1e-12 * np.sum(ff[0]) ** 2
+
+
+# ---------------------------------------------------------------- gradient (sas_profile_vjp_atomic)
+
+def _grad_ok(g, ref, tol=1e-4):
+    g, ref = np.asarray(g, np.float64), np.asarray(ref, np.float64)
+    assert np.linalg.norm(g - ref) <= tol * np.linalg.norm(ref), np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    assert np.max(np.abs(g - ref)) <= tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("n,q_hi,n_q,batch", [(333, 0.5, 101, 1), (1500, 1.0, 201, 2), (129, 0.3, 7, 1),
+                                              (2000, 0.5, 53, 1)])
+def test_atomic_vjp_matches_oracle(n, q_hi, n_q, batch):
+    """Per-atom form factors with a water-layer term, passes of at most 52 q (201 q: four passes, the
+    last ragged; 53 q: one full pass and a single q), ragged tiles, a batch of conformers."""
+    q = wl.q_grid(0.0, q_hi, n_q)
+    rng = np.random.default_rng(n + n_q)
+    X = np.stack([wl.random_walk_globule(n, 2, 610 + n + b).coords for b in range(batch)]).astype(np.float32)
+    ff = np.stack([wl.atomic_form_factor_table(n, q, 620 + n + b) for b in range(batch)])
+    gI = rng.standard_normal((batch, n_q)) / np.stack([oracle.profile_atomic(X[b], ff[b], q) for b in range(batch)])
+    p = Profile(wl.form_factor_coefficients(2, 5), q)
+    g = p.vjp_atomic(torch.as_tensor(X).cuda(), torch.as_tensor(ff).cuda(), torch.as_tensor(gI).cuda()).cpu().numpy()
+    p.close()
+    for b in range(batch):
+        _grad_ok(g[b], oracle.vjp_atomic(X[b], ff[b], q, gI[b]))
+
+
+def test_atomic_vjp_rigid_motion_and_types_limit():
+    """Sum of the gradient and of its torques vanish (rigid motions leave I unchanged); with every
+    atom's form factor equal to its type's, the per-atom VJP equals the typed one (sas_profile_vjp)."""
+    mol = wl.random_walk_globule(1200, 4, 631).as_f32()
+    coef = wl.form_factor_coefficients(4, 632)
+    q = wl.q_grid(0.0, 0.6, 121)
+    ff = oracle.form_factors(mol.types, coef, q).T.copy()   # [n_q, n]
+    gI = np.random.default_rng(633).standard_normal(q.size) / oracle.profile(mol.coords, mol.types, coef, q)
+    x = torch.as_tensor(mol.coords).cuda()
+    p = Profile(coef, q)
+    ga = p.vjp_atomic(x, torch.as_tensor(ff).cuda(), torch.as_tensor(gI).cuda()).double().cpu().numpy()
+    gt = p.vjp(x, mol.types, torch.as_tensor(gI).cuda()).double().cpu().numpy()
+    p.close()
+    _grad_ok(ga, gt, 1e-5)
+    assert np.all(np.abs(ga.sum(0)) <= 1e-4 * np.abs(ga).sum())
+    tq = np.cross(mol.coords.astype(np.float64) - mol.coords.mean(0), ga)
+    assert np.all(np.abs(tq.sum(0)) <= 1e-4 * np.abs(tq).sum())
+
+
+def test_atomic_vjp_host_buffers_small_cases_and_unsupported_contexts():
+    q = wl.q_grid(0.0, 0.5, 51)
+    coef = wl.form_factor_coefficients(2, 5)
+    for n in (1, 2, 3, 130):
+        mol = wl.random_walk_globule(n, 2, 640 + n).as_f32()
+        ff = wl.atomic_form_factor_table(n, q, 650 + n)
+        gI = np.random.default_rng(n).standard_normal(q.size)
+        out = np.full((1, n, 3), np.nan, np.float32)
+        p = Profile(coef, q)
+        _lib.sas_profile_vjp_atomic(p._ctx, mol.coords[None], n, 1, ff[None], gI[None], out)
+        p.close()
+        ref = oracle.vjp_atomic(mol.coords, ff, q, gI)
+        if n == 1:
+            assert np.all(out == 0.0)
+        else:
+            _grad_ok(out[0], ref)
+    mol = wl.random_walk_globule(50, 2, 660).as_f32()
+    ff = torch.as_tensor(wl.atomic_form_factor_table(50, q, 661)).cuda()
+    gI = torch.ones(q.size, dtype=torch.float64, device="cuda")
+    for kw in ({"precision": "fp64"}, {"deterministic": True}):
+        p = Profile(coef, q, **kw)
+        with pytest.raises(_lib.SasError) as e:
+            p.vjp_atomic(torch.as_tensor(mol.coords).cuda(), ff, gI)
+        assert e.value.status == _lib.SAS_ERR_UNSUPPORTED
+        p.close()
+    p = Profile(coef, q)
+    bad = ff.clone()
+    bad[3, 7] = float("nan")
+    with pytest.raises(_lib.SasError) as e:
+        p.vjp_atomic(torch.as_tensor(mol.coords).cuda(), bad, gI)
+    assert e.value.status == _lib.SAS_ERR_INVALID_ARG
+    p.close()
+
+
+def test_atomic_vjp_6000_atoms_q101():
+    mol = wl.random_walk_globule(6000, 2, 671).as_f32()
+    q = wl.q_grid(0.0, 0.5, 101)
+    ff = wl.atomic_form_factor_table(6000, q, 672)
+    gI = np.random.default_rng(673).standard_normal(q.size) / oracle.profile_atomic(mol.coords, ff, q)
+    p = Profile(wl.form_factor_coefficients(2, 5), q)
+    g = p.vjp_atomic(torch.as_tensor(mol.coords).cuda(), torch.as_tensor(ff).cuda(), torch.as_tensor(gI).cuda())
+    p.close()
+    _grad_ok(g.cpu().numpy(), oracle.vjp_atomic(mol.coords, ff, q, gI))
