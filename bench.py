@@ -561,7 +561,7 @@ def run_strong(args):
 
     from paper_1306_2258_gb300 import _lib, workloads as wl
     from paper_1306_2258_gb300.profile import Profile
-    from paper_1306_2258_gb300.shard import allreduce_shares, set_shard
+    from paper_1306_2258_gb300.shard import allreduce_exact, allreduce_shares, set_shard
 
     rank, world, local = _dist()
     if "MASTER_ADDR" not in os.environ:   # a plain single-process run: a group of one
@@ -572,17 +572,26 @@ def run_strong(args):
     w = wl.c2_globule(N_ATOMS)
     n, Q = w.mol.n, w.q.size
     pq = n * (n - 1) // 2 * Q
-    prof = Profile(w.coef, w.q, "mixed")
+    prof = Profile(w.coef, w.q, "mixed", deterministic=args.exact)
     set_shard(prof, rank, world)
     x = torch.as_tensor(w.mol.coords, device=dev)
     t = torch.as_tensor(w.mol.types, device=dev)
     share = torch.empty((1, Q), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     result = {}
+    T = w.coef.shape[0]
+    Ush = np.empty((1, T * (T + 1) // 2, Q, 2), dtype=np.int64)   # this shard's exact sums (host)
+    whole_I = torch.empty((1, Q), dtype=torch.float64, device=dev)
 
     def step():
         _lib.sas_profile_batch(prof._ctx, x, _lib.SAS_COORDS_F32, t, n, 1, share, stream)
-        result["I"] = allreduce_shares(share[0])
+        if args.exact:   # exact 128-bit sums all-reduced as 32-bit limbs: the unsplit profile's bits
+            _lib.sas_exact_sums(prof._ctx, Ush, Ush.size)
+            U = allreduce_exact(torch.as_tensor(Ush, device=dev)).cpu().numpy()
+            _lib.sas_assemble_exact(prof._ctx, U, 1, whole_I)
+            result["I"] = whole_I[0]
+        else:
+            result["I"] = allreduce_shares(share[0])
 
     for _ in range(args.warmup):
         step()
@@ -597,7 +606,7 @@ def run_strong(args):
     dist.barrier()
     ms = torch.tensor([a.elapsed_time(b) / args.steps], dtype=torch.float64, device=dev)
     dist.all_reduce(ms, op=dist.ReduceOp.MAX)
-    whole = Profile(w.coef, w.q, "mixed")   # unsharded, untimed: the shares must sum to it
+    whole = Profile(w.coef, w.q, "mixed", deterministic=args.exact)   # unsharded, untimed: the shares sum to it
     ref = whole(x, t).cpu().numpy()
     whole.close()
     I = result["I"].cpu().numpy()
@@ -608,16 +617,20 @@ def run_strong(args):
             "warmup": args.warmup, "ms_per_step": t_s * 1e3, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "globule 50,000 atoms x 201 q, one molecule split over the ranks "
-                                   "(shards of equal pair work, NCCL all-gather of the Q-vector shares)",
-                       "n_atoms": n, "n_q": Q, "parallelism": f"shards{world}"},
+                                   + ("(shards of equal pair work on deterministic contexts, NCCL all-reduce of their "
+                                      "exact 128-bit sums as 32-bit limbs)" if args.exact else
+                                      "(shards of equal pair work, NCCL all-gather of the Q-vector shares)"),
+                       "n_atoms": n, "n_q": Q, "parallelism": f"shards{world}", "exact": bool(args.exact)},
             "rel_diff_vs_unsharded": float(np.max(np.abs(I - ref) / np.abs(ref))),
+            "identical_to_unsharded": bool(np.array_equal(I, ref)),
         }))
     prof.close()
     dist.destroy_process_group()
     return 0
 
 
-PROFILE_CASES = ("histogram", "gradient", "gradient_recurrence", "gemm", "atomic", "quadrature", "binned", "rod")
+PROFILE_CASES = ("histogram", "gradient", "gradient_recurrence", "gemm", "atomic", "quadrature", "binned", "rod",
+                 "train")
 
 
 def run_profile_case(args):
@@ -630,6 +643,7 @@ def run_profile_case(args):
       gradient_recurrence  the same with the sums over q by the recurrence (SAS_OPT_ADJOINT 1)
       binned       the Debye sum at bin centres over the histograms of 4,096 ensemble conformers
       rod          the 30,000-atom double-helix rod x 101 q (the benchmark row's profile)
+      train        four Adam steps of the 3840-512-512-101 surrogate at batch 256 (the epoch row's step)
       gemm         4096 x 4096 x 4096 bfloat16 -> float32 on the tcgen05 GEMM
       atomic       20,000-atom globule x 201 q with a per-atom form-factor table
       quadrature   20,000-atom globule x 65 q (0..0.32 A^-1), orientation average of Eq. 1 on every q
@@ -665,6 +679,16 @@ def run_profile_case(args):
             chi2, _, _ = p4.chi2_grad(X4, tt, T, 1.0 / T ** 2)
         report["chi2_sum_" + case] = float(chi2.sum())
         p4.close()
+    if "train" in cases:
+        from paper_1306_2258_gb300.surrogate import SurrogateMLP
+        rng = np.random.default_rng(5)
+        net = SurrogateMLP(3840, 512, 101, max_batch=256, seed=0)
+        xs = torch.as_tensor(rng.standard_normal((256, 3840)).astype(np.float32), device=dev)
+        ts = torch.zeros((256, 101), dtype=torch.float32, device=dev)
+        for _ in range(4):
+            net.train_step(xs, ts, 1e-3)
+        report["train_steps"] = 4
+        net.close()
     if "rod" in cases:
         w3 = wl.c3_rod()
         p = Profile(w3.coef, w3.q)
@@ -729,6 +753,9 @@ def main():
                     help="CPU time of the whole --impl reference run (each step a subsample sized to its share)")
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
                     help="weak (default): one molecule per rank; strong: one molecule split over the ranks")
+    ap.add_argument("--exact", action="store_true",
+                    help="with --scaling strong: deterministic contexts whose exact shard sums are all-reduced, "
+                         "so that every rank holds the unsplit profile bit for bit")
     ap.add_argument("--profile-case", default=None, choices=("all",) + PROFILE_CASES,
                     help="run reduced launches of the secondary kernels for a profiler capture, then exit")
     args = ap.parse_args()

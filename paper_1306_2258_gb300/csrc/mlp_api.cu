@@ -71,6 +71,10 @@ struct sas_mlp {
          *dYt = nullptr, *dZ2b = nullptr, *dZ2t = nullptr, *dZ1b = nullptr, *dZ1t = nullptr;
     std::vector<void *> owned;
     int64_t step = 0;
+    // the forward and backward launches of a training step, captured once per batch size on an
+    // internal stream and replayed on the caller's stream (they read the inputs from Xf and Tf)
+    cudaStream_t capture_stream = nullptr;
+    std::vector<std::pair<int, cudaGraphExec_t>> step_graphs;
 };
 
 namespace {
@@ -94,20 +98,9 @@ void mlp_free(sas_mlp *m)
     m->owned.clear();
 }
 
-// x (host or device, [B][n_in] f32) and optionally t ([B][n_out]) to device; forward to Y.
-sas_status mlp_forward(sas_mlp *m, const float *x, const float *t, int B, cudaStream_t s)
+// The forward launches from device input xd [B][n_in] f32 to Y.
+sas_status mlp_forward_dev(sas_mlp *m, const float *xd, int B, cudaStream_t s)
 {
-    if (B < 1 || B > m->max_b) return mlp_fail(SAS_ERR_INVALID_ARG, "batch outside [1, max_batch]");
-    const int Bp = round16(B);
-    const float *xd = x;
-    if (!on_device_ptr(x)) {
-        MLP_TRY(cudaMemcpyAsync(m->Xf, x, sizeof(float) * (size_t)B * m->n_in, cudaMemcpyHostToDevice, s));
-        xd = m->Xf;
-    }
-    if (t) {
-        MLP_TRY(cudaMemcpyAsync(m->Tf, t, sizeof(float) * (size_t)B * m->n_out,
-                                on_device_ptr(t) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    }
     MLP_TRY(launch_to_bf16((int64_t)B * m->n_in, xd, m->Xb, s));
     const bf16 *W1b = m->Pb + m->oW1, *W2b = m->Pb + m->oW2, *W3b = m->Pb + m->oW3;
     MLP_TRY(launch_gemm(B, m->h, m->n_in, m->Xb, m->n_in, W1b, m->n_in, m->P + m->ob1, m->Z1, m->h, m->A1b, m->h, 1,
@@ -115,8 +108,25 @@ sas_status mlp_forward(sas_mlp *m, const float *x, const float *t, int B, cudaSt
     MLP_TRY(launch_gemm(B, m->h, m->h, m->A1b, m->h, W2b, m->h, m->P + m->ob2, m->Z2, m->h, m->A2b, m->h, 1, s));
     MLP_TRY(launch_gemm(B, m->n_outp, m->h, m->A2b, m->h, W3b, m->h, m->P + m->ob3, m->Y, m->n_outp, nullptr, 0, 0,
                            s));
-    (void)Bp;
     return SAS_OK;
+}
+
+// x (host or device, [B][n_in] f32) and optionally t ([B][n_out]) to device; forward to Y.  With
+// `stage_x` the input is always copied into Xf (the captured graph reads it there).
+sas_status mlp_forward(sas_mlp *m, const float *x, const float *t, int B, cudaStream_t s, bool stage_x = false)
+{
+    if (B < 1 || B > m->max_b) return mlp_fail(SAS_ERR_INVALID_ARG, "batch outside [1, max_batch]");
+    const float *xd = x;
+    if (stage_x || !on_device_ptr(x)) {
+        MLP_TRY(cudaMemcpyAsync(m->Xf, x, sizeof(float) * (size_t)B * m->n_in, cudaMemcpyDefault, s));
+        xd = m->Xf;
+    }
+    if (t) {
+        MLP_TRY(cudaMemcpyAsync(m->Tf, t, sizeof(float) * (size_t)B * m->n_out,
+                                on_device_ptr(t) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    }
+    if (stage_x) return SAS_OK;   // the launches are the captured graph's
+    return mlp_forward_dev(m, xd, B, s);
 }
 
 // Gradients of the MSE loss for the batch already in Xb/Tf (after mlp_forward) into G.
@@ -146,12 +156,44 @@ sas_status mlp_backward(sas_mlp *m, int B, cudaStream_t s)
     return SAS_OK;
 }
 
-// bfloat16 mirror of the masters and the transposed weights the backward pass uses
-sas_status mlp_refresh(sas_mlp *m, cudaStream_t s)
+// bfloat16 mirror of the masters (unless the Adam step has just written it) and the transposed
+// weights the backward pass uses
+sas_status mlp_refresh(sas_mlp *m, cudaStream_t s, bool convert = true)
 {
-    MLP_TRY(launch_to_bf16(m->np, m->P, m->Pb, s));
+    if (convert) MLP_TRY(launch_to_bf16(m->np, m->P, m->Pb, s));
     MLP_TRY(launch_transpose_bf16(m->h, m->h, m->h, m->Pb + m->oW2, m->h, m->W2t, m->h, s));
     MLP_TRY(launch_transpose_bf16(m->n_outp, m->n_outp, m->h, m->Pb + m->oW3, m->h, m->W3t, m->n_outp, s));
+    return SAS_OK;
+}
+
+// The training step's forward and backward launches for batch B as a graph (captured on first use).
+sas_status step_graph(sas_mlp *m, int B, cudaGraphExec_t &ex)
+{
+    for (auto &g : m->step_graphs)
+        if (g.first == B) {
+            ex = g.second;
+            return SAS_OK;
+        }
+    if (!m->capture_stream) MLP_TRY(cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = m->capture_stream;
+    MLP_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    sas_status st = mlp_forward_dev(m, m->Xf, B, cs);
+    if (st == SAS_OK) st = mlp_backward(m, B, cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (st != SAS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return mlp_fail(SAS_ERR_CUDA, "capture of the training step", e);
+    const cudaError_t ei = cudaGraphInstantiate(&ex, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return mlp_fail(SAS_ERR_CUDA, "instantiation of the training step", ei);
+    if (m->step_graphs.size() >= 8) {   // a small cache: the oldest batch size goes
+        cudaGraphExecDestroy(m->step_graphs.front().second);
+        m->step_graphs.erase(m->step_graphs.begin());
+    }
+    m->step_graphs.emplace_back(B, ex);
     return SAS_OK;
 }
 
@@ -240,6 +282,11 @@ sas_status sas_mlp_create(int n_in, int n_hidden, int n_out, int max_batch, sas_
 sas_status sas_mlp_destroy(sas_mlp *m)
 {
     if (!m) return SAS_OK;
+    cudaDeviceSynchronize();
+    for (auto &g : m->step_graphs) cudaGraphExecDestroy(g.second);
+    m->step_graphs.clear();
+    if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
+    m->capture_stream = nullptr;
     mlp_free(m);
     delete m;
     return SAS_OK;
@@ -320,12 +367,16 @@ sas_status sas_mlp_train_step(sas_mlp *m, const float *x, const float *t, int ba
     if (!m || !x || !t) return mlp_fail(SAS_ERR_INVALID_ARG, "null argument");
     if (!(lr > 0.f) || !std::isfinite(lr)) return mlp_fail(SAS_ERR_INVALID_ARG, "learning rate must be positive");
     cudaStream_t s = (cudaStream_t)stream;
-    sas_status st = mlp_forward(m, x, t, batch, s);
-    if (st == SAS_OK) st = mlp_backward(m, batch, s);
+    // inputs into Xf and Tf, then the captured forward and backward launches (the same kernels in the
+    // same order as sas_mlp_grads), then Adam, which writes the bfloat16 copy of the masters itself
+    sas_status st = mlp_forward(m, x, t, batch, s, true);
     if (st != SAS_OK) return st;
+    cudaGraphExec_t ex = nullptr;
+    if ((st = step_graph(m, batch, ex)) != SAS_OK) return st;
+    MLP_TRY(cudaGraphLaunch(ex, s));
     m->step += 1;
     MLP_TRY(launch_adam(m->np, m->P, m->G, m->Mo, m->Vo, lr, 0.9f, 0.999f, 1e-8f, m->step, m->Pb, s));
-    st = mlp_refresh(m, s);
+    st = mlp_refresh(m, s, false);
     if (st != SAS_OK) return st;
     if (loss_out) {
         const bool host = !on_device_ptr(loss_out);
