@@ -17,10 +17,28 @@ namespace {
 
 constexpr int kWarps = kTile / 32;
 
+// The rare correction of a bin guess k that an edge comparison rejected: walk down while e_k^2 > r2,
+// then up while e_{k+1}^2 <= r2 (a step or two at most).  Out of line, so that the common path
+// branches around it instead of carrying it predicated.
+__device__ __noinline__ float bin_fixup(float k, float r2, float w, float nb)
+{
+    for (int guard = 0; guard < 8 && k > 0.f; ++guard) {
+        const float ek = __fmul_rn(k, w);
+        if (__fmul_rn(ek, ek) <= r2) break;
+        k -= 1.f;
+    }
+    for (int guard = 0; guard < 8 && k < nb; ++guard) {
+        const float ek = __fmul_rn(k + 1.f, w);
+        if (__fmul_rn(ek, ek) > r2) break;
+        k += 1.f;
+    }
+    return k;
+}
+
 // Bin of r2 under the rule above: max{k : e_k^2 <= r2} with e_k^2 = fl(fl(k w)^2), capped at
 // n_bins.  The first guess comes from the hardware reciprocal square root; the edge comparisons
 // (the rule's own float32 roundings) decide: straight-line when the guess is right (almost
-// always), a short walk otherwise.
+// always), the out-of-line walk otherwise.
 __device__ __forceinline__ int bin_of(float r2, float w, float inv_w, int n_bins)
 {
     const float nb = (float)n_bins;
@@ -28,18 +46,7 @@ __device__ __forceinline__ int bin_of(float r2, float w, float inv_w, int n_bins
     const float elo = __fmul_rn(k, w), ehi = __fmul_rn(k + 1.f, w);
     const bool lo_ok = k == 0.f || __fmul_rn(elo, elo) <= r2;
     const bool hi_ok = k == nb || __fmul_rn(ehi, ehi) > r2;
-    if (!(lo_ok && hi_ok)) {
-        for (int guard = 0; guard < 8 && k > 0.f; ++guard) {   // never more than a step or two
-            const float ek = __fmul_rn(k, w);
-            if (__fmul_rn(ek, ek) <= r2) break;
-            k -= 1.f;
-        }
-        for (int guard = 0; guard < 8 && k < nb; ++guard) {
-            const float ek = __fmul_rn(k + 1.f, w);
-            if (__fmul_rn(ek, ek) > r2) break;
-            k += 1.f;
-        }
-    }
+    if (!(lo_ok && hi_ok)) k = bin_fixup(k, r2, w, nb);
     return __float_as_int(k + 8388608.f) - 0x4B000000;   // k < 2^23: its integer value
 }
 
@@ -47,7 +54,7 @@ __device__ __forceinline__ int bin_of(float r2, float w, float inv_w, int n_bins
 // padding slots at the end of a type group are skipped) and its lanes take 32 consecutive J atoms
 // at a time, so every lane holds a real pair except at the end of a row.  Counts go to one shared
 // histogram per warp, then to the global histogram with integer atomics.
-__global__ void __launch_bounds__(kTile)
+__global__ void __launch_bounds__(kTile, 12)
     k_pair_histogram(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items, int n_items,
                      int n_bins, float r_max, int n_pairs, int *__restrict__ hist,
                      unsigned long long *__restrict__ dropped, int jcap, int *__restrict__ ticket)
