@@ -8,6 +8,7 @@ import torch
 from oracle import mlp as ref
 from paper_1306_2258_gb300 import _lib
 from paper_1306_2258_gb300.surrogate import SurrogateMLP, run_screen
+from tests import mlp_bounds
 
 pytestmark = pytest.mark.gpu
 
@@ -70,7 +71,7 @@ def _net_and_data(n_in=64, h=48, n_out=13, B=40, seed=7):
 
 def test_forward_and_gradients_match_reference():
     net, x, t = _net_and_data()
-    p = net.unpack(net.state()["params"])
+    p = net.unpack(net.init_params(7))
     y = net.predict(torch.as_tensor(x).cuda()).cpu().numpy()
     y_ref, _ = ref.forward(p, x)
     assert _rel(y, y_ref) <= 1e-3
@@ -84,19 +85,13 @@ def test_forward_and_gradients_match_reference():
 
 
 def test_adam_steps_match_reference():
+    """Three steps on ragged sizes (batch 40, 13 outputs: partial tiles everywhere), each from the
+    reference's own state, element by element."""
     net, x, t = _net_and_data(seed=8)
-    st = net.state()
-    p = {k: v.astype(np.float64) for k, v in net.unpack(st["params"]).items()}
-    m = {k: np.zeros_like(v) for k, v in p.items()}
-    v = {k: np.zeros_like(vv) for k, vv in p.items()}
-    for step in (1, 2, 3):
-        _, g = net.grads(x, t)
-        gd = {k: vv.astype(np.float64) for k, vv in net.unpack(g).items()}
-        net.train_step(x, t, 1e-3)
-        p, m, v = ref.adam_step(p, gd, m, v, step, lr=1e-3)
-        got = net.unpack(net.state()["params"])
-        for k in p:
-            assert np.max(np.abs(got[k] - p[k])) <= 1e-6, (step, k)
+    rng = np.random.default_rng(80)
+    batches = [(x, t)] + [(rng.standard_normal(x.shape).astype(np.float32),
+                           rng.standard_normal(t.shape).astype(np.float32)) for _ in range(2)]
+    mlp_bounds.adam_steps(net, batches, 1e-3, 8)
     net.close()
 
 
