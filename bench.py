@@ -540,6 +540,13 @@ def run_ours(args):
     }
     if not args.skip_rows:
         line["rows"] = run_rows(dev, stream)
+        h = line["rows"].get("histogram_c5")
+        if h and meas.get("atoms_shared"):
+            # one shared-memory atomic add per pair: the conflict-free atomic rate bounds the kernel
+            h["roofline"] = {"bound": "shared atomics", "achieved": h["value"], "peak": meas["atoms_shared"],
+                             "unit": "pairs/s (one shared atomic add each)",
+                             "frac": h["value"] / meas["atoms_shared"],
+                             "peak_basis": "sas_measure_peaks: conflict-free shared-memory integer atomic adds/s"}
     if not args.skip_cpu and world == 1:
         line["cpu_baseline"], _ = _cpu_oracle_sample(w, seconds_hint=15.0)
         line["cpu_baseline"]["cases"] = _cpu_oracle_cases()

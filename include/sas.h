@@ -208,8 +208,9 @@ sas_status sas_profile_vjp_atomic(sas_ctx *ctx, const float *coords, int64_t n_a
  * out[0] FP32 FMA lane operations/s (scalar FFMA), out[1] the same with packed f32x2 FMA (2 per
  * instruction and lane), out[2] MUFU sine operations/s (__sinf), out[3] FP64 FMA lane
  * operations/s, out[4] the SM clock (MHz) seen during the FFMA run (clock64 against the global
- * timer).  Each kernel runs about 10 ms on `stream`; the call waits for them.  out is host memory
- * of n_out >= 5 doubles.  Errors: INVALID_ARG, CUDA.
+ * timer), and with n_out >= 6 out[5] shared-memory integer atomic adds/s without bank conflicts
+ * (each lane adding to a word of its own bank).  Each kernel runs about 10 ms on `stream`; the
+ * call waits for them.  out is host memory of n_out >= 5 doubles.  Errors: INVALID_ARG, CUDA.
  */
 sas_status sas_measure_peaks(double *out, int n_out, void *stream);
 
@@ -220,6 +221,8 @@ sas_status sas_measure_peaks(double *out, int n_out, void *stream);
  * Distance rule (identical on every platform): dx = x_i - x_j (likewise dy, dz) in float32,
  *   r2 = fmaf(dz, dz, fmaf(dy, dy, dx*dx)); w = r_max / n_bins; e_k = (float)k * w; e_k2 = e_k*e_k;
  *   bin = max{k : e_k2 <= r2}, dropped if bin >= n_bins.
+ * n_bins in [1, 4096]; r_max <= 1e18 and r_max / n_bins >= 1e-12 (so that every e_k2 is a normal
+ * float), else SAS_ERR_INVALID_ARG.
  * The caller's float32 coordinates are used unchanged (no centering).
  */
 sas_status sas_pair_histogram(sas_ctx *ctx, const float *coords, const int32_t *types, int64_t n_atoms,

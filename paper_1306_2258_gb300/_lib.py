@@ -294,11 +294,12 @@ def sas_gather_rows(src, row_bytes, idx, n_idx, dst, stream=None):
 
 def sas_measure_peaks(stream=None) -> dict:
     """Measured peaks of the current device: FP32 FMA and packed-FMA lane-ops/s, MUFU sine ops/s,
-    FP64 FMA lane-ops/s and the SM clock (MHz) of the FMA run."""
-    out = np.zeros(5)
-    check(load().sas_measure_peaks(out.ctypes.data, 5, stream_handle(stream)))
+    FP64 FMA lane-ops/s, the SM clock (MHz) of the FMA run, and conflict-free shared-memory integer
+    atomic adds/s."""
+    out = np.zeros(6)
+    check(load().sas_measure_peaks(out.ctypes.data, 6, stream_handle(stream)))
     return {"ffma": float(out[0]), "ffma2": float(out[1]), "mufu_sin": float(out[2]), "dfma": float(out[3]),
-            "sm_mhz": float(out[4])}
+            "sm_mhz": float(out[4]), "atoms_shared": float(out[5])}
 
 
 def sas_last_error() -> str:

@@ -6,9 +6,21 @@
 // Bin rule, identical to the CPU oracle bit for bit: dx = x_i - x_j (float32,
 // likewise dy, dz), r2 = fma(dz, dz, fma(dy, dy, dx*dx)), w = r_max / n_bins,
 // e_k = k*w, e_k^2 = e_k*e_k (each one float32 rounding), and the pair goes to
-// bin max{k : e_k^2 <= r2}, or is dropped when that is n_bins.  The square
-// root only gives a first guess; the edge comparisons decide.  Counts are
-// integers, so the result does not depend on the order of the atomics.
+// bin max{k : e_k^2 <= r2}, or is dropped when that is n_bins or more.  Counts
+// are integers, so the result does not depend on the order of the atomics.
+//
+// The bin takes one edge comparison.  With s = sqrt(r2) / w and u = 2^-24,
+// e_k^2 lies within 3u (relative) of k^2 w^2, so the rule's k satisfies
+// s (1 - 2u) - 1 < k < s (1 + 2u).  The guess g = floor(r2 * rsqrt(r2) * c),
+// c = (1 - 2^-16) / w, carries a relative error below 2^-21 (the approximate
+// reciprocal square root within 2^-22, four float32 roundings) against the
+// 2^-16 bias, so g <= k; and g > k - 2 while s (2^-16 + 2^-21 + 2u) < 1, that
+// is for s below 60,000: n_bins <= 4096 leaves a wide margin.  So k = g + 1
+// exactly when e_{g+1}^2 <= r2, and e_{g+1} = fma(g, w, w) is the rule's
+// float32 (g + 1) * w.  The argument checks of the host keep w^2 and every
+// e_k^2 normal and finite (w >= 1e-12, r_max <= 1e18).
+#include <climits>
+
 #include "sas_internal.h"
 
 namespace sas {
@@ -17,44 +29,36 @@ namespace {
 
 constexpr int kWarps = kTile / 32;
 
-// The rare correction of a bin guess k that an edge comparison rejected: walk down while e_k^2 > r2,
-// then up while e_{k+1}^2 <= r2 (a step or two at most).  Out of line, so that the common path
-// branches around it instead of carrying it predicated.
-__device__ __noinline__ float bin_fixup(float k, float r2, float w, float nb)
+__device__ __forceinline__ float rsqrt_approx(float x)
 {
-    for (int guard = 0; guard < 8 && k > 0.f; ++guard) {
-        const float ek = __fmul_rn(k, w);
-        if (__fmul_rn(ek, ek) <= r2) break;
-        k -= 1.f;
-    }
-    for (int guard = 0; guard < 8 && k < nb; ++guard) {
-        const float ek = __fmul_rn(k + 1.f, w);
-        if (__fmul_rn(ek, ek) > r2) break;
-        k += 1.f;
-    }
-    return k;
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
-// Bin of r2 under the rule above: max{k : e_k^2 <= r2} with e_k^2 = fl(fl(k w)^2), capped at
-// n_bins.  The first guess comes from the hardware reciprocal square root; the edge comparisons
-// (the rule's own float32 roundings) decide: straight-line when the guess is right (almost
-// always), the out-of-line walk otherwise.
-__device__ __forceinline__ int bin_of(float r2, float w, float inv_w, int n_bins)
+// Bin indices of two squared distances (packed), n_bins or more for a dropped pair.  A guess at or
+// above n_bins is clamped to it (the pair is dropped either way, and the clamp keeps the guess an
+// exact float32 integer).
+__device__ __forceinline__ int2 bins_of(float2 r2, float w, float c, float nb)
 {
-    const float nb = (float)n_bins;
-    float k = fminf(fmaxf(floorf(r2 * rsqrtf(fmaxf(r2, 1e-30f)) * inv_w), 0.f), nb);
-    const float elo = __fmul_rn(k, w), ehi = __fmul_rn(k + 1.f, w);
-    const bool lo_ok = k == 0.f || __fmul_rn(elo, elo) <= r2;
-    const bool hi_ok = k == nb || __fmul_rn(ehi, ehi) > r2;
-    if (!(lo_ok && hi_ok)) k = bin_fixup(k, r2, w, nb);
-    return __float_as_int(k + 8388608.f) - 0x4B000000;   // k < 2^23: its integer value
+    // r2 = 0 reads the reciprocal square root of 1e-30 (guess 0); r2 = inf gives a NaN guess, which
+    // fminf turns into n_bins, and e^2 <= inf then makes it n_bins + 1: dropped, as the rule says
+    const float2 rs = make_float2(rsqrt_approx(fmaxf(r2.x, 1e-30f)), rsqrt_approx(fmaxf(r2.y, 1e-30f)));
+    const float2 sc = __fmul2_rn(__fmul2_rn(r2, rs), make_float2(c, c));
+    const float2 g = make_float2(fminf(floorf(sc.x), nb), fminf(floorf(sc.y), nb));
+    const float2 e = __ffma2_rn(g, make_float2(w, w), make_float2(w, w));   // (g + 1) w, one rounding
+    const float2 e2 = __fmul2_rn(e, e);
+    const float2 gb = __fadd2_rn(g, make_float2(8388608.f, 8388608.f));   // g <= 4096: its integer value
+    return make_int2(__float_as_int(gb.x) - 0x4B000000 + (e2.x <= r2.x),
+                     __float_as_int(gb.y) - 0x4B000000 + (e2.y <= r2.y));
 }
 
-// One work item per CTA at a time.  Warp v takes the real rows i = v, v+4, ... of the I-tile (the
-// padding slots at the end of a type group are skipped) and its lanes take 32 consecutive J atoms
-// at a time, so every lane holds a real pair except at the end of a row.  Counts go to one shared
-// histogram per warp, then to the global histogram with integer atomics.
-__global__ void __launch_bounds__(kTile, 12)
+// One work item per CTA at a time.  Warp v takes the real rows of the I-tile two at a time,
+// i0 = v + 8m and i1 = i0 + 4 (the padding slots at the end of a type group are skipped), and its
+// lanes take 32 consecutive J atoms at a time: each lane bins the pairs (i0, j) and (i1, j) with
+// packed FP32 arithmetic.  Counts go to one shared histogram per warp with an overflow bin for the
+// dropped pairs, then to the global histogram with integer atomics.
+__global__ void __launch_bounds__(kTile, 10)
     k_pair_histogram(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items, int n_items,
                      int n_bins, float r_max, int n_pairs, int *__restrict__ hist,
                      unsigned long long *__restrict__ dropped, int jcap, int *__restrict__ ticket)
@@ -62,11 +66,13 @@ __global__ void __launch_bounds__(kTile, 12)
     extern __shared__ float4 smem[];
     float4 *sj = smem;                                            // [jcap]
     float4 *si = sj + jcap;                                       // [kTile]
-    int *wh = reinterpret_cast<int *>(si + kTile);                // [kWarps][n_bins]
+    int *wh = reinterpret_cast<int *>(si + kTile);                // [kWarps][n_bins + 1]
     __shared__ int next_item, jreal;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int stride = n_bins + 1;
     const float w = __fdiv_rn(r_max, (float)n_bins);
-    const float inv_w = __fdiv_rn(1.0f, w);
+    const float c = __fmul_rn(__fdiv_rn(1.0f, w), 1.0f - 0x1p-16f);
+    const float nb = (float)n_bins;
     int it = blockIdx.x;
     while (it < n_items) {
         const Item item = items[it];
@@ -83,7 +89,7 @@ __global__ void __launch_bounds__(kTile, 12)
             sj[j] = x;
             real += x.w != 0.f;
         }
-        for (int k = tid; k < kWarps * n_bins; k += kTile) wh[k] = 0;
+        for (int k = tid; k < kWarps * stride; k += kTile) wh[k] = 0;
         const float4 xt = Xb[item.i0 + tid];
         si[tid] = xt;
         if (real) atomicAdd(&jreal, real);
@@ -91,32 +97,37 @@ __global__ void __launch_bounds__(kTile, 12)
         // type group)
         const int ilen = __syncthreads_count(xt.w != 0.f);
         const int jlen = jreal;
-        int *h = wh + warp * n_bins;
-        unsigned drop = 0;
-        for (int i = warp; i < ilen; i += kWarps) {
-            const float4 xi = si[i];
-            const int jstart = item.diag ? i + 1 : 0;   // pairs with j <= i are not pairs of i<j
+        int *h = wh + warp * stride;
+        for (int i0 = warp; i0 < ilen; i0 += 2 * kWarps) {
+            const int i1 = i0 + kWarps;
+            const float4 a = si[i0];
+            const float4 b = si[i1 < ilen ? i1 : i0];
+            // pairs with j <= i are not pairs of i<j; a missing second row takes no pair
+            const int jstart = item.diag ? i0 + 1 : 0;
+            const int jmin1 = i1 < ilen ? (item.diag ? i1 : -1) : INT_MAX;
 #pragma unroll 2
             for (int j = jstart + lane; j < jlen; j += 32) {
                 const float4 xj = sj[j];
-                const float dx = __fsub_rn(xi.x, xj.x), dy = __fsub_rn(xi.y, xj.y), dz = __fsub_rn(xi.z, xj.z);
-                const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                const int k = bin_of(r2, w, inv_w, n_bins);
-                if (k >= n_bins)
-                    ++drop;
-                else
-                    atomicAdd(&h[k], 1);
+                const float2 dx = make_float2(__fsub_rn(a.x, xj.x), __fsub_rn(b.x, xj.x));
+                const float2 dy = make_float2(__fsub_rn(a.y, xj.y), __fsub_rn(b.y, xj.y));
+                const float2 dz = make_float2(__fsub_rn(a.z, xj.z), __fsub_rn(b.z, xj.z));
+                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                const int2 k = bins_of(r2, w, c, nb);
+                atomicAdd(&h[min(k.x, n_bins)], 1);
+                if (j > jmin1) atomicAdd(&h[min(k.y, n_bins)], 1);
             }
         }
-        for (int o = 16; o > 0; o >>= 1) drop += __shfl_xor_sync(0xffffffffu, drop, o);
-        if (lane == 0 && drop) atomicAdd(&dropped[item.batch], (unsigned long long)drop);
         __syncthreads();
         int *hb = hist + ((int64_t)item.batch * n_pairs + item.pair) * n_bins;
-        for (int k = tid; k < n_bins; k += kTile) {
+        for (int k = tid; k <= n_bins; k += kTile) {
             int sum = 0;
 #pragma unroll
-            for (int v = 0; v < kWarps; ++v) sum += wh[v * n_bins + k];
-            if (sum) atomicAdd(&hb[k], sum);
+            for (int v = 0; v < kWarps; ++v) sum += wh[v * stride + k];
+            if (sum == 0) continue;
+            if (k < n_bins)
+                atomicAdd(&hb[k], sum);
+            else
+                atomicAdd(&dropped[item.batch], (unsigned long long)sum);
         }
         it = next_item;
     }
@@ -126,7 +137,7 @@ __global__ void __launch_bounds__(kTile, 12)
 
 size_t histogram_smem(int jcap, int n_bins)
 {
-    return (size_t)(jcap + kTile) * sizeof(float4) + (size_t)kWarps * n_bins * sizeof(int);
+    return (size_t)(jcap + kTile) * sizeof(float4) + (size_t)kWarps * (n_bins + 1) * sizeof(int);
 }
 
 cudaError_t launch_pair_histogram(const float4 *X, int64_t npad, const Item *items, int n_items,

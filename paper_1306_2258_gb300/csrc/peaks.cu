@@ -5,6 +5,8 @@
 //   FFMA2  packed f32x2 fused multiply-add             2 lane operations
 //   MUFU   __sinf (one multiply and one MUFU.SIN)      counted as 1 MUFU operation
 //   DFMA   FP64 fused multiply-add                     1 lane operation
+//   ATOMS  shared-memory integer atomic add            1 lane operation (each lane its own word,
+//          a bank of its own: the conflict-free rate, the denominator of the pair histogram)
 // The chains contract toward a fixed point (x -> 0.999 x + 1e-3), so no value overflows or
 // becomes subnormal.  The FFMA kernel also reads the SM clock against the global timer, which
 // gives the clock the measurement ran at.
@@ -59,6 +61,17 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak(int iters, float m, float
             for (int c = 0; c < kChains; ++c) a[c] = __sinf(a[c]) + k;
 #pragma unroll
         for (int c = 0; c < kChains; ++c) r += a[c];
+    } else if (KIND == 4) {
+        __shared__ int cnt[kChains][kPeakThreads];
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) cnt[c][threadIdx.x] = 0;
+        __syncthreads();
+        for (int i = 0; i < iters; ++i)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) atomicAdd(&cnt[c][threadIdx.x], 1);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) r += (float)cnt[c][threadIdx.x];
     } else {
         double a[kChains];
         const double md = m, kd = k;
@@ -121,13 +134,14 @@ extern "C" sas_status sas_measure_peaks(double *out, int n_out, void *stream)
     if (e == cudaSuccess) e = cudaMalloc(&clk, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    float ms[4] = {0.f, 0.f, 0.f, 0.f};
+    float ms[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     // iterations: about 10 ms per kernel at the expected rates
-    const int it_f = 160000, it_f2 = 80000, it_m = 20000, it_d = 2500;
+    const int it_f = 160000, it_f2 = 80000, it_m = 20000, it_d = 2500, it_a = 20000;
     if (e == cudaSuccess) e = timed<0>(grid, it_f, sink, clk, e0, e1, s, ms[0]);
     if (e == cudaSuccess) e = timed<1>(grid, it_f2, sink, clk, e0, e1, s, ms[1]);
     if (e == cudaSuccess) e = timed<2>(grid, it_m, sink, clk, e0, e1, s, ms[2]);
     if (e == cudaSuccess) e = timed<3>(grid, it_d, sink, clk, e0, e1, s, ms[3]);
+    if (e == cudaSuccess && n_out >= 6) e = timed<4>(grid, it_a, sink, clk, e0, e1, s, ms[4]);
     unsigned long long hclk[2] = {0, 0};
     if (e == cudaSuccess) e = cudaMemcpy(hclk, clk, sizeof hclk, cudaMemcpyDeviceToHost);
     if (e0) cudaEventDestroy(e0);
@@ -145,5 +159,6 @@ extern "C" sas_status sas_measure_peaks(double *out, int n_out, void *stream)
     out[2] = threads * kChains * it_m / (ms[2] * 1e-3);         // MUFU sin ops/s
     out[3] = threads * kChains * it_d / (ms[3] * 1e-3);         // DFMA lane-ops/s
     out[4] = hclk[1] ? (double)hclk[0] / (double)hclk[1] * 1e3 : 0.0;   // SM MHz during the FFMA run
+    if (n_out >= 6) out[5] = threads * kChains * it_a / (ms[4] * 1e-3);   // shared atomic adds/s
     return SAS_OK;
 }

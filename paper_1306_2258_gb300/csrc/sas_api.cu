@@ -1124,6 +1124,8 @@ sas_status sas_pair_histogram(sas_ctx *ctx, const float *coords, const int32_t *
     if (st != SAS_OK) return st;
     if (n_bins < 1 || n_bins > 4096) return fail(SAS_ERR_INVALID_ARG, "n_bins must be in [1, 4096]");
     if (!(r_max > 0.f) || !std::isfinite(r_max)) return fail(SAS_ERR_INVALID_ARG, "r_max must be positive");
+    if (!(r_max <= 1e18f) || !(r_max / (float)n_bins >= 1e-12f))
+        return fail(SAS_ERR_INVALID_ARG, "r_max must be at most 1e18 and r_max / n_bins at least 1e-12");
     if (batch > 0 && !hist_out) return fail(SAS_ERR_INVALID_ARG, "null output");
     if (batch == 0) return SAS_OK;
     cudaStream_t s = (cudaStream_t)stream;

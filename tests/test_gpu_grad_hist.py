@@ -232,6 +232,53 @@ def test_histogram_lattice_edges_and_drops_exact():
     p.close()
 
 
+def _edge_pairs(n_bins, r_max, seed, n_k=400):
+    """Two-atom conformers whose distance lies on a bin edge e_k = fl(k w) or a few float32 steps to
+    either side of it, along random directions from random origins (so that every rounding of the
+    distance rule takes part)."""
+    rng = np.random.default_rng(seed)
+    w = np.float32(np.float32(r_max) / np.float32(n_bins))
+    ks = np.unique(np.concatenate([[0, 1, 2, n_bins - 1, n_bins, n_bins + 1], rng.integers(0, n_bins + 2, n_k)]))
+    X = []
+    for k in ks:
+        e = np.float32(np.float32(k) * w)
+        for m in (-3, -1, 0, 1, 3):
+            r = np.float32(e * np.float32(1.0 + m * 2.0 ** -24)) if e > 0 else np.float32(abs(m) * 1e-6)
+            # from the origin along an axis (r2 = fl(r*r), equal to e_k^2 = fl(e_k*e_k) for m = 0), and
+            # from a random origin along a random direction
+            X.append([np.zeros(3, np.float32), np.array([r, 0, 0], np.float32)])
+            o = rng.uniform(-50, 50, 3).astype(np.float32)
+            d = rng.standard_normal(3)
+            X.append([o, (o + r * d / np.linalg.norm(d)).astype(np.float32)])
+    return np.asarray(X, np.float32)
+
+
+@pytest.mark.parametrize("n_bins,r_max", [(256, 120.0), (4096, 97.3), (1, 5.0), (1000, 0.013), (333, 3.0e4)])
+def test_histogram_bin_edges_exact(n_bins, r_max):
+    """Distances on and beside every kind of bin edge (the first, the last, beyond the last) take
+    the oracle's bin, and drops are counted as it counts them."""
+    X = _edge_pairs(n_bins, r_max, n_bins)
+    types = np.zeros(2, np.int32)
+    p = Profile(wl.form_factor_coefficients(1, 1), wl.q_grid(0, 0.5, 11))
+    h, d = p.pair_histogram(torch.as_tensor(X).cuda(), types, n_bins=n_bins, r_max=r_max)
+    h, d = h.cpu().numpy(), d.cpu().numpy()
+    p.close()
+    for c in range(X.shape[0]):
+        hr, dr = oracle.pair_histogram(X[c], types, 1, n_bins, r_max)
+        assert int(d[c]) == dr, c
+        assert np.array_equal(h[c], hr), c
+
+
+def test_histogram_rejects_bins_outside_the_float_range():
+    p = Profile(wl.form_factor_coefficients(1, 1), wl.q_grid(0, 0.5, 11))
+    x = torch.zeros((2, 3), device="cuda")
+    for n_bins, r_max in ((4096, 1e-9), (10, 1e19), (0, 10.0), (4097, 10.0), (10, float("inf"))):
+        with pytest.raises(_lib.SasError) as e:
+            p.pair_histogram(x, np.zeros(2, np.int32), n_bins=n_bins, r_max=r_max)
+        assert e.value.status == _lib.SAS_ERR_INVALID_ARG
+    p.close()
+
+
 def test_histogram_batch_of_conformers():
     w = wl.c5_ensemble(n_conf=6, n=2000)
     p = Profile(w["coef"], w["q"])

@@ -5,8 +5,10 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from oracle import mlp as ref
-from paper_1306_2258_gb300 import _lib
+from paper_1306_2258_gb300 import _lib, workloads as wl
+from paper_1306_2258_gb300.profile import Profile
 from paper_1306_2258_gb300.surrogate import SurrogateMLP, run_screen
 from tests import mlp_bounds
 
@@ -144,3 +146,22 @@ def test_network_gains_over_the_binned_debye_sum_at_the_same_exact_budget():
     assert net["recall_of_exact_top_k"] >= base["recall_of_exact_top_k"]
     assert net["spearman_rank_corr"] >= base["spearman_rank_corr"]
     assert net["exact_rank_of_found"] <= base["exact_rank_of_found"]
+
+
+def test_the_exact_profiles_the_screens_are_scored_by_match_the_oracle():
+    """The screen tests score both rankings by the exact kernel's profiles of the 768-conformer,
+    600-atom ensemble; conformers from its start, middle and end, and the target, agree with the
+    oracle's FP64 sum."""
+    w = wl.c5_ensemble(n_conf=768, n=600)
+    types = w["base"].types
+    p = Profile(w["coef"], w["q"])
+    tt = torch.as_tensor(types).cuda()
+    idx = [0, 383, 767]
+    I = p(torch.as_tensor(w["conformers"][idx]).cuda(), tt).cpu().numpy()
+    It = p(torch.as_tensor(w["target"].coords).cuda(), tt).cpu().numpy()
+    p.close()
+    for row, c in zip(I, idx):
+        ref_I = oracle.profile(w["conformers"][c].astype(np.float64), types, w["coef"], w["q"])
+        assert np.max(np.abs(row - ref_I) / ref_I) <= 1e-5, c
+    ref_t = oracle.profile(w["target"].coords.astype(np.float64), types, w["coef"], w["q"])
+    assert np.max(np.abs(It - ref_t) / ref_t) <= 1e-5

@@ -19,3 +19,4 @@ def test_measured_peaks_are_physical():
         assert 0.5 * lanes < m[k] <= 1.05 * lanes, (k, m[k], lanes)
     assert 0.0 < m["mufu_sin"] <= 0.3 * lanes        # MUFU: a fraction of the FP32 rate
     assert 0.0 < m["dfma"] <= 0.1 * lanes            # FP64 is a small fraction on this part
+    assert 0.0 < m["atoms_shared"] <= 0.25 * lanes   # at most one 32-lane atomic per SM clock
