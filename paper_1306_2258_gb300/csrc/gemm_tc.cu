@@ -12,7 +12,9 @@
 //    descriptors into an FP32 accumulator in tensor memory, and frees a stage by committing the
 //    stage's MMAs to its "empty" mbarrier; a last commit signals "done";
 //  * then every warp reads its 32 accumulator lanes (rows) with tcgen05.ld and applies the
-//    epilogue.
+//    epilogue (eight independent columns at a time, 16-byte stores where aligned).
+// Split-K (launch_gemm_splitk): the grid's z dimension cuts K into slices of whole stages, each
+// CTA writing its slice's FP32 product to its own output plane; the caller sums the planes.
 // Problems of at least two 128 x 256 tiles per SM take the persistent form k_gemm_tcp instead: one
 // CTA per SM walks its tiles with warp-specialized roles (producer, MMA issuer, four epilogue warps)
 // and two accumulators in tensor memory, so a tile's epilogue runs under the next tile's main loop.
@@ -146,12 +148,54 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 
+// Epilogue of 8 consecutive columns col0.. of one row (col0 < N): x = accumulator (+ bias) to C in
+// FP32 and bfloat16(x or GELU(x)) to D.  The eight values are independent (their GELUs overlap),
+// and whole aligned groups go out as 16-byte stores.
+__device__ __forceinline__ void store8(const float (&v)[8], bool have_acc, int row, int col0, int N,
+                                       const float *__restrict__ bias, float *__restrict__ C, int ldc,
+                                       bf16 *__restrict__ D, int ldd, int gelu)
+{
+    const bool whole = col0 + 8 <= N;
+    float x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        x[k] = have_acc ? v[k] : 0.f;
+        if (bias && (whole || col0 + k < N)) x[k] += bias[col0 + k];
+    }
+    if (C) {
+        float *cp = C + (size_t)row * ldc + col0;
+        if (whole && (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
+            reinterpret_cast<float4 *>(cp)[0] = make_float4(x[0], x[1], x[2], x[3]);
+            reinterpret_cast<float4 *>(cp)[1] = make_float4(x[4], x[5], x[6], x[7]);
+        } else {
+            for (int k = 0; k < 8 && col0 + k < N; ++k) cp[k] = x[k];
+        }
+    }
+    if (D) {
+        uint32_t p[4];
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+            const float a = gelu ? gelu_f(x[k]) : x[k], b = gelu ? gelu_f(x[k + 1]) : x[k + 1];
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);   // .x = a (lower address), .y = b
+            p[k / 2] = *reinterpret_cast<const uint32_t *>(&h2);
+        }
+        bf16 *dp = D + (size_t)row * ldd + col0;
+        if (whole && (reinterpret_cast<uintptr_t>(dp) & 15) == 0) {
+            *reinterpret_cast<uint4 *>(dp) = make_uint4(p[0], p[1], p[2], p[3]);
+        } else {
+            const bf16 *h = reinterpret_cast<const bf16 *>(p);
+            for (int k = 0; k < 8 && col0 + k < N; ++k) dp[k] = h[k];
+        }
+    }
+}
+
 // S shared-memory stages (launch_bn chooses: a deep ring for grids that leave SMs idle, else about
 // 97 KB so that two CTAs share an SM and one's epilogue overlaps the other's main loop).
 template <int BN, int S>
 __global__ void __launch_bounds__(128, 2)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
-              const float *__restrict__ bias, float *__restrict__ C, int ldc, bf16 *__restrict__ D, int ldd, int gelu)
+              const float *__restrict__ bias, float *__restrict__ C, int ldc, bf16 *__restrict__ D, int ldd, int gelu,
+              int kper, int64_t c_split)
 {
     constexpr uint32_t kBBytes = BN * kTcK * 2;
     extern __shared__ uint8_t smem_raw[];
@@ -164,7 +208,10 @@ __global__ void __launch_bounds__(128, 2)
     __shared__ int fail;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * BN;
-    const int ksteps = (K + kTcK - 1) / kTcK;
+    // split-K: slice z of the K range (kper stages of 64) into its own FP32 output C + z c_split
+    const int kbeg = blockIdx.z * kper;
+    const int ksteps = max(0, min(kper, (K + kTcK - 1) / kTcK - kbeg));
+    if (C) C += blockIdx.z * c_split;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -195,8 +242,8 @@ __global__ void __launch_bounds__(128, 2)
                 break;
             }
             mbar_expect_tx(&full[s], kABytes + kBBytes);
-            tma_load_2d(sA + s * kABytes, &tmA, &full[s], ks * kTcK, m0);
-            tma_load_2d(sB + s * kBBytes, &tmB, &full[s], ks * kTcK, n0);
+            tma_load_2d(sA + s * kABytes, &tmA, &full[s], (kbeg + ks) * kTcK, m0);
+            tma_load_2d(sB + s * kBBytes, &tmB, &full[s], (kbeg + ks) * kTcK, n0);
             issued = ks + 1;
         }
         // the copies still in flight (normally all were consumed already): wait for the last phase
@@ -232,17 +279,8 @@ __global__ void __launch_bounds__(128, 2)
     for (int c0 = 0; c0 < BN; c0 += 8) {
         float v[8];
         tmem_ld8(trow + (uint32_t)c0, v);   // warp-collective: every lane of the warp takes part
-        if (row < M) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int col = n0 + c0 + k;
-                if (col >= N) break;
-                float x = ksteps > 0 ? v[k] : 0.f;
-                if (bias) x += bias[col];
-                if (C) C[(size_t)row * ldc + col] = x;
-                if (D) D[(size_t)row * ldd + col] = __float2bfloat16_rn(gelu ? gelu_f(x) : x);
-            }
-        }
+        if (row < M && n0 + c0 < N)
+            store8(v, ksteps > 0, row, n0 + c0, N, bias, C, ldc, D, ldd, gelu);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -455,15 +493,19 @@ bool make_map(CUtensorMap &map, const void *base, int rows, int K, int ld, int b
 
 template <int BN, int S>
 cudaError_t launch_bs(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias, float *C,
-                      int ldc, void *D, int ldd, int gelu, cudaStream_t s)
+                      int ldc, void *D, int ldd, int gelu, cudaStream_t s,
+                      int splits = 1)
 {
     CUtensorMap ta, tb;
     if (!make_map(ta, A, M, K, lda, kTcM) || !make_map(tb, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
     const size_t smem = (size_t)S * (kABytes + BN * kTcK * 2) + 1024;
     cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + kTcM - 1) / kTcM));
-    k_gemm_tc<BN, S><<<grid, 128, smem, s>>>(ta, tb, M, N, K, bias, C, ldc, static_cast<bf16 *>(D), ldd, gelu);
+    const int kt = (K + kTcK - 1) / kTcK;
+    const int kper = splits > 1 ? (kt + splits - 1) / splits : kt;
+    const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + kTcM - 1) / kTcM), (unsigned)(splits > 1 ? splits : 1));
+    k_gemm_tc<BN, S><<<grid, 128, smem, s>>>(ta, tb, M, N, K, bias, C, ldc, static_cast<bf16 *>(D), ldd, gelu, kper,
+                                             (int64_t)M * ldc);
     return cudaGetLastError();
 }
 
@@ -527,6 +569,22 @@ cudaError_t launch_gemm_tc(int M, int N, int K, const void *A, int lda, const vo
     const int tiles128 = mt * ((N + 127) / 128);
     if (N <= 64 || tiles128 < 64) return launch_bn<64>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s);
     return launch_bn<128>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s);
+}
+
+cudaError_t launch_gemm_splitk(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *ws, int splits,
+                               cudaStream_t s)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const int kt = (K + kTcK - 1) / kTcK;
+    if (splits < 1 || (kt + splits - 1) / splits * (splits - 1) >= kt || !gemm_tc_supported(K, A, lda, B, ldb))
+        return cudaErrorInvalidValue;   // every slice must hold at least one stage
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaErrorInvalidDevice;
+    const int64_t ctas = (int64_t)((N + 63) / 64) * ((M + kTcM - 1) / kTcM) * splits;
+    return ctas <= sms ? launch_bs<64, 8>(M, N, K, A, lda, B, ldb, nullptr, ws, N, nullptr, 0, 0, s, splits)
+                       : launch_bs<64, 4>(M, N, K, A, lda, B, ldb, nullptr, ws, N, nullptr, 0, 0, s, splits);
 }
 
 cudaError_t launch_gemm(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,

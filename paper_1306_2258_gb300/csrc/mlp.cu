@@ -9,9 +9,12 @@
 //                  FP32 accumulation with mma.sync m16n8k16 (64x64 CTA tile, four 32x32 warp
 //                  tiles); epilogue writes FP32 and/or bfloat16 of the value or of GELU(value).
 //   k_transpose    bfloat16 [R][C] -> [C][R] (the backward GEMMs' operands)
-//   k_mse_rows, k_mse_total  dY = 2 (Y - T) / (B Q) and the loss (per-row sums, then their sum; fixed order)
-//   k_gelu_bwd     dZ = dA * GELU'(Z), as FP32 and bfloat16
-//   k_colsum       bias gradients (8 row groups per column, then their sum; fixed order)
+//   k_splitk_gelu  the first layer's split-K slices summed in order, bias, GELU, bfloat16 and its
+//                  transpose
+//   k_mse_fused    dY = 2 (Y - T) / (B Q) as FP32, bfloat16 and transposed bfloat16, the output
+//                  bias gradient and the loss (fixed summation orders)
+//   k_act_bwd      dZ = dA * GELU'(Z) as FP32, bfloat16 and transposed bfloat16, and the bias
+//                  gradient (fixed summation order)
 //   k_adam         Adam on the FP32 masters, refreshing their bfloat16 copies
 // Every GEMM operand is rounded to bfloat16 exactly where the FP64 reference rounds it.
 #include <cuda_bf16.h>
@@ -139,78 +142,193 @@ __global__ void k_transpose(int R, int Rpad, int C, const bf16 *__restrict__ in,
     }
 }
 
-// dY = 2 (Y - T) / (B Q) on the valid [B][Q] block (zero in the padding), loss = mean square
-// One block per padded row b: dY, its bfloat16 copy, and the row's squared error (FP64, fixed
-// tree order).
-__global__ void k_mse_rows(int B, int Q, int Qpad, const float *__restrict__ Y, const float *__restrict__ T,
-                           float *__restrict__ dY, bf16 *__restrict__ dYb, double *__restrict__ rows)
+// Split-K epilogue of the first layer: x = the slices' FP32 partials ws[z][M][N] summed in slice
+// order, plus the bias; Z = x, A = bfloat16(GELU(x)), and the bfloat16 transpose At [N][ldt] of A
+// with zero rows [M, Mpad) (batch padding), the operand of the weight-gradient GEMM.  32 x 32
+// tiles, 32 x 8 threads.
+__global__ void __launch_bounds__(256)
+    k_splitk_gelu(int M, int Mpad, int N, int splits, const float *__restrict__ ws, const float *__restrict__ bias,
+                  float *__restrict__ Z, bf16 *__restrict__ A, bf16 *__restrict__ At, int ldt)
+{
+    __shared__ bf16 tile[32][34];
+    const int tx = threadIdx.x, ty = threadIdx.y, c0 = blockIdx.x * 32, r0 = blockIdx.y * 32, c = c0 + tx;
+    // the four rows' sums side by side, so that their loads are in flight together
+    float x[4] = {0.f, 0.f, 0.f, 0.f};
+    bool in[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) in[k] = r0 + ty + 8 * k < M && c < N;
+    for (int z = 0; z < splits; ++z) {
+        const float *w = ws + (size_t)z * M * N + c;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (in[k]) x[k] += w[(size_t)(r0 + ty + 8 * k) * N];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = r0 + ty + 8 * k;
+        bf16 a = __float2bfloat16_rn(0.f);
+        if (in[k]) {
+            const float v = x[k] + bias[c];
+            Z[(size_t)r * N + c] = v;
+            a = __float2bfloat16_rn(gelu_f(v));
+            A[(size_t)r * N + c] = a;
+        }
+        tile[ty + 8 * k][tx] = a;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {   // rows c0 + ty + 8k of At, columns r0 + tx
+        const int cc = c0 + ty + 8 * k, rr = r0 + tx;
+        if (cc < N && rr < Mpad) At[(size_t)cc * ldt + rr] = tile[tx][ty + 8 * k];
+    }
+}
+
+// The fused backward kernels below work on 32 x 32 tiles with 32 x 8 threads: thread (tx, ty) takes
+// column c0 + tx of rows r0 + ty + 8k, k = 0..3.  Column sums (the bias gradients) run in a fixed
+// order: a thread's 4 rows in order, then the 8 thread rows in order, then the row tiles in order,
+// summed by the last row tile of each column strip to finish (a counter per strip, reset by that
+// tile), so they repeat bit for bit.
+
+// Column partials of one tile in order, then, in the last row tile of the strip to finish, the
+// strip's column sums over the row tiles in order.  part: [row tiles][C] partials.
+__device__ __forceinline__ void strip_sums(float s, int c, int C, float *__restrict__ part, float *__restrict__ out,
+                                           unsigned *__restrict__ count)
+{
+    __shared__ float ps[8][33];
+    __shared__ bool last;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    ps[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && c < C) {
+        float t = ps[0][tx];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) t += ps[k][tx];
+        part[(size_t)blockIdx.y * C + c] = t;
+        __threadfence();
+    }
+    __syncthreads();
+    if (tx == 0 && ty == 0) last = atomicAdd(&count[blockIdx.x], 1u) == gridDim.y - 1;
+    __syncthreads();
+    if (!last) return;
+    if (ty == 0 && c < C) {
+        __threadfence();
+        float t = 0.f;
+        for (int y = 0; y < (int)gridDim.y; ++y) t += __ldcg(&part[(size_t)y * C + c]);
+        out[c] = t;
+    }
+    if (tx == 0 && ty == 0) count[blockIdx.x] = 0u;
+}
+
+// Backward of z -> GELU(z) on rows [0, B) of [B][C]: dZ = dA GELU'(Z) (FP32) and bfloat16(dZ); the
+// bfloat16 transpose dZt [C][ldt] with zero rows [B, Bpad) (batch padding) for the weight-gradient
+// GEMM; and the bias gradient db = the column sums of dZ.
+__global__ void __launch_bounds__(256)
+    k_act_bwd(int B, int Bpad, int C, const float *__restrict__ dA, const float *__restrict__ Z, float *__restrict__ dZ,
+              bf16 *__restrict__ dZb, bf16 *__restrict__ dZt, int ldt, float *__restrict__ part,
+              float *__restrict__ db, unsigned *__restrict__ count)
+{
+    __shared__ bf16 tile[32][34];
+    const int tx = threadIdx.x, ty = threadIdx.y, c0 = blockIdx.x * 32, r0 = blockIdx.y * 32, c = c0 + tx;
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = r0 + ty + 8 * k;
+        float v = 0.f;
+        if (r < B && c < C) {
+            const size_t i = (size_t)r * C + c;
+            v = dA[i] * gelu_grad_f(Z[i]);
+            dZ[i] = v;
+            dZb[i] = __float2bfloat16_rn(v);
+        }
+        s += v;
+        tile[ty + 8 * k][tx] = __float2bfloat16_rn(v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {   // rows c0 + ty + 8k of dZt, columns r0 + tx
+        const int cc = c0 + ty + 8 * k, rr = r0 + tx;
+        if (cc < C && rr < Bpad) dZt[(size_t)cc * ldt + rr] = tile[tx][ty + 8 * k];
+    }
+    strip_sums(s, c, C, part, db, count);
+}
+
+// The MSE loss of Y [Bpad][Qpad] against T [B][Q] and its gradient, one block per 8 padded rows
+// (Bpad is a multiple of 16), thread q on column q of each row in order: dY = 2 (Y - T) / (B Q) on
+// [B][Q] (zero in the rest of [Bpad][Qpad]), bfloat16(dY), and its transpose dYt [Qpad][ldt] (the
+// 8 rows of a column as one 16-byte store).  Per block, FP64 squared errors (a thread's rows in
+// order, then a fixed tree over the threads) into lpart and FP32 column partials into part.  The
+// last block to finish then forms, in fixed orders, the loss = sum of lpart / (B Q) and the bias
+// gradient db = the column partials summed over the blocks.  count: one zero-initialized counter
+// (left zero).
+__global__ void __launch_bounds__(128)
+    k_mse_fused(int B, int Bpad, int Q, int Qpad, const float *__restrict__ Y, const float *__restrict__ T,
+                float *__restrict__ dY, bf16 *__restrict__ dYb, bf16 *__restrict__ dYt, int ldt,
+                double *__restrict__ lpart, float *__restrict__ part, float *__restrict__ db, float *__restrict__ loss,
+                unsigned *__restrict__ count)
 {
     __shared__ double red[128];
-    const int b = blockIdx.x;
+    __shared__ bool last;
+    const int r0 = blockIdx.x * 8, tid = threadIdx.x;
     const double scale = 2.0 / ((double)B * Q);
     double s = 0.0;
-    for (int q = threadIdx.x; q < Qpad; q += blockDim.x) {
-        const int64_t i = (int64_t)b * Qpad + q;
-        float d = 0.f;
-        if (b < B && q < Q) {
-            const double e = (double)Y[i] - (double)T[(int64_t)b * Q + q];
-            s += e * e;
-            d = (float)(scale * e);
-        }
-        dY[i] = d;
-        dYb[i] = __float2bfloat16_rn(d);
-    }
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) rows[b] = red[0];
-}
-
-// loss = (sum of the row sums, fixed tree order) / (B Q)
-__global__ void k_mse_total(int B, int Q, int Bpad, const double *__restrict__ rows, float *__restrict__ loss)
-{
-    __shared__ double red[256];
-    double s = 0.0;
-    for (int b = threadIdx.x; b < Bpad; b += blockDim.x) s += rows[b];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *loss = (float)(red[0] / ((double)B * Q));
-}
-
-__global__ void k_gelu_bwd(int64_t n, const float *__restrict__ dA, const float *__restrict__ Z, float *__restrict__ dZ,
-                           bf16 *__restrict__ dZb)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float v = dA[i] * gelu_grad_f(Z[i]);
-    dZ[i] = v;
-    dZb[i] = __float2bfloat16_rn(v);
-}
-
-// out[c] = sum_r in[r][c] over r < R, in fixed order
-// out[c] = sum over rows of in[r][c]: 32 columns per block, 8 row groups (rows r = g, g+8, ...),
-// then the 8 partial sums in a fixed order.
-__global__ void k_colsum(int R, int C, const float *__restrict__ in, int ld, float *__restrict__ out)
-{
-    __shared__ float part[8][33];
-    const int c = blockIdx.x * 32 + threadIdx.x, g = threadIdx.y;
-    float s = 0.f;
-    if (c < C)
-        for (int r = g; r < R; r += 8) s += in[(size_t)r * ld + c];
-    part[g][threadIdx.x] = s;
-    __syncthreads();
-    if (g == 0 && c < C) {
-        float t = part[0][threadIdx.x];
+    for (int q = tid; q < Qpad; q += blockDim.x) {
+        float cs = 0.f;
+        uint32_t p[4];
 #pragma unroll
-        for (int k = 1; k < 8; ++k) t += part[k][threadIdx.x];
-        out[c] = t;
+        for (int k = 0; k < 8; ++k) {
+            const int r = r0 + k;
+            const int64_t i = (int64_t)r * Qpad + q;
+            float d = 0.f;
+            if (r < B && q < Q) {
+                const double e = (double)Y[i] - (double)T[(int64_t)r * Q + q];
+                s += e * e;
+                d = (float)(scale * e);
+            }
+            dY[i] = d;
+            const bf16 h = __float2bfloat16_rn(d);
+            dYb[i] = h;
+            cs += d;
+            const uint32_t u = (uint32_t)__bfloat16_as_ushort(h);
+            p[k / 2] = (k & 1) ? (p[k / 2] | (u << 16)) : u;
+        }
+        *reinterpret_cast<uint4 *>(dYt + (int64_t)q * ldt + r0) = make_uint4(p[0], p[1], p[2], p[3]);
+        part[(int64_t)blockIdx.x * Qpad + q] = cs;
+    }
+    red[tid] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (tid < o) red[tid] += red[tid + o];
+        __syncthreads();
+    }
+    __threadfence();   // this block's partials before the counter
+    __syncthreads();
+    if (tid == 0) {
+        lpart[blockIdx.x] = red[0];
+        __threadfence();
+        last = atomicAdd(count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // the loss: the blocks' sums, strided over the threads in order, then a fixed tree
+    double t = 0.0;
+    for (int y = tid; y < (int)gridDim.x; y += blockDim.x) t += __ldcg(&lpart[y]);
+    red[tid] = t;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (tid < o) red[tid] += red[tid + o];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        *loss = (float)(red[0] / ((double)B * Q));
+        *count = 0u;
+    }
+    // the bias gradient: each column's block partials in block order
+    for (int q = tid; q < Qpad; q += blockDim.x) {
+        float c = 0.f;
+#pragma unroll 8
+        for (int y = 0; y < (int)gridDim.x; ++y) c += __ldcg(&part[(int64_t)y * Qpad + q]);
+        db[q] = c;
     }
 }
 
@@ -260,26 +378,34 @@ cudaError_t launch_transpose_bf16(int R, int Rpad, int C, const void *in, int ld
     return cudaGetLastError();
 }
 
-cudaError_t launch_mse(int B, int Bpad, int Q, int Qpad, const float *Y, const float *T, float *dY, void *dYb,
-                       double *rows, float *loss, cudaStream_t s)
+cudaError_t launch_splitk_gelu(int M, int Mpad, int N, int splits, const float *ws, const float *bias, float *Z, void *A,
+                               void *At, int ldt, cudaStream_t s)
 {
-    if (Bpad <= 0) return cudaSuccess;
-    k_mse_rows<<<Bpad, 128, 0, s>>>(B, Q, Qpad, Y, T, dY, static_cast<bf16 *>(dYb), rows);
-    k_mse_total<<<1, 256, 0, s>>>(B, Q, Bpad, rows, loss);
+    if (Mpad <= 0 || N <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((N + 31) / 32), (unsigned)((Mpad + 31) / 32));
+    k_splitk_gelu<<<grid, dim3(32, 8), 0, s>>>(M, Mpad, N, splits, ws, bias, Z, static_cast<bf16 *>(A),
+                                               static_cast<bf16 *>(At), ldt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gelu_bwd(int64_t n, const float *dA, const float *Z, float *dZ, void *dZb, cudaStream_t s)
+cudaError_t launch_mse_fused(int B, int Bpad, int Q, int Qpad, const float *Y, const float *T, float *dY, void *dYb,
+                             void *dYt, int ldt, double *lpart, float *part, float *db, float *loss, unsigned *count,
+                             cudaStream_t s)
 {
-    if (n <= 0) return cudaSuccess;
-    k_gelu_bwd<<<blocks_for(n, 256), 256, 0, s>>>(n, dA, Z, dZ, static_cast<bf16 *>(dZb));
+    if (Bpad <= 0 || Qpad <= 0) return cudaSuccess;
+    if (Bpad % 8 != 0 || ldt % 8 != 0) return cudaErrorInvalidValue;   // 16-byte column stores of dYt
+    k_mse_fused<<<Bpad / 8, 128, 0, s>>>(B, Bpad, Q, Qpad, Y, T, dY, static_cast<bf16 *>(dYb), static_cast<bf16 *>(dYt),
+                                         ldt, lpart, part, db, loss, count);
     return cudaGetLastError();
 }
 
-cudaError_t launch_colsum(int R, int C, const float *in, int ld, float *out, cudaStream_t s)
+cudaError_t launch_act_bwd(int B, int Bpad, int C, const float *dA, const float *Z, float *dZ, void *dZb, void *dZt,
+                           int ldt, float *part, float *db, unsigned *count, cudaStream_t s)
 {
-    if (C <= 0) return cudaSuccess;
-    k_colsum<<<(C + 31) / 32, dim3(32, 8), 0, s>>>(R, C, in, ld, out);
+    if (Bpad <= 0 || C <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((C + 31) / 32), (unsigned)((Bpad + 31) / 32));
+    k_act_bwd<<<grid, dim3(32, 8), 0, s>>>(B, Bpad, C, dA, Z, dZ, static_cast<bf16 *>(dZb), static_cast<bf16 *>(dZt),
+                                           ldt, part, db, count);
     return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // inference, state transfer for checkpoints, and a plain bfloat16 GEMM for tests.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -66,7 +67,13 @@ struct sas_mlp {
     bf16 *W2t = nullptr, *W3t = nullptr;
     float *Xf = nullptr, *Tf = nullptr, *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dY = nullptr, *dA2 = nullptr,
           *dZ2 = nullptr, *dA1 = nullptr, *dZ1 = nullptr, *loss = nullptr;
-    double *rowloss = nullptr;   // per-row squared-error sums of the MSE
+    // scratch of the fused backward kernels: column partials, row losses, counters (left zero)
+    float *part = nullptr;
+    double *lpart = nullptr;
+    unsigned *count = nullptr;
+    // split-K slices of the first layer for small batches (few output tiles, K = n_in long)
+    float *ws = nullptr;
+    int ws_rows = 0, ws_splits = 0;
     bf16 *Xb = nullptr, *Xt = nullptr, *A1b = nullptr, *A1t = nullptr, *A2b = nullptr, *A2t = nullptr, *dYb = nullptr,
          *dYt = nullptr, *dZ2b = nullptr, *dZ2t = nullptr, *dZ1b = nullptr, *dZ1t = nullptr;
     std::vector<void *> owned;
@@ -98,13 +105,38 @@ void mlp_free(sas_mlp *m)
     m->owned.clear();
 }
 
+// Slices of the first layer's K range for batch B: 0 (one pass) unless its output tiles (128 x 64)
+// would leave three quarters of the SMs idle and K holds at least 8 stages of 64; then enough
+// slices of at least 4 stages to bring the CTAs near the SM count.
+int splitk_slices(const sas_mlp *m, int B)
+{
+    if (!m->ws || B > m->ws_rows) return 0;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int tiles = ((B + 127) / 128) * ((m->h + 63) / 64), kt = (m->n_in + 63) / 64;
+    if (kt < 8 || 4 * tiles > sms) return 0;
+    int z = std::min({m->ws_splits, sms / tiles, kt / 4});
+    while (z > 1 && (kt + z - 1) / z * (z - 1) >= kt) --z;   // no empty slice
+    return z >= 2 ? z : 0;
+}
+
 // The forward launches from device input xd [B][n_in] f32 to Y.
 sas_status mlp_forward_dev(sas_mlp *m, const float *xd, int B, cudaStream_t s)
 {
     MLP_TRY(launch_to_bf16((int64_t)B * m->n_in, xd, m->Xb, s));
     const bf16 *W1b = m->Pb + m->oW1, *W2b = m->Pb + m->oW2, *W3b = m->Pb + m->oW3;
-    MLP_TRY(launch_gemm(B, m->h, m->n_in, m->Xb, m->n_in, W1b, m->n_in, m->P + m->ob1, m->Z1, m->h, m->A1b, m->h, 1,
-                           s));
+    if (const int z = splitk_slices(m, B)) {
+        // first layer in K slices, then their sum, the bias, GELU and A1's transpose in one pass
+        MLP_TRY(launch_gemm_splitk(B, m->h, m->n_in, m->Xb, m->n_in, W1b, m->n_in, m->ws, z, s));
+        MLP_TRY(launch_splitk_gelu(B, round16(B), m->h, z, m->ws, m->P + m->ob1, m->Z1, m->A1b, m->A1t, round16(B), s));
+    } else {
+        MLP_TRY(launch_gemm(B, m->h, m->n_in, m->Xb, m->n_in, W1b, m->n_in, m->P + m->ob1, m->Z1, m->h, m->A1b, m->h,
+                            1, s));
+    }
     MLP_TRY(launch_gemm(B, m->h, m->h, m->A1b, m->h, W2b, m->h, m->P + m->ob2, m->Z2, m->h, m->A2b, m->h, 1, s));
     MLP_TRY(launch_gemm(B, m->n_outp, m->h, m->A2b, m->h, W3b, m->h, m->P + m->ob3, m->Y, m->n_outp, nullptr, 0, 0,
                            s));
@@ -133,26 +165,23 @@ sas_status mlp_forward(sas_mlp *m, const float *x, const float *t, int B, cudaSt
 sas_status mlp_backward(sas_mlp *m, int B, cudaStream_t s)
 {
     const int Bp = round16(B), h = m->h, Qp = m->n_outp;
-    MLP_TRY(launch_mse(B, Bp, m->n_out, Qp, m->Y, m->Tf, m->dY, m->dYb, m->rowloss, m->loss, s));
-    // layer 3
-    MLP_TRY(launch_transpose_bf16(Bp, Bp, Qp, m->dYb, Qp, m->dYt, Bp, s));
+    // layer 3: dY (with its transpose, the bias gradient and the loss)
+    MLP_TRY(launch_mse_fused(B, Bp, m->n_out, Qp, m->Y, m->Tf, m->dY, m->dYb, m->dYt, Bp, m->lpart, m->part,
+                             m->G + m->ob3, m->loss, m->count, s));
     MLP_TRY(launch_transpose_bf16(B, Bp, h, m->A2b, h, m->A2t, Bp, s));
     MLP_TRY(launch_gemm(Qp, h, Bp, m->dYt, Bp, m->A2t, Bp, nullptr, m->G + m->oW3, h, nullptr, 0, 0, s));
-    MLP_TRY(launch_colsum(Bp, Qp, m->dY, Qp, m->G + m->ob3, s));
     MLP_TRY(launch_gemm(B, h, Qp, m->dYb, Qp, m->W3t, Qp, nullptr, m->dA2, h, nullptr, 0, 0, s));
     // layer 2
-    MLP_TRY(launch_gelu_bwd((int64_t)B * h, m->dA2, m->Z2, m->dZ2, m->dZ2b, s));
-    MLP_TRY(launch_transpose_bf16(B, Bp, h, m->dZ2b, h, m->dZ2t, Bp, s));
-    MLP_TRY(launch_transpose_bf16(B, Bp, h, m->A1b, h, m->A1t, Bp, s));
+    MLP_TRY(launch_act_bwd(B, Bp, h, m->dA2, m->Z2, m->dZ2, m->dZ2b, m->dZ2t, Bp, m->part, m->G + m->ob2, m->count,
+                           s));
+    if (!splitk_slices(m, B)) MLP_TRY(launch_transpose_bf16(B, Bp, h, m->A1b, h, m->A1t, Bp, s));   // else done
     MLP_TRY(launch_gemm(h, h, Bp, m->dZ2t, Bp, m->A1t, Bp, nullptr, m->G + m->oW2, h, nullptr, 0, 0, s));
-    MLP_TRY(launch_colsum(B, h, m->dZ2, h, m->G + m->ob2, s));
     MLP_TRY(launch_gemm(B, h, h, m->dZ2b, h, m->W2t, h, nullptr, m->dA1, h, nullptr, 0, 0, s));
     // layer 1
-    MLP_TRY(launch_gelu_bwd((int64_t)B * h, m->dA1, m->Z1, m->dZ1, m->dZ1b, s));
-    MLP_TRY(launch_transpose_bf16(B, Bp, h, m->dZ1b, h, m->dZ1t, Bp, s));
+    MLP_TRY(launch_act_bwd(B, Bp, h, m->dA1, m->Z1, m->dZ1, m->dZ1b, m->dZ1t, Bp, m->part, m->G + m->ob1, m->count,
+                           s));
     MLP_TRY(launch_transpose_bf16(B, Bp, m->n_in, m->Xb, m->n_in, m->Xt, Bp, s));
     MLP_TRY(launch_gemm(h, m->n_in, Bp, m->dZ1t, Bp, m->Xt, Bp, nullptr, m->G + m->oW1, m->n_in, nullptr, 0, 0, s));
-    MLP_TRY(launch_colsum(B, h, m->dZ1, h, m->G + m->ob1, s));
     return SAS_OK;
 }
 
@@ -250,12 +279,19 @@ sas_status sas_mlp_create(int n_in, int n_hidden, int n_out, int max_batch, sas_
     m->oW3 = m->ob2 + h;
     m->ob3 = m->oW3 + Qp * h;
     m->np = m->ob3 + Qp;
+    // split-K slices of the first layer: batches up to 512 rows, at most 16 slices and 32 MB
+    m->ws_rows = (int)std::min<int64_t>(Bp, 512);
+    m->ws_splits = (int)std::max<int64_t>(2, std::min<int64_t>(16, ((int64_t)32 << 20) / ((int64_t)m->ws_rows * h * 4)));
     bool ok = mlp_alloc(m, m->P, m->np) && mlp_alloc(m, m->G, m->np) && mlp_alloc(m, m->Mo, m->np) &&
               mlp_alloc(m, m->Vo, m->np) && mlp_alloc(m, m->Pb, m->np) && mlp_alloc(m, m->W2t, h * h) &&
               mlp_alloc(m, m->W3t, h * Qp) && mlp_alloc(m, m->Xf, Bp * n_in) && mlp_alloc(m, m->Tf, Bp * n_out) &&
               mlp_alloc(m, m->Z1, Bp * h) && mlp_alloc(m, m->Z2, Bp * h) && mlp_alloc(m, m->Y, Bp * Qp) &&
               mlp_alloc(m, m->dY, Bp * Qp) && mlp_alloc(m, m->dA2, Bp * h) && mlp_alloc(m, m->dZ2, Bp * h) &&
-              mlp_alloc(m, m->dA1, Bp * h) && mlp_alloc(m, m->dZ1, Bp * h) && mlp_alloc(m, m->loss, 1) && mlp_alloc(m, m->rowloss, Bp) &&
+              mlp_alloc(m, m->dA1, Bp * h) && mlp_alloc(m, m->dZ1, Bp * h) && mlp_alloc(m, m->loss, 1) &&
+              mlp_alloc(m, m->part, std::max((Bp + 31) / 32 * h, Bp / 8 * Qp)) &&
+              mlp_alloc(m, m->lpart, Bp / 8) &&
+              mlp_alloc(m, m->count, std::max(h, Qp) / 32 + 2) &&
+              mlp_alloc(m, m->ws, (int64_t)m->ws_rows * h * m->ws_splits) &&
               mlp_alloc(m, m->Xb, Bp * n_in) && mlp_alloc(m, m->Xt, Bp * n_in) && mlp_alloc(m, m->A1b, Bp * h) &&
               mlp_alloc(m, m->A1t, Bp * h) && mlp_alloc(m, m->A2b, Bp * h) && mlp_alloc(m, m->A2t, Bp * h) &&
               mlp_alloc(m, m->dYb, Bp * Qp) && mlp_alloc(m, m->dYt, Bp * Qp) && mlp_alloc(m, m->dZ2b, Bp * h) &&
@@ -268,7 +304,9 @@ sas_status sas_mlp_create(int n_in, int n_hidden, int n_out, int max_batch, sas_
     if (cudaMemset(m->P, 0, sizeof(float) * m->np) != cudaSuccess ||
         cudaMemset(m->Mo, 0, sizeof(float) * m->np) != cudaSuccess ||
         cudaMemset(m->Vo, 0, sizeof(float) * m->np) != cudaSuccess ||
-        cudaMemset(m->G, 0, sizeof(float) * m->np) != cudaSuccess || mlp_refresh(m, 0) != SAS_OK ||
+        cudaMemset(m->G, 0, sizeof(float) * m->np) != cudaSuccess ||
+        cudaMemset(m->count, 0, sizeof(unsigned) * (size_t)(std::max(h, Qp) / 32 + 2)) != cudaSuccess ||
+        mlp_refresh(m, 0) != SAS_OK ||
         cudaStreamSynchronize(0) != cudaSuccess) {
         cudaGetLastError();
         mlp_free(m);

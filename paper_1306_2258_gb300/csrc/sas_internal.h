@@ -204,16 +204,27 @@ cudaError_t launch_surrogate_chi2(int n_conf, int n_q, const float *z, int ld, c
 cudaError_t launch_select_topk(int n, const double *chi2, int k, int32_t *top_idx, double *top_chi2, cudaStream_t s);
 cudaError_t launch_gather_rows(const void *src, int64_t row_bytes, const int32_t *idx, int64_t n_idx, void *dst,
                                cudaStream_t s);
+// Split-K on the tcgen05 GEMM: K cut into `splits` slices of whole 64-wide stages (none empty), slice
+// z's FP32 product of A [M][K] and B [N][K] into ws + z M N ([M][N], no bias).  cudaErrorInvalidValue
+// where the operands do not suit TMA or a slice would be empty.
+cudaError_t launch_gemm_splitk(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *ws, int splits,
+                               cudaStream_t s);
+cudaError_t launch_splitk_gelu(int M, int Mpad, int N, int splits, const float *ws, const float *bias, float *Z, void *A,
+                               void *At, int ldt, cudaStream_t s);
 // launch_gemm_tc where supported, else launch_gemm_tn.
 cudaError_t launch_gemm(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
                         float *C, int ldc, void *D, int ldd, int gelu, cudaStream_t s);
 cudaError_t launch_to_bf16(int64_t n, const float *x, void *y, cudaStream_t s);
 cudaError_t launch_transpose_bf16(int R, int Rpad, int C, const void *in, int ldin, void *out, int ldout,
                                   cudaStream_t s);
-cudaError_t launch_mse(int B, int Bpad, int Q, int Qpad, const float *Y, const float *T, float *dY, void *dYb,
-                       double *rows, float *loss, cudaStream_t s);
-cudaError_t launch_gelu_bwd(int64_t n, const float *dA, const float *Z, float *dZ, void *dZb, cudaStream_t s);
-cudaError_t launch_colsum(int R, int C, const float *in, int ld, float *out, cudaStream_t s);
+// Fused backward steps of the surrogate (mlp.cu).  lpart: [Bpad / 8] FP64; part: FP32 partials,
+// [Bpad / 8][Qpad] for the MSE and [ceil(Bpad / 32)][C] for the activation; count: zero-initialized
+// counters, at least ceil(C / 32) (each launch leaves them zero).
+cudaError_t launch_mse_fused(int B, int Bpad, int Q, int Qpad, const float *Y, const float *T, float *dY, void *dYb,
+                             void *dYt, int ldt, double *lpart, float *part, float *db, float *loss, unsigned *count,
+                             cudaStream_t s);
+cudaError_t launch_act_bwd(int B, int Bpad, int C, const float *dA, const float *Z, float *dZ, void *dZb, void *dZt,
+                           int ldt, float *part, float *db, unsigned *count, cudaStream_t s);
 cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,
                         int64_t step, void *pb, cudaStream_t s);
 
