@@ -148,12 +148,20 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 
+// Optional transposed copy of the bfloat16 output: Dt[col][row] (leading dimension ld), with zero
+// columns for the rows [M, mpad) (batch padding of the operand that multiplies along the batch).
+struct TOut {
+    bf16 *p;
+    int ld, mpad;
+};
+
 // Epilogue of 8 consecutive columns col0.. of one row (col0 < N): x = accumulator (+ bias) to C in
-// FP32 and bfloat16(x or GELU(x)) to D.  The eight values are independent (their GELUs overlap),
-// and whole aligned groups go out as 16-byte stores.
+// FP32 and bfloat16(x or GELU(x)) to D (and its transpose to t.p).  The eight values are
+// independent (their GELUs overlap), and whole aligned groups go out as 16-byte stores; the
+// transposed stores of a warp's 32 rows are contiguous.
 __device__ __forceinline__ void store8(const float (&v)[8], bool have_acc, int row, int col0, int N,
                                        const float *__restrict__ bias, float *__restrict__ C, int ldc,
-                                       bf16 *__restrict__ D, int ldd, int gelu)
+                                       bf16 *__restrict__ D, int ldd, int gelu, TOut t = TOut{nullptr, 0, 0})
 {
     const bool whole = col0 + 8 <= N;
     float x[8];
@@ -180,12 +188,14 @@ __device__ __forceinline__ void store8(const float (&v)[8], bool have_acc, int r
             p[k / 2] = *reinterpret_cast<const uint32_t *>(&h2);
         }
         bf16 *dp = D + (size_t)row * ldd + col0;
+        const bf16 *h = reinterpret_cast<const bf16 *>(p);
         if (whole && (reinterpret_cast<uintptr_t>(dp) & 15) == 0) {
             *reinterpret_cast<uint4 *>(dp) = make_uint4(p[0], p[1], p[2], p[3]);
         } else {
-            const bf16 *h = reinterpret_cast<const bf16 *>(p);
             for (int k = 0; k < 8 && col0 + k < N; ++k) dp[k] = h[k];
         }
+        if (t.p)
+            for (int k = 0; k < 8 && col0 + k < N; ++k) t.p[(size_t)(col0 + k) * t.ld + row] = h[k];
     }
 }
 
@@ -195,7 +205,7 @@ template <int BN, int S>
 __global__ void __launch_bounds__(128, 2)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
               const float *__restrict__ bias, float *__restrict__ C, int ldc, bf16 *__restrict__ D, int ldd, int gelu,
-              int kper, int64_t c_split)
+              int kper, int64_t c_split, TOut tout)
 {
     constexpr uint32_t kBBytes = BN * kTcK * 2;
     extern __shared__ uint8_t smem_raw[];
@@ -279,8 +289,12 @@ __global__ void __launch_bounds__(128, 2)
     for (int c0 = 0; c0 < BN; c0 += 8) {
         float v[8];
         tmem_ld8(trow + (uint32_t)c0, v);   // warp-collective: every lane of the warp takes part
-        if (row < M && n0 + c0 < N)
-            store8(v, ksteps > 0, row, n0 + c0, N, bias, C, ldc, D, ldd, gelu);
+        if (row < M && n0 + c0 < N) {
+            store8(v, ksteps > 0, row, n0 + c0, N, bias, C, ldc, D, ldd, gelu, tout);
+        } else if (tout.p && row < tout.mpad) {   // zero padding of the transposed copy
+            for (int k = 0; k < 8 && n0 + c0 + k < N; ++k)
+                tout.p[(size_t)(n0 + c0 + k) * tout.ld + row] = __float2bfloat16_rn(0.f);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -494,7 +508,7 @@ bool make_map(CUtensorMap &map, const void *base, int rows, int K, int ld, int b
 template <int BN, int S>
 cudaError_t launch_bs(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias, float *C,
                       int ldc, void *D, int ldd, int gelu, cudaStream_t s,
-                      int splits = 1)
+                      int splits = 1, TOut tout = TOut{nullptr, 0, 0})
 {
     CUtensorMap ta, tb;
     if (!make_map(ta, A, M, K, lda, kTcM) || !make_map(tb, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
@@ -505,7 +519,7 @@ cudaError_t launch_bs(int M, int N, int K, const void *A, int lda, const void *B
     const int kper = splits > 1 ? (kt + splits - 1) / splits : kt;
     const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + kTcM - 1) / kTcM), (unsigned)(splits > 1 ? splits : 1));
     k_gemm_tc<BN, S><<<grid, 128, smem, s>>>(ta, tb, M, N, K, bias, C, ldc, static_cast<bf16 *>(D), ldd, gelu, kper,
-                                             (int64_t)M * ldc);
+                                             (int64_t)M * ldc, tout);
     return cudaGetLastError();
 }
 
@@ -530,7 +544,7 @@ cudaError_t launch_persistent(int M, int N, int K, const void *A, int lda, const
 // 97 KB per CTA so that two CTAs share an SM.
 template <int BN>
 cudaError_t launch_bn(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias, float *C,
-                      int ldc, void *D, int ldd, int gelu, cudaStream_t s)
+                      int ldc, void *D, int ldd, int gelu, cudaStream_t s, TOut tout = TOut{nullptr, 0, 0})
 {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
@@ -539,10 +553,10 @@ cudaError_t launch_bn(int M, int N, int K, const void *A, int lda, const void *B
     const int64_t ctas = (int64_t)((N + BN - 1) / BN) * ((M + kTcM - 1) / kTcM);
     const bool deep = ctas <= sms;
     if (BN == 64)
-        return deep ? launch_bs<64, 8>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s)
-                    : launch_bs<64, 4>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s);
-    return deep ? launch_bs<128, 5>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s)
-                : launch_bs<128, 3>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s);
+        return deep ? launch_bs<64, 8>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s, 1, tout)
+                    : launch_bs<64, 4>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s, 1, tout);
+    return deep ? launch_bs<128, 5>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s, 1, tout)
+                : launch_bs<128, 3>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s, 1, tout);
 }
 
 }  // namespace
@@ -593,6 +607,28 @@ cudaError_t launch_gemm(int M, int N, int K, const void *A, int lda, const void 
     if (gemm_tc_supported(K, A, lda, B, ldb))
         return launch_gemm_tc(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s);
     return launch_gemm_tn(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s);
+}
+
+cudaError_t launch_gemm_t(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
+                          float *C, int ldc, void *D, int ldd, int gelu, void *Dt, int ldt, int Mpad, cudaStream_t s)
+{
+    if (!D || !Dt || Mpad < M || ldt < Mpad) return cudaErrorInvalidValue;
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaErrorInvalidDevice;
+    const int mt = (M + kTcM - 1) / kTcM;
+    const bool persistent = N >= 256 && mt * ((N + 255) / 256) >= 2 * sms;
+    if (gemm_tc_supported(K, A, lda, B, ldb) && !persistent) {   // the transposed copy from the epilogue
+        const TOut t{static_cast<bf16 *>(Dt), ldt, Mpad};
+        const int tiles128 = mt * ((N + 127) / 128);
+        if (N <= 64 || tiles128 < 64) return launch_bn<64>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s, t);
+        return launch_bn<128>(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s, t);
+    }
+    cudaError_t e = launch_gemm(M, N, K, A, lda, B, ldb, bias, C, ldc, D, ldd, gelu, s);
+    if (e != cudaSuccess) return e;
+    return launch_transpose_bf16(M, Mpad, N, D, ldd, Dt, ldt, s);
 }
 
 cudaError_t gemm_tc_error(int *err)

@@ -8,6 +8,7 @@
 //                  fallback of the tcgen05 GEMM in gemm_tc.cu for operands TMA cannot describe),
 //                  FP32 accumulation with mma.sync m16n8k16 (64x64 CTA tile, four 32x32 warp
 //                  tiles); epilogue writes FP32 and/or bfloat16 of the value or of GELU(value).
+//   k_to_bf16_t    the input to bfloat16, with its transpose (the first layer's weight-gradient operand)
 //   k_transpose    bfloat16 [R][C] -> [C][R] (the backward GEMMs' operands)
 //   k_splitk_gelu  the first layer's split-K slices summed in order, bias, GELU, bfloat16 and its
 //                  transpose
@@ -122,6 +123,32 @@ __global__ void k_to_bf16(int64_t n, const float *__restrict__ x, bf16 *__restri
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// x [R][C] FP32 -> bfloat16 Xb [R][C] and its transpose Xt [C][ldt] with zero rows [R, Rpad) (batch
+// padding), the operand of the first layer's weight gradient.  32 x 32 tiles, 32 x 8 threads.
+__global__ void __launch_bounds__(256)
+    k_to_bf16_t(int R, int Rpad, int C, const float *__restrict__ x, bf16 *__restrict__ xb, bf16 *__restrict__ xt,
+                int ldt)
+{
+    __shared__ bf16 tile[32][34];
+    const int tx = threadIdx.x, ty = threadIdx.y, c0 = blockIdx.x * 32, r0 = blockIdx.y * 32, c = c0 + tx;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = r0 + ty + 8 * k;
+        bf16 h = __float2bfloat16_rn(0.f);
+        if (r < R && c < C) {
+            h = __float2bfloat16_rn(x[(size_t)r * C + c]);
+            xb[(size_t)r * C + c] = h;
+        }
+        tile[ty + 8 * k][tx] = h;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {   // rows c0 + ty + 8k of xt, columns r0 + tx
+        const int cc = c0 + ty + 8 * k, rr = r0 + tx;
+        if (cc < C && rr < Rpad) xt[(size_t)cc * ldt + rr] = tile[tx][ty + 8 * k];
+    }
 }
 
 // rows [0, R) x cols [0, C) of a [R][ldin] matrix into [C][ldout]; rows R..Rpad of the output
@@ -366,6 +393,14 @@ cudaError_t launch_to_bf16(int64_t n, const float *x, void *y, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     k_to_bf16<<<blocks_for(n, 256), 256, 0, s>>>(n, x, static_cast<bf16 *>(y));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16_t(int R, int Rpad, int C, const float *x, void *xb, void *xt, int ldt, cudaStream_t s)
+{
+    if (Rpad <= 0 || C <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((C + 31) / 32), (unsigned)((Rpad + 31) / 32));
+    k_to_bf16_t<<<grid, dim3(32, 8), 0, s>>>(R, Rpad, C, x, static_cast<bf16 *>(xb), static_cast<bf16 *>(xt), ldt);
     return cudaGetLastError();
 }
 

@@ -124,20 +124,23 @@ int splitk_slices(const sas_mlp *m, int B)
     return z >= 2 ? z : 0;
 }
 
-// The forward launches from device input xd [B][n_in] f32 to Y.
+// The forward launches from device input xd [B][n_in] f32 to Y.  The bfloat16 operands X, A1 and A2
+// are also written transposed (batch padding zero), as the weight-gradient GEMMs take them.
 sas_status mlp_forward_dev(sas_mlp *m, const float *xd, int B, cudaStream_t s)
 {
-    MLP_TRY(launch_to_bf16((int64_t)B * m->n_in, xd, m->Xb, s));
+    const int Bp = round16(B);
+    MLP_TRY(launch_to_bf16_t(B, Bp, m->n_in, xd, m->Xb, m->Xt, Bp, s));
     const bf16 *W1b = m->Pb + m->oW1, *W2b = m->Pb + m->oW2, *W3b = m->Pb + m->oW3;
     if (const int z = splitk_slices(m, B)) {
         // first layer in K slices, then their sum, the bias, GELU and A1's transpose in one pass
         MLP_TRY(launch_gemm_splitk(B, m->h, m->n_in, m->Xb, m->n_in, W1b, m->n_in, m->ws, z, s));
-        MLP_TRY(launch_splitk_gelu(B, round16(B), m->h, z, m->ws, m->P + m->ob1, m->Z1, m->A1b, m->A1t, round16(B), s));
+        MLP_TRY(launch_splitk_gelu(B, Bp, m->h, z, m->ws, m->P + m->ob1, m->Z1, m->A1b, m->A1t, Bp, s));
     } else {
-        MLP_TRY(launch_gemm(B, m->h, m->n_in, m->Xb, m->n_in, W1b, m->n_in, m->P + m->ob1, m->Z1, m->h, m->A1b, m->h,
-                            1, s));
+        MLP_TRY(launch_gemm_t(B, m->h, m->n_in, m->Xb, m->n_in, W1b, m->n_in, m->P + m->ob1, m->Z1, m->h, m->A1b, m->h,
+                              1, m->A1t, Bp, Bp, s));
     }
-    MLP_TRY(launch_gemm(B, m->h, m->h, m->A1b, m->h, W2b, m->h, m->P + m->ob2, m->Z2, m->h, m->A2b, m->h, 1, s));
+    MLP_TRY(launch_gemm_t(B, m->h, m->h, m->A1b, m->h, W2b, m->h, m->P + m->ob2, m->Z2, m->h, m->A2b, m->h, 1, m->A2t,
+                          Bp, Bp, s));
     MLP_TRY(launch_gemm(B, m->n_outp, m->h, m->A2b, m->h, W3b, m->h, m->P + m->ob3, m->Y, m->n_outp, nullptr, 0, 0,
                            s));
     return SAS_OK;
@@ -168,19 +171,16 @@ sas_status mlp_backward(sas_mlp *m, int B, cudaStream_t s)
     // layer 3: dY (with its transpose, the bias gradient and the loss)
     MLP_TRY(launch_mse_fused(B, Bp, m->n_out, Qp, m->Y, m->Tf, m->dY, m->dYb, m->dYt, Bp, m->lpart, m->part,
                              m->G + m->ob3, m->loss, m->count, s));
-    MLP_TRY(launch_transpose_bf16(B, Bp, h, m->A2b, h, m->A2t, Bp, s));
     MLP_TRY(launch_gemm(Qp, h, Bp, m->dYt, Bp, m->A2t, Bp, nullptr, m->G + m->oW3, h, nullptr, 0, 0, s));
     MLP_TRY(launch_gemm(B, h, Qp, m->dYb, Qp, m->W3t, Qp, nullptr, m->dA2, h, nullptr, 0, 0, s));
     // layer 2
     MLP_TRY(launch_act_bwd(B, Bp, h, m->dA2, m->Z2, m->dZ2, m->dZ2b, m->dZ2t, Bp, m->part, m->G + m->ob2, m->count,
                            s));
-    if (!splitk_slices(m, B)) MLP_TRY(launch_transpose_bf16(B, Bp, h, m->A1b, h, m->A1t, Bp, s));   // else done
     MLP_TRY(launch_gemm(h, h, Bp, m->dZ2t, Bp, m->A1t, Bp, nullptr, m->G + m->oW2, h, nullptr, 0, 0, s));
     MLP_TRY(launch_gemm(B, h, h, m->dZ2b, h, m->W2t, h, nullptr, m->dA1, h, nullptr, 0, 0, s));
     // layer 1
     MLP_TRY(launch_act_bwd(B, Bp, h, m->dA1, m->Z1, m->dZ1, m->dZ1b, m->dZ1t, Bp, m->part, m->G + m->ob1, m->count,
                            s));
-    MLP_TRY(launch_transpose_bf16(B, Bp, m->n_in, m->Xb, m->n_in, m->Xt, Bp, s));
     MLP_TRY(launch_gemm(h, m->n_in, Bp, m->dZ1t, Bp, m->Xt, Bp, nullptr, m->G + m->oW1, m->n_in, nullptr, 0, 0, s));
     return SAS_OK;
 }

@@ -211,10 +211,15 @@ cudaError_t launch_gemm_splitk(int M, int N, int K, const void *A, int lda, cons
                                cudaStream_t s);
 cudaError_t launch_splitk_gelu(int M, int Mpad, int N, int splits, const float *ws, const float *bias, float *Z, void *A,
                                void *At, int ldt, cudaStream_t s);
+// launch_gemm with D (required) also written transposed: Dt[col][row] (leading dimension ldt >= Mpad),
+// zero for rows [M, Mpad); from the tcgen05 epilogue where it runs that form, else by a transpose.
+cudaError_t launch_gemm_t(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
+                          float *C, int ldc, void *D, int ldd, int gelu, void *Dt, int ldt, int Mpad, cudaStream_t s);
 // launch_gemm_tc where supported, else launch_gemm_tn.
 cudaError_t launch_gemm(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias,
                         float *C, int ldc, void *D, int ldd, int gelu, cudaStream_t s);
 cudaError_t launch_to_bf16(int64_t n, const float *x, void *y, cudaStream_t s);
+cudaError_t launch_to_bf16_t(int R, int Rpad, int C, const float *x, void *xb, void *xt, int ldt, cudaStream_t s);
 cudaError_t launch_transpose_bf16(int R, int Rpad, int C, const void *in, int ldin, void *out, int ldout,
                                   cudaStream_t s);
 // Fused backward steps of the surrogate (mlp.cu).  lpart: [Bpad / 8] FP64; part: FP32 partials,
