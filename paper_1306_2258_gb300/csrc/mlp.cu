@@ -359,20 +359,37 @@ __global__ void __launch_bounds__(128)
     }
 }
 
-__global__ void k_adam(int64_t n, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
-                       float *__restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2,
-                       bf16 *__restrict__ pb)
+// One Adam step of element i (bias corrections c1 = 1 - b1^t, c2 = 1 - b2^t).
+__device__ __forceinline__ float adam_elem(float &p, float g, float &m, float &v, float lr, float b1, float b2, float eps,
+                                           float c1, float c2)
+{
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    p = p - lr * (m / c1) / (sqrtf(v / c2) + eps);
+    return p;
+}
+
+// Four elements per thread (n is a multiple of 4: every parameter block is), 16-byte loads and
+// stores; the arithmetic of each element is that of adam_elem.
+__global__ void k_adam(int64_t n4, float4 *__restrict__ p, const float4 *__restrict__ g, float4 *__restrict__ m,
+                       float4 *__restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2,
+                       uint2 *__restrict__ pb)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    if (i >= n4) return;
+    float4 pi = p[i], mi = m[i], vi = v[i];
+    const float4 gi = g[i];
+    adam_elem(pi.x, gi.x, mi.x, vi.x, lr, b1, b2, eps, c1, c2);
+    adam_elem(pi.y, gi.y, mi.y, vi.y, lr, b1, b2, eps, c1, c2);
+    adam_elem(pi.z, gi.z, mi.z, vi.z, lr, b1, b2, eps, c1, c2);
+    adam_elem(pi.w, gi.w, mi.w, vi.w, lr, b1, b2, eps, c1, c2);
+    p[i] = pi;
     m[i] = mi;
     v[i] = vi;
-    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    p[i] = pi;
-    if (pb) pb[i] = __float2bfloat16_rn(pi);
+    if (pb) {
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(pi.x, pi.y), hi = __floats2bfloat162_rn(pi.z, pi.w);
+        pb[i] = make_uint2(*reinterpret_cast<const uint32_t *>(&lo), *reinterpret_cast<const uint32_t *>(&hi));
+    }
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -450,7 +467,10 @@ cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v,
     if (n <= 0) return cudaSuccess;
     const float c1 = (float)(1.0 - std::pow((double)b1, (double)step));
     const float c2 = (float)(1.0 - std::pow((double)b2, (double)step));
-    k_adam<<<blocks_for(n, 256), 256, 0, s>>>(n, p, g, m, v, lr, b1, b2, eps, c1, c2, static_cast<bf16 *>(pb));
+    if (n % 4 != 0) return cudaErrorInvalidValue;
+    k_adam<<<blocks_for(n / 4, 256), 256, 0, s>>>(n / 4, reinterpret_cast<float4 *>(p), reinterpret_cast<const float4 *>(g),
+                                                  reinterpret_cast<float4 *>(m), reinterpret_cast<float4 *>(v), lr, b1,
+                                                  b2, eps, c1, c2, static_cast<uint2 *>(pb));
     return cudaGetLastError();
 }
 
