@@ -44,6 +44,22 @@ def test_full_size_forward_backward_and_two_adam_steps_element_by_element(net):
     mlp_bounds.adam_steps(net, [_inputs(41), _inputs(42)], 1e-3, 31)
 
 
+@pytest.mark.parametrize("batch", [200, 600])
+def test_ragged_batches_element_by_element(batch):
+    """A batch of 200 rows takes the first layer's split-K path with a partial row tile (200 -> 208
+    padded rows); 600 rows take the one-pass GEMMs whose epilogues write the transposed operands with
+    their zero padding (600 -> 608).  One Adam step each, checked as above."""
+    n = SurrogateMLP(N_IN, H, N_OUT, max_batch=batch, seed=37)
+    try:
+        rng = np.random.default_rng(batch)
+        x = rng.standard_normal((batch, N_IN))
+        x[:, rng.random(N_IN) < 0.2] = 0.0
+        t = rng.standard_normal((batch, N_OUT))
+        mlp_bounds.adam_steps(n, [(x.astype(np.float32), t.astype(np.float32))], 1e-3, 37)
+    finally:
+        n.close()
+
+
 def test_forward_alone_writes_the_same_activations(net):
     """sas_mlp_forward (inference) takes the forward kernels of a training step: same bits."""
     x, _ = _inputs(43)
