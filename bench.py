@@ -406,6 +406,13 @@ def run_rows(dev, stream):
                                  "unit": "TFLOP/s", "peak": peak, "frac": (tflops / peak) if peak else None,
                                  "peak_basis": "cuBLAS bf16 burst, MEASURED_PEAKS.json"}
     del gA, gB, gC
+    # the FP32-recurrence profile rows against the nominal FP32 lane rate, at the headline's count
+    # of two lane operations per pair·q (whole call: packing, reductions and assembly included)
+    peak_ops = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6
+    for k in ("profile_rod_c3", "profile_sparse_chain_c3", "profile_atomic_ff_globule50k",
+              "profile_globule200k_saxs_direct", "profiles_c5"):
+        if k in rows and rows[k].get("unit") == "pair·q/s":
+            rows[k]["fp32_frac_whole_call"] = rows[k]["value"] * OPS_PER_PAIR_Q / peak_ops
     return rows
 
 
