@@ -169,6 +169,8 @@ sas_status forward_hybrid(sas_ctx *ctx, const void *coords, int coords_type, con
         ALLOC_TRY(ctx->partial, (size_t)std::max(ctx->n_items, 1) * kQChunk * sizeof(double));
         ALLOC_TRY(ctx->ticket, sizeof(int));
         CUDA_TRY(cudaMemsetAsync(ctx->ticket.p, 0, sizeof(int), s));
+        st = with_sincos_table(ctx, qd, s);
+        if (st != SAS_OK) return st;
         CUDA_TRY(launch_debye_mixed(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, qd, ctx->opt_step,
                                     reseed_for(ctx->opt_reseed, n, std::min(Qd, kQChunk), step_phase(ctx, qd)),
                                     mixed_variant(ctx->opt_variant), ctx->partial.as<double>(),

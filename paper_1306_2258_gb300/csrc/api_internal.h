@@ -95,7 +95,8 @@ struct sas_ctx {
     sas::api::DevBuf coef_d, F, meta, blockcounts, blockoffs, centroid, X, slot_of, items, group_items,
         group_off, partial, ticket, S, in_coords, in_types, out_buf, Ibuf, gbuf, chi2buf, H, G, gout, tgt, wts,
         hist, dropped, in_ff, zero_types, FJ, FI, F64t, D2, segbuf, cen, qdirs, qwts, type_off, Apart, Fsub, Itmp, qplan,
-        tile_off, tile_ent, adj_pi, adj_pj, Ufix, segfix, Ustage, Sx, Ix, btab, bdiag, bhist, bout, adj_k, adj_wn, adj_tab, adj_ai;
+        tile_off, tile_ent, adj_pi, adj_pj, Ufix, segfix, Ustage, Sx, Ix, btab, bdiag, bhist, bout, adj_k, adj_wn, adj_tab, adj_ai, sct;
+    int sct_n = 0;            // entries of the (sin, cos)(k/64) table in sct
     int btab_bins = 0;        // (n_bins, r_max) of the binned-sum table in btab (0: none)
     float btab_rmax = 0.f;
     int det_ntiles = -1;   // I-tiles per conformer of the current schedule's tile lists (-1: none built)
@@ -126,6 +127,7 @@ struct HostCopies {
 };
 
 bool on_device(const void *p);
+sas_status with_sincos_table(sas_ctx *ctx, QChunks &qc, cudaStream_t s);
 int reseed_for(int opt, int64_t n_atoms, int n_q_chunk, double step_phase_max);
 int mixed_variant(int opt);
 double step_phase(const sas_ctx *ctx, const QChunks &qc);

@@ -53,7 +53,8 @@ __device__ __forceinline__ void core2_atomic(const PairState2 &p, const float4 *
 template <int NB, int NV, bool ZERO_START>
 __device__ __forceinline__ void run_atomic2(const float4 *sxy, const float4 *szw, const float4 *sf, int k0, int k1,
                                             const float4 xi, const Item &item, int tid, int jmask, float2 qs_hi,
-                                            float2 qs_lo, float2 dq_hi, float2 dq_lo, float2 (&acc)[2 * NB])
+                                            float2 qs_lo, float2 dq_hi, float2 dq_lo, float2 (&acc)[2 * NB],
+                                            const float4 *__restrict__ sct, int sct_n)
 {
     const float2 nX = bc(-xi.x), nY = bc(-xi.y), nZ = bc(-xi.z), wi = bc(xi.w);
     const unsigned ih = item.i0 + tid;
@@ -63,8 +64,8 @@ __device__ __forceinline__ void run_atomic2(const float4 *sxy, const float4 *szw
     for (int k = k0; k < k1; ++k) {
         const int j = 2 * k;
         PairState2 p;
-        setup2_tail<ZERO_START>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
-                                pair_hash(ih, item.j0 + j + 1), p);
+        setup2_tail<ZERO_START, false>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
+                                pair_hash(ih, item.j0 + j + 1), p, sct, sct_n);
         const bool more = k + 1 < k1;
         const int kn = more ? k + 1 : k;
         setup2_head(sxy[kn], szw[kn], nX, nY, nZ, wi, more && j + 2 > jmask, more && j + 3 > jmask, head);
@@ -123,10 +124,10 @@ __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
             __syncthreads();
             if (zero_start)
                 run_atomic2<NB, NV, true>(sxy, szw, sf, k0, k1, xi, item, tid, jmask, qs_hi, qs_lo,
-                                          bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), acc);
+                                          bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), acc, qc.sct, qc.sct_n);
             else
                 run_atomic2<NB, NV, false>(sxy, szw, sf, k0, k1, xi, item, tid, jmask, qs_hi, qs_lo,
-                                           bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), acc);
+                                           bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), acc, qc.sct, qc.sct_n);
         }
         // f_i(q) of this thread's atom (zero on padding slots)
         const float2 *fi = FI + tab * NV * npad + item.i0 + tid;

@@ -57,7 +57,8 @@ using namespace mixed;
 template <bool ZERO_START>
 __device__ __forceinline__ void setup_m2(const float4 xi, const float4 xj, float w, float qs_hi,
                                          float qs_lo, float dq_hi, float dq_lo, unsigned hash,
-                                         float2 &w0, float2 &w1, float2 &Cp, float2 &Cn)
+                                         float2 &w0, float2 &w1, float2 &Cp, float2 &Cn,
+                                         const float4 *__restrict__ sct, int sct_n)
 {
     const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
     float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -66,7 +67,7 @@ __device__ __forceinline__ void setup_m2(const float4 xi, const float4 xj, float
     dist_rsqrt(r2, r, y);
     const float scale = w * y;   // amplitude w_i w_j / r
     const float t = fmaf(dq_hi, r, dq_lo * r);
-    const SinCos b1 = sincos_f32(t);
+    const SinCos b1 = sct ? sincos_tab(t, sct, sct_n) : sincos_f32(t);
     const float c1 = b1.c, s1 = b1.s;
     const float s2 = 2.f * s1 * c1, c2 = fmaf(-2.f * s1, s1, 1.f);
     const float s3 = fmaf(s2, c1, c2 * s1);
@@ -112,12 +113,12 @@ struct M2Pair {
 template <bool ZERO_START>
 __device__ __forceinline__ void setup_at(const float4 xi, const float4 *sj, const Item &item, int tid,
                                          int jmask, int j, bool valid, float qs_hi, float qs_lo, float dq_hi,
-                                         float dq_lo, M2Pair &o)
+                                         float dq_lo, M2Pair &o, const float4 *__restrict__ sct, int sct_n)
 {
     const float4 xj = sj[j];
     const float w = (!valid || j <= jmask) ? 0.f : xi.w * xj.w;
     setup_m2<ZERO_START>(xi, xj, w, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(item.i0 + tid, item.j0 + j), o.w0,
-                         o.w1, o.Cp, o.Cn);
+                         o.w1, o.Cp, o.Cn, sct, sct_n);
 }
 
 // Pairs (i, j) over the item's J-range, software-pipelined: the set-up of pair j+1 does not
@@ -126,19 +127,20 @@ __device__ __forceinline__ void setup_at(const float4 xi, const float4 *sj, cons
 template <int NB, int NV, bool ZERO_START>
 __device__ __forceinline__ void run_m2_pipelined(const float4 xi, const float4 *sj, const Item &item,
                                                  int tid, int jmask, float qs_hi, float qs_lo, float dq_hi,
-                                                 float dq_lo, float2 (&acc)[2 * NB])
+                                                 float dq_lo, float2 (&acc)[2 * NB], const float4 *__restrict__ sct,
+                                                 int sct_n)
 {
     const int jlen = item.jlen;
     if (jlen <= 0) return;
     M2Pair a, b;
-    setup_at<ZERO_START>(xi, sj, item, tid, jmask, 0, true, qs_hi, qs_lo, dq_hi, dq_lo, a);
+    setup_at<ZERO_START>(xi, sj, item, tid, jmask, 0, true, qs_hi, qs_lo, dq_hi, dq_lo, a, sct, sct_n);
     int j = 0;
     for (; j + 1 < jlen; j += 2) {
-        setup_at<ZERO_START>(xi, sj, item, tid, jmask, j + 1, true, qs_hi, qs_lo, dq_hi, dq_lo, b);
+        setup_at<ZERO_START>(xi, sj, item, tid, jmask, j + 1, true, qs_hi, qs_lo, dq_hi, dq_lo, b, sct, sct_n);
         core_m2<NB, NV>(a.w0, a.w1, a.Cp, a.Cn, acc);
         const bool more = j + 2 < jlen;
         setup_at<ZERO_START>(xi, sj, item, tid, jmask, more ? j + 2 : j + 1, more, qs_hi, qs_lo, dq_hi, dq_lo,
-                             a);
+                             a, sct, sct_n);
         core_m2<NB, NV>(b.w0, b.w1, b.Cp, b.Cn, acc);
     }
     if (j < jlen) core_m2<NB, NV>(a.w0, a.w1, a.Cp, a.Cn, acc);   // odd J-range: its last pair
@@ -148,11 +150,11 @@ __device__ __forceinline__ void run_m2_pipelined(const float4 xi, const float4 *
 template <int NB, bool ZERO_START>
 __device__ __forceinline__ void run_m2(const float4 xi, const float4 *sj, const Item &item, int tid,
                                        int jmask, float qs_hi, float qs_lo, float dq_hi, float dq_lo,
-                                       float2 (&acc)[2 * NB])
+                                       float2 (&acc)[2 * NB], const float4 *__restrict__ sct, int sct_n)
 {
     for (int j = 0; j < item.jlen; ++j) {
         M2Pair a;
-        setup_at<ZERO_START>(xi, sj, item, tid, jmask, j, true, qs_hi, qs_lo, dq_hi, dq_lo, a);
+        setup_at<ZERO_START>(xi, sj, item, tid, jmask, j, true, qs_hi, qs_lo, dq_hi, dq_lo, a, sct, sct_n);
         core_m2<NB, 2 * NB>(a.w0, a.w1, a.Cp, a.Cn, acc);
     }
 }
@@ -162,20 +164,25 @@ __device__ __forceinline__ void run_m2(const float4 xi, const float4 *sj, const 
 template <int NB, bool ZERO_START>
 __device__ __forceinline__ void run_m2_fitted(int nv, const float4 xi, const float4 *sj, const Item &item,
                                               int tid, int jmask, float qs_hi, float qs_lo, float dq_hi,
-                                              float dq_lo, float2 (&acc)[2 * NB])
+                                              float dq_lo, float2 (&acc)[2 * NB], const float4 *__restrict__ sct,
+                                              int sct_n)
 {
     switch (2 * NB - nv) {
     case 1:
-        run_m2_pipelined<NB, 2 * NB - 1, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc);
+        run_m2_pipelined<NB, 2 * NB - 1, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc, sct,
+                                                     sct_n);
         break;
     case 2:
-        run_m2_pipelined<NB, 2 * NB - 2, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc);
+        run_m2_pipelined<NB, 2 * NB - 2, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc, sct,
+                                                     sct_n);
         break;
     case 3:
-        run_m2_pipelined<NB, 2 * NB - 3, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc);
+        run_m2_pipelined<NB, 2 * NB - 3, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc, sct,
+                                                     sct_n);
         break;
     default:
-        run_m2_pipelined<NB, 2 * NB, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc);
+        run_m2_pipelined<NB, 2 * NB, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc, sct,
+                                                     sct_n);
         break;
     }
 }
@@ -319,17 +326,24 @@ __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
 #pragma unroll
         for (int k = 0; k < 2 * NB; ++k) acc[k] = make_float2(0.f, 0.f);
         const int jmask = item.diag ? tid : -1;   // pairs with j <= i are not pairs of i<j
+        // the sine table for the 208-q form only (its 101-q and 52-q forms measured faster without:
+        // there the table load's latency sits in a shorter set-up)
+        const float4 *sct = NB == 52 ? qc.sct : nullptr;
         if (P == 3) {
             const int nv = (qlen + 1) >> 1;
             if (zero_start)
-                run_m2_fitted<NB, true>(nv, xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc);
+                run_m2_fitted<NB, true>(nv, xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc, sct,
+                                        qc.sct_n);
             else
-                run_m2_fitted<NB, false>(nv, xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc);
+                run_m2_fitted<NB, false>(nv, xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc, sct,
+                                        qc.sct_n);
         } else if (P == 4) {
             if (zero_start)
-                run_m2<NB, true>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc);
+                run_m2<NB, true>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc, sct,
+                                        qc.sct_n);
             else
-                run_m2<NB, false>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc);
+                run_m2<NB, false>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc, sct,
+                                        qc.sct_n);
         } else {
             for (int j = 0; j < item.jlen; ++j) {
                 const float4 xj = sj[j];

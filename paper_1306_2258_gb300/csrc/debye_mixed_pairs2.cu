@@ -52,7 +52,8 @@ __device__ __forceinline__ void core2(const PairState2 &p, float2 (&acc)[2 * NB]
 template <int NB, int NV, bool ZERO_START>
 __device__ __forceinline__ void run_pairs2(const float4 *sxy, const float4 *szw, int jpairs, const float4 xi,
                                            const Item &item, int tid, int jmask, float2 qs_hi, float2 qs_lo,
-                                           float2 dq_hi, float2 dq_lo, float2 (&acc)[2 * NB])
+                                           float2 dq_hi, float2 dq_lo, float2 (&acc)[2 * NB],
+                                            const float4 *__restrict__ sct, int sct_n)
 {
     const float2 nX = bc(-xi.x), nY = bc(-xi.y), nZ = bc(-xi.z), wi = bc(xi.w);
     const unsigned ih = item.i0 + tid;
@@ -63,7 +64,7 @@ __device__ __forceinline__ void run_pairs2(const float4 *sxy, const float4 *szw,
         const int j = 2 * k;
         PairState2 p;
         setup2_tail<ZERO_START>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
-                                pair_hash(ih, item.j0 + j + 1), p);
+                                pair_hash(ih, item.j0 + j + 1), p, sct, sct_n);
         // the next two pairs' distances, issued ahead of this step's recurrences (the last step
         // reads its own slot again and discards the result)
         const bool more = k + 1 < jpairs;
@@ -109,12 +110,14 @@ __global__ void __launch_bounds__(TILE, mixed_ctas_per_sm(NB) * (kTile / TILE))
 #pragma unroll
         for (int k = 0; k < 2 * NB; ++k) acc[k] = make_float2(0.f, 0.f);
         const int jmask = item.diag ? tid : -1;   // pairs with j <= i are not pairs of i<j
+        // the sine table for the 208-q form only (the 104-q and 52-q forms measured faster without)
+        const float4 *sct = NB == 52 ? qc.sct : nullptr;
         if (zero_start)
             run_pairs2<NB, NV, true>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
-                                     bc(qc.dq_lo[ch]), acc);
+                                     bc(qc.dq_lo[ch]), acc, sct, qc.sct_n);
         else
             run_pairs2<NB, NV, false>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
-                                      bc(qc.dq_lo[ch]), acc);
+                                      bc(qc.dq_lo[ch]), acc, sct, qc.sct_n);
         flush_warp<NB, 2>(acc, red[warp], lane);
         __syncthreads();
         const int qlen = qc.q_len[ch];

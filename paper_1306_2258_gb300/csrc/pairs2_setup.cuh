@@ -45,14 +45,17 @@ __device__ __forceinline__ void setup2_head(const float4 pxy, const float4 pzw, 
 }
 
 // Second part: sin t, cos t of t = dq r, the seeds of the first two blocks and the coefficient.
-template <bool ZERO_START>
+// sct: the table of (sin, cos)(k/64) of the call (sincos2_tab), or null for the polynomial form;
+// TAB false compiles the polynomial form alone (kernels at the register cap).
+template <bool ZERO_START, bool TAB = true>
 __device__ __forceinline__ void setup2_tail(const PairHead2 &h, float2 qs_hi, float2 qs_lo, float2 dq_hi,
-                                            float2 dq_lo, unsigned hA, unsigned hB, PairState2 &o)
+                                            float2 dq_lo, unsigned hA, unsigned hB, PairState2 &o,
+                                            const float4 *__restrict__ sct, int sct_n)
 {
     const float2 r = h.r;
     const float2 scale = f2mul(h.w, h.y);
     const float2 t = f2fma(dq_hi, r, f2mul(dq_lo, r));
-    const SinCos2 b1 = sincos2_f32(t);
+    const SinCos2 b1 = (TAB && sct) ? sincos2_tab(t, sct, sct_n) : sincos2_f32(t);
     const float2 s1 = b1.s, c1 = b1.c;
     const float2 s2 = f2mul(f2add(s1, s1), c1);
     const float2 c2 = f2fma(f2mul(s1, bc(-2.f)), s1, bc(1.f));

@@ -145,6 +145,41 @@ bool on_device(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The table of (sin, cos)(k/64) (sincos_tab) covering every pair's step phase dq r of a call: r is
+// at most the diameter bound of the call's conformers (ctx->diam, set by prepare), so 64 dq diam + 3
+// entries suffice (the 3 cover the float32 rounding of r and t).  Built in FP64 on the host once per
+// context and rebuilt larger when a call needs more.  Beyond 8,192 entries (t above 128 rad: a
+// table past what L1 holds) the kernels keep the polynomial sincos.
+constexpr int kSincosTabMax = 8192;
+
+sas_status with_sincos_table(sas_ctx *ctx, QChunks &qc, cudaStream_t s)
+{
+    qc.sct = nullptr;
+    qc.sct_n = 0;
+    double dq = 0.0;
+    for (int c = 0; c < qc.n_chunks; ++c) dq = std::max(dq, qc.dqd[c]);
+    const double tmax = dq * ctx->diam;
+    if (!(tmax >= 0.0) || tmax * 64.0 > kSincosTabMax - 3) return SAS_OK;
+    const int n = (int)std::floor(tmax * 64.0 * (1.0 + 1e-6)) + 3;
+    if (ctx->sct_n < n) {
+        const int m = std::max(n, 1024);
+        std::vector<float4> h((size_t)m);
+        for (int k = 0; k < m; ++k) {
+            const double x = k / 64.0, sv = std::sin(x), cv = std::cos(x);
+            const float sh = (float)sv, ch = (float)cv;
+            h[(size_t)k] = make_float4(sh, ch, (float)(sv - (double)sh), (float)(cv - (double)ch));
+        }
+        ctx->sct_n = 0;
+        ALLOC_TRY(ctx->sct, (size_t)m * sizeof(float4));
+        // pageable source: the call returns once the data are staged, so h may go out of scope
+        CUDA_TRY(cudaMemcpyAsync(ctx->sct.p, h.data(), (size_t)m * sizeof(float4), cudaMemcpyHostToDevice, s));
+        ctx->sct_n = m;
+    }
+    qc.sct = ctx->sct.as<float4>();
+    qc.sct_n = ctx->sct_n;
+    return SAS_OK;
+}
+
 int reseed_for(int opt, int64_t n_atoms, int n_q_chunk, double step_phase_max)
 {
     if (opt >= 0) return opt;
@@ -613,19 +648,24 @@ sas_status forward(sas_ctx *ctx, const void *coords, int coords_type, const int3
         ALLOC_TRY(ctx->ticket, sizeof(int));
         CUDA_TRY(cudaMemsetAsync(ctx->ticket.p, 0, sizeof(int), s));
     }
+    QChunks qk = ctx->qc;   // with the call's sine table for the mixed kernels
+    if (!fp64) {
+        st = with_sincos_table(ctx, qk, s);
+        if (st != SAS_OK) return st;
+    }
     CUDA_TRY(cudaEventRecord(ctx->ev0, s));
     if (fp64) {
         CUDA_TRY(launch_debye_fp64(ctx->X.as<double4>(), npad, ctx->items.as<Item>(), ctx->n_items,
                                    ctx->qc, ctx->partial.as<double>(), kQChunk, grid, s));
     } else if (ctx->tile_used != kTile) {   // the two-pair kernel on 64-atom tiles (chosen in prepare)
-        CUDA_TRY(launch_debye_mixed_pairs2(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, ctx->qc,
+        CUDA_TRY(launch_debye_mixed_pairs2(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, qk,
                                            ctx->partial.as<double>(), kQChunk,
                                            ctx->opt_grid > 0 ? ctx->opt_grid * ctx->sms : 0,
                                            std::min(ctx->jmax_used, ctx->jlen_max + (ctx->jlen_max & 1)),
                                            ctx->ticket.as<int>(), s, ctx->tile_used));
     } else {
         CUDA_TRY(launch_debye_mixed(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items,
-                                    ctx->qc, ctx->opt_step,
+                                    qk, ctx->opt_step,
                                     reseed_for(ctx->opt_reseed, n, std::min(ctx->n_q, kQChunk), step_phase(ctx, ctx->qc)),
                                     mixed_variant(ctx->opt_variant), ctx->partial.as<double>(),
                                     kQChunk, ctx->opt_grid > 0 ? ctx->opt_grid * ctx->sms : 0, ctx->jmax_used,

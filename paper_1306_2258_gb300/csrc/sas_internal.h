@@ -46,6 +46,10 @@ struct QChunks {
     float dq_lo[kMaxChunks];
     double qsd[kMaxChunks];    // the same in FP64
     double dqd[kMaxChunks];
+    // (sin, cos)(k/64) for k < sct_n as float32 hi/lo (sincos_tab), covering every pair's step phase
+    // dq r of the call; null: the polynomial sincos
+    const float4 *sct = nullptr;
+    int sct_n = 0;
 };
 
 // q_k of the grid (a short scan over the chunks).

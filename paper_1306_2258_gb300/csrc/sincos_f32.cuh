@@ -127,4 +127,60 @@ __device__ __forceinline__ SinCos2 sincos2_f32(float2 x)
     return r;
 }
 
+// Table-driven sine and cosine of the per-pair phase step t = dq r >= 0, for passes whose t is
+// bounded (dq times the molecule's diameter) so that a table of (sin, cos)(k/64) covers it:
+//   t = k/64 + d, k the nearest integer to 64 t, |d| <= 1/128, d exact (Sterbenz);
+//   sin t = S_k cos d + C_k sin d,  cos t = C_k cos d - S_k sin d,
+//   sin d = d - d^3/6 and cos d = 1 - d^2/2 (truncation below 2^-32 relative for |d| <= 1/128).
+// (S_k, C_k) come from FP64 and are stored as float32 pairs hi + lo, the lo part entering the
+// innermost fused multiply-add: a table entry's own rounding, shared by every t near k/64, stays
+// at 2^-48 instead of becoming a coherent float32 error.  The result's errors are the roundings of
+// a few products, which vary with t.  Entry k = (S_hi, C_hi, S_lo, C_lo); k is clamped to the n
+// entries.  The packed form performs the same operations lane by lane.
+namespace sc {
+constexpr float kSixth = 0.16666667163372039794921875f;   // float32(1/6)
+constexpr float kTabScale = 64.f;
+constexpr float kTabStep = 0.015625f;                      // 1/64
+}  // namespace sc
+
+__device__ __forceinline__ SinCos sincos_tab(float t, const float4 *__restrict__ tab, int n)
+{
+    using namespace sc;
+    const float kr = __fmaf_rn(t, kTabScale, kRound);   // nearest integer in the low mantissa bits
+    const float kf = __fadd_rn(kr, -kRound);
+    const float d = __fmaf_rn(kf, -kTabStep, t);
+    const int k = min(max(__float_as_int(kr) - __float_as_int(kRound), 0), n - 1);
+    const float4 e = __ldg(tab + k);
+    const float d2 = __fmul_rn(d, d);
+    const float d3 = __fmul_rn(d2, d);
+    const float sd = __fmaf_rn(d3, -kSixth, d);
+    const float nsd = __fmul_rn(sd, -1.f);
+    const float cd = __fmaf_rn(d2, -0.5f, 1.f);
+    SinCos r;
+    r.s = __fmaf_rn(e.x, cd, __fmaf_rn(e.y, sd, e.z));
+    r.c = __fmaf_rn(e.y, cd, __fmaf_rn(e.x, nsd, e.w));
+    return r;
+}
+
+__device__ __forceinline__ SinCos2 sincos2_tab(float2 t, const float4 *__restrict__ tab, int n)
+{
+    using namespace sc;
+    const float2 kr = __ffma2_rn(t, sc_bcast(kTabScale), sc_bcast(kRound));
+    const float2 kf = __fadd2_rn(kr, sc_bcast(-kRound));
+    const float2 d = __ffma2_rn(kf, sc_bcast(-kTabStep), t);
+    const int kA = min(max(__float_as_int(kr.x) - __float_as_int(kRound), 0), n - 1);
+    const int kB = min(max(__float_as_int(kr.y) - __float_as_int(kRound), 0), n - 1);
+    const float4 eA = __ldg(tab + kA), eB = __ldg(tab + kB);
+    const float2 d2 = __fmul2_rn(d, d);
+    const float2 d3 = __fmul2_rn(d2, d);
+    const float2 sd = __ffma2_rn(d3, sc_bcast(-kSixth), d);
+    const float2 nsd = __fmul2_rn(sd, sc_bcast(-1.f));
+    const float2 cd = __ffma2_rn(d2, sc_bcast(-0.5f), sc_bcast(1.f));
+    const float2 Sh = make_float2(eA.x, eB.x), Ch = make_float2(eA.y, eB.y);
+    SinCos2 r;
+    r.s = __ffma2_rn(Sh, cd, __ffma2_rn(Ch, sd, make_float2(eA.z, eB.z)));
+    r.c = __ffma2_rn(Ch, cd, __ffma2_rn(Sh, nsd, make_float2(eA.w, eB.w)));
+    return r;
+}
+
 }  // namespace sas
