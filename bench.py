@@ -645,7 +645,7 @@ def run_strong(args):
     return 0
 
 
-PROFILE_CASES = ("histogram", "gradient", "gradient_recurrence", "gemm", "atomic", "quadrature", "binned", "rod",
+PROFILE_CASES = ("histogram", "gradient", "gradient_recurrence", "gemm", "atomic", "quadrature", "binned", "rod", "pairs2",
                  "train")
 
 
@@ -663,6 +663,7 @@ def run_profile_case(args):
       gemm         4096 x 4096 x 4096 bfloat16 -> float32 on the tcgen05 GEMM
       atomic       20,000-atom globule x 201 q with a per-atom form-factor table
       quadrature   20,000-atom globule x 65 q (0..0.32 A^-1), orientation average of Eq. 1 on every q
+      pairs2       20,000-atom globule x 201 q (0..1 A^-1): the headline's pair kernel on a smaller molecule
     """
     import torch
 
@@ -742,6 +743,12 @@ def run_profile_case(args):
             Ia = pa.atomic(xa, ffa)
         report["atomic_I0"] = float(Ia[0])
         pa.close()
+    if "pairs2" in cases:
+        pp = Profile(w.coef, w.q)
+        for _ in range(2):
+            Ip = pp(xa, torch.as_tensor(w.mol.types, device=dev))
+        report["pairs2_I0"] = float(Ip[0])
+        pp.close()
     if "quadrature" in cases:
         pq = Profile(w.coef, wl.q_grid(0.0, 0.32, 65))
         pq.set_option(_lib.SAS_OPT_METHOD, 2)
