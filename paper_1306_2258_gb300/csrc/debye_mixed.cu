@@ -54,7 +54,7 @@ using namespace mixed;
 
 // One pair's first two float2 blocks (q 0..3 of the chunk, block signs +, +) and its
 // stochastically rounded coefficient 2cos(2t), as +C and -C.
-template <bool ZERO_START>
+template <bool ZERO_START, bool PRODUCT_SEEDS>
 __device__ __forceinline__ void setup_m2(const float4 xi, const float4 xj, float w, float qs_hi,
                                          float qs_lo, float dq_hi, float dq_lo, unsigned hash,
                                          float2 &w0, float2 &w1, float2 &Cp, float2 &Cn,
@@ -69,11 +69,18 @@ __device__ __forceinline__ void setup_m2(const float4 xi, const float4 xj, float
     const float t = fmaf(dq_hi, r, dq_lo * r);
     const SinCos b1 = sct ? sincos_tab(t, sct, sct_n) : sincos_f32(t);
     const float c1 = b1.c, s1 = b1.s;
-    const float s2 = 2.f * s1 * c1, c2 = fmaf(-2.f * s1, s1, 1.f);
-    const float s3 = fmaf(s2, c1, c2 * s1);
-    const float CM = coef_dither(4.f * s1 * s1, hash);   // 2cos(2t) = 2 - 4 sin^2 t
+    const float mu = (2.f * s1) * (2.f * s1);   // 4 sin^2 t
+    const float CM = coef_dither(mu, hash);     // 2cos(2t) = 2 - 4 sin^2 t
     Cp = make_float2(CM, CM);
     Cn = make_float2(-CM, -CM);
+    if (ZERO_START && PRODUCT_SEEDS) {   // the two-pair kernel's 208-q seeds (pairs2_setup.cuh)
+        const float a1 = scale * s1;
+        w0 = make_float2(0.f, a1);
+        w1 = make_float2((a1 + a1) * c1, a1 * (3.f - mu));
+        return;
+    }
+    const float s2 = 2.f * s1 * c1, c2 = fmaf(-2.f * s1, s1, 1.f);
+    const float s3 = fmaf(s2, c1, c2 * s1);
     if (ZERO_START) {
         w0 = make_float2(0.f, scale * s1);
         w1 = make_float2(scale * s2, scale * s3);
@@ -110,14 +117,14 @@ struct M2Pair {
 };
 
 // Set-up of pair (i, j) of the item; `valid` false gives a zero-weight stand-in (no pair).
-template <bool ZERO_START>
+template <bool ZERO_START, bool PRODUCT_SEEDS>
 __device__ __forceinline__ void setup_at(const float4 xi, const float4 *sj, const Item &item, int tid,
                                          int jmask, int j, bool valid, float qs_hi, float qs_lo, float dq_hi,
                                          float dq_lo, M2Pair &o, const float4 *__restrict__ sct, int sct_n)
 {
     const float4 xj = sj[j];
     const float w = (!valid || j <= jmask) ? 0.f : xi.w * xj.w;
-    setup_m2<ZERO_START>(xi, xj, w, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(item.i0 + tid, item.j0 + j), o.w0,
+    setup_m2<ZERO_START, PRODUCT_SEEDS>(xi, xj, w, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(item.i0 + tid, item.j0 + j), o.w0,
                          o.w1, o.Cp, o.Cn, sct, sct_n);
 }
 
@@ -133,13 +140,13 @@ __device__ __forceinline__ void run_m2_pipelined(const float4 xi, const float4 *
     const int jlen = item.jlen;
     if (jlen <= 0) return;
     M2Pair a, b;
-    setup_at<ZERO_START>(xi, sj, item, tid, jmask, 0, true, qs_hi, qs_lo, dq_hi, dq_lo, a, sct, sct_n);
+    setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, 0, true, qs_hi, qs_lo, dq_hi, dq_lo, a, sct, sct_n);
     int j = 0;
     for (; j + 1 < jlen; j += 2) {
-        setup_at<ZERO_START>(xi, sj, item, tid, jmask, j + 1, true, qs_hi, qs_lo, dq_hi, dq_lo, b, sct, sct_n);
+        setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, j + 1, true, qs_hi, qs_lo, dq_hi, dq_lo, b, sct, sct_n);
         core_m2<NB, NV>(a.w0, a.w1, a.Cp, a.Cn, acc);
         const bool more = j + 2 < jlen;
-        setup_at<ZERO_START>(xi, sj, item, tid, jmask, more ? j + 2 : j + 1, more, qs_hi, qs_lo, dq_hi, dq_lo,
+        setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, more ? j + 2 : j + 1, more, qs_hi, qs_lo, dq_hi, dq_lo,
                              a, sct, sct_n);
         core_m2<NB, NV>(b.w0, b.w1, b.Cp, b.Cn, acc);
     }
@@ -154,7 +161,7 @@ __device__ __forceinline__ void run_m2(const float4 xi, const float4 *sj, const 
 {
     for (int j = 0; j < item.jlen; ++j) {
         M2Pair a;
-        setup_at<ZERO_START>(xi, sj, item, tid, jmask, j, true, qs_hi, qs_lo, dq_hi, dq_lo, a, sct, sct_n);
+        setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, j, true, qs_hi, qs_lo, dq_hi, dq_lo, a, sct, sct_n);
         core_m2<NB, 2 * NB>(a.w0, a.w1, a.Cp, a.Cn, acc);
     }
 }

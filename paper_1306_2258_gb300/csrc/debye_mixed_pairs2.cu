@@ -63,7 +63,7 @@ __device__ __forceinline__ void run_pairs2(const float4 *sxy, const float4 *szw,
     for (int k = 0; k < jpairs; ++k) {
         const int j = 2 * k;
         PairState2 p;
-        setup2_tail<ZERO_START>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
+        setup2_tail<ZERO_START, true, NB == 52>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
                                 pair_hash(ih, item.j0 + j + 1), p, sct, sct_n);
         // the next two pairs' distances, issued ahead of this step's recurrences (the last step
         // reads its own slot again and discards the result)
