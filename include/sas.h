@@ -52,7 +52,8 @@ typedef enum {
     SAS_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed */
     SAS_ERR_ALLOC = 3,       /* device or host allocation failed (nothing leaked) */
     SAS_ERR_UNSUPPORTED = 4, /* q grid of too many uniform runs, too many q values or types */
-    SAS_ERR_TIMEOUT = 5      /* a wait on the device exceeded its limit */
+    SAS_ERR_TIMEOUT = 5,     /* a wait on the device exceeded its limit */
+    SAS_ERR_CORRUPT = 6      /* a guard band around a device buffer was overwritten (sas_guard_check) */
 } sas_status;
 
 /* precision (sas_create flags) */
@@ -407,6 +408,28 @@ sas_status sas_screen_select(int n_conf, int n_q, const float *z, int ld, const 
  * must address rows of src).  Packs selected conformers for the exact kernels. */
 sas_status sas_gather_rows(const void *src, int64_t row_bytes, const int32_t *idx, int64_t n_idx, void *dst,
                            void *stream);
+
+/* ---- guard bands (a debugging aid; the paper has no counterpart) --------------------------
+ * With guard bands on, every device buffer the library allocates from then on (context and network
+ * workspace, microbenchmark scratch) lies between two 256-byte bands of a fixed byte pattern, the
+ * second starting at the buffer's exact end, so that a kernel writing past either end of a buffer
+ * leaves a trace that sas_guard_check finds.  They stand in for a device memory checker in tests and
+ * debugging.  Buffers allocated while the bands are off stay plain; a guarded buffer keeps its bands
+ * until freed.  Setting up the bands waits for the device: do not allocate (first calls, larger
+ * sizes) under stream capture while they are on.  The environment variable SAS_GUARD_BANDS=1 turns
+ * them on when the library is loaded.  The fixed array of sas_profile_static has none.
+ *
+ * sas_guard_bands: enable 1 (on) or 0 (off) for later allocations.  Errors: INVALID_ARG.
+ * sas_guard_check: waits for every device holding a guarded buffer, then compares every band of
+ *   every live guarded buffer with the pattern; *n_checked_out (may be NULL) gets the number of
+ *   buffers checked.  Errors: CORRUPT (a band changed; the message names the first buffer and side),
+ *   CUDA.  Thread-safe.
+ * sas_guard_list: the live guarded buffers' device addresses and sizes, up to cap of them, into
+ *   ptr_out [cap] and bytes_out [cap] (host); *n_out gets their total count.  Errors: INVALID_ARG.
+ */
+sas_status sas_guard_bands(int enable);
+sas_status sas_guard_check(int64_t *n_checked_out);
+sas_status sas_guard_list(int64_t cap, void **ptr_out, int64_t *bytes_out, int64_t *n_out);
 
 /* Thread-local message of the calling thread's last failure ("" if none). */
 const char *sas_last_error(void);

@@ -15,8 +15,8 @@ import numpy as np
 
 from . import build as _build
 
-SAS_OK, SAS_ERR_INVALID_ARG, SAS_ERR_CUDA, SAS_ERR_ALLOC, SAS_ERR_UNSUPPORTED, SAS_ERR_TIMEOUT = range(6)
-STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "ALLOC", 4: "UNSUPPORTED", 5: "TIMEOUT"}
+SAS_OK, SAS_ERR_INVALID_ARG, SAS_ERR_CUDA, SAS_ERR_ALLOC, SAS_ERR_UNSUPPORTED, SAS_ERR_TIMEOUT, SAS_ERR_CORRUPT = range(7)
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "ALLOC", 4: "UNSUPPORTED", 5: "TIMEOUT", 6: "CORRUPT"}
 SAS_MIXED, SAS_FP64 = 0, 1
 SAS_DETERMINISTIC = 16
 SAS_COORDS_F32, SAS_COORDS_F64 = 0, 1
@@ -35,7 +35,7 @@ EXPORTS = (
     "sas_mlp_param_count", "sas_mlp_set_state", "sas_mlp_get_state", "sas_mlp_forward", "sas_mlp_train_step",
     "sas_mlp_grads", "sas_gemm_bf16", "sas_screen_select", "sas_gather_rows", "sas_profile_atomic",
     "sas_measure_peaks", "sas_exact_sums", "sas_assemble_exact", "sas_mlp_read_buffer",
-    "sas_binned_profile", "sas_profile_vjp_atomic",
+    "sas_binned_profile", "sas_profile_vjp_atomic", "sas_guard_bands", "sas_guard_check", "sas_guard_list",
 )
 
 
@@ -91,6 +91,9 @@ def load():
                 "sas_assemble_exact": [_vp, _vp, _i64, _vp, _vp],
                 "sas_binned_profile": [_vp, _vp, _i64, _int, ctypes.c_float, _vp, _vp, _vp],
                 "sas_profile_vjp_atomic": [_vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp],
+                "sas_guard_bands": [_int],
+                "sas_guard_check": [_vp],
+                "sas_guard_list": [_i64, _vp, _vp, _vp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -304,6 +307,32 @@ def sas_measure_peaks(stream=None) -> dict:
 
 def sas_last_error() -> str:
     return load().sas_last_error().decode()
+
+
+def sas_guard_bands(enable: bool):
+    """Guard bands around device buffers allocated from now on (on) or not (off)."""
+    check(load().sas_guard_bands(1 if enable else 0))
+
+
+def sas_guard_check() -> int:
+    """Compare every band of every live guarded buffer with its pattern; returns the number of
+    buffers checked, raises SasError (SAS_ERR_CORRUPT) if a band was overwritten."""
+    n = ctypes.c_int64(0)
+    check(load().sas_guard_check(ctypes.byref(n)))
+    return int(n.value)
+
+
+def sas_guard_list():
+    """[(device address, bytes)] of the live guarded buffers."""
+    lib = load()
+    n = ctypes.c_int64(0)
+    check(lib.sas_guard_list(0, None, None, ctypes.byref(n)))
+    cap = int(n.value)
+    ptrs = (ctypes.c_void_p * max(cap, 1))()
+    sizes = np.zeros(max(cap, 1), dtype=np.int64)
+    check(lib.sas_guard_list(cap, ptrs, sizes.ctypes.data, ctypes.byref(n)))
+    k = min(cap, int(n.value))
+    return [(int(ptrs[i]), int(sizes[i])) for i in range(k)]
 
 
 def sas_version() -> str:

@@ -39,7 +39,7 @@ struct DevBuf {
     ~DevBuf() { release(); }
     void release()
     {
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
         p = nullptr;
         cap = 0;
     }
@@ -50,7 +50,7 @@ struct DevBuf {
         release();
         ++g_alloc_count;
         if (alloc_fail_at() > 0 && g_alloc_count == alloc_fail_at()) return false;
-        if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+        if (dev_malloc(&p, bytes ? bytes : 16) != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
             return false;

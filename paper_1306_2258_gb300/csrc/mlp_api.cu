@@ -90,7 +90,7 @@ template <class T>
 bool mlp_alloc(sas_mlp *m, T *&p, int64_t n)
 {
     void *q = nullptr;
-    if (cudaMalloc(&q, sizeof(T) * (size_t)(n > 0 ? n : 1)) != cudaSuccess) {
+    if (sas::api::dev_malloc(&q, sizeof(T) * (size_t)(n > 0 ? n : 1)) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -101,7 +101,7 @@ bool mlp_alloc(sas_mlp *m, T *&p, int64_t n)
 
 void mlp_free(sas_mlp *m)
 {
-    for (void *p : m->owned) cudaFree(p);
+    for (void *p : m->owned) sas::api::dev_free(p);
     m->owned.clear();
 }
 

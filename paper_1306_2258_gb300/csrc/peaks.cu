@@ -130,8 +130,8 @@ extern "C" sas_status sas_measure_peaks(double *out, int n_out, void *stream)
     float *sink = nullptr;
     unsigned long long *clk = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaMalloc(&sink, sizeof(float) * (size_t)grid * kPeakThreads);
-    if (e == cudaSuccess) e = cudaMalloc(&clk, 2 * sizeof(unsigned long long));
+    cudaError_t e = sas::api::dev_malloc((void **)&sink, sizeof(float) * (size_t)grid * kPeakThreads);
+    if (e == cudaSuccess) e = sas::api::dev_malloc((void **)&clk, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     float ms[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -146,8 +146,8 @@ extern "C" sas_status sas_measure_peaks(double *out, int n_out, void *stream)
     if (e == cudaSuccess) e = cudaMemcpy(hclk, clk, sizeof hclk, cudaMemcpyDeviceToHost);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    cudaFree(sink);
-    cudaFree(clk);
+    sas::api::dev_free(sink);
+    sas::api::dev_free(clk);
     if (e != cudaSuccess) {
         cudaGetLastError();
         char buf[160];

@@ -292,4 +292,11 @@ cudaError_t launch_quad(const float4 *X, int64_t npad, int64_t batch, const int 
                         const double4 *cen, const double *F, int n_q, const QuadPlan &pl, const QuadPlan *pl_dev,
                         const float4 *dirs, const double *wts, double2 *Apart, double *I, cudaStream_t s);
 
+namespace api {
+// Every device allocation of the library (guard.cu): cudaMalloc / cudaFree, with guard bands
+// around the buffer while they are switched on (sas_guard_bands).
+cudaError_t dev_malloc(void **p, size_t bytes);
+void dev_free(void *p);
+}  // namespace api
+
 }  // namespace sas

@@ -160,3 +160,14 @@ def test_plain_c_client_links_and_gets_status_codes(tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
+
+
+def test_guard_band_calls_need_no_gpu_when_nothing_is_guarded():
+    """sas_guard_bands validates its switch; with no guarded buffer alive, sas_guard_check and
+    sas_guard_list make no CUDA call and report nothing."""
+    lib = _lib.load()
+    assert lib.sas_guard_bands(2) == _lib.SAS_ERR_INVALID_ARG
+    assert lib.sas_guard_bands(0) == _lib.SAS_OK
+    assert _lib.sas_guard_check() == 0
+    assert _lib.sas_guard_list() == []
+    assert lib.sas_guard_list(-1, None, None, None) == _lib.SAS_ERR_INVALID_ARG
