@@ -148,9 +148,10 @@ bool on_device(const void *p)
 // The table of (sin, cos)(k/64) (sincos_tab) covering every pair's step phase dq r of a call: r is
 // at most the diameter bound of the call's conformers (ctx->diam, set by prepare), so 64 dq diam + 3
 // entries suffice (the 3 cover the float32 rounding of r and t).  Built in FP64 on the host once per
-// context and rebuilt larger when a call needs more.  Beyond 8,192 entries (t above 128 rad: a
-// table past what L1 holds) the kernels keep the polynomial sincos.
-constexpr int kSincosTabMax = 8192;
+// context and rebuilt larger when a call needs more.  Beyond kSincosTabMax = 2,048 entries (t above
+// 32 rad, a molecule thousands of Å long) the kernels keep the polynomial sincos: the two-pair
+// kernel copies the table into shared memory beside its J-range, 32 KB at most.
+constexpr int kSincosTabMax = kStagedSincosTab;
 
 sas_status with_sincos_table(sas_ctx *ctx, QChunks &qc, cudaStream_t s)
 {
@@ -176,7 +177,7 @@ sas_status with_sincos_table(sas_ctx *ctx, QChunks &qc, cudaStream_t s)
         ctx->sct_n = m;
     }
     qc.sct = ctx->sct.as<float4>();
-    qc.sct_n = ctx->sct_n;
+    qc.sct_n = n;   // the entries this call can index (the allocation may hold more)
     return SAS_OK;
 }
 

@@ -35,6 +35,10 @@ struct Item {
 // The q grid as runs of uniform spacing (one run for a uniform grid), each run split into passes
 // of at most kQChunk values: chunk c holds q_k = qsd[c] + (k - q_begin[c]) dqd[c] for
 // q_begin[c] <= k < q_begin[c] + q_len[c].
+// Largest (sin, cos)(k/64) table a call uses (entries): the 208-q two-pair kernel stages it in
+// shared memory.
+constexpr int kStagedSincosTab = 2048;
+
 struct QChunks {
     int n_q;
     int n_chunks;
@@ -46,8 +50,8 @@ struct QChunks {
     float dq_lo[kMaxChunks];
     double qsd[kMaxChunks];    // the same in FP64
     double dqd[kMaxChunks];
-    // (sin, cos)(k/64) for k < sct_n as float32 hi/lo (sincos_tab), covering every pair's step phase
-    // dq r of the call; null: the polynomial sincos
+    // (sin, cos)(k/64) for k < sct_n <= kStagedSincosTab as float32 hi/lo (sincos_tab), covering every
+    // pair's step phase dq r of the call; null: the polynomial sincos
     const float4 *sct = nullptr;
     int sct_n = 0;
 };

@@ -170,7 +170,7 @@ __device__ __forceinline__ SinCos2 sincos2_tab(float2 t, const float4 *__restric
     const float2 d = __ffma2_rn(kf, sc_bcast(-kTabStep), t);
     const int kA = min(max(__float_as_int(kr.x) - __float_as_int(kRound), 0), n - 1);
     const int kB = min(max(__float_as_int(kr.y) - __float_as_int(kRound), 0), n - 1);
-    const float4 eA = __ldg(tab + kA), eB = __ldg(tab + kB);
+    const float4 eA = tab[kA], eB = tab[kB];   // a shared-memory copy or the global table
     const float2 d2 = __fmul2_rn(d, d);
     const float2 d3 = __fmul2_rn(d2, d);
     const float2 sd = __ffma2_rn(d3, sc_bcast(-kSixth), d);
