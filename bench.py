@@ -35,7 +35,7 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
 OPS_PER_PAIR_Q = 2   # FP32 lane operations per pair*q: one FMA (recurrence) + one add (accumulate)
-PAIR_KERNEL = "k_debye_mixed_pairs2<52,101,128>"
+PAIR_KERNEL = "k_debye_mixed_pairs2<52,101,128,2>"
 # DRAM bytes (read + write) of one pair-kernel launch on this workload, from the one-launch ncu
 # capture summarised under profiles/ (same kernel source); None while the kernel has changed since
 # that capture.

@@ -64,7 +64,7 @@ __device__ __forceinline__ void run_atomic2(const float4 *sxy, const float4 *szw
     for (int k = k0; k < k1; ++k) {
         const int j = 2 * k;
         PairState2 p;
-        setup2_tail<ZERO_START, false>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
+        setup2_tail<ZERO_START, 0>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
                                 pair_hash(ih, item.j0 + j + 1), p, sct, sct_n);
         const bool more = k + 1 < k1;
         const int kn = more ? k + 1 : k;

@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
         const int jmask = item.diag ? tid : -1;   // pairs with j <= i are not pairs of i<j
         // the sine table for the 208-q form only (its 101-q and 52-q forms measured faster without:
         // there the table load's latency sits in a shorter set-up)
-        const float4 *sct = NB == 52 ? qc.sct : nullptr;
+        const float4 *sct = (NB == 52 || NB == 26) ? qc.sct : nullptr;   // as the two-pair kernel
         if (P == 3) {
             const int nv = (qlen + 1) >> 1;
             if (zero_start)

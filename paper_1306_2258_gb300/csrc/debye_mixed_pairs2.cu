@@ -49,7 +49,7 @@ __device__ __forceinline__ void core2(const PairState2 &p, float2 (&acc)[2 * NB]
     }
 }
 
-template <int NB, int NV, bool ZERO_START>
+template <int NB, int NV, bool ZERO_START, int TAB>
 __device__ __forceinline__ void run_pairs2(const float4 *sxy, const float4 *szw, int jpairs, const float4 xi,
                                            const Item &item, int tid, int jmask, float2 qs_hi, float2 qs_lo,
                                            float2 dq_hi, float2 dq_lo, float2 (&acc)[2 * NB],
@@ -63,7 +63,7 @@ __device__ __forceinline__ void run_pairs2(const float4 *sxy, const float4 *szw,
     for (int k = 0; k < jpairs; ++k) {
         const int j = 2 * k;
         PairState2 p;
-        setup2_tail<ZERO_START, true, NB == 52>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
+        setup2_tail<ZERO_START, TAB, NB == 52>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
                                 pair_hash(ih, item.j0 + j + 1), p, sct, sct_n);
         // the next two pairs' distances, issued ahead of this step's recurrences (the last step
         // reads its own slot again and discards the result)
@@ -75,8 +75,12 @@ __device__ __forceinline__ void run_pairs2(const float4 *sxy, const float4 *szw,
 }
 
 // TILE: the I-tile (= threads per CTA), 128, or 64 for small molecules whose type groups padded to
-// 128 would waste slots.
-template <int NB, int NV, int TILE>
+// 128 would waste slots.  TAB: the step's sin/cos (setup2_tail): the 208-q form is compiled with
+// both the table and the polynomial and picks at run time (2), the 104-q form with one of them
+// (1 where the call has a table, else 0), the 52-q form with the polynomial (0): each the faster
+// build of its form (GB300: the 208-q form with the table alone 6 % slower, the 104-q form with
+// both 5-8 % slower than with the table alone, and 4-5 % slower with the polynomial alone).
+template <int NB, int NV, int TILE, int TAB>
 __global__ void __launch_bounds__(TILE, mixed_ctas_per_sm(NB) * (kTile / TILE))
     k_debye_mixed_pairs2(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items,
                          int n_items, QChunks qc, double *__restrict__ partial, int part_stride, int jmax,
@@ -85,14 +89,14 @@ __global__ void __launch_bounds__(TILE, mixed_ctas_per_sm(NB) * (kTile / TILE))
     extern __shared__ float4 smem[];
     float4 *sxy = smem;              // [jmax / 2]: (x_j, x_j+1, y_j, y_j+1)
     float4 *szw = smem + jmax / 2;   // [jmax / 2]: (z_j, z_j+1, w_j, w_j+1)
-    float4 *stab = smem + jmax;      // [qc.sct_n]: the 208-q form's copy of the sine table
+    float4 *stab = smem + jmax;      // [qc.sct_n]: the copy of the sine table (TAB 1, or 2 with a table)
     __shared__ double red[TILE / 32][4 * NB];
     __shared__ int next_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // the sine table for the 208-q form only (the 104-q and 52-q forms measured faster without),
-    // read from shared memory (1.2 % faster than through L1); visible after the loop's first barrier
+    // the sine table, read from shared memory (1.2 % faster than through L1 on the 208-q form);
+    // visible after the loop's first barrier
     const float4 *sct = nullptr;
-    if (NB == 52 && qc.sct != nullptr) {
+    if (TAB == 1 || (TAB == 2 && qc.sct != nullptr)) {
         for (int k = tid; k < qc.sct_n; k += TILE) stab[k] = qc.sct[k];
         sct = stab;
     }
@@ -119,10 +123,10 @@ __global__ void __launch_bounds__(TILE, mixed_ctas_per_sm(NB) * (kTile / TILE))
         for (int k = 0; k < 2 * NB; ++k) acc[k] = make_float2(0.f, 0.f);
         const int jmask = item.diag ? tid : -1;   // pairs with j <= i are not pairs of i<j
         if (zero_start)
-            run_pairs2<NB, NV, true>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
+            run_pairs2<NB, NV, true, TAB>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
                                      bc(qc.dq_lo[ch]), acc, sct, qc.sct_n);
         else
-            run_pairs2<NB, NV, false>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
+            run_pairs2<NB, NV, false, TAB>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
                                       bc(qc.dq_lo[ch]), acc, sct, qc.sct_n);
         flush_warp<NB, 2>(acc, red[warp], lane);
         __syncthreads();
@@ -137,28 +141,46 @@ __global__ void __launch_bounds__(TILE, mixed_ctas_per_sm(NB) * (kTile / TILE))
     }
 }
 
-template <int NB, int NV, int TILE>
-cudaError_t launch_nv(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
-                      double *partial, int part_stride, int grid, int jmax, int *ticket, cudaStream_t s)
+template <int NB, int NV, int TILE, int TAB>
+cudaError_t launch_tab(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
+                       double *partial, int part_stride, int grid, int jmax, int *ticket, cudaStream_t s)
 {
-    const bool staged = NB == 52 && qc.sct != nullptr;
-    if (staged && (qc.sct_n <= 0 || qc.sct_n > kStagedSincosTab)) return cudaErrorInvalidValue;
+    const bool staged = TAB == 1 || (TAB == 2 && qc.sct != nullptr);
+    if (staged && (qc.sct == nullptr || qc.sct_n <= 0 || qc.sct_n > kStagedSincosTab))
+        return cudaErrorInvalidValue;
     const size_t smem = ((size_t)jmax + (staged ? (size_t)qc.sct_n : 0)) * sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(k_debye_mixed_pairs2<NB, NV, TILE>,
+    cudaError_t e = cudaFuncSetAttribute(k_debye_mixed_pairs2<NB, NV, TILE, TAB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (grid <= 0) {   // persistent grid: every resident CTA slot of every SM
         int occ = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_mixed_pairs2<NB, NV, TILE>, TILE, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_mixed_pairs2<NB, NV, TILE, TAB>, TILE, smem);
         if (e != cudaSuccess) return e;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         grid = (occ > 0 ? occ : 1) * sms;
     }
     if (grid > n_items) grid = n_items;
-    k_debye_mixed_pairs2<NB, NV, TILE><<<grid, TILE, smem, s>>>(X, npad, items, n_items, qc, partial, part_stride,
-                                                                 jmax, ticket);
+    k_debye_mixed_pairs2<NB, NV, TILE, TAB><<<grid, TILE, smem, s>>>(X, npad, items, n_items, qc, partial,
+                                                                      part_stride, jmax, ticket);
     return cudaGetLastError();
+}
+
+// The build of each form (TAB above).
+template <int NB, int NV, int TILE>
+cudaError_t launch_nv(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
+                      double *partial, int part_stride, int grid, int jmax, int *ticket, cudaStream_t s)
+{
+    if constexpr (NB == 52) {
+        return launch_tab<NB, NV, TILE, 2>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+    } else if constexpr (NB == 26) {
+        if (qc.sct != nullptr)
+            return launch_tab<NB, NV, TILE, 1>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket,
+                                               s);
+        return launch_tab<NB, NV, TILE, 0>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+    } else {
+        return launch_tab<NB, NV, TILE, 0>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
+    }
 }
 
 // NV: the slots of the longest chunk when within 3 of the capacity 2*NB, else the capacity.

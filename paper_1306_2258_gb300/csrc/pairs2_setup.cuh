@@ -45,13 +45,14 @@ __device__ __forceinline__ void setup2_head(const float4 pxy, const float4 pzw, 
 }
 
 // Second part: sin t, cos t of t = dq r, the seeds of the first two blocks and the coefficient.
-// sct: the table of (sin, cos)(k/64) of the call (sincos2_tab), or null for the polynomial form;
-// TAB false compiles the polynomial form alone (kernels at the register cap).
+// TAB: 0 the polynomial sin/cos alone; 1 the table of (sin, cos)(k/64) of the call alone (sct, not
+// null; sincos2_tab); 2 the table where sct is not null, else the polynomial (both compiled).  Which
+// compiles to the faster kernel differs by form, so each kernel picks its own (measured).
 // PRODUCT_SEEDS (zero start only): the seeds from the scaled sine and 4 sin^2 t, which the
 // coefficient needs anyway: scale sin 2t = (2 scale sin t) cos t and scale sin 3t =
 // (scale sin t)(3 - 4 sin^2 t), four packed operations fewer than by angle addition.  Used by the
 // 208-q form, where it measured faster (1 %); the 104-q form measured 2-3 % slower with it.
-template <bool ZERO_START, bool TAB = true, bool PRODUCT_SEEDS = false>
+template <bool ZERO_START, int TAB = 2, bool PRODUCT_SEEDS = false>
 __device__ __forceinline__ void setup2_tail(const PairHead2 &h, float2 qs_hi, float2 qs_lo, float2 dq_hi,
                                             float2 dq_lo, unsigned hA, unsigned hB, PairState2 &o,
                                             const float4 *__restrict__ sct, int sct_n)
@@ -59,7 +60,7 @@ __device__ __forceinline__ void setup2_tail(const PairHead2 &h, float2 qs_hi, fl
     const float2 r = h.r;
     const float2 scale = f2mul(h.w, h.y);
     const float2 t = f2fma(dq_hi, r, f2mul(dq_lo, r));
-    const SinCos2 b1 = (TAB && sct) ? sincos2_tab(t, sct, sct_n) : sincos2_f32(t);
+    const SinCos2 b1 = (TAB == 1 || (TAB == 2 && sct)) ? sincos2_tab(t, sct, sct_n) : sincos2_f32(t);
     const float2 s1 = b1.s, c1 = b1.c;
     const float2 s1x2 = f2add(s1, s1);
     // 2cos(2t) = 2 - 4 sin^2 t, rounded stochastically (dither from the pair hash)
