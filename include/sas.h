@@ -210,7 +210,9 @@ sas_status sas_profile_vjp_atomic(sas_ctx *ctx, const float *coords, int64_t n_a
  * instruction and lane), out[2] MUFU sine operations/s (__sinf), out[3] FP64 FMA lane
  * operations/s, out[4] the SM clock (MHz) seen during the FFMA run (clock64 against the global
  * timer), and with n_out >= 6 out[5] shared-memory integer atomic adds/s without bank conflicts
- * (each lane adding to a word of its own bank).  Each kernel runs about 10 ms on `stream`; the
+ * (each lane adding to a word of its own bank), with n_out >= 7 out[6] packed FMA lane operations/s
+ * when every instruction reads three distinct register pairs (no operand shared with the previous
+ * instruction).  Each kernel runs about 10 ms on `stream`; the
  * call waits for them.  out is host memory of n_out >= 5 doubles.  Errors: INVALID_ARG, CUDA.
  */
 sas_status sas_measure_peaks(double *out, int n_out, void *stream);

@@ -297,12 +297,12 @@ def sas_gather_rows(src, row_bytes, idx, n_idx, dst, stream=None):
 
 def sas_measure_peaks(stream=None) -> dict:
     """Measured peaks of the current device: FP32 FMA and packed-FMA lane-ops/s, MUFU sine ops/s,
-    FP64 FMA lane-ops/s, the SM clock (MHz) of the FMA run, and conflict-free shared-memory integer
-    atomic adds/s."""
-    out = np.zeros(6)
-    check(load().sas_measure_peaks(out.ctypes.data, 6, stream_handle(stream)))
+    FP64 FMA lane-ops/s, the SM clock (MHz) of the FMA run, conflict-free shared-memory integer
+    atomic adds/s, and packed-FMA lane-ops/s with three distinct source register pairs."""
+    out = np.zeros(7)
+    check(load().sas_measure_peaks(out.ctypes.data, 7, stream_handle(stream)))
     return {"ffma": float(out[0]), "ffma2": float(out[1]), "mufu_sin": float(out[2]), "dfma": float(out[3]),
-            "sm_mhz": float(out[4]), "atoms_shared": float(out[5])}
+            "sm_mhz": float(out[4]), "atoms_shared": float(out[5]), "ffma2_3op": float(out[6])}
 
 
 def sas_last_error() -> str:

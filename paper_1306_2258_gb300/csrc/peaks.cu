@@ -7,6 +7,10 @@
 //   DFMA   FP64 fused multiply-add                     1 lane operation
 //   ATOMS  shared-memory integer atomic add            1 lane operation (each lane its own word,
 //          a bank of its own: the conflict-free rate, the denominator of the pair histogram)
+//   FFMA2 with three distinct source register pairs (each chain its own multiplier and addend, so
+//          that no operand repeats between consecutive instructions): the form of the per-atom
+//          kernels' cores, where every packed FMA reads three values of its own (a recurrence
+//          coefficient, state and previous state; a form factor, state and accumulator)
 // The chains contract toward a fixed point (x -> 0.999 x + 1e-3), so no value overflows or
 // becomes subnormal.  The FFMA kernel also reads the SM clock against the global timer, which
 // gives the clock the measurement ran at.
@@ -61,6 +65,19 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak(int iters, float m, float
             for (int c = 0; c < kChains; ++c) a[c] = __sinf(a[c]) + k;
 #pragma unroll
         for (int c = 0; c < kChains; ++c) r += a[c];
+    } else if (KIND == 5) {
+        float2 a[kChains], b[kChains], d[kChains];
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) {
+            a[c] = make_float2(1.f + 0.01f * c, 1.f - 0.01f * (float)(tid & 7));
+            b[c] = make_float2(m - 1e-6f * c, m - 2e-6f * c - 1e-7f * (float)(tid & 3));
+            d[c] = make_float2(k + 1e-6f * c, k + 2e-6f * c + 1e-7f * (float)(tid & 5));
+        }
+        for (int i = 0; i < iters; ++i)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) a[c] = __ffma2_rn(b[c], a[c], d[c]);
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) r += a[c].x + a[c].y;
     } else if (KIND == 4) {
         __shared__ int cnt[kChains][kPeakThreads];
 #pragma unroll
@@ -134,7 +151,7 @@ extern "C" sas_status sas_measure_peaks(double *out, int n_out, void *stream)
     if (e == cudaSuccess) e = sas::api::dev_malloc((void **)&clk, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    float ms[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float ms[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     // iterations: about 10 ms per kernel at the expected rates
     const int it_f = 160000, it_f2 = 80000, it_m = 20000, it_d = 2500, it_a = 20000;
     if (e == cudaSuccess) e = timed<0>(grid, it_f, sink, clk, e0, e1, s, ms[0]);
@@ -142,6 +159,7 @@ extern "C" sas_status sas_measure_peaks(double *out, int n_out, void *stream)
     if (e == cudaSuccess) e = timed<2>(grid, it_m, sink, clk, e0, e1, s, ms[2]);
     if (e == cudaSuccess) e = timed<3>(grid, it_d, sink, clk, e0, e1, s, ms[3]);
     if (e == cudaSuccess && n_out >= 6) e = timed<4>(grid, it_a, sink, clk, e0, e1, s, ms[4]);
+    if (e == cudaSuccess && n_out >= 7) e = timed<5>(grid, it_f2 / 2, sink, clk, e0, e1, s, ms[5]);
     unsigned long long hclk[2] = {0, 0};
     if (e == cudaSuccess) e = cudaMemcpy(hclk, clk, sizeof hclk, cudaMemcpyDeviceToHost);
     if (e0) cudaEventDestroy(e0);
@@ -160,5 +178,6 @@ extern "C" sas_status sas_measure_peaks(double *out, int n_out, void *stream)
     out[3] = threads * kChains * it_d / (ms[3] * 1e-3);         // DFMA lane-ops/s
     out[4] = hclk[1] ? (double)hclk[0] / (double)hclk[1] * 1e3 : 0.0;   // SM MHz during the FFMA run
     if (n_out >= 6) out[5] = threads * kChains * it_a / (ms[4] * 1e-3);   // shared atomic adds/s
+    if (n_out >= 7) out[6] = threads * kChains * (it_f2 / 2) * 2.0 / (ms[5] * 1e-3);   // FFMA2, 3 operands
     return SAS_OK;
 }
