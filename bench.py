@@ -35,7 +35,7 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
 OPS_PER_PAIR_Q = 2   # FP32 lane operations per pair*q: one FMA (recurrence) + one add (accumulate)
-PAIR_KERNEL = "k_debye_mixed_pairs2<52,101,128,2>"
+PAIR_KERNEL = "k_debye_mixed_pairs2<52,101,128,2,false>"
 # DRAM bytes (read + write) of one pair-kernel launch on this workload, from the one-launch ncu
 # capture summarised under profiles/ (same kernel source); None while the kernel has changed since
 # that capture.
@@ -48,6 +48,10 @@ MIXED_KERNEL_DRAM_BYTES = 1_213_696
 def _table1(n, seconds):
     return {"atoms": n, "s": seconds, "pair_q_per_s": n * (n + 1) / 2 * 50 / seconds}
 
+
+# Table 1 in full: atoms -> (GT 330M s, GTX 295 s), single-precision OpenCL, 50-point profiles.
+PAPER_TABLE1 = {1000: (0.03, 0.02), 2000: (0.07, 0.03), 4000: (0.25, 0.08), 10000: (1.34, 0.34),
+                20000: (5.02, 1.14), 40000: (20.4, 3.94), 100000: (121.0, 22.5)}
 
 PAPER_CONTEXT = {
     "source": "Table 1 (50-point profiles, 0 < q <= 1 A^-1, FP32 OpenCL GPU, parallel Java CPU)",
@@ -276,6 +280,31 @@ def run_rows(dev, stream):
                                             "pair_kernel_ms": int(p.stats()[4]) / 1e6}
     p.close()
     del ffa
+
+    # the paper's own timing workload (Table 1: globules of 1,000-100,000 atoms, 50 q on 0 < q <= 1),
+    # whole mixed calls beside the paper's GPU times, each checked against the FP64 kernel per q
+    entries = []
+    for n_t1, (s330, s295) in PAPER_TABLE1.items():
+        w1 = wl.table1_globule(n_t1)
+        x1 = torch.as_tensor(w1.mol.coords, device=dev)
+        t1 = torch.as_tensor(w1.mol.types, device=dev)
+        p = Profile(w1.coef, w1.q, "mixed")
+        ms = _timed(lambda: p(x1, t1, stream), stream)
+        I_mixed = p(x1, t1, stream).cpu().numpy()
+        p.close()
+        p = Profile(w1.coef, w1.q, "fp64")
+        I_64 = p(x1, t1, stream).cpu().numpy()
+        p.close()
+        entries.append({"atoms": n_t1, "ms": ms, "value": pairs(n_t1) * w1.q.size / (ms / 1e3),
+                        "rel_err_vs_fp64": float(np.max(np.abs(I_mixed - I_64) / I_64)),
+                        "paper_gtx295_s": s295, "paper_gt330m_s": s330,
+                        "paper_gtx295_over_this": s295 / (ms / 1e3)})
+    rows["table1_paper_workload"] = {
+        "workload": "Table 1's workload: random-walk globules of 1,000-100,000 atoms (5 types) x 50 q, "
+                    "q = 0.02..1.0 A^-1, mixed, whole calls",
+        "unit": "pair·q/s", "entries": entries,
+        "note": "the paper's times are single-precision OpenCL on a 2009 GTX 295 and a GT 330M: context, "
+                "not a measured ratio of two implementations on this GPU"}
 
     # large compact molecule at small-angle q: direct sum against the hybrid (orientation average of
     # Eq. 1 by quadrature where cheaper, the direct sum elsewhere)

@@ -71,7 +71,7 @@ __device__ __forceinline__ void setup_adj2_head(const float4 pxy, const float4 p
 // Second part: sin t, cos t, the chains' first two blocks and the coefficient.
 template <bool ZERO_START>
 __device__ __forceinline__ void setup_adj2_tail(const AdjHead2 &h, float2 qs_hi, float2 qs_lo, float2 dq_hi,
-                                                float2 dq_lo, unsigned hA, unsigned hB, AdjPair2 &o)
+                                                float2 dq_lo, unsigned hA, unsigned hB, AdjPair2 &o, bool coef_both)
 {
     const float2 r = h.r;
     const float2 t = f2fma(dq_hi, r, f2mul(dq_lo, r));
@@ -85,9 +85,23 @@ __device__ __forceinline__ void setup_adj2_tail(const AdjHead2 &h, float2 qs_hi,
     const float2 u = f2add(make_float2(__int_as_float(0x3f800000u | (hA >> 9)),
                                        __int_as_float(0x3f800000u | (hB >> 9))),
                            bc(-1.5f));
-    const float2 md = f2fma(u, bc(1.1920928955078125e-7f), mu);
-    const float2 C = f2fma(md, bc(-1.f), bc(2.f));
-    const float2 Cn = f2add(md, bc(-2.f));
+    // the small square that keeps full relative accuracy (coef_dither): 4 sin^2 t where cos 2t >= 0,
+    // 4 cos^2 t where cos 2t < 0, the coefficient then 2 - 4 sin^2 t or 4 cos^2 t - 2 (calls with
+    // coef_both; the others 2 - 4 sin^2 t alone)
+    float2 C, Cn;
+    if (coef_both) {
+        const float2 c1x2 = f2add(c1, c1);
+        const float2 mc = f2mul(c1x2, c1x2);
+        const bool nA = mu.x > mc.x, nB = mu.y > mc.y;
+        const float2 md = f2fma(u, bc(1.1920928955078125e-7f), make_float2(nA ? mc.x : mu.x, nB ? mc.y : mu.y));
+        const float2 two_minus = f2fma(md, bc(-1.f), bc(2.f)), minus_two = f2add(md, bc(-2.f));
+        C = make_float2(nA ? minus_two.x : two_minus.x, nB ? minus_two.y : two_minus.y);
+        Cn = make_float2(nA ? two_minus.x : minus_two.x, nB ? two_minus.y : minus_two.y);
+    } else {
+        const float2 md = f2fma(u, bc(1.1920928955078125e-7f), mu);
+        C = f2fma(md, bc(-1.f), bc(2.f));
+        Cn = f2add(md, bc(-2.f));
+    }
     o.CpA = bc(C.x);
     o.CpB = bc(C.y);
     o.CnA = bc(Cn.x);
@@ -192,7 +206,7 @@ template <int NV, bool ZERO_START, bool DET>
 __device__ __forceinline__ void run_adj2(const float4 *sxy, const float4 *szw, const float4 *sh, float *gj,
                                          int jpairs, const float4 xi, const Item &item, int tid, int lane, int jmask,
                                          float2 qs_hi, float2 qs_lo, float2 dq_hi, float2 dq_lo, float2 &gx,
-                                         float2 &gy, float2 &gz)
+                                         float2 &gy, float2 &gz, bool coef_both)
 {
     const float2 nX = bc(-xi.x), nY = bc(-xi.y), nZ = bc(-xi.z), wi = bc(xi.w);
     const unsigned ih = item.i0 + tid;
@@ -204,7 +218,7 @@ __device__ __forceinline__ void run_adj2(const float4 *sxy, const float4 *szw, c
         const int j = 2 * k;
         AdjPair2 p;
         setup_adj2_tail<ZERO_START>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
-                                    pair_hash(ih, item.j0 + j + 1), p);
+                                    pair_hash(ih, item.j0 + j + 1), p, coef_both);
         const float2 y = head.y, w = head.w;
         // the next two pairs' distances, issued ahead of this step's recurrences (the last step
         // reads its own slot again and discards the result)
@@ -289,10 +303,10 @@ __global__ void __launch_bounds__(kTile, 4)
         float *gw = DET ? gj + (tid >> 5) * 3 * jcap : gj;
         if (zero_start)
             run_adj2<NV, true, DET>(sxy, szw, sh, gw, jpairs, xi, item, tid, lane, jmask, qs_hi, qs_lo,
-                                    bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), gx, gy, gz);
+                                    bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), gx, gy, gz, qc.coef_both != 0);
         else
             run_adj2<NV, false, DET>(sxy, szw, sh, gw, jpairs, xi, item, tid, lane, jmask, qs_hi, qs_lo,
-                                     bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), gx, gy, gz);
+                                     bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), gx, gy, gz, qc.coef_both != 0);
         if (DET) {
             float *pi = PI + ((int64_t)it * kTile + tid) * 3;
             pi[0] = gx.x + gx.y;
@@ -377,7 +391,7 @@ __device__ __forceinline__ void run_adj2_atomic(const float4 *sxy, const float4 
                                                 const float4 *__restrict__ fjrows, float *gj, int jpairs,
                                                 const float4 xi, const Item &item, int tid, int lane, int jmask,
                                                 float2 qs_hi, float2 qs_lo, float2 dq_hi, float2 dq_lo, float2 &gx,
-                                                float2 &gy, float2 &gz)
+                                                float2 &gy, float2 &gz, bool coef_both)
 {
     const float2 nX = bc(-xi.x), nY = bc(-xi.y), nZ = bc(-xi.z), wi = bc(xi.w);
     const unsigned ih = item.i0 + tid;
@@ -389,7 +403,7 @@ __device__ __forceinline__ void run_adj2_atomic(const float4 *sxy, const float4 
         const int j = 2 * k;
         AdjPair2 p;
         setup_adj2_tail<ZERO_START>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
-                                    pair_hash(ih, item.j0 + j + 1), p);
+                                    pair_hash(ih, item.j0 + j + 1), p, coef_both);
         const float2 y = head.y, w = head.w;
         const bool more = k + 1 < jpairs;
         const int kn = more ? k + 1 : k;
@@ -454,10 +468,10 @@ __global__ void __launch_bounds__(kTile, 2)
         float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
         if (zero_start)
             run_adj2_atomic<NV, true>(sxy, szw, sa + tid, fjrows, gj, jpairs, xi, item, tid, lane, jmask, qs_hi, qs_lo,
-                                      bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), gx, gy, gz);
+                                      bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), gx, gy, gz, qc.coef_both != 0);
         else
             run_adj2_atomic<NV, false>(sxy, szw, sa + tid, fjrows, gj, jpairs, xi, item, tid, lane, jmask, qs_hi,
-                                       qs_lo, bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), gx, gy, gz);
+                                       qs_lo, bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), gx, gy, gz, qc.coef_both != 0);
         double *Gb = G + (int64_t)item.batch * npad * 3;
         atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid)], (double)(gx.x + gx.y));
         atomicAdd(&Gb[3 * (int64_t)(item.i0 + tid) + 1], (double)(gy.x + gy.y));

@@ -69,6 +69,7 @@ sas_status sas_profile_atomic(sas_ctx *ctx, const void *coords, int coords_type,
         if (st != SAS_OK) return st;
     }
     const int nv = atomic_slots(qf);
+    if (!fp64) with_coef_form(ctx, qf);
     if (fp64) {
         ALLOC_TRY(ctx->F64t, (size_t)batch * npad * Q * sizeof(double));
         CUDA_TRY(cudaMemsetAsync(ctx->F64t.p, 0, (size_t)batch * npad * Q * sizeof(double), s));
@@ -160,6 +161,7 @@ sas_status sas_profile_vjp_atomic(sas_ctx *ctx, const float *coords, int64_t n_a
                  launches, 1, F, (int64_t)batch * Q * n);
     if (st != SAS_OK) return st;
     const int64_t npad = ctx->h_meta[2];
+    with_coef_form(ctx, qf);
     const int nv = adjoint_atomic_slots();
     const size_t fj = (size_t)batch * qf.n_chunks * (npad / 2) * nv * sizeof(float4);
     const size_t fi = (size_t)batch * qf.n_chunks * nv * npad * sizeof(float2);

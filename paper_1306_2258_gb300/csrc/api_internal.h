@@ -131,6 +131,8 @@ sas_status with_sincos_table(sas_ctx *ctx, QChunks &qc, cudaStream_t s);
 int reseed_for(int opt, int64_t n_atoms, int n_q_chunk, double step_phase_max);
 int mixed_variant(int opt);
 double step_phase(const sas_ctx *ctx, const QChunks &qc);
+// Sets qc.coef_both from the call's step phase (the validation read-back's diameter bound).
+void with_coef_form(const sas_ctx *ctx, QChunks &qc);
 sas_status wait_stream(sas_ctx *ctx, cudaStream_t s);
 sas_status schedule_for(sas_ctx *ctx, int T, int64_t batch, int tile, int n_chunks, int64_t jmax_cap, cudaStream_t s);
 sas_status prepare(sas_ctx *ctx, const void *coords, int coords_f64, const int32_t *types, int64_t n,

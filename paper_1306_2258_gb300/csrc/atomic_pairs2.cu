@@ -50,7 +50,7 @@ __device__ __forceinline__ void core2_atomic(const PairState2 &p, const float4 *
 
 // Pair steps k0 <= k < k1 of the item (pairs j = 2k, 2k+1 relative to item.j0); sf holds the form
 // factors of steps k0.. (sub-block staging).
-template <int NB, int NV, bool ZERO_START>
+template <int NB, int NV, bool ZERO_START, bool CB>
 __device__ __forceinline__ void run_atomic2(const float4 *sxy, const float4 *szw, const float4 *sf, int k0, int k1,
                                             const float4 xi, const Item &item, int tid, int jmask, float2 qs_hi,
                                             float2 qs_lo, float2 dq_hi, float2 dq_lo, float2 (&acc)[2 * NB],
@@ -64,8 +64,8 @@ __device__ __forceinline__ void run_atomic2(const float4 *sxy, const float4 *szw
     for (int k = k0; k < k1; ++k) {
         const int j = 2 * k;
         PairState2 p;
-        setup2_tail<ZERO_START, 0>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
-                                pair_hash(ih, item.j0 + j + 1), p, sct, sct_n);
+        setup2_tail<ZERO_START, 0, false, CB>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
+                                              pair_hash(ih, item.j0 + j + 1), p, sct, sct_n);
         const bool more = k + 1 < k1;
         const int kn = more ? k + 1 : k;
         setup2_head(sxy[kn], szw[kn], nX, nY, nZ, wi, more && j + 2 > jmask, more && j + 3 > jmask, head);
@@ -77,7 +77,8 @@ __device__ __forceinline__ void run_atomic2(const float4 *sxy, const float4 *szw
 __host__ __device__ constexpr int atomic_sub_pairs(int NB) { return NB >= 52 ? 32 : 64; }
 
 // FJ: [batch][chunk][npad / 2][NV] float4, FI: [batch][chunk][NV][npad] float2 (see atomic.cu).
-template <int NB, int NV>
+// CB: the coefficient formed both ways (calls with QChunks::coef_both, setup2_tail).
+template <int NB, int NV, bool CB>
 __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
     k_debye_atomic_pairs2(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items, int n_items,
                           QChunks qc, const float4 *__restrict__ FJ, const float2 *__restrict__ FI,
@@ -123,11 +124,11 @@ __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
             for (int k = tid; k < (k1 - k0) * NV; k += kTile) sf[k] = fsrc[k0 * NV + k];
             __syncthreads();
             if (zero_start)
-                run_atomic2<NB, NV, true>(sxy, szw, sf, k0, k1, xi, item, tid, jmask, qs_hi, qs_lo,
-                                          bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), acc, qc.sct, qc.sct_n);
+                run_atomic2<NB, NV, true, CB>(sxy, szw, sf, k0, k1, xi, item, tid, jmask, qs_hi, qs_lo,
+                                              bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), acc, qc.sct, qc.sct_n);
             else
-                run_atomic2<NB, NV, false>(sxy, szw, sf, k0, k1, xi, item, tid, jmask, qs_hi, qs_lo,
-                                           bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), acc, qc.sct, qc.sct_n);
+                run_atomic2<NB, NV, false, CB>(sxy, szw, sf, k0, k1, xi, item, tid, jmask, qs_hi, qs_lo,
+                                               bc(qc.dq_hi[ch]), bc(qc.dq_lo[ch]), acc, qc.sct, qc.sct_n);
         }
         // f_i(q) of this thread's atom (zero on padding slots)
         const float2 *fi = FI + tab * NV * npad + item.i0 + tid;
@@ -146,27 +147,39 @@ __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
     }
 }
 
-template <int NB, int NV>
-cudaError_t launch_atomic_nv(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
+template <int NB, int NV, bool CB>
+cudaError_t launch_atomic_cb(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
                              const float4 *FJ, const float2 *FI, double *partial, int part_stride, int grid, int jmax,
                              int *ticket, cudaStream_t s)
 {
     const size_t smem = (size_t)jmax * sizeof(float4) + (size_t)atomic_sub_pairs(NB) * NV * sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(k_debye_atomic_pairs2<NB, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_debye_atomic_pairs2<NB, NV, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     if (grid <= 0) {   // every resident CTA slot of every SM
         int occ = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_atomic_pairs2<NB, NV>, kTile, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_atomic_pairs2<NB, NV, CB>, kTile, smem);
         if (e != cudaSuccess) return e;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         grid = (occ > 0 ? occ : 1) * sms;
     }
     if (grid > n_items) grid = n_items;
-    k_debye_atomic_pairs2<NB, NV><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, FJ, FI, partial, part_stride,
+    k_debye_atomic_pairs2<NB, NV, CB><<<grid, kTile, smem, s>>>(X, npad, items, n_items, qc, FJ, FI, partial, part_stride,
                                                             jmax, ticket);
     return cudaGetLastError();
+}
+
+template <int NB, int NV>
+cudaError_t launch_atomic_nv(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
+                             const float4 *FJ, const float2 *FI, double *partial, int part_stride, int grid, int jmax,
+                             int *ticket, cudaStream_t s)
+{
+    if (qc.coef_both)
+        return launch_atomic_cb<NB, NV, true>(X, npad, items, n_items, qc, FJ, FI, partial, part_stride, grid, jmax,
+                                              ticket, s);
+    return launch_atomic_cb<NB, NV, false>(X, npad, items, n_items, qc, FJ, FI, partial, part_stride, grid, jmax,
+                                           ticket, s);
 }
 
 int qlen_max(const QChunks &qc)

@@ -25,7 +25,8 @@
 //    the sign of the coefficient alternating with b and known at compile
 //    time.  The accumulators hold sums of W; sigma is applied once, when they
 //    are lifted to FP64.
-//  * The coefficient 2cos(Mt) = 2 - 4 sin^2(Mt/2) is rounded stochastically
+//  * The coefficient 2cos(Mt), as 2 - 4 sin^2(Mt/2) or 4 cos^2(Mt/2) - 2 (whichever keeps
+//    full relative accuracy: coef_dither), is rounded stochastically
 //    (a dither from a hash of the pair's slots): molecules hold thousands of
 //    pairs at the same distance (bonds), whose identical rounding errors would
 //    otherwise drift in phase together.
@@ -58,7 +59,7 @@ template <bool ZERO_START, bool PRODUCT_SEEDS>
 __device__ __forceinline__ void setup_m2(const float4 xi, const float4 xj, float w, float qs_hi,
                                          float qs_lo, float dq_hi, float dq_lo, unsigned hash,
                                          float2 &w0, float2 &w1, float2 &Cp, float2 &Cn,
-                                         const float4 *__restrict__ sct, int sct_n)
+                                         const float4 *__restrict__ sct, int sct_n, bool coef_both)
 {
     const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
     float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -70,9 +71,10 @@ __device__ __forceinline__ void setup_m2(const float4 xi, const float4 xj, float
     const SinCos b1 = sct ? sincos_tab(t, sct, sct_n) : sincos_f32(t);
     const float c1 = b1.c, s1 = b1.s;
     const float mu = (2.f * s1) * (2.f * s1);   // 4 sin^2 t
-    const float CM = coef_dither(mu, hash);     // 2cos(2t) = 2 - 4 sin^2 t
+    float CM, CMn;
+    coef_dither(s1, c1, hash, coef_both, CM, CMn);   // 2cos(2t)
     Cp = make_float2(CM, CM);
-    Cn = make_float2(-CM, -CM);
+    Cn = make_float2(CMn, CMn);
     if (ZERO_START && PRODUCT_SEEDS) {   // the two-pair kernel's 208-q seeds (pairs2_setup.cuh)
         const float a1 = scale * s1;
         w0 = make_float2(0.f, a1);
@@ -120,12 +122,12 @@ struct M2Pair {
 template <bool ZERO_START, bool PRODUCT_SEEDS>
 __device__ __forceinline__ void setup_at(const float4 xi, const float4 *sj, const Item &item, int tid,
                                          int jmask, int j, bool valid, float qs_hi, float qs_lo, float dq_hi,
-                                         float dq_lo, M2Pair &o, const float4 *__restrict__ sct, int sct_n)
+                                         float dq_lo, M2Pair &o, const float4 *__restrict__ sct, int sct_n, bool coef_both)
 {
     const float4 xj = sj[j];
     const float w = (!valid || j <= jmask) ? 0.f : xi.w * xj.w;
     setup_m2<ZERO_START, PRODUCT_SEEDS>(xi, xj, w, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(item.i0 + tid, item.j0 + j), o.w0,
-                         o.w1, o.Cp, o.Cn, sct, sct_n);
+                         o.w1, o.Cp, o.Cn, sct, sct_n, coef_both);
 }
 
 // Pairs (i, j) over the item's J-range, software-pipelined: the set-up of pair j+1 does not
@@ -135,19 +137,19 @@ template <int NB, int NV, bool ZERO_START>
 __device__ __forceinline__ void run_m2_pipelined(const float4 xi, const float4 *sj, const Item &item,
                                                  int tid, int jmask, float qs_hi, float qs_lo, float dq_hi,
                                                  float dq_lo, float2 (&acc)[2 * NB], const float4 *__restrict__ sct,
-                                                 int sct_n)
+                                                 int sct_n, bool coef_both)
 {
     const int jlen = item.jlen;
     if (jlen <= 0) return;
     M2Pair a, b;
-    setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, 0, true, qs_hi, qs_lo, dq_hi, dq_lo, a, sct, sct_n);
+    setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, 0, true, qs_hi, qs_lo, dq_hi, dq_lo, a, sct, sct_n, coef_both);
     int j = 0;
     for (; j + 1 < jlen; j += 2) {
-        setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, j + 1, true, qs_hi, qs_lo, dq_hi, dq_lo, b, sct, sct_n);
+        setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, j + 1, true, qs_hi, qs_lo, dq_hi, dq_lo, b, sct, sct_n, coef_both);
         core_m2<NB, NV>(a.w0, a.w1, a.Cp, a.Cn, acc);
         const bool more = j + 2 < jlen;
         setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, more ? j + 2 : j + 1, more, qs_hi, qs_lo, dq_hi, dq_lo,
-                             a, sct, sct_n);
+                             a, sct, sct_n, coef_both);
         core_m2<NB, NV>(b.w0, b.w1, b.Cp, b.Cn, acc);
     }
     if (j < jlen) core_m2<NB, NV>(a.w0, a.w1, a.Cp, a.Cn, acc);   // odd J-range: its last pair
@@ -157,11 +159,11 @@ __device__ __forceinline__ void run_m2_pipelined(const float4 xi, const float4 *
 template <int NB, bool ZERO_START>
 __device__ __forceinline__ void run_m2(const float4 xi, const float4 *sj, const Item &item, int tid,
                                        int jmask, float qs_hi, float qs_lo, float dq_hi, float dq_lo,
-                                       float2 (&acc)[2 * NB], const float4 *__restrict__ sct, int sct_n)
+                                       float2 (&acc)[2 * NB], const float4 *__restrict__ sct, int sct_n, bool coef_both)
 {
     for (int j = 0; j < item.jlen; ++j) {
         M2Pair a;
-        setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, j, true, qs_hi, qs_lo, dq_hi, dq_lo, a, sct, sct_n);
+        setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, j, true, qs_hi, qs_lo, dq_hi, dq_lo, a, sct, sct_n, coef_both);
         core_m2<NB, 2 * NB>(a.w0, a.w1, a.Cp, a.Cn, acc);
     }
 }
@@ -172,24 +174,24 @@ template <int NB, bool ZERO_START>
 __device__ __forceinline__ void run_m2_fitted(int nv, const float4 xi, const float4 *sj, const Item &item,
                                               int tid, int jmask, float qs_hi, float qs_lo, float dq_hi,
                                               float dq_lo, float2 (&acc)[2 * NB], const float4 *__restrict__ sct,
-                                              int sct_n)
+                                              int sct_n, bool coef_both)
 {
     switch (2 * NB - nv) {
     case 1:
         run_m2_pipelined<NB, 2 * NB - 1, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc, sct,
-                                                     sct_n);
+                                                     sct_n, coef_both);
         break;
     case 2:
         run_m2_pipelined<NB, 2 * NB - 2, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc, sct,
-                                                     sct_n);
+                                                     sct_n, coef_both);
         break;
     case 3:
         run_m2_pipelined<NB, 2 * NB - 3, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc, sct,
-                                                     sct_n);
+                                                     sct_n, coef_both);
         break;
     default:
         run_m2_pipelined<NB, 2 * NB, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc, sct,
-                                                     sct_n);
+                                                     sct_n, coef_both);
         break;
     }
 }
@@ -228,7 +230,7 @@ __device__ __forceinline__ void multiples(float c1, float s1, Multiples &m)
 template <int NB, int M, int KQ>
 __device__ __forceinline__ void pair_terms(const float4 xi, const float4 xj, float w, float qs_hi,
                                            float qs_lo, bool zero_start, float dq_hi, float dq_lo,
-                                           unsigned hash, float2 (&acc)[2 * NB])
+                                           unsigned hash, bool coef_both, float2 (&acc)[2 * NB])
 {
     static_assert(M == 2 || M == 4, "step must be 2 or 4");
     static_assert(KQ == 0 || KQ % (2 * M) == 0, "re-seed interval must be a multiple of 2M");
@@ -245,9 +247,9 @@ __device__ __forceinline__ void pair_terms(const float4 xi, const float4 xj, flo
     const SinCos b1 = sincos_f32(t);
     Multiples m;
     multiples(b1.c, b1.s, m);
-    const float sh = m.s[M / 2];                                   // sin(M t / 2)
-    const float CM = coef_dither(4.f * sh * sh, hash);             // 2cos(Mt) = 2 - 4 sin^2(Mt/2)
-    const float2 Cp = make_float2(CM, CM), Cn = make_float2(-CM, -CM);
+    float CM, CMn;
+    coef_dither(m.s[M / 2], m.c[M / 2], hash, coef_both, CM, CMn);   // 2cos(Mt) from (sin, cos)(Mt/2)
+    const float2 Cp = make_float2(CM, CM), Cn = make_float2(CMn, CMn);
     float S, C;
     if (zero_start) {
         S = 0.f;
@@ -340,23 +342,23 @@ __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
             const int nv = (qlen + 1) >> 1;
             if (zero_start)
                 run_m2_fitted<NB, true>(nv, xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc, sct,
-                                        qc.sct_n);
+                                        qc.sct_n, qc.coef_both != 0);
             else
                 run_m2_fitted<NB, false>(nv, xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc, sct,
-                                        qc.sct_n);
+                                        qc.sct_n, qc.coef_both != 0);
         } else if (P == 4) {
             if (zero_start)
                 run_m2<NB, true>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc, sct,
-                                        qc.sct_n);
+                                        qc.sct_n, qc.coef_both != 0);
             else
                 run_m2<NB, false>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc, sct,
-                                        qc.sct_n);
+                                        qc.sct_n, qc.coef_both != 0);
         } else {
             for (int j = 0; j < item.jlen; ++j) {
                 const float4 xj = sj[j];
                 const float w = (j <= jmask) ? 0.f : xi.w * xj.w;
                 pair_terms<NB, M, KQ>(xi, xj, w, qs_hi, qs_lo, zero_start, qc.dq_hi[ch], qc.dq_lo[ch],
-                                      pair_hash(item.i0 + tid, item.j0 + j), acc);
+                                      pair_hash(item.i0 + tid, item.j0 + j), qc.coef_both != 0, acc);
             }
         }
         flush_warp<NB, (P == 1 ? M : 2)>(acc, red[warp], lane);

@@ -27,12 +27,32 @@ __device__ __forceinline__ void dist_rsqrt(float r2, float &r, float &y)
     r = fmaf(0.5f * y, fmaf(-r0, r0, r2), r0);
 }
 
-// 2 - mu rounded stochastically by dithering: a uniform offset of at most half an ulp of [1, 2)
-// enters before the one rounding, so the expected coefficient is exact.
-__device__ __forceinline__ float coef_dither(float mu, unsigned hash)
+// The coefficient 2cos(2x) of the recurrence from s = sin x, c = cos x, rounded stochastically.
+// It is formed from whichever small square keeps full relative accuracy: 2 - 4s^2 where
+// cos 2x >= 0 (the 4s^2 <= 4c^2 side, where it nears +2 as x nears a multiple of pi) and
+// 4c^2 - 2 where cos 2x < 0 (where it nears -2).  Near -2 the form 2 - 4s^2 would take the
+// rounding of s and of a square near 4 into the coefficient, several ulps that the recurrence
+// turns into a phase drift shared by every pair of about the same distance.  A uniform offset of
+// at most half an ulp of [1, 2) enters the small square before the last rounding, so the expected
+// coefficient is exact (pairs at one distance, such as bonds, then do not share its rounding).
+// Returns +C in Cp and -C in Cn.  both = 0 (calls whose step phase 2x stays below 0.8 pi, where the
+// coefficient stays above -1.62 and 2 - 4s^2 is accurate enough): the first form alone.
+__device__ __forceinline__ void coef_dither(float s, float c, unsigned hash, bool both, float &Cp, float &Cn)
 {
     const float u = __int_as_float(0x3f800000u | (hash >> 9)) - 1.5f;   // uniform in [-0.5, 0.5)
-    return 2.f - fmaf(u, 1.1920928955078125e-7f, mu);
+    const float ms = (2.f * s) * (2.f * s);
+    if (both) {
+        const float mc = (2.f * c) * (2.f * c);
+        const bool near_minus2 = ms > mc;
+        const float md = fmaf(u, 1.1920928955078125e-7f, near_minus2 ? mc : ms);
+        const float two_minus = 2.f - md, minus_two = md - 2.f;
+        Cp = near_minus2 ? minus_two : two_minus;
+        Cn = near_minus2 ? two_minus : minus_two;
+    } else {
+        const float md = fmaf(u, 1.1920928955078125e-7f, ms);
+        Cp = 2.f - md;
+        Cn = md - 2.f;
+    }
 }
 
 // Cheap pair hash on the integer ALU (one multiply, then xorshift).

@@ -52,7 +52,9 @@ __device__ __forceinline__ void setup2_head(const float4 pxy, const float4 pzw, 
 // coefficient needs anyway: scale sin 2t = (2 scale sin t) cos t and scale sin 3t =
 // (scale sin t)(3 - 4 sin^2 t), four packed operations fewer than by angle addition.  Used by the
 // 208-q form, where it measured faster (1 %); the 104-q form measured 2-3 % slower with it.
-template <bool ZERO_START, int TAB = 2, bool PRODUCT_SEEDS = false>
+// COEF_BOTH: the coefficient formed both ways (QChunks::coef_both; a template parameter, so that
+// the kernels of calls without it are the one-form code).
+template <bool ZERO_START, int TAB = 2, bool PRODUCT_SEEDS = false, bool COEF_BOTH = false>
 __device__ __forceinline__ void setup2_tail(const PairHead2 &h, float2 qs_hi, float2 qs_lo, float2 dq_hi,
                                             float2 dq_lo, unsigned hA, unsigned hB, PairState2 &o,
                                             const float4 *__restrict__ sct, int sct_n)
@@ -63,14 +65,28 @@ __device__ __forceinline__ void setup2_tail(const PairHead2 &h, float2 qs_hi, fl
     const SinCos2 b1 = (TAB == 1 || (TAB == 2 && sct)) ? sincos2_tab(t, sct, sct_n) : sincos2_f32(t);
     const float2 s1 = b1.s, c1 = b1.c;
     const float2 s1x2 = f2add(s1, s1);
-    // 2cos(2t) = 2 - 4 sin^2 t, rounded stochastically (dither from the pair hash)
+    // 2cos(2t), rounded stochastically (dither from the pair hash)
     const float2 mu = f2mul(s1x2, s1x2);
     const float2 u = f2add(make_float2(__int_as_float(0x3f800000u | (hA >> 9)),
                                        __int_as_float(0x3f800000u | (hB >> 9))),
                            bc(-1.5f));
-    const float2 md = f2fma(u, bc(1.1920928955078125e-7f), mu);
-    const float2 C = f2fma(md, bc(-1.f), bc(2.f));
-    const float2 Cn = f2add(md, bc(-2.f));
+    // the small square that keeps full relative accuracy (coef_dither): 4 sin^2 t where cos 2t >= 0,
+    // 4 cos^2 t where cos 2t < 0, the coefficient then 2 - 4 sin^2 t or 4 cos^2 t - 2 (calls with
+    // coef_both; the others 2 - 4 sin^2 t alone)
+    float2 C, Cn;
+    if (COEF_BOTH) {
+        const float2 c1x2 = f2add(c1, c1);
+        const float2 mc = f2mul(c1x2, c1x2);
+        const bool nA = mu.x > mc.x, nB = mu.y > mc.y;
+        const float2 md = f2fma(u, bc(1.1920928955078125e-7f), make_float2(nA ? mc.x : mu.x, nB ? mc.y : mu.y));
+        const float2 two_minus = f2fma(md, bc(-1.f), bc(2.f)), minus_two = f2add(md, bc(-2.f));
+        C = make_float2(nA ? minus_two.x : two_minus.x, nB ? minus_two.y : two_minus.y);
+        Cn = make_float2(nA ? two_minus.x : minus_two.x, nB ? two_minus.y : minus_two.y);
+    } else {
+        const float2 md = f2fma(u, bc(1.1920928955078125e-7f), mu);
+        C = f2fma(md, bc(-1.f), bc(2.f));
+        Cn = f2add(md, bc(-2.f));
+    }
     o.CpA = bc(C.x);
     o.CpB = bc(C.y);
     o.CnA = bc(Cn.x);

@@ -157,6 +157,7 @@ sas_status with_sincos_table(sas_ctx *ctx, QChunks &qc, cudaStream_t s)
 {
     qc.sct = nullptr;
     qc.sct_n = 0;
+    with_coef_form(ctx, qc);
     double dq = 0.0;
     for (int c = 0; c < qc.n_chunks; ++c) dq = std::max(dq, qc.dqd[c]);
     const double tmax = dq * ctx->diam;
@@ -218,6 +219,16 @@ double step_phase(const sas_ctx *ctx, const QChunks &qc)
     double dq = 0.0;
     for (int c = 0; c < qc.n_chunks; ++c) dq = std::max(dq, std::fabs(qc.dqd[c]));
     return ctx->opt_step * dq * ctx->diam;
+}
+
+// The mixed kernels form the recurrence coefficient both ways (QChunks::coef_both) where the
+// call's step phase can come near pi.  Measured (GB300, 50 q at spacing 0.02 A^-1 and 100 q at
+// 0.01, random-walk globules): 2 - 4 sin^2 t alone reached 5.3e-5 and 2.5e-4 at 100,000 atoms
+// (3.9e-5 and 7.1e-5 at 40,000), both forms 3.8e-6 and 8.5e-6; below the threshold (the 201-q
+// grids up to 50,000 atoms, step phase <= 2.2) the one form stays within the bound.
+void with_coef_form(const sas_ctx *ctx, QChunks &qc)
+{
+    qc.coef_both = step_phase(ctx, qc) >= kCoefBothPhase ? 1 : 0;
 }
 
 // Wait for the work queued on `s` so far, giving up after the context's time limit.
@@ -835,7 +846,9 @@ sas_status adjoint(sas_ctx *ctx, int64_t n, int64_t batch, const double *g_dev, 
                                           ctx->G.as<double>(), ctx->jlen_max, ctx->ticket.as<int>(), PI, PJ, s));
         launches += 3;
     } else {
-        CUDA_TRY(launch_debye_adjoint(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, ctx->qc,
+        QChunks qa = ctx->qc;
+        with_coef_form(ctx, qa);
+        CUDA_TRY(launch_debye_adjoint(ctx->X.as<float4>(), npad, ctx->items.as<Item>(), ctx->n_items, qa,
                                       ctx->H.as<float2>(), Pn, Q, ctx->G.as<double>(), ctx->jlen_max,
                                       ctx->ticket.as<int>(), PI, PJ, s));
     }

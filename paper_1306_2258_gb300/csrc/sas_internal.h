@@ -54,7 +54,13 @@ struct QChunks {
     // pair's step phase dq r of the call; null: the polynomial sincos
     const float4 *sct = nullptr;
     int sct_n = 0;
+    // 1: the mixed kernels form each pair's coefficient 2cos(2t) from 4 sin^2 t or 4 cos^2 t,
+    // whichever is smaller (set where the call's step phase can come near pi); 0: from 4 sin^2 t
+    int coef_both = 0;
 };
+
+// Largest step phase M dq D from which the mixed kernels form their coefficients both ways.
+constexpr double kCoefBothPhase = 0.8 * 3.14159265358979323846;
 
 // q_k of the grid (a short scan over the chunks).
 __host__ __device__ inline double q_at(const QChunks &qc, int k)

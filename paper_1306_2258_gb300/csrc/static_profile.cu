@@ -235,7 +235,9 @@ extern "C" sas_status sas_profile_static(const float *coords, const int32_t *typ
     float r2;
     const unsigned bits = (unsigned)h_meta[2 * T + 2];
     std::memcpy(&r2, &bits, sizeof r2);
-    const int reseed = reseed_auto(n, std::min(n_q, kQChunk), 2.0 * std::fabs(dq) * 2.0 * std::sqrt((double)r2));
+    const double phase = 2.0 * std::fabs(dq) * 2.0 * std::sqrt((double)r2);   // step phase 2 dq D
+    const int reseed = reseed_auto(n, std::min(n_q, kQChunk), phase);
+    qc.coef_both = phase >= kCoefBothPhase ? 1 : 0;
     STATIC_TRY(cudaMemsetAsync(ticket, 0, sizeof(int), s));
     STATIC_TRY(launch_debye_mixed(X, npad, items, ni, qc, 2, reseed, reseed == 0 ? 5 : 1, partial, kQChunk, 0,
                                   kStaticJmax, ticket, s));

@@ -24,7 +24,7 @@ BASE_SEED = 1306
 
 
 def seed_for(config: int, index: int = 0) -> int:
-    """Seed of input ``index`` of workload family ``config`` (1..5)."""
+    """Seed of input ``index`` of workload family ``config`` (1..5; 6 for Table 1's workload)."""
     return BASE_SEED + 1000 * config + index
 
 
@@ -292,6 +292,15 @@ def c4_refinement(n: int = 5000, batch: int = 64):
     confs = np.stack([perturbed(base, 1.0, seed_for(4, 100 + b)).coords for b in range(batch)])
     return dict(base=base, target=target, conformers=confs.astype(np.float32),
                 coef=form_factor_coefficients(5, seed_for(4, 2)), q=q_grid(0.01, 0.5, 101))
+
+
+def table1_globule(n: int) -> Workload:
+    """The workload of the paper's Table 1: a "randomly generated protein" of ``n`` atoms (here the
+    confined random walk, R = 30 (n/1000)^(1/3) Å, 5 types) and 50-point profiles on 0 < q <= 1 Å^-1,
+    read as q_k = 0.02 k for k = 1..50 (Section III)."""
+    mol = random_walk_globule(n, 5, seed_for(6, n)).as_f32()
+    return Workload(mol, form_factor_coefficients(5, seed_for(6, 1)), q_grid(0.02, 1.0, 50),
+                    f"globule {n:,} atoms x 50 q on 0.02..1.0 (Table 1's grid)")
 
 
 def c5_ensemble(n_conf: int = 4096, n: int = 2000):
