@@ -282,12 +282,20 @@ enum {
                                 1e-10 of the amplitude terms; sas_partials is not available after 1 or 2;
                                 sas_last_stats entry 6 gives the q values computed by quadrature and
                                 entry 7 its directions */
-    SAS_OPT_ADJOINT = 10     /* gradient kernels (sas_profile_grad, sas_profile_vjp): 0 (default) the pair weight
+    SAS_OPT_ADJOINT = 10,    /* gradient kernels (sas_profile_grad, sas_profile_vjp): 0 (default) the pair weight
                                 W(r) = 2 sum_q h_q (cos(q r) - sinc(q r)) / r^2, a function of the distance alone
                                 within one conformer and type pair, tabulated on nodes 0.05 / q_max apart up to
                                 the diameter bound and interpolated by cubics (error below 2e-7 of its scale),
                                 falling back to 1 when the tables would exceed 2 GB or 65535 conformer type
                                 pairs; 1 the sums over q by the three-term recurrence for every pair */
+    SAS_OPT_COEF = 11        /* how the mixed kernels form the recurrence coefficient 2cos(2t), t = dq r, of each
+                                pair: 0 (default) automatic, both ways once the call's step phase 2 dq D (D as for
+                                SAS_OPT_RESEED) reaches 0.8 pi, else as 2 - 4 sin^2 t; 1 always as 2 - 4 sin^2 t;
+                                2 always both ways: 2 - 4 sin^2 t where cos 2t >= 0 and 4 cos^2 t - 2 where
+                                cos 2t < 0, each from the square that keeps full relative accuracy.  Near
+                                2t = pi the first form carries the rounding of sin t and of a square near 4 into
+                                the coefficient, which the recurrence turns into a phase drift shared by pairs of
+                                similar distance (coarse q grids on large molecules) */
 };
 sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value);
 

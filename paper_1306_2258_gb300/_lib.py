@@ -21,7 +21,7 @@ SAS_MIXED, SAS_FP64 = 0, 1
 SAS_DETERMINISTIC = 16
 SAS_COORDS_F32, SAS_COORDS_F64 = 0, 1
 SAS_OPT_JMAX, SAS_OPT_RESEED, SAS_OPT_VALIDATE, SAS_OPT_GRID, SAS_OPT_TIMEOUT_MS, SAS_OPT_STEP, SAS_OPT_VARIANT = 1, 2, 3, 4, 5, 6, 7
-SAS_OPT_SHARD, SAS_OPT_METHOD, SAS_OPT_ADJOINT = 8, 9, 10
+SAS_OPT_SHARD, SAS_OPT_METHOD, SAS_OPT_ADJOINT, SAS_OPT_COEF = 8, 9, 10, 11
 SAS_MAX_TYPES, SAS_MAX_Q = 16, 1664
 (SAS_MLP_BUF_XB, SAS_MLP_BUF_Z1, SAS_MLP_BUF_A1B, SAS_MLP_BUF_Z2, SAS_MLP_BUF_A2B, SAS_MLP_BUF_Y, SAS_MLP_BUF_DY,
  SAS_MLP_BUF_DYB, SAS_MLP_BUF_DA2, SAS_MLP_BUF_DZ2, SAS_MLP_BUF_DZ2B, SAS_MLP_BUF_DA1, SAS_MLP_BUF_DZ1,

@@ -88,7 +88,8 @@ struct sas_ctx {
     int opt_grid = 0;
     int opt_shard_rank = 0, opt_shard_world = 1;   // this call computes shard rank of world
     int opt_method = 0;                             // 0 direct sum, 1 hybrid by qD and N, 2 quadrature
-    int opt_adjoint = 0;                            // 0 tabulated radial weight (if it fits), 1 q recurrence
+    int opt_adjoint = 0;
+    int opt_coef = 0;                               // 0 automatic, 1 one form, 2 both forms (SAS_OPT_COEF)                            // 0 tabulated radial weight (if it fits), 1 q recurrence
     double diam = 0.0;                              // bound on the diameter of the last call's conformers
     int pad = sas::kTile, tile_used = sas::kTile;             // type-group padding and I-tile of the last packing
     int64_t opt_timeout_ms = 600000;

@@ -228,7 +228,10 @@ double step_phase(const sas_ctx *ctx, const QChunks &qc)
 // grids up to 50,000 atoms, step phase <= 2.2) the one form stays within the bound.
 void with_coef_form(const sas_ctx *ctx, QChunks &qc)
 {
-    qc.coef_both = step_phase(ctx, qc) >= kCoefBothPhase ? 1 : 0;
+    if (ctx->opt_coef != 0)
+        qc.coef_both = ctx->opt_coef == 2 ? 1 : 0;
+    else
+        qc.coef_both = step_phase(ctx, qc) >= kCoefBothPhase ? 1 : 0;
 }
 
 // Wait for the work queued on `s` so far, giving up after the context's time limit.
@@ -1067,6 +1070,10 @@ sas_status sas_set_option(sas_ctx *ctx, int option, int64_t value)
     case SAS_OPT_ADJOINT:
         if (value < 0 || value > 1) return fail(SAS_ERR_INVALID_ARG, "ADJOINT must be 0 or 1");
         ctx->opt_adjoint = (int)value;
+        return SAS_OK;
+    case SAS_OPT_COEF:
+        if (value < 0 || value > 2) return fail(SAS_ERR_INVALID_ARG, "COEF must be 0, 1 or 2");
+        ctx->opt_coef = (int)value;
         return SAS_OK;
     case SAS_OPT_SHARD: {
         const int64_t world = value >> 16, rank = value & 0xFFFF;

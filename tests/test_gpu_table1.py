@@ -63,3 +63,36 @@ def test_100k_atoms_mixed_vs_fp64_kernel_and_oracle_on_sampled_q():
     ref = oracle.profile(w.mol.coords, w.mol.types, w.coef, w.q[ks])
     assert _rel(I[ks], ref) <= TOL_MIXED
     assert _rel(I64[ks], ref) <= TOL_FP64
+
+
+def test_coef_option_rejects_bad_values():
+    w = wl.table1_globule(1000)
+    p = Profile(w.coef, w.q, "mixed")
+    try:
+        for bad in (-1, 3):
+            with pytest.raises(_lib.SasError):
+                p.set_option(_lib.SAS_OPT_COEF, bad)
+    finally:
+        p.close()
+
+
+def _with_coef(w, coef):
+    p = Profile(w.coef, w.q, "mixed")
+    try:
+        p.set_option(_lib.SAS_OPT_COEF, coef)
+        dev = torch.device("cuda:0")
+        return p(torch.as_tensor(w.mol.coords, device=dev), torch.as_tensor(w.mol.types, device=dev)).cpu().numpy()
+    finally:
+        p.close()
+
+
+def test_coefficient_forms_on_a_coarse_grid():
+    """20,000 atoms on Table 1's grid: the step phase 2 dq D passes 0.8 pi, so the automatic choice
+    forms the coefficient both ways (the same bits as forcing it) and holds 1e-5; the form
+    2 - 4 sin^2 t alone drifts where 2t nears pi."""
+    w = wl.table1_globule(20000)
+    I64 = _gpu(w, "fp64")
+    auto, one, both = _with_coef(w, 0), _with_coef(w, 1), _with_coef(w, 2)
+    assert np.array_equal(auto, both)
+    assert _rel(both, I64) <= TOL_MIXED
+    assert _rel(one, I64) > _rel(both, I64)
