@@ -96,3 +96,24 @@ def test_coefficient_forms_on_a_coarse_grid():
     assert np.array_equal(auto, both)
     assert _rel(both, I64) <= TOL_MIXED
     assert _rel(one, I64) > _rel(both, I64)
+
+
+def test_per_atom_form_factors_on_a_coarse_grid():
+    """Per-atom form factors on Table 1's grid (20,000 atoms): the per-atom pair kernel forms its
+    coefficient both ways too (2.4e-5 from the FP64 kernel with the one form)."""
+    w = wl.table1_globule(20000)
+    ff = wl.atomic_form_factor_table(w.mol.n, w.q, 771)
+    dev = torch.device("cuda:0")
+    x = torch.as_tensor(w.mol.coords, device=dev)
+    out = {}
+    for precision in ("mixed", "fp64"):
+        p = Profile(w.coef, w.q, precision)
+        try:
+            out[precision] = p.atomic(x, torch.as_tensor(ff, device=dev)).cpu().numpy()
+        finally:
+            p.close()
+    assert _rel(out["mixed"], out["fp64"]) <= TOL_MIXED
+    ks = np.array([0, 49])
+    ref = oracle.profile_atomic(w.mol.coords, ff[ks], w.q[ks])
+    assert _rel(out["mixed"][ks], ref) <= TOL_MIXED
+    assert _rel(out["fp64"][ks], ref) <= TOL_FP64
