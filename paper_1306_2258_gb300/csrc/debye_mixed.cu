@@ -59,7 +59,8 @@ template <bool ZERO_START, bool PRODUCT_SEEDS>
 __device__ __forceinline__ void setup_m2(const float4 xi, const float4 xj, float w, float qs_hi,
                                          float qs_lo, float dq_hi, float dq_lo, unsigned hash,
                                          float2 &w0, float2 &w1, float2 &Cp, float2 &Cn,
-                                         const float4 *__restrict__ sct, int sct_n, bool coef_both)
+                                         const float4 *__restrict__ sct, int sct_n, bool coef_both,
+                                         int start_is_step)
 {
     const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
     float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -88,7 +89,14 @@ __device__ __forceinline__ void setup_m2(const float4 xi, const float4 xj, float
         w1 = make_float2(scale * s2, scale * s3);
     } else {
         const float c3 = fmaf(c2, c1, -s2 * s1);
-        const SinCos ph = sincos_f32(fmaf(qs_hi, r, qs_lo * r));
+        // the start phase q0 r (for q0 = dq the step phase t, at hand)
+        SinCos ph;
+        if (start_is_step) {
+            ph.s = s1;
+            ph.c = c1;
+        } else {
+            ph = sincos_f32(fmaf(qs_hi, r, qs_lo * r));
+        }
         const float S = scale * ph.s, C = scale * ph.c;
         w0 = make_float2(S, fmaf(S, c1, C * s1));
         w1 = make_float2(fmaf(S, c2, C * s2), fmaf(S, c3, C * s3));
@@ -122,12 +130,13 @@ struct M2Pair {
 template <bool ZERO_START, bool PRODUCT_SEEDS>
 __device__ __forceinline__ void setup_at(const float4 xi, const float4 *sj, const Item &item, int tid,
                                          int jmask, int j, bool valid, float qs_hi, float qs_lo, float dq_hi,
-                                         float dq_lo, M2Pair &o, const float4 *__restrict__ sct, int sct_n, bool coef_both)
+                                         float dq_lo, M2Pair &o, const float4 *__restrict__ sct, int sct_n, bool coef_both,
+                                         int start_is_step)
 {
     const float4 xj = sj[j];
     const float w = (!valid || j <= jmask) ? 0.f : xi.w * xj.w;
     setup_m2<ZERO_START, PRODUCT_SEEDS>(xi, xj, w, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(item.i0 + tid, item.j0 + j), o.w0,
-                         o.w1, o.Cp, o.Cn, sct, sct_n, coef_both);
+                         o.w1, o.Cp, o.Cn, sct, sct_n, coef_both, start_is_step);
 }
 
 // Pairs (i, j) over the item's J-range, software-pipelined: the set-up of pair j+1 does not
@@ -137,19 +146,20 @@ template <int NB, int NV, bool ZERO_START>
 __device__ __forceinline__ void run_m2_pipelined(const float4 xi, const float4 *sj, const Item &item,
                                                  int tid, int jmask, float qs_hi, float qs_lo, float dq_hi,
                                                  float dq_lo, float2 (&acc)[2 * NB], const float4 *__restrict__ sct,
-                                                 int sct_n, bool coef_both)
+                                                 int sct_n, bool coef_both,
+                                         int start_is_step)
 {
     const int jlen = item.jlen;
     if (jlen <= 0) return;
     M2Pair a, b;
-    setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, 0, true, qs_hi, qs_lo, dq_hi, dq_lo, a, sct, sct_n, coef_both);
+    setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, 0, true, qs_hi, qs_lo, dq_hi, dq_lo, a, sct, sct_n, coef_both, start_is_step);
     int j = 0;
     for (; j + 1 < jlen; j += 2) {
-        setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, j + 1, true, qs_hi, qs_lo, dq_hi, dq_lo, b, sct, sct_n, coef_both);
+        setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, j + 1, true, qs_hi, qs_lo, dq_hi, dq_lo, b, sct, sct_n, coef_both, start_is_step);
         core_m2<NB, NV>(a.w0, a.w1, a.Cp, a.Cn, acc);
         const bool more = j + 2 < jlen;
         setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, more ? j + 2 : j + 1, more, qs_hi, qs_lo, dq_hi, dq_lo,
-                             a, sct, sct_n, coef_both);
+                             a, sct, sct_n, coef_both, start_is_step);
         core_m2<NB, NV>(b.w0, b.w1, b.Cp, b.Cn, acc);
     }
     if (j < jlen) core_m2<NB, NV>(a.w0, a.w1, a.Cp, a.Cn, acc);   // odd J-range: its last pair
@@ -159,11 +169,12 @@ __device__ __forceinline__ void run_m2_pipelined(const float4 xi, const float4 *
 template <int NB, bool ZERO_START>
 __device__ __forceinline__ void run_m2(const float4 xi, const float4 *sj, const Item &item, int tid,
                                        int jmask, float qs_hi, float qs_lo, float dq_hi, float dq_lo,
-                                       float2 (&acc)[2 * NB], const float4 *__restrict__ sct, int sct_n, bool coef_both)
+                                       float2 (&acc)[2 * NB], const float4 *__restrict__ sct, int sct_n, bool coef_both,
+                                         int start_is_step)
 {
     for (int j = 0; j < item.jlen; ++j) {
         M2Pair a;
-        setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, j, true, qs_hi, qs_lo, dq_hi, dq_lo, a, sct, sct_n, coef_both);
+        setup_at<ZERO_START, NB == 52>(xi, sj, item, tid, jmask, j, true, qs_hi, qs_lo, dq_hi, dq_lo, a, sct, sct_n, coef_both, start_is_step);
         core_m2<NB, 2 * NB>(a.w0, a.w1, a.Cp, a.Cn, acc);
     }
 }
@@ -174,24 +185,25 @@ template <int NB, bool ZERO_START>
 __device__ __forceinline__ void run_m2_fitted(int nv, const float4 xi, const float4 *sj, const Item &item,
                                               int tid, int jmask, float qs_hi, float qs_lo, float dq_hi,
                                               float dq_lo, float2 (&acc)[2 * NB], const float4 *__restrict__ sct,
-                                              int sct_n, bool coef_both)
+                                              int sct_n, bool coef_both,
+                                         int start_is_step)
 {
     switch (2 * NB - nv) {
     case 1:
         run_m2_pipelined<NB, 2 * NB - 1, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc, sct,
-                                                     sct_n, coef_both);
+                                                     sct_n, coef_both, start_is_step);
         break;
     case 2:
         run_m2_pipelined<NB, 2 * NB - 2, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc, sct,
-                                                     sct_n, coef_both);
+                                                     sct_n, coef_both, start_is_step);
         break;
     case 3:
         run_m2_pipelined<NB, 2 * NB - 3, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc, sct,
-                                                     sct_n, coef_both);
+                                                     sct_n, coef_both, start_is_step);
         break;
     default:
         run_m2_pipelined<NB, 2 * NB, ZERO_START>(xi, sj, item, tid, jmask, qs_hi, qs_lo, dq_hi, dq_lo, acc, sct,
-                                                     sct_n, coef_both);
+                                                     sct_n, coef_both, start_is_step);
         break;
     }
 }
@@ -342,17 +354,17 @@ __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
             const int nv = (qlen + 1) >> 1;
             if (zero_start)
                 run_m2_fitted<NB, true>(nv, xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc, sct,
-                                        qc.sct_n, qc.coef_both != 0);
+                                        qc.sct_n, qc.coef_both != 0, qc.start_is_step[ch]);
             else
                 run_m2_fitted<NB, false>(nv, xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc, sct,
-                                        qc.sct_n, qc.coef_both != 0);
+                                        qc.sct_n, qc.coef_both != 0, qc.start_is_step[ch]);
         } else if (P == 4) {
             if (zero_start)
                 run_m2<NB, true>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc, sct,
-                                        qc.sct_n, qc.coef_both != 0);
+                                        qc.sct_n, qc.coef_both != 0, qc.start_is_step[ch]);
             else
                 run_m2<NB, false>(xi, sj, item, tid, jmask, qs_hi, qs_lo, qc.dq_hi[ch], qc.dq_lo[ch], acc, sct,
-                                        qc.sct_n, qc.coef_both != 0);
+                                        qc.sct_n, qc.coef_both != 0, qc.start_is_step[ch]);
         } else {
             for (int j = 0; j < item.jlen; ++j) {
                 const float4 xj = sj[j];

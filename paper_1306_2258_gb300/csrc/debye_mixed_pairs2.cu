@@ -49,7 +49,7 @@ __device__ __forceinline__ void core2(const PairState2 &p, float2 (&acc)[2 * NB]
     }
 }
 
-template <int NB, int NV, bool ZERO_START, int TAB, bool CB>
+template <int NB, int NV, bool ZERO_START, int TAB, bool CB, bool SS>
 __device__ __forceinline__ void run_pairs2(const float4 *sxy, const float4 *szw, int jpairs, const float4 xi,
                                            const Item &item, int tid, int jmask, float2 qs_hi, float2 qs_lo,
                                            float2 dq_hi, float2 dq_lo, float2 (&acc)[2 * NB],
@@ -63,8 +63,8 @@ __device__ __forceinline__ void run_pairs2(const float4 *sxy, const float4 *szw,
     for (int k = 0; k < jpairs; ++k) {
         const int j = 2 * k;
         PairState2 p;
-        setup2_tail<ZERO_START, TAB, NB == 52, CB>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
-                                                   pair_hash(ih, item.j0 + j + 1), p, sct, sct_n);
+        setup2_tail<ZERO_START, TAB, NB == 52, CB, SS>(head, qs_hi, qs_lo, dq_hi, dq_lo, pair_hash(ih, item.j0 + j),
+                                                       pair_hash(ih, item.j0 + j + 1), p, sct, sct_n);
         // the next two pairs' distances, issued ahead of this step's recurrences (the last step
         // reads its own slot again and discards the result)
         const bool more = k + 1 < jpairs;
@@ -80,8 +80,9 @@ __device__ __forceinline__ void run_pairs2(const float4 *sxy, const float4 *szw,
 // (1 where the call has a table, else 0), the 52-q form with the polynomial (0): each the faster
 // build of its form (GB300: the 208-q form with the table alone 6 % slower, the 104-q form with
 // both 5-8 % slower than with the table alone, and 4-5 % slower with the polynomial alone).
-// CB: the coefficient formed both ways (calls with QChunks::coef_both, setup2_tail).
-template <int NB, int NV, int TILE, int TAB, bool CB>
+// CB: the coefficient formed both ways (calls with QChunks::coef_both, setup2_tail).  SS: every
+// chunk of the call that does not start at q = 0 starts at its step (QChunks::start_is_step).
+template <int NB, int NV, int TILE, int TAB, bool CB, bool SS>
 __global__ void __launch_bounds__(TILE, mixed_ctas_per_sm(NB) * (kTile / TILE))
     k_debye_mixed_pairs2(const float4 *__restrict__ X, int64_t npad, const Item *__restrict__ items,
                          int n_items, QChunks qc, double *__restrict__ partial, int part_stride, int jmax,
@@ -124,10 +125,10 @@ __global__ void __launch_bounds__(TILE, mixed_ctas_per_sm(NB) * (kTile / TILE))
         for (int k = 0; k < 2 * NB; ++k) acc[k] = make_float2(0.f, 0.f);
         const int jmask = item.diag ? tid : -1;   // pairs with j <= i are not pairs of i<j
         if (zero_start)
-            run_pairs2<NB, NV, true, TAB, CB>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
+            run_pairs2<NB, NV, true, TAB, CB, SS>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
                                               bc(qc.dq_lo[ch]), acc, sct, qc.sct_n);
         else
-            run_pairs2<NB, NV, false, TAB, CB>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
+            run_pairs2<NB, NV, false, TAB, CB, SS>(sxy, szw, jpairs, xi, item, tid, jmask, qs_hi, qs_lo, bc(qc.dq_hi[ch]),
                                                bc(qc.dq_lo[ch]), acc, sct, qc.sct_n);
         flush_warp<NB, 2>(acc, red[warp], lane);
         __syncthreads();
@@ -142,29 +143,55 @@ __global__ void __launch_bounds__(TILE, mixed_ctas_per_sm(NB) * (kTile / TILE))
     }
 }
 
-template <int NB, int NV, int TILE, int TAB, bool CB>
-cudaError_t launch_cb(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
+template <int NB, int NV, int TILE, int TAB, bool CB, bool SS>
+cudaError_t launch_ss(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
                        double *partial, int part_stride, int grid, int jmax, int *ticket, cudaStream_t s)
 {
     const bool staged = TAB == 1 || (TAB == 2 && qc.sct != nullptr);
     if (staged && (qc.sct == nullptr || qc.sct_n <= 0 || qc.sct_n > kStagedSincosTab))
         return cudaErrorInvalidValue;
     const size_t smem = ((size_t)jmax + (staged ? (size_t)qc.sct_n : 0)) * sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(k_debye_mixed_pairs2<NB, NV, TILE, TAB, CB>,
+    cudaError_t e = cudaFuncSetAttribute(k_debye_mixed_pairs2<NB, NV, TILE, TAB, CB, SS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (grid <= 0) {   // persistent grid: every resident CTA slot of every SM
         int occ = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_mixed_pairs2<NB, NV, TILE, TAB, CB>, TILE, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_debye_mixed_pairs2<NB, NV, TILE, TAB, CB, SS>, TILE, smem);
         if (e != cudaSuccess) return e;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         grid = (occ > 0 ? occ : 1) * sms;
     }
     if (grid > n_items) grid = n_items;
-    k_debye_mixed_pairs2<NB, NV, TILE, TAB, CB><<<grid, TILE, smem, s>>>(X, npad, items, n_items, qc, partial,
+    k_debye_mixed_pairs2<NB, NV, TILE, TAB, CB, SS><<<grid, TILE, smem, s>>>(X, npad, items, n_items, qc, partial,
                                                                       part_stride, jmax, ticket);
     return cudaGetLastError();
+}
+
+// Every chunk of the call starts at q = 0 or at its step, and at least one at its step.
+bool starts_at_step(const QChunks &qc)
+{
+    bool any = false;
+    for (int c = 0; c < qc.n_chunks; ++c) {
+        if (qc.qs_hi[c] == 0.f && qc.qs_lo[c] == 0.f) continue;
+        if (!qc.start_is_step[c]) return false;
+        any = true;
+    }
+    return any;
+}
+
+// SS instantiated for the 52- and 104-q forms only (coarse grids such as q_k = k dq, k >= 1).
+template <int NB, int NV, int TILE, int TAB, bool CB>
+cudaError_t launch_cb(const float4 *X, int64_t npad, const Item *items, int n_items, const QChunks &qc,
+                      double *partial, int part_stride, int grid, int jmax, int *ticket, cudaStream_t s)
+{
+    if constexpr (NB <= 26) {
+        if (starts_at_step(qc))
+            return launch_ss<NB, NV, TILE, TAB, CB, true>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax,
+                                                          ticket, s);
+    }
+    return launch_ss<NB, NV, TILE, TAB, CB, false>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket,
+                                                   s);
 }
 
 template <int NB, int NV, int TILE, int TAB>

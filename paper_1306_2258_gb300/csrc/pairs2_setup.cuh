@@ -54,7 +54,8 @@ __device__ __forceinline__ void setup2_head(const float4 pxy, const float4 pzw, 
 // 208-q form, where it measured faster (1 %); the 104-q form measured 2-3 % slower with it.
 // COEF_BOTH: the coefficient formed both ways (QChunks::coef_both; a template parameter, so that
 // the kernels of calls without it are the one-form code).
-template <bool ZERO_START, int TAB = 2, bool PRODUCT_SEEDS = false, bool COEF_BOTH = false>
+// START_IS_STEP (offset start only): the chunk's first q equals its step, so the start phase is t.
+template <bool ZERO_START, int TAB = 2, bool PRODUCT_SEEDS = false, bool COEF_BOTH = false, bool START_IS_STEP = false>
 __device__ __forceinline__ void setup2_tail(const PairHead2 &h, float2 qs_hi, float2 qs_lo, float2 dq_hi,
                                             float2 dq_lo, unsigned hA, unsigned hB, PairState2 &o,
                                             const float4 *__restrict__ sct, int sct_n)
@@ -111,7 +112,14 @@ __device__ __forceinline__ void setup2_tail(const PairHead2 &h, float2 qs_hi, fl
         o.w1B = make_float2(a2.y, a3.y);
     } else {
         const float2 c3 = f2fma(c2, c1, f2mul(s2, f2mul(s1, bc(-1.f))));
-        const SinCos2 ph = sincos2_f32(f2fma(qs_hi, r, f2mul(qs_lo, r)));
+        // the start phase q0 r (START_IS_STEP: the step phase t, at hand)
+        SinCos2 ph;
+        if (START_IS_STEP) {
+            ph.s = s1;
+            ph.c = c1;
+        } else {
+            ph = sincos2_f32(f2fma(qs_hi, r, f2mul(qs_lo, r)));
+        }
         const float2 S = f2mul(scale, ph.s), Cc = f2mul(scale, ph.c);
         const float2 v1 = f2fma(S, c1, f2mul(Cc, s1));
         const float2 v2 = f2fma(S, c2, f2mul(Cc, s2));

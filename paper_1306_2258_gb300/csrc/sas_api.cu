@@ -86,6 +86,7 @@ bool make_chunks(const double *q, int n_q, QChunks &qc, int max_len)
             qc.qs_lo[nc] = (float)(qs - (double)qc.qs_hi[nc]);
             qc.dq_hi[nc] = (float)step;
             qc.dq_lo[nc] = (float)(step - (double)qc.dq_hi[nc]);
+            qc.start_is_step[nc] = (step > 0.0 && std::fabs(qs - step) <= 1e-12 * qs) ? 1 : 0;
             ++nc;
         }
         s = e;

@@ -50,6 +50,9 @@ struct QChunks {
     float dq_lo[kMaxChunks];
     double qsd[kMaxChunks];    // the same in FP64
     double dqd[kMaxChunks];
+    // 1 when the chunk's first q equals its step (a grid q_k = k dq, k >= 1): the start phase of a
+    // pair is then its step phase dq r, whose sin and cos the mixed kernels form anyway
+    int start_is_step[kMaxChunks];
     // (sin, cos)(k/64) for k < sct_n <= kStagedSincosTab as float32 hi/lo (sincos_tab), covering every
     // pair's step phase dq r of the call; null: the polynomial sincos
     const float4 *sct = nullptr;

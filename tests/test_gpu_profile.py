@@ -265,13 +265,20 @@ def _variant_case(name):
     if name == "globule3k_q300_offset":   # two q chunks, neither starting at q = 0
         m = wl.random_walk_globule(3000, 4, 78)
         return m.as_f32(), wl.form_factor_coefficients(4, 79), wl.q_grid(0.05, 1.2, 300)
+    if name == "globule3k_q50_from_dq":   # q0 = dq: the start phase is the step phase t
+        m = wl.random_walk_globule(3000, 4, 82)
+        return m.as_f32(), wl.form_factor_coefficients(4, 83), wl.q_grid(0.02, 1.0, 50)
+    if name == "globule3k_q49_from_2dq":   # q0 = 2 dq: the start phase is 2t
+        m = wl.random_walk_globule(3000, 4, 84)
+        return m.as_f32(), wl.form_factor_coefficients(4, 85), wl.q_grid(0.04, 1.0, 49)
     if name == "n37_q51":
         m = wl.random_walk_globule(37, 3, 80)
         return m.as_f32(), wl.form_factor_coefficients(3, 81), wl.q_grid(0.0, 0.5, 51)
     raise KeyError(name)
 
 
-@pytest.mark.parametrize("name", ["globule10k_q201", "rod6k_q101", "globule3k_q300_offset", "n37_q51"])
+@pytest.mark.parametrize("name", ["globule10k_q201", "rod6k_q101", "globule3k_q300_offset", "globule3k_q50_from_dq",
+                                  "globule3k_q49_from_2dq", "n37_q51"])
 def test_two_pair_kernel_is_bitwise_equal_to_one_pair_kernels(name):
     """Variant 4 (two pairs per step, packed set-up) performs the same operations lane by lane and
     adds pair j before pair j+1 into every accumulator: I(q) and S_ab(q) equal bit for bit."""
