@@ -686,7 +686,7 @@ def run_strong(args):
 
 
 PROFILE_CASES = ("histogram", "gradient", "gradient_recurrence", "gemm", "atomic", "quadrature", "binned", "rod", "pairs2",
-                 "train")
+                 "train", "table1")
 
 
 def run_profile_case(args):
@@ -704,6 +704,8 @@ def run_profile_case(args):
       atomic       20,000-atom globule x 201 q with a per-atom form-factor table
       quadrature   20,000-atom globule x 65 q (0..0.32 A^-1), orientation average of Eq. 1 on every q
       pairs2       20,000-atom globule x 201 q (0..1 A^-1): the headline's pair kernel on a smaller molecule
+      table1       20,000-atom globule of Table 1's workload x 50 q (0.02..1.0 A^-1): the 52-q two-pair form
+                   with the coefficient formed both ways and the start phase taken from the step phase
     """
     import torch
 
@@ -746,6 +748,15 @@ def run_profile_case(args):
             net.train_step(xs, ts, 1e-3)
         report["train_steps"] = 4
         net.close()
+    if "table1" in cases:
+        w6 = wl.table1_globule(20000)
+        p = Profile(w6.coef, w6.q)
+        x6 = torch.as_tensor(w6.mol.coords, device=dev)
+        t6 = torch.as_tensor(w6.mol.types, device=dev)
+        for _ in range(2):
+            I6 = p(x6, t6)
+        report["table1_I0"] = float(I6[0])
+        p.close()
     if "rod" in cases:
         w3 = wl.c3_rod()
         p = Profile(w3.coef, w3.q)
