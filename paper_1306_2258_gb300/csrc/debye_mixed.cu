@@ -347,9 +347,9 @@ __global__ void __launch_bounds__(kTile, mixed_ctas_per_sm(NB))
 #pragma unroll
         for (int k = 0; k < 2 * NB; ++k) acc[k] = make_float2(0.f, 0.f);
         const int jmask = item.diag ? tid : -1;   // pairs with j <= i are not pairs of i<j
-        // the sine table for the 208-q form only (its 101-q and 52-q forms measured faster without:
-        // there the table load's latency sits in a shorter set-up)
-        const float4 *sct = (NB == 52 || NB == 26) ? qc.sct : nullptr;   // as the two-pair kernel
+        // the step's sin/cos from the call's table where it has one, as the two-pair kernel (the same
+        // operations lane by lane)
+        const float4 *sct = qc.sct;
         if (P == 3) {
             const int nv = (qlen + 1) >> 1;
             if (zero_start)

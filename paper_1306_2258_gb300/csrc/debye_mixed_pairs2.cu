@@ -77,9 +77,10 @@ __device__ __forceinline__ void run_pairs2(const float4 *sxy, const float4 *szw,
 // TILE: the I-tile (= threads per CTA), 128, or 64 for small molecules whose type groups padded to
 // 128 would waste slots.  TAB: the step's sin/cos (setup2_tail): the 208-q form is compiled with
 // both the table and the polynomial and picks at run time (2), the 104-q form with one of them
-// (1 where the call has a table, else 0), the 52-q form with the polynomial (0): each the faster
-// build of its form (GB300: the 208-q form with the table alone 6 % slower, the 104-q form with
-// both 5-8 % slower than with the table alone, and 4-5 % slower with the polynomial alone).
+// (1 where the call has a table, else 0), and so the 52-q form: each the faster build of its form
+// (GB300: the 208-q form with the table alone 6 % slower, the 104-q form with both 5-8 % slower
+// than with the table alone and 4-5 % slower with the polynomial alone; the 52-q form on Table 1's
+// grid 8 % faster with the table than with the polynomial).
 // CB: the coefficient formed both ways (calls with QChunks::coef_both, setup2_tail).  SS: every
 // chunk of the call that does not start at q = 0 starts at its step (QChunks::start_is_step).
 template <int NB, int NV, int TILE, int TAB, bool CB, bool SS>
@@ -211,7 +212,7 @@ cudaError_t launch_nv(const float4 *X, int64_t npad, const Item *items, int n_it
 {
     if constexpr (NB == 52) {
         return launch_tab<NB, NV, TILE, 2>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket, s);
-    } else if constexpr (NB == 26) {
+    } else if constexpr (NB == 26 || NB == 13) {
         if (qc.sct != nullptr)
             return launch_tab<NB, NV, TILE, 1>(X, npad, items, n_items, qc, partial, part_stride, grid, jmax, ticket,
                                                s);
